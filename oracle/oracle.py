@@ -1,0 +1,284 @@
+"""ctypes wrapper and plain simulation driver for the C oracle.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  The arithmetic of the
+method lives in ``pic_oracle.c``; this module only moves arrays in and out and
+computes grid diagnostics by their plain definitions with numpy in FP64.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pic_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+ORC_EPARTICLE = 1
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile the oracle (both precisions) into oracle/liboracle.so."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    objs = []
+    flags = ["-O2", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-std=c11"]
+    for real, sfx, extra in (("double", "_f64", ["-DREAL_IS_DOUBLE"]),
+                             ("float", "_f32", [])):
+        obj = os.path.join(_HERE, f"_pic_oracle{sfx}.o")
+        cmd = ["gcc", *flags, f"-DREAL={real}", f"-DSFX={sfx}", *extra,
+               "-c", _SRC, "-o", obj]
+        subprocess.run(cmd, check=True)
+        objs.append(obj)
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-shared", "-o", tmp, *objs, "-lm"], check=True)
+    os.replace(tmp, _LIB)
+    for o in objs:
+        os.remove(o)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build_oracle()
+        _lib = C.CDLL(_LIB)
+        _declare(_lib)
+    return _lib
+
+
+_P = C.c_void_p
+_I = C.c_int
+_I64 = C.c_int64
+_D = C.c_double
+
+
+def _declare(L):
+    for sfx, real in (("_f64", C.c_double), ("_f32", C.c_float)):
+        getattr(L, "orc_gather" + sfx).argtypes = [_I, _I, _P, _P, _I, _I, real, real, _P, _P]
+        getattr(L, "orc_gather" + sfx).restype = None
+        getattr(L, "orc_boris" + sfx).argtypes = [_P, _P, _P, real]
+        getattr(L, "orc_boris" + sfx).restype = real
+        getattr(L, "orc_deposit_move" + sfx).argtypes = [_I, _I, _P, _I, _I, real, real, real, real, real, real, real]
+        getattr(L, "orc_deposit_move" + sfx).restype = None
+        getattr(L, "orc_advance" + sfx).argtypes = [_I, _I, _D, _D, _D, _D, _D, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+        getattr(L, "orc_advance" + sfx).restype = _I
+        getattr(L, "orc_yee" + sfx).argtypes = [_I, _I, _D, _D, _D, _P, _P, _P]
+        getattr(L, "orc_yee" + sfx).restype = None
+        getattr(L, "orc_rho" + sfx).argtypes = [_I, _I, _D, _I64, _P, _P, _P, _P, _P]
+        getattr(L, "orc_rho" + sfx).restype = None
+    L.orc_tile_sort.argtypes = [_I, _I, _I, _I64, _P, _P, _P, _P, _P]
+    L.orc_tile_sort.restype = None
+
+
+def _sfx(dtype) -> str:
+    dt = np.dtype(dtype)
+    if dt == np.float64:
+        return "_f64"
+    if dt == np.float32:
+        return "_f32"
+    raise TypeError(f"oracle precision must be float64 or float32, not {dt}")
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"], "oracle arrays must be C-contiguous"
+    return a.ctypes.data_as(C.c_void_p)
+
+
+# ---------------------------------------------------------------- primitives
+
+def gather(E, B, ix, iy, x, y):
+    """Fields at one particle (Fig. 3.1 staggering). E, B: (3, ny, nx)."""
+    E = np.ascontiguousarray(E)
+    B = np.ascontiguousarray(B, dtype=E.dtype)
+    _, ny, nx = E.shape
+    real = E.dtype.type
+    Ep = np.zeros(3, E.dtype)
+    Bp = np.zeros(3, E.dtype)
+    getattr(lib(), "orc_gather" + _sfx(E.dtype))(nx, ny, _ptr(E), _ptr(B), int(ix), int(iy),
+                                                  real(x), real(y), _ptr(Ep), _ptr(Bp))
+    return Ep, Bp
+
+
+def boris(u, Ep, Bp, tem):
+    """One Boris push (Eqs. 6-10). Returns (u_new, gamma_minus)."""
+    u = np.array(u, copy=True)
+    Ep = np.ascontiguousarray(Ep, dtype=u.dtype)
+    Bp = np.ascontiguousarray(Bp, dtype=u.dtype)
+    g = getattr(lib(), "orc_boris" + _sfx(u.dtype))(_ptr(u), _ptr(Ep), _ptr(Bp), u.dtype.type(tem))
+    return u, float(g)
+
+
+def deposit_move(J, ix, iy, x0, y0, x1, y1, qjx, qjy, qvz):
+    """Add the current of one straight move (cell frame of (ix, iy)) into J."""
+    _, ny, nx = J.shape
+    r = J.dtype.type
+    getattr(lib(), "orc_deposit_move" + _sfx(J.dtype))(
+        nx, ny, _ptr(J), int(ix), int(iy), r(x0), r(y0), r(x1), r(y1), r(qjx), r(qjy), r(qvz))
+
+
+def advance(sp: "SpeciesState", E, B, J, dx, dy, dt):
+    """Particle loop of Listing 3.1 for one species; returns (status, sum(gamma-1))."""
+    _, ny, nx = E.shape
+    ke = C.c_double(0.0)
+    st = getattr(lib(), "orc_advance" + _sfx(E.dtype))(
+        nx, ny, dx, dy, dt, sp.q_over_m, sp.qtilde, sp.n,
+        _ptr(sp.ix), _ptr(sp.iy), _ptr(sp.x), _ptr(sp.y),
+        _ptr(sp.ux), _ptr(sp.uy), _ptr(sp.uz), _ptr(E), _ptr(B), _ptr(J), C.byref(ke))
+    return st, ke.value
+
+
+def yee(E, B, J, dx, dy, dt):
+    _, ny, nx = E.shape
+    getattr(lib(), "orc_yee" + _sfx(E.dtype))(nx, ny, dx, dy, dt, _ptr(E), _ptr(B), _ptr(J))
+
+
+def rho_nodes(nx, ny, species, dtype=np.float64, background=0.0):
+    """Charge density on nodes (area weighting) plus a uniform background."""
+    rho = np.zeros((ny, nx), dtype)
+    for sp in species:
+        getattr(lib(), "orc_rho" + _sfx(dtype))(nx, ny, sp.qtilde, sp.n, _ptr(sp.ix), _ptr(sp.iy),
+                                                _ptr(sp.x), _ptr(sp.y), _ptr(rho))
+    return rho.astype(np.float64) + background
+
+
+def tile_sort(nx, ny, T, ix, iy):
+    """Stable counting sort by tile id; returns (perm, counts, offsets)."""
+    ix = np.ascontiguousarray(ix, np.int32)
+    iy = np.ascontiguousarray(iy, np.int32)
+    n = ix.size
+    nt = (nx // T) * (ny // T)
+    perm = np.zeros(n, np.int64)
+    counts = np.zeros(nt, np.int64)
+    offsets = np.zeros(nt + 1, np.int64)
+    lib().orc_tile_sort(nx, ny, T, n, _ptr(ix), _ptr(iy), _ptr(perm), _ptr(counts), _ptr(offsets))
+    return perm, counts, offsets
+
+
+# ---------------------------------------------------------- grid diagnostics
+
+def field_energy(F, dx, dy):
+    """0.5 * sum(F^2) dx dy over the three components (FP64)."""
+    F = np.asarray(F, np.float64)
+    return 0.5 * float(np.sum(F * F)) * dx * dy
+
+
+def div_e(E, dx, dy):
+    """Discrete div E on nodes (Eq. 17 on the Yee grid), periodic, FP64."""
+    E = np.asarray(E, np.float64)
+    return ((E[0] - np.roll(E[0], 1, axis=1)) / dx
+            + (E[1] - np.roll(E[1], 1, axis=0)) / dy)
+
+
+def div_j(J, dx, dy):
+    """Discrete div J on nodes (J co-located with E), periodic, FP64."""
+    return div_e(J, dx, dy)
+
+
+# ---------------------------------------------------------------- simulation
+
+@dataclass
+class SpeciesState:
+    """One species: cell index (ix, iy), in-cell offset (x, y), momentum u."""
+    q_over_m: float
+    qtilde: float          # charge density carried by one particle: sign(q) n_s / ppc_s
+    ix: np.ndarray
+    iy: np.ndarray
+    x: np.ndarray
+    y: np.ndarray
+    ux: np.ndarray
+    uy: np.ndarray
+    uz: np.ndarray
+    pid: np.ndarray | None = None
+
+    @property
+    def n(self) -> int:
+        return int(self.ix.size)
+
+    def astype(self, dtype) -> "SpeciesState":
+        c = lambda a: np.ascontiguousarray(a, dtype)
+        return SpeciesState(self.q_over_m, self.qtilde,
+                            np.ascontiguousarray(self.ix, np.int32),
+                            np.ascontiguousarray(self.iy, np.int32),
+                            c(self.x), c(self.y), c(self.ux), c(self.uy), c(self.uz),
+                            None if self.pid is None else self.pid.copy())
+
+    def permute(self, perm):
+        for name in ("ix", "iy", "x", "y", "ux", "uy", "uz"):
+            setattr(self, name, np.ascontiguousarray(getattr(self, name)[perm]))
+        if self.pid is not None:
+            self.pid = np.ascontiguousarray(self.pid[perm])
+
+
+@dataclass
+class OracleSim:
+    """Plain serial PIC following Listing 3.1 (no filter, no moving window).
+
+    E, B, J are (3, ny, nx) arrays at the Yee locations of Fig. 3.1.  Each step:
+    zero J; for each species push every particle and deposit its current; Yee
+    B/2, E, B/2; then re-sort each species by tile (stable counting sort, §4.3).
+    ``background`` is the fixed neutralising ion density added to rho.
+    """
+    nx: int
+    ny: int
+    dx: float
+    dy: float
+    dt: float
+    tile: int
+    species: list
+    dtype: type = np.float64
+    background: float = 0.0
+    E: np.ndarray = None
+    B: np.ndarray = None
+    J: np.ndarray = None
+    step_count: int = 0
+    status: int = 0
+    ke_history: list = field(default_factory=list)
+
+    def __post_init__(self):
+        shape = (3, self.ny, self.nx)
+        self.E = np.zeros(shape, self.dtype) if self.E is None else np.ascontiguousarray(self.E, self.dtype)
+        self.B = np.zeros(shape, self.dtype) if self.B is None else np.ascontiguousarray(self.B, self.dtype)
+        self.J = np.zeros(shape, self.dtype)
+        self.species = [s.astype(self.dtype) for s in self.species]
+
+    def kinetic_energy_of(self, sp, gsum):
+        # W_K = sum (gamma - 1) m_s n_s/ppc_s dx dy, with m_s n_s/ppc_s = qtilde / (q/m)
+        return gsum * (sp.qtilde / sp.q_over_m) * self.dx * self.dy
+
+    def step(self, nsteps: int = 1, sort: bool = True):
+        for _ in range(nsteps):
+            self.J[...] = 0
+            ke = 0.0
+            for sp in self.species:
+                st, g = advance(sp, self.E, self.B, self.J, self.dx, self.dy, self.dt)
+                self.status |= st
+                ke += self.kinetic_energy_of(sp, g)
+            self.ke_history.append(ke)
+            yee(self.E, self.B, self.J, self.dx, self.dy, self.dt)
+            if sort:
+                self.sort()
+            self.step_count += 1
+
+    def sort(self):
+        for sp in self.species:
+            perm, _, _ = tile_sort(self.nx, self.ny, self.tile, sp.ix, sp.iy)
+            sp.permute(perm)
+
+    def tile_offsets(self, s: int = 0):
+        sp = self.species[s]
+        return tile_sort(self.nx, self.ny, self.tile, sp.ix, sp.iy)[2]
+
+    def rho(self):
+        return rho_nodes(self.nx, self.ny, self.species, np.float64, self.background)
+
+    def energies(self):
+        return (field_energy(self.E, self.dx, self.dy),
+                field_energy(self.B, self.dx, self.dy))
