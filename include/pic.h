@@ -1,0 +1,189 @@
+/*
+ * pic.h -- C ABI of the GB300 (sm_103a) particle-in-cell library.
+ *
+ * One simulation = one periodic 2D electromagnetic PIC box (Guidotti 2021,
+ * §3.1-3.2): fields E, B on a Yee grid (Fig. 3.1), particles sorted by tiles
+ * of T x T cells (§4.1, Figs. 4.2-4.3), advanced by the loop of Listing 3.1:
+ * zero J; gather E and B at each particle, Boris push (Eqs. 6-10), move
+ * (Eq. 11), charge-conserving current deposit (Eqs. 12-16); guard-cell
+ * reduction of J; Yee advance B/2, E, B/2 (Eqs. 19-20); guard-cell copy.  The
+ * particles are re-sorted into tiles every step (§4.3).
+ *
+ * Units are the normalised units of Eqs. 21-22 (c = 1).  Conventions:
+ *   node (i,j) at (i dx, j dy); a particle in cell (ix,iy) with offset (x,y)
+ *   in [0,1)^2 sits at ((ix+x) dx, (iy+y) dy).
+ *   Ex at (i+1/2, j), Ey at (i, j+1/2), Ez at (i, j);
+ *   Bx at (i, j+1/2), By at (i+1/2, j), Bz at (i+1/2, j+1/2);
+ *   J co-located with E; rho on nodes.
+ *   Field arrays exchanged through this ABI are float32, component-major:
+ *   three blocks of ny rows of nx values (element (c, j, i) at
+ *   c*nx*ny + j*nx + i), at the Yee locations above.
+ *
+ * Ownership: the library owns all of its device memory from pic_init until
+ * pic_destroy.  Every buffer a caller passes is owned by the caller; the
+ * library copies from it (load/set) or into it (get) before the call returns
+ * (get/diagnostics synchronise the simulation's stream; load/set copy on the
+ * stream and synchronise it before returning).  "on_device" = 1 means the
+ * caller's pointers are CUDA device pointers (any device memory of the current
+ * device), 0 means host memory.
+ *
+ * Errors: every call returns a pic_status.  Errors raised on the device
+ * (a particle moving a cell or more in one step, a non-finite momentum, a
+ * bounded wait that ran out, an inconsistent re-sort) set sticky bits in a
+ * per-simulation status word; pic_step does not wait for the device, so they
+ * are reported by the next call that synchronises (pic_sync, pic_get_*,
+ * pic_diagnostics), and by every later call until pic_clear_status.  No call
+ * aborts the process or traps the GPU.  pic_last_error gives a message.
+ *
+ * Threading: a handle is not thread-safe; all work is ordered on the CUDA
+ * stream given to pic_init.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_sim pic_sim; /* opaque */
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_EINVAL = 1,     /* bad argument, size or configuration */
+    PIC_ECFL = 2,       /* dt violates the Courant condition of Eq. 1 */
+    PIC_ENOMEM = 3,     /* device or host allocation failed */
+    PIC_ECUDA = 4,      /* a CUDA runtime call failed */
+    PIC_EOVERFLOW = 5,  /* re-sort bookkeeping inconsistent (counts do not add up) */
+    PIC_EPARTICLE = 6,  /* a particle tried to move one cell or more in a step, or
+                           its momentum or position is not finite */
+    PIC_ETIMEOUT = 7    /* a bounded device-side wait ran out */
+} pic_status;
+
+#define PIC_MAX_SPECIES 4
+
+/* config flags */
+#define PIC_STRICT_FP 1u  /* per-particle path without fused multiply-add, in the
+                             operation order of the FP32 reference, so that cells
+                             and offsets are reproducible bit for bit */
+#define PIC_TRACK_IDS 2u  /* carry an int32 particle id through the re-sort */
+#define PIC_TIMING 4u     /* record CUDA events around each particle-advance launch */
+#define PIC_NO_GRAPH 8u   /* launch kernels one by one instead of a CUDA graph */
+
+typedef struct {
+    double q_over_m; /* charge-to-mass ratio (electrons: -1) */
+    double density;  /* n_s, number density in units of n0 (> 0) */
+    double ppc;      /* particles per cell; each particle carries the charge
+                        density qtilde = sign(q/m) * density / ppc */
+} pic_species_cfg;
+
+typedef struct {
+    int nx, ny;       /* cells; multiples of tile, 8 <= n <= 32768 */
+    double dx, dy, dt;/* dt must satisfy Eq. 1: dt < (1/dx^2 + 1/dy^2)^-1/2 */
+    int tile;         /* T in {8, 16, 32}; 0 = 16 */
+    int threads;      /* threads per tile in the particle kernels: 64..1024, multiple
+                         of 32; 0 = 256 */
+    int n_species;    /* 1..PIC_MAX_SPECIES */
+    pic_species_cfg species[PIC_MAX_SPECIES];
+    double background;/* fixed neutralising ion charge density (enters rho only) */
+    unsigned flags;   /* PIC_STRICT_FP | PIC_TRACK_IDS | PIC_TIMING | PIC_NO_GRAPH */
+} pic_config;
+
+typedef struct {
+    int64_t step;          /* time level n of E and B */
+    double time;           /* n dt */
+    double w_e, w_b;       /* field energies 1/2 sum(E^2) dx dy, 1/2 sum(B^2) dx dy at n (FP64 sums) */
+    double w_k;            /* kinetic energy sum (gamma(u-) - 1) m n_s/ppc dx dy of the last
+                              particle push, i.e. at time level n-1 (NaN before the first step) */
+    double gauss_max;      /* max over nodes of |div E - rho| at n (FP64), rho including the background */
+    double continuity_max; /* max over nodes of |(rho^n - rho^(n-1))/dt + div J^(n-1/2)| if the previous
+                              pic_diagnostics call was at n-1 and no state was loaded since, else NaN */
+    double charge_total;   /* sum over nodes of rho dx dy (FP64) */
+    int64_t n_particles[PIC_MAX_SPECIES];
+    int64_t leavers;       /* particles that changed tile in the last step (all species) */
+    uint32_t status_bits;  /* sticky device status: 1 = particle, 2 = timeout, 4 = re-sort */
+} pic_diag;
+
+/* Create a simulation.  Validates the configuration (Eq. 1 for dt, tile
+ * divisibility, sizes) and allocates the grid.  `cuda_stream` is a cudaStream_t
+ * (NULL = the legacy default stream).  Fields start at zero, no particles.
+ * Returns PIC_EINVAL / PIC_ECFL / PIC_ENOMEM / PIC_ECUDA; *out is NULL on error. */
+pic_status pic_init(const pic_config* cfg, void* cuda_stream, pic_sim** out);
+
+/* Load (replace) the particles of one species: n particles given as seven
+ * arrays (cell ix, iy as int32; offsets x, y in [0,1) and momenta ux, uy, uz as
+ * float32), plus an optional int32 id array (used when PIC_TRACK_IDS is set;
+ * NULL = ids 0..n-1).  The library copies them and sorts them into tiles
+ * (§4.1: one contiguous array with a tile_offset bookmark array).  Rejects
+ * cells outside the grid, offsets outside [0,1) and non-finite values with
+ * PIC_EINVAL (nothing is changed then).  n may be 0. */
+pic_status pic_load_particles(pic_sim* sim, int species, int64_t n, const int32_t* ix,
+                              const int32_t* iy, const float* x, const float* y,
+                              const float* ux, const float* uy, const float* uz,
+                              const int32_t* id, int on_device);
+
+/* Set E and B (each 3*nx*ny float32 values in the ABI field layout) at the
+ * current time level.  Either pointer may be NULL to leave that field as is. */
+pic_status pic_set_fields(pic_sim* sim, const float* E, const float* B, int on_device);
+
+/* Advance nsteps >= 0 time steps (Listing 3.1 without filter or moving
+ * window).  Asynchronous: enqueues the work on the stream and returns. */
+pic_status pic_step(pic_sim* sim, int nsteps);
+
+/* Copy a grid quantity into the caller's buffer: which = 0 E, 1 B (3*nx*ny
+ * values each, at time level n), 2 J (the current deposited by the last step,
+ * at n-1/2, 3*nx*ny values), 3 rho (nx*ny values at nodes, including the
+ * background; computed from the particles now).  Synchronises the stream. */
+pic_status pic_get_fields(pic_sim* sim, int which, float* out, int on_device);
+
+/* Copy one species' particles out, in the library's current (tile-sorted)
+ * order.  Each non-NULL array receives n_particles values; id is filled only
+ * with PIC_TRACK_IDS.  tile_offset, if non-NULL, receives the ntiles+1
+ * bookmark array of §4.1 (int64; tile t = ty*(nx/T) + tx owns particles
+ * [tile_offset[t], tile_offset[t+1])).  Synchronises. */
+pic_status pic_get_particles(pic_sim* sim, int species, int32_t* ix, int32_t* iy, float* x,
+                             float* y, float* ux, float* uy, float* uz, int32_t* id,
+                             int64_t* tile_offset, int on_device);
+
+/* Number of particles of a species (host value, no synchronisation). */
+int64_t pic_num_particles(const pic_sim* sim, int species);
+
+/* Number of tiles (nx/T)*(ny/T). */
+int64_t pic_num_tiles(const pic_sim* sim);
+
+/* Diagnostics at the current time level (see pic_diag).  Synchronises; FP64
+ * reductions on the device. */
+pic_status pic_diagnostics(pic_sim* sim, pic_diag* out);
+
+/* Energy history kept on the device for the last 65536 time levels: w_e[k],
+ * w_b[k] at time level first+k, w_k[k] from the push at time level first+k.
+ * Any output pointer may be NULL.  Levels not (or no longer) recorded give NaN.
+ * Synchronises. */
+pic_status pic_get_history(pic_sim* sim, int64_t first, int64_t count, double* w_e,
+                           double* w_b, double* w_k);
+
+/* Wait for the stream; return the sticky device status as a pic_status. */
+pic_status pic_sync(pic_sim* sim);
+
+/* Clear the sticky device status bits. */
+pic_status pic_clear_status(pic_sim* sim);
+
+/* Timing of the particle-advance launches (PIC_TIMING): sum of their CUDA
+ * event durations in ms and their count since the last reset.  Synchronises. */
+pic_status pic_timing(pic_sim* sim, double* advance_ms, int64_t* advance_launches, int reset);
+
+/* Number of kernels this simulation has launched (graph nodes included). */
+int64_t pic_kernel_launches(const pic_sim* sim);
+
+/* Message for the last error on this handle ("" if none); valid until the next call. */
+const char* pic_last_error(const pic_sim* sim);
+
+/* Free everything.  NULL is accepted. */
+void pic_destroy(pic_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_H */

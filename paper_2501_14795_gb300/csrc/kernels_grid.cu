@@ -1,0 +1,467 @@
+// Grid kernels: the fused Yee advance (§3.1 three-step scheme, §4.4 tiled
+// field advance), guard-cell copies, field energies, charge density and the
+// FP64 charge-conservation residuals, and the initial particle load/sort.
+#include "device_util.cuh"
+#include "pic_internal.h"
+
+namespace pic {
+
+namespace {
+
+__device__ __forceinline__ long long gidx(const Geom& g, int i, int j) {
+    return (long long)(j + GY) * g.P + (i + GX);
+}
+
+// ---------------------------------------------------------------- Yee
+// One CTA per field tile of YX x YY cells.  Shared memory holds E on cells
+// [-1, YX+2) x [-1, YY+2), B on [-1, YX+1) x [-1, YY+1), J on [0, YX+1) x
+// [0, YY+1).  In place: B <- B - dt/2 curl E on the B region, then
+// E <- E + dt (curl B - J) on [0, YX+1)^2, then B <- B - dt/2 curl E on the
+// tile (Eqs. 19-20 on the staggered grid of Fig. 3.1).  The tile of E|B at
+// n+1 is written with its periodic images (update_gc_copy), the field
+// energies of level n+1 are summed in FP64, and the shared ring of the next
+// step's J buffer (cells a neighbouring particle tile's halo reaches) is
+// zeroed.
+constexpr int YX = 32, YY = 16, YTHREADS = 256;
+constexpr int EW = YX + 3, EH = YY + 3;
+constexpr int BW = YX + 2, BH = YY + 2;
+constexpr int JWY = YX + 1, JHY = YY + 1;
+
+__global__ void __launch_bounds__(YTHREADS) k_yee(const YeeParams prm) {
+    __shared__ float sE[3][EH][EW];
+    __shared__ float sB[3][BH][BW];
+    __shared__ float sJ[3][JHY][JWY];
+    __shared__ double sRed[32];
+    const Geom& g = prm.g;
+    const int i0 = blockIdx.x * YX, j0 = blockIdx.y * YY;
+    const int tid = threadIdx.x;
+    const long long cs = g.cstride;
+    const float* Ein = prm.Fin;
+    const float* Bin = prm.Fin + 3 * cs;
+
+    for (int k = tid; k < EW * EH; k += YTHREADS) {
+        const int r = k / EW, q = k - r * EW;
+        const int i = i0 - 1 + q, j = j0 - 1 + r;
+        const bool in = i <= g.nx + 1 && j <= g.ny + 1;
+        const long long o = gidx(g, i, j);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sE[c][r][q] = in ? Ein[c * cs + o] : 0.f;
+    }
+    for (int k = tid; k < BW * BH; k += YTHREADS) {
+        const int r = k / BW, q = k - r * BW;
+        const int i = i0 - 1 + q, j = j0 - 1 + r;
+        const bool in = i <= g.nx + 1 && j <= g.ny + 1;
+        const long long o = gidx(g, i, j);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sB[c][r][q] = in ? Bin[c * cs + o] : 0.f;
+    }
+    for (int k = tid; k < JWY * JHY; k += YTHREADS) {
+        const int r = k / JWY, q = k - r * JWY;
+        int i = i0 + q, j = j0 + r;
+        i = i >= g.nx ? i - g.nx : i;
+        j = j >= g.ny ? j - g.ny : j;
+        const bool in = i < g.nx && j < g.ny;
+        const long long o = gidx(g, i, j);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sJ[c][r][q] = in ? prm.J[c * cs + o] : 0.f;
+    }
+    __syncthreads();
+
+    const float hx = g.hdt_dx, hy = g.hdt_dy;
+    // B half step on [-1, YX+1) x [-1, YY+1): local (q, r) <-> cell (i0-1+q, j0-1+r)
+    for (int k = tid; k < BW * BH; k += YTHREADS) {
+        const int r = k / BW, q = k - r * BW;
+        sB[0][r][q] -= hy * (sE[2][r + 1][q] - sE[2][r][q]);
+        sB[1][r][q] += hx * (sE[2][r][q + 1] - sE[2][r][q]);
+        sB[2][r][q] -= hx * (sE[1][r][q + 1] - sE[1][r][q]) - hy * (sE[0][r + 1][q] - sE[0][r][q]);
+    }
+    __syncthreads();
+    // E full step on cells [0, YX+1) x [0, YY+1): E at (q+1, r+1), B at (q+1, r+1)
+    const float dtx = g.dt_dx, dty = g.dt_dy, dt = g.dt;
+    for (int k = tid; k < JWY * JHY; k += YTHREADS) {
+        const int r = k / JWY, q = k - r * JWY;
+        const int e = q + 1, f = r + 1;
+        sE[0][f][e] += dty * (sB[2][f][e] - sB[2][f - 1][e]) - dt * sJ[0][r][q];
+        sE[1][f][e] += -dtx * (sB[2][f][e] - sB[2][f][e - 1]) - dt * sJ[1][r][q];
+        sE[2][f][e] += dtx * (sB[1][f][e] - sB[1][f][e - 1]) -
+                       dty * (sB[0][f][e] - sB[0][f - 1][e]) - dt * sJ[2][r][q];
+    }
+    __syncthreads();
+    // B second half step on the tile, write out with images, energies, J ring
+    float we = 0.f, wb = 0.f;
+    float* Eout = prm.Fout;
+    float* Bout = prm.Fout + 3 * cs;
+    const int T = g.T;
+    for (int k = tid; k < YX * YY; k += YTHREADS) {
+        const int r = k / YX, q = k - r * YX;
+        const int i = i0 + q, j = j0 + r;
+        if (i >= g.nx || j >= g.ny) continue;
+        const int e = q + 1, f = r + 1;
+        float bx = sB[0][f][e] - hy * (sE[2][f + 1][e] - sE[2][f][e]);
+        float by = sB[1][f][e] + hx * (sE[2][f][e + 1] - sE[2][f][e]);
+        float bz = sB[2][f][e] - (hx * (sE[1][f][e + 1] - sE[1][f][e]) -
+                                  hy * (sE[0][f + 1][e] - sE[0][f][e]));
+        const float ex = sE[0][f][e], ey = sE[1][f][e], ez = sE[2][f][e];
+        we += ex * ex + ey * ey + ez * ez;
+        wb += bx * bx + by * by + bz * bz;
+        // images: i' in {i, i+nx if i<2, i-nx if i==nx-1}, same for j
+        int ii[2], jj[2], ni = 1, nj = 1;
+        ii[0] = i;
+        jj[0] = j;
+        if (i < 2) ii[ni++] = i + g.nx;
+        else if (i == g.nx - 1) ii[ni++] = -1;
+        if (j < 2) jj[nj++] = j + g.ny;
+        else if (j == g.ny - 1) jj[nj++] = -1;
+        for (int a = 0; a < ni; ++a)
+            for (int b = 0; b < nj; ++b) {
+                const long long o = gidx(g, ii[a], jj[b]);
+                Eout[o] = ex;
+                Eout[cs + o] = ey;
+                Eout[2 * cs + o] = ez;
+                Bout[o] = bx;
+                Bout[cs + o] = by;
+                Bout[2 * cs + o] = bz;
+            }
+        const int mi = i % T, mj = j % T;
+        const bool ring = mi < 2 || mi == T - 1 || mj < 2 || mj == T - 1;
+        if (ring) {
+            const long long o = gidx(g, i, j);
+            prm.Jnext[o] = 0.f;
+            prm.Jnext[cs + o] = 0.f;
+            prm.Jnext[2 * cs + o] = 0.f;
+        }
+    }
+    const double dxdy = g.dx * g.dy;
+    const long long n = *((volatile long long*)&prm.st->step);
+    const double se = dev::block_sum((double)we, sRed);
+    if (tid == 0) atomicAdd(&prm.hist_e[n & (HIST - 1)], 0.5 * se * dxdy);
+    const double sb = dev::block_sum((double)wb, sRed);
+    if (tid == 0) atomicAdd(&prm.hist_b[n & (HIST - 1)], 0.5 * sb * dxdy);
+}
+
+// -------------------------------------------------------- grid utilities
+// src is component-major (c, j, i) with nx*ny values per component; writes
+// the interior and the periodic images.
+__global__ void k_set_grid(const Geom g, float* F, int ncomp, const float* src) {
+    const long long n = (long long)g.nx * g.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n * ncomp;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(k / n);
+        const long long r = k - c * n;
+        const int j = (int)(r / g.nx), i = (int)(r - (long long)j * g.nx);
+        const float v = src[k];
+        int ii[2], jj[2], ni = 1, nj = 1;
+        ii[0] = i;
+        jj[0] = j;
+        if (i < 2) ii[ni++] = i + g.nx;
+        else if (i == g.nx - 1) ii[ni++] = -1;
+        if (j < 2) jj[nj++] = j + g.ny;
+        else if (j == g.ny - 1) jj[nj++] = -1;
+        for (int a = 0; a < ni; ++a)
+            for (int b = 0; b < nj; ++b) F[c * g.cstride + gidx(g, ii[a], jj[b])] = v;
+    }
+}
+
+__global__ void k_get_grid(const Geom g, const float* F, int ncomp, float* dst) {
+    const long long n = (long long)g.nx * g.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n * ncomp;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(k / n);
+        const long long r = k - c * n;
+        const int j = (int)(r / g.nx), i = (int)(r - (long long)j * g.nx);
+        dst[k] = F[c * g.cstride + gidx(g, i, j)];
+    }
+}
+
+__global__ void k_field_energy(const Geom g, const float* F, double* out_e, double* out_b) {
+    __shared__ double sRed[32];
+    const long long n = (long long)g.nx * g.ny;
+    float we = 0.f, wb = 0.f;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(k / g.nx), i = (int)(k - (long long)j * g.nx);
+        const long long o = gidx(g, i, j);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float e = F[c * g.cstride + o], b = F[(3 + c) * g.cstride + o];
+            we += e * e;
+            wb += b * b;
+        }
+    }
+    const double dxdy = g.dx * g.dy;
+    const double se = dev::block_sum((double)we, sRed);
+    if (threadIdx.x == 0) atomicAdd(out_e, 0.5 * se * dxdy);
+    const double sb = dev::block_sum((double)wb, sRed);
+    if (threadIdx.x == 0) atomicAdd(out_b, 0.5 * sb * dxdy);
+}
+
+// charge density on nodes by area weighting, accumulated in FP64: one CTA
+// per tile, nodes [0, T+1)^2 of the tile in shared memory, then FP64 atomics
+struct RhoSpecies {
+    const int32_t* cell;
+    const float *x, *y;
+    const int32_t* off;
+    double q;
+};
+struct RhoParams {
+    Geom g;
+    int nsp;
+    RhoSpecies sp[MAX_SPECIES];
+    double* rho;
+};
+
+__global__ void k_rho(const RhoParams prm) {
+    extern __shared__ double sR[];
+    const Geom& g = prm.g;
+    const int T = g.T, W = T + 1;
+    const int t = blockIdx.x;
+    const int tx = t % g.ntx, ty = t / g.ntx;
+    const int ix0 = tx * T, iy0 = ty * T;
+    for (int k = threadIdx.x; k < W * W; k += blockDim.x) sR[k] = 0.0;
+    __syncthreads();
+    for (int s = 0; s < prm.nsp; ++s) {
+        const RhoSpecies& S = prm.sp[s];
+        for (int p = S.off[t] + threadIdx.x; p < S.off[t + 1]; p += blockDim.x) {
+            const int c = S.cell[p];
+            const int lx = (c & 0xffff) - ix0, ly = (int)((unsigned)c >> 16) - iy0;
+            if (c == HOLE || lx < 0 || lx >= T || ly < 0 || ly >= T) continue;
+            const double x = S.x[p], y = S.y[p];
+            double* r = sR + ly * W + lx;
+            atomicAdd(r, S.q * (1.0 - x) * (1.0 - y));
+            atomicAdd(r + 1, S.q * x * (1.0 - y));
+            atomicAdd(r + W, S.q * (1.0 - x) * y);
+            atomicAdd(r + W + 1, S.q * x * y);
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < W * W; k += blockDim.x) {
+        const double v = sR[k];
+        if (v == 0.0) continue;
+        const int ly = k / W, lx = k - ly * W;
+        int i = ix0 + lx, j = iy0 + ly;
+        i = i >= g.nx ? i - g.nx : i;
+        j = j >= g.ny ? j - g.ny : j;
+        atomicAdd(&prm.rho[(long long)j * g.nx + i], v);
+    }
+}
+
+// FP64 residuals on nodes: max |div E - rho|, max |(rho - rho_prev)/dt +
+// div J| (if rho_prev), sum rho dx dy.  rho excludes the background, which
+// is added here.
+__global__ void k_residuals(const Geom g, const float* F, const float* J, const double* rho,
+                            const double* rho_prev, double background, double* out) {
+    __shared__ double sRed[32];
+    const long long n = (long long)g.nx * g.ny;
+    double gmax = 0.0, cmax = 0.0, qsum = 0.0;
+    const long long cs = g.cstride;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(k / g.nx), i = (int)(k - (long long)j * g.nx);
+        const long long o = gidx(g, i, j);
+        const int im = i == 0 ? g.nx - 1 : i - 1, jm = j == 0 ? g.ny - 1 : j - 1;
+        const long long oxm = gidx(g, im, j), oym = gidx(g, i, jm);
+        const double r = rho[k] + background;
+        const double dive = ((double)F[o] - (double)F[oxm]) / g.dx +
+                            ((double)F[cs + o] - (double)F[cs + oym]) / g.dy;
+        gmax = fmax(gmax, fabs(dive - r));
+        qsum += r;
+        if (rho_prev) {
+            const double divj = ((double)J[o] - (double)J[oxm]) / g.dx +
+                                ((double)J[cs + o] - (double)J[cs + oym]) / g.dy;
+            cmax = fmax(cmax, fabs((rho[k] - rho_prev[k]) / g.dtd + divj));
+        }
+    }
+    const double a = dev::block_max(gmax, sRed);
+    if (threadIdx.x == 0) dev::atomic_max_nonneg(&out[0], a);
+    const double b = dev::block_max(cmax, sRed);
+    if (threadIdx.x == 0) dev::atomic_max_nonneg(&out[1], b);
+    const double c = dev::block_sum(qsum, sRed);
+    if (threadIdx.x == 0) atomicAdd(&out[2], c * g.dx * g.dy);
+}
+
+// ------------------------------------------------------- particle load
+// phase 0: validate the staged input (out arrays; ocell holds ix, hole holds
+//          iy on entry) and count per tile;
+// phase 1: scatter into the particle arrays at off[tile] + cursor.
+__global__ void k_load_count(const Geom g, SpeciesDev sp, int n, DevState* st) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int ix = sp.ocell[k], iy = sp.hole[k];
+        const float x = sp.ox[k], y = sp.oy[k];
+        const bool ok = ix >= 0 && ix < g.nx && iy >= 0 && iy < g.ny && x >= 0.f && x < 1.f &&
+                        y >= 0.f && y < 1.f && isfinite(sp.oux[k]) && isfinite(sp.ouy[k]) &&
+                        isfinite(sp.ouz[k]);
+        if (!ok) {
+            atomicAdd(&st->load_bad, 1);
+            continue;
+        }
+        const int t = (iy / g.T) * g.ntx + ix / g.T;
+        atomicAdd(&sp.cursor[t], 1);
+    }
+}
+
+__global__ void k_load_scatter(const Geom g, SpeciesDev sp, int n, const int32_t* ids,
+                               const int32_t* off, int track) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int ix = sp.ocell[k], iy = sp.hole[k];
+        const int t = (iy / g.T) * g.ntx + ix / g.T;
+        const int p = off[t] + atomicAdd(&sp.cursor[t], 1);
+        sp.cell[p] = ix | (iy << 16);
+        sp.x[p] = sp.ox[k];
+        sp.y[p] = sp.oy[k];
+        sp.ux[p] = sp.oux[k];
+        sp.uy[p] = sp.ouy[k];
+        sp.uz[p] = sp.ouz[k];
+        if (track) sp.id[p] = ids ? ids[k] : k;
+    }
+}
+
+// exclusive scan of per-tile counts (single CTA)
+__global__ void __launch_bounds__(1024) k_scan_counts(const int32_t* cnt, int nt, int32_t* off) {
+    __shared__ int sWarp[32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int per = (nt + 1023) / 1024;
+    const int t0 = min(tid * per, nt), t1 = min(t0 + per, nt);
+    int mysum = 0;
+    for (int t = t0; t < t1; ++t) mysum += cnt[t];
+    int incl = mysum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) sWarp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int w = sWarp[lane];
+        int wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += v;
+        }
+        sWarp[lane] = wi - w;
+    }
+    __syncthreads();
+    int run = sWarp[wid] + incl - mysum;
+    for (int t = t0; t < t1; ++t) {
+        off[t] = run;
+        run += cnt[t];
+    }
+    if (tid == 1023) off[nt] = run;
+}
+
+__global__ void k_unpack(const int32_t* cell, int n, int32_t* ix, int32_t* iy) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int c = cell[k];
+        if (ix) ix[k] = c & 0xffff;
+        if (iy) iy[k] = (int)((unsigned)c >> 16);
+    }
+}
+
+__global__ void k_off64(const int32_t* off, int n, int64_t* out) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        out[k] = off[k];
+}
+
+__global__ void k_hist_prime(double* he, double* hb, double* hk, DevState* st) {
+    const long long n = st->step;
+    he[n & (HIST - 1)] = 0.0;
+    hb[n & (HIST - 1)] = 0.0;
+    hk[n & (HIST - 1)] = 0.0;
+}
+
+int grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_yee(const YeeParams& p, cudaStream_t s) {
+    dim3 grid((p.g.nx + YX - 1) / YX, (p.g.ny + YY - 1) / YY);
+    k_yee<<<grid, YTHREADS, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_grid(const Geom& g, float* F, int ncomp, const float* src,
+                            cudaStream_t s) {
+    k_set_grid<<<grid_for((long long)g.nx * g.ny * ncomp, 256), 256, 0, s>>>(g, F, ncomp, src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_grid(const Geom& g, const float* F, int ncomp, float* dst,
+                            cudaStream_t s) {
+    k_get_grid<<<grid_for((long long)g.nx * g.ny * ncomp, 256), 256, 0, s>>>(g, F, ncomp, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_energy(const Geom& g, const float* F, double* out_e, double* out_b,
+                                cudaStream_t s) {
+    k_field_energy<<<grid_for((long long)g.nx * g.ny, 256), 256, 0, s>>>(g, F, out_e, out_b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rho(const Geom& g, const SpeciesDev* sp, int nsp, const int32_t* const* off,
+                       double* rho, cudaStream_t s) {
+    RhoParams p;
+    p.g = g;
+    p.nsp = nsp;
+    for (int k = 0; k < nsp; ++k) {
+        p.sp[k].cell = sp[k].cell;
+        p.sp[k].x = sp[k].x;
+        p.sp[k].y = sp[k].y;
+        p.sp[k].off = off[k];
+        p.sp[k].q = sp[k].qtilde;
+    }
+    p.rho = rho;
+    const size_t bytes = (size_t)(g.T + 1) * (g.T + 1) * sizeof(double);
+    k_rho<<<g.ntiles, 256, bytes, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_residuals(const Geom& g, const float* F, const float* J,
+                                  const double* rho, const double* rho_prev, double background,
+                                  double* out, cudaStream_t s) {
+    k_residuals<<<grid_for((long long)g.nx * g.ny, 256), 256, 0, s>>>(g, F, J, rho, rho_prev,
+                                                                     background, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load(const Geom& g, SpeciesDev& sp, int track_ids, int64_t n, int32_t* off,
+                        DevState* st, cudaStream_t s, int phase, const int32_t* staged_ids) {
+    const int nn = (int)n;
+    if (phase == 0) {
+        cudaError_t e = cudaMemsetAsync(sp.cursor, 0, sizeof(int32_t) * g.ntiles, s);
+        if (e != cudaSuccess) return e;
+        if (nn > 0) k_load_count<<<grid_for(nn, 256), 256, 0, s>>>(g, sp, nn, st);
+        return cudaGetLastError();
+    }
+    // phase 1: offsets from the counts, then scatter
+    k_scan_counts<<<1, 1024, 0, s>>>(sp.cursor, g.ntiles, off);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(sp.cursor, 0, sizeof(int32_t) * g.ntiles, s);
+    if (e != cudaSuccess) return e;
+    if (nn > 0)
+        k_load_scatter<<<grid_for(nn, 256), 256, 0, s>>>(g, sp, nn, staged_ids, off, track_ids);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_cells(const int32_t* cell, int64_t n, int32_t* ix, int32_t* iy,
+                                cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_unpack<<<grid_for(n, 256), 256, 0, s>>>(cell, (int)n, ix, iy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_offsets_to_i64(const int32_t* off, int64_t n, int64_t* out, cudaStream_t s) {
+    k_off64<<<grid_for(n, 256), 256, 0, s>>>(off, (int)n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist_prime(double* he, double* hb, double* hk, DevState* st, cudaStream_t s) {
+    k_hist_prime<<<1, 1, 0, s>>>(he, hb, hk, st);
+    return cudaGetLastError();
+}
+
+}  // namespace pic

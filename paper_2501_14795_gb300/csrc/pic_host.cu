@@ -1,0 +1,781 @@
+// Host runtime behind the C ABI of include/pic.h: configuration checks,
+// device memory, TMA descriptors, the per-step launch sequence, CUDA-graph
+// capture (one graph per buffer parity), timing events and diagnostics.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "pic_internal.h"
+
+using namespace pic;
+
+struct pic_sim {
+    pic_config cfg;
+    Geom g;
+    cudaStream_t stream = nullptr;
+    DevState* st = nullptr;
+    float* F[2] = {nullptr, nullptr};  // E|B, ping-pong
+    float* J[2] = {nullptr, nullptr};  // current, ping-pong
+    CUtensorMap fmap[2];
+    float* gtmp = nullptr;             // 3*nx*ny staging for set/get
+    double* rho = nullptr;             // nx*ny FP64 charge density (no background)
+    double* rho_prev = nullptr;
+    long long rho_prev_step = -1;
+    double* hist_e = nullptr;
+    double* hist_b = nullptr;
+    double* hist_k = nullptr;
+    double* dred = nullptr;            // small FP64 reduction outputs
+    SpeciesDev sp[MAX_SPECIES];
+    int cur = 0;                       // parity: F[cur], J[cur] current, off[cur] current
+    long long step = 0;                // host mirror of the time level
+    // graphs
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraphNode_t ev_node[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaEvent_t ev_placeholder[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> ev_pool;  // timing pairs
+    size_t ev_used = 0;                // pairs recorded since reset
+    long long launches = 0;
+    int launches_per_step = 0;
+    std::string err;
+};
+
+namespace {
+
+pic_status fail(pic_sim* s, pic_status code, const char* fmt, ...) {
+    if (s) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        s->err = buf;
+    }
+    return code;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(sim, e_ == cudaErrorMemoryAllocation ? PIC_ENOMEM : PIC_ECUDA,    \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                  \
+    } while (0)
+
+template <class P>
+cudaError_t dalloc(P** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, sizeof(P) * count);
+}
+
+void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 3D map over the six E|B components: x = column (P), y = row (R), z = component;
+// box = the tile's halo, (T+8) columns x (T+3) rows x 6 components.
+bool make_field_map(CUtensorMap* map, const Geom& g, float* base) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)g.P, (cuuint64_t)g.R, 6};
+    cuuint64_t strides[2] = {(cuuint64_t)g.P * 4, (cuuint64_t)g.cstride * 4};
+    cuuint32_t box[3] = {(cuuint32_t)(g.T + 8), (cuuint32_t)(g.T + 3), 6};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+void free_species(SpeciesDev& s) {
+    void* ptrs[] = {s.cell, s.x,  s.y,  s.ux,   s.uy,   s.uz,    s.id,     s.ocell, s.ox,
+                    s.oy,   s.oux, s.ouy, s.ouz, s.oid, s.hole, s.fslot, s.isrc};
+    for (void* p : ptrs) dfree(p);
+    s.cell = s.id = s.ocell = s.oid = s.hole = s.fslot = s.isrc = nullptr;
+    s.x = s.y = s.ux = s.uy = s.uz = s.ox = s.oy = s.oux = s.ouy = s.ouz = nullptr;
+    s.cap = 0;
+}
+
+cudaError_t alloc_particles(SpeciesDev& s, int64_t cap) {
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto** p) {
+        if (e == cudaSuccess) e = dalloc(p, (size_t)cap);
+    };
+    A(&s.cell); A(&s.x); A(&s.y); A(&s.ux); A(&s.uy); A(&s.uz); A(&s.id);
+    A(&s.ocell); A(&s.ox); A(&s.oy); A(&s.oux); A(&s.ouy); A(&s.ouz); A(&s.oid);
+    A(&s.hole); A(&s.fslot); A(&s.isrc);
+    if (e == cudaSuccess) s.cap = cap;
+    return e;
+}
+
+void invalidate_graphs(pic_sim* sim) {
+    for (int b = 0; b < 2; ++b) {
+        if (sim->gexec[b]) cudaGraphExecDestroy(sim->gexec[b]);
+        sim->gexec[b] = nullptr;
+        sim->ev_node[b][0] = sim->ev_node[b][1] = nullptr;
+    }
+}
+
+PushParams push_params(const pic_sim* sim, int b) {
+    PushParams p;
+    memset(&p, 0, sizeof p);
+    p.g = sim->g;
+    p.J = sim->J[b];
+    p.nsp = sim->cfg.n_species;
+    p.track_ids = (sim->cfg.flags & PIC_TRACK_IDS) ? 1 : 0;
+    for (int k = 0; k < p.nsp; ++k) {
+        const SpeciesDev& s = sim->sp[k];
+        PushSpecies& q = p.sp[k];
+        q.off = s.off[b];
+        q.cell = s.cell; q.id = s.id; q.ocell = s.ocell; q.oid = s.oid; q.hole = s.hole;
+        q.stay = s.stay; q.leave = s.leave; q.dirc = s.dirc;
+        q.x = s.x; q.y = s.y; q.ux = s.ux; q.uy = s.uy; q.uz = s.uz;
+        q.ox = s.ox; q.oy = s.oy; q.oux = s.oux; q.ouy = s.ouy; q.ouz = s.ouz;
+        q.tem = s.tem; q.qjx = s.qjx; q.qjy = s.qjy; q.qjz = s.qjz; q.ke_w = s.ke_w;
+    }
+    p.hist_k = sim->hist_k;
+    p.st = sim->st;
+    return p;
+}
+
+SortParams sort_params(const pic_sim* sim, int b) {
+    SortParams p;
+    memset(&p, 0, sizeof p);
+    p.g = sim->g;
+    p.nsp = sim->cfg.n_species;
+    p.track_ids = (sim->cfg.flags & PIC_TRACK_IDS) ? 1 : 0;
+    for (int k = 0; k < p.nsp; ++k) {
+        const SpeciesDev& s = sim->sp[k];
+        SortSpecies& q = p.sp[k];
+        q.off_old = s.off[b];
+        q.off_new = s.off[1 - b];
+        q.cell = s.cell; q.id = s.id; q.ocell = s.ocell; q.oid = s.oid; q.hole = s.hole;
+        q.fslot = s.fslot; q.isrc = s.isrc; q.stay = s.stay; q.leave = s.leave;
+        q.dirc = s.dirc; q.evict = s.evict;
+        q.x = s.x; q.y = s.y; q.ux = s.ux; q.uy = s.uy; q.uz = s.uz;
+        q.ox = s.ox; q.oy = s.oy; q.oux = s.oux; q.ouy = s.ouy; q.ouz = s.ouz;
+        q.n = (int)s.n;
+    }
+    p.hist_e = sim->hist_e;
+    p.hist_b = sim->hist_b;
+    p.hist_k = sim->hist_k;
+    p.st = sim->st;
+    return p;
+}
+
+// Enqueue one step at parity b.  Returns the number of kernels launched or
+// -1 on a launch error (message in sim->err).  ev_a/ev_b bracket the particle
+// advance when non-null (external event records inside a capture).
+int enqueue_step(pic_sim* sim, int b, cudaEvent_t ev_a, cudaEvent_t ev_b, bool capturing) {
+    cudaStream_t s = sim->stream;
+    const int threads = sim->cfg.threads;
+    const PushParams pp = push_params(sim, b);
+    const SortParams sp = sort_params(sim, b);
+    YeeParams yp;
+    yp.g = sim->g;
+    yp.Fin = sim->F[b];
+    yp.Fout = sim->F[1 - b];
+    yp.J = sim->J[b];
+    yp.Jnext = sim->J[1 - b];
+    yp.hist_e = sim->hist_e;
+    yp.hist_b = sim->hist_b;
+    yp.st = sim->st;
+    int n = 0;
+    cudaError_t e;
+    const unsigned rec = capturing ? cudaEventRecordExternal : 0u;
+    if (ev_a && (e = cudaEventRecordWithFlags(ev_a, s, rec)) != cudaSuccess) goto bad;
+    e = (sim->cfg.flags & PIC_STRICT_FP) ? launch_push_strict(&sim->fmap[b], pp, threads, s)
+                                         : launch_push_fast(&sim->fmap[b], pp, threads, s);
+    if (e != cudaSuccess) goto bad;
+    n += sim->g.ntiles > 0;
+    if (ev_b && (e = cudaEventRecordWithFlags(ev_b, s, rec)) != cudaSuccess) goto bad;
+    if ((e = launch_scan(sp, s)) != cudaSuccess) goto bad;
+    n += 1;
+    if ((e = launch_evict(sp, threads, s)) != cudaSuccess) goto bad;
+    if ((e = launch_fill(sp, threads, s)) != cudaSuccess) goto bad;
+    n += (sp.nsp > 0 && sim->g.ntiles > 0) ? 2 : 0;
+    if ((e = launch_yee(yp, s)) != cudaSuccess) goto bad;
+    n += 1;
+    return n;
+bad:
+    sim->err = std::string("kernel launch failed: ") + cudaGetErrorString(e);
+    return -1;
+}
+
+pic_status build_graph(pic_sim* sim, int b) {
+    cudaGraph_t graph = nullptr;
+    const bool timing = (sim->cfg.flags & PIC_TIMING) != 0;
+    CK(cudaStreamBeginCapture(sim->stream, cudaStreamCaptureModeThreadLocal));
+    const int n = enqueue_step(sim, b, timing ? sim->ev_placeholder[0] : nullptr,
+                               timing ? sim->ev_placeholder[1] : nullptr, true);
+    cudaError_t e = cudaStreamEndCapture(sim->stream, &graph);
+    if (n < 0) {
+        if (graph) cudaGraphDestroy(graph);
+        return PIC_ECUDA;
+    }
+    CK(e);
+    sim->launches_per_step = n;
+    if (timing) {
+        size_t count = 0;
+        CK(cudaGraphGetNodes(graph, nullptr, &count));
+        std::vector<cudaGraphNode_t> nodes(count);
+        CK(cudaGraphGetNodes(graph, nodes.data(), &count));
+        for (auto nd : nodes) {
+            cudaGraphNodeType ty;
+            CK(cudaGraphNodeGetType(nd, &ty));
+            if (ty != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev;
+            CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+            if (ev == sim->ev_placeholder[0]) sim->ev_node[b][0] = nd;
+            if (ev == sim->ev_placeholder[1]) sim->ev_node[b][1] = nd;
+        }
+    }
+    e = cudaGraphInstantiate(&sim->gexec[b], graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    return PIC_OK;
+}
+
+pic_status timing_pair(pic_sim* sim, cudaEvent_t* a, cudaEvent_t* b) {
+    const size_t need = 2 * (sim->ev_used + 1);
+    while (sim->ev_pool.size() < need) {
+        cudaEvent_t ev;
+        CK(cudaEventCreate(&ev));
+        sim->ev_pool.push_back(ev);
+    }
+    *a = sim->ev_pool[2 * sim->ev_used];
+    *b = sim->ev_pool[2 * sim->ev_used + 1];
+    sim->ev_used += 1;
+    return PIC_OK;
+}
+
+pic_status read_state(pic_sim* sim, DevState* h) {
+    CK(cudaMemcpyAsync(h, sim->st, sizeof(DevState), cudaMemcpyDeviceToHost, sim->stream));
+    CK(cudaStreamSynchronize(sim->stream));
+    return PIC_OK;
+}
+
+pic_status status_from_bits(pic_sim* sim, unsigned bits) {
+    if (bits & ST_TIMEOUT) return fail(sim, PIC_ETIMEOUT, "a bounded device wait ran out");
+    if (bits & ST_SORT)
+        return fail(sim, PIC_EOVERFLOW, "tile re-sort bookkeeping inconsistent");
+    if (bits & ST_PARTICLE)
+        return fail(sim, PIC_EPARTICLE,
+                    "a particle moved one cell or more in a step or has a non-finite momentum");
+    return PIC_OK;
+}
+
+pic_status sync_status(pic_sim* sim) {
+    DevState h;
+    pic_status r = read_state(sim, &h);
+    if (r != PIC_OK) return r;
+    return status_from_bits(sim, h.status);
+}
+
+// zero the history slots of the current level and record the field energy
+pic_status refresh_level_energy(pic_sim* sim) {
+    CK(launch_hist_prime(sim->hist_e, sim->hist_b, sim->hist_k, sim->st, sim->stream));
+    const long long n = sim->step & (HIST - 1);
+    CK(launch_field_energy(sim->g, sim->F[sim->cur], sim->hist_e + n, sim->hist_b + n,
+                           sim->stream));
+    return PIC_OK;
+}
+
+const void* stage_in(pic_sim* sim, const void* src, size_t bytes, void* staging, int on_device,
+                     pic_status* st) {
+    *st = PIC_OK;
+    if (on_device || bytes == 0) return src;
+    cudaError_t e = cudaMemcpyAsync(staging, src, bytes, cudaMemcpyHostToDevice, sim->stream);
+    if (e != cudaSuccess) {
+        *st = fail(sim, PIC_ECUDA, "host-to-device copy failed: %s", cudaGetErrorString(e));
+        return nullptr;
+    }
+    return staging;
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_init(const pic_config* cfg, void* cuda_stream, pic_sim** out) {
+    if (!out) return PIC_EINVAL;
+    *out = nullptr;
+    if (!cfg) return PIC_EINVAL;
+    pic_config c = *cfg;
+    if (c.tile == 0) c.tile = 16;
+    if (c.threads == 0) c.threads = 256;
+    if (!(c.tile == 8 || c.tile == 16 || c.tile == 32)) return PIC_EINVAL;
+    if (c.threads < 64 || c.threads > 1024 || c.threads % 32) return PIC_EINVAL;
+    if (c.nx < 8 || c.ny < 8 || c.nx > 32768 || c.ny > 32768) return PIC_EINVAL;
+    if (c.nx % c.tile || c.ny % c.tile) return PIC_EINVAL;
+    if (c.n_species < 1 || c.n_species > PIC_MAX_SPECIES) return PIC_EINVAL;
+    if (!(c.dx > 0 && c.dy > 0 && c.dt > 0) || !std::isfinite(c.dx) || !std::isfinite(c.dy) ||
+        !std::isfinite(c.dt))
+        return PIC_EINVAL;
+    for (int k = 0; k < c.n_species; ++k)
+        if (!(c.species[k].density > 0) || !(c.species[k].ppc > 0) ||
+            !(c.species[k].q_over_m != 0) || !std::isfinite(c.species[k].q_over_m))
+            return PIC_EINVAL;
+    // Courant condition, Eq. 1 (c = 1)
+    const double lim = 1.0 / std::sqrt(1.0 / (c.dx * c.dx) + 1.0 / (c.dy * c.dy));
+    if (!(c.dt < lim)) return PIC_ECFL;
+
+    pic_sim* sim = new pic_sim();
+    sim->cfg = c;
+    sim->stream = (cudaStream_t)cuda_stream;
+    Geom& g = sim->g;
+    g.nx = c.nx;
+    g.ny = c.ny;
+    g.T = c.tile;
+    g.ntx = c.nx / c.tile;
+    g.nty = c.ny / c.tile;
+    g.ntiles = g.ntx * g.nty;
+    g.P = c.nx + 2 * GX;
+    g.R = c.ny + 3;
+    g.cstride = (long long)g.P * g.R;
+    g.cx = (float)(c.dt / c.dx);
+    g.cy = (float)(c.dt / c.dy);
+    g.hdt_dx = (float)(0.5 * c.dt / c.dx);
+    g.hdt_dy = (float)(0.5 * c.dt / c.dy);
+    g.dt_dx = (float)(c.dt / c.dx);
+    g.dt_dy = (float)(c.dt / c.dy);
+    g.dt = (float)c.dt;
+    g.dx = c.dx;
+    g.dy = c.dy;
+    g.dtd = c.dt;
+
+    auto cleanup_fail = [&](pic_status code, const char* what, cudaError_t e) {
+        pic_destroy(sim);
+        (void)what;
+        (void)e;
+        return code;
+    };
+    cudaError_t e = cudaSuccess;
+    const size_t gsz = (size_t)g.cstride;
+    for (int b = 0; b < 2; ++b) {
+        if (e == cudaSuccess) e = dalloc(&sim->F[b], 6 * gsz);
+        if (e == cudaSuccess) e = dalloc(&sim->J[b], 3 * gsz);
+        if (e == cudaSuccess) e = cudaMemsetAsync(sim->F[b], 0, 6 * gsz * 4, sim->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(sim->J[b], 0, 3 * gsz * 4, sim->stream);
+    }
+    const size_t ncell = (size_t)c.nx * c.ny;
+    if (e == cudaSuccess) e = dalloc(&sim->gtmp, 3 * ncell);
+    if (e == cudaSuccess) e = dalloc(&sim->rho, ncell);
+    if (e == cudaSuccess) e = dalloc(&sim->rho_prev, ncell);
+    if (e == cudaSuccess) e = dalloc(&sim->hist_e, HIST);
+    if (e == cudaSuccess) e = dalloc(&sim->hist_b, HIST);
+    if (e == cudaSuccess) e = dalloc(&sim->hist_k, HIST);
+    if (e == cudaSuccess) e = dalloc(&sim->dred, 8);
+    if (e == cudaSuccess) e = dalloc(&sim->st, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sim->st, 0, sizeof(DevState), sim->stream);
+    // NaN everywhere: levels never recorded read as NaN
+    if (e == cudaSuccess) e = cudaMemsetAsync(sim->hist_e, 0xff, HIST * 8, sim->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sim->hist_b, 0xff, HIST * 8, sim->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sim->hist_k, 0xff, HIST * 8, sim->stream);
+    for (int k = 0; k < c.n_species && e == cudaSuccess; ++k) {
+        SpeciesDev& s = sim->sp[k];
+        memset(&s, 0, sizeof s);
+        if (e == cudaSuccess) e = dalloc(&s.off[0], g.ntiles + 1);
+        if (e == cudaSuccess) e = dalloc(&s.off[1], g.ntiles + 1);
+        if (e == cudaSuccess) e = dalloc(&s.stay, g.ntiles);
+        if (e == cudaSuccess) e = dalloc(&s.leave, g.ntiles);
+        if (e == cudaSuccess) e = dalloc(&s.dirc, 8 * (size_t)g.ntiles);
+        if (e == cudaSuccess) e = dalloc(&s.evict, g.ntiles);
+        if (e == cudaSuccess) e = dalloc(&s.cursor, g.ntiles);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+            e = cudaMemsetAsync(s.off[b], 0, sizeof(int32_t) * (g.ntiles + 1), sim->stream);
+        const auto& sc = c.species[k];
+        const double qt = (sc.q_over_m > 0 ? 1.0 : -1.0) * sc.density / sc.ppc;
+        s.qtilde = qt;
+        s.tem = (float)(0.5 * sc.q_over_m * c.dt);
+        s.qjx = (float)(qt * c.dx / c.dt);
+        s.qjy = (float)(qt * c.dy / c.dt);
+        s.qjz = (float)qt;
+        s.ke_w = qt / sc.q_over_m * c.dx * c.dy;
+    }
+    if (e != cudaSuccess) return cleanup_fail(e == cudaErrorMemoryAllocation ? PIC_ENOMEM : PIC_ECUDA,
+                                              "alloc", e);
+    for (int b = 0; b < 2; ++b)
+        if (!make_field_map(&sim->fmap[b], g, sim->F[b])) return cleanup_fail(PIC_ECUDA, "tmap", e);
+    {
+        // raise the particle kernels' shared-memory limit before any capture
+        PushParams p0;
+        memset(&p0, 0, sizeof p0);
+        p0.g = g;
+        if (launch_push_fast(nullptr, p0, c.threads, sim->stream) != cudaSuccess ||
+            launch_push_strict(nullptr, p0, c.threads, sim->stream) != cudaSuccess)
+            return cleanup_fail(PIC_ECUDA, "smem attribute", e);
+    }
+    if (c.flags & PIC_TIMING)
+        for (int k = 0; k < 2; ++k)
+            if (cudaEventCreate(&sim->ev_placeholder[k]) != cudaSuccess)
+                return cleanup_fail(PIC_ECUDA, "event", e);
+    if (refresh_level_energy(sim) != PIC_OK) return cleanup_fail(PIC_ECUDA, "energy", e);
+    if (cudaStreamSynchronize(sim->stream) != cudaSuccess)
+        return cleanup_fail(PIC_ECUDA, "sync", e);
+    *out = sim;
+    return PIC_OK;
+}
+
+pic_status pic_load_particles(pic_sim* sim, int species, int64_t n, const int32_t* ix,
+                              const int32_t* iy, const float* x, const float* y,
+                              const float* ux, const float* uy, const float* uz,
+                              const int32_t* id, int on_device) {
+    if (!sim) return PIC_EINVAL;
+    sim->err.clear();
+    if (species < 0 || species >= sim->cfg.n_species)
+        return fail(sim, PIC_EINVAL, "species %d out of range", species);
+    if (n < 0 || n > 0x7fffffffLL) return fail(sim, PIC_EINVAL, "bad particle count %lld", (long long)n);
+    if (n > 0 && (!ix || !iy || !x || !y || !ux || !uy || !uz))
+        return fail(sim, PIC_EINVAL, "null particle array");
+    cudaStream_t s = sim->stream;
+    SpeciesDev& S = sim->sp[species];
+    const bool track = (sim->cfg.flags & PIC_TRACK_IDS) != 0;
+    // stage into the out arrays of a (possibly new) allocation
+    SpeciesDev W = S;
+    const bool grow = n > S.cap;
+    if (grow) {
+        SpeciesDev fresh = S;
+        fresh.cell = fresh.id = fresh.ocell = fresh.oid = fresh.hole = fresh.fslot = fresh.isrc =
+            nullptr;
+        fresh.x = fresh.y = fresh.ux = fresh.uy = fresh.uz = nullptr;
+        fresh.ox = fresh.oy = fresh.oux = fresh.ouy = fresh.ouz = nullptr;
+        fresh.cap = 0;
+        cudaError_t e = alloc_particles(fresh, n);
+        if (e != cudaSuccess) {
+            free_species(fresh);
+            return fail(sim, PIC_ENOMEM, "cannot allocate %lld particles", (long long)n);
+        }
+        W = fresh;
+    }
+    const size_t b4 = 4 * (size_t)n;
+    auto copy_in = [&](void* dst, const void* src) -> cudaError_t {
+        if (n == 0) return cudaSuccess;
+        return cudaMemcpyAsync(dst, src, b4, on_device ? cudaMemcpyDeviceToDevice
+                                                       : cudaMemcpyHostToDevice, s);
+    };
+    cudaError_t e = cudaSuccess;
+    // staging: ix -> ocell, iy -> hole, x.. -> ox.., ids -> isrc
+    if (e == cudaSuccess) e = copy_in(W.ocell, ix);
+    if (e == cudaSuccess) e = copy_in(W.hole, iy);
+    if (e == cudaSuccess) e = copy_in(W.ox, x);
+    if (e == cudaSuccess) e = copy_in(W.oy, y);
+    if (e == cudaSuccess) e = copy_in(W.oux, ux);
+    if (e == cudaSuccess) e = copy_in(W.ouy, uy);
+    if (e == cudaSuccess) e = copy_in(W.ouz, uz);
+    if (e == cudaSuccess && track && id) e = copy_in(W.isrc, id);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&sim->st->load_bad, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_load(sim->g, W, track, n, W.off[sim->cur], sim->st, s, 0, nullptr);
+    DevState h;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sim->st, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess || h.load_bad) {
+        if (grow) free_species(W);
+        if (e != cudaSuccess)
+            return fail(sim, PIC_ECUDA, "particle load failed: %s", cudaGetErrorString(e));
+        return fail(sim, PIC_EINVAL, "%d particles with a cell outside the grid, an offset outside [0,1) or a non-finite momentum",
+                    h.load_bad);
+    }
+    e = launch_load(sim->g, W, track, n, W.off[sim->cur], sim->st, s, 1,
+                    (track && id) ? W.isrc : nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        if (grow) free_species(W);
+        return fail(sim, PIC_ECUDA, "particle scatter failed: %s", cudaGetErrorString(e));
+    }
+    if (grow) {
+        SpeciesDev old = S;
+        free_species(old);
+    }
+    W.n = n;
+    S = W;
+    invalidate_graphs(sim);
+    sim->rho_prev_step = -1;
+    pic_status r = refresh_level_energy(sim);
+    if (r != PIC_OK) return r;
+    CK(cudaStreamSynchronize(s));
+    return PIC_OK;
+}
+
+pic_status pic_set_fields(pic_sim* sim, const float* E, const float* B, int on_device) {
+    if (!sim) return PIC_EINVAL;
+    sim->err.clear();
+    const size_t bytes = 3 * (size_t)sim->g.nx * sim->g.ny * 4;
+    const float* srcs[2] = {E, B};
+    for (int f = 0; f < 2; ++f) {
+        if (!srcs[f]) continue;
+        pic_status st;
+        const float* src = (const float*)stage_in(sim, srcs[f], bytes, sim->gtmp, on_device, &st);
+        if (st != PIC_OK) return st;
+        CK(launch_set_grid(sim->g, sim->F[sim->cur] + 3 * f * sim->g.cstride, 3, src,
+                           sim->stream));
+        CK(cudaStreamSynchronize(sim->stream));
+    }
+    sim->rho_prev_step = -1;
+    pic_status r = refresh_level_energy(sim);
+    if (r != PIC_OK) return r;
+    CK(cudaStreamSynchronize(sim->stream));
+    return PIC_OK;
+}
+
+pic_status pic_step(pic_sim* sim, int nsteps) {
+    if (!sim) return PIC_EINVAL;
+    if (nsteps < 0) return fail(sim, PIC_EINVAL, "negative step count");
+    sim->err.clear();
+    const bool timing = (sim->cfg.flags & PIC_TIMING) != 0;
+    const bool graph = (sim->cfg.flags & PIC_NO_GRAPH) == 0;
+    for (int k = 0; k < nsteps; ++k) {
+        const int b = sim->cur;
+        cudaEvent_t ea = nullptr, eb = nullptr;
+        if (timing) {
+            pic_status r = timing_pair(sim, &ea, &eb);
+            if (r != PIC_OK) return r;
+        }
+        if (graph) {
+            if (!sim->gexec[b]) {
+                pic_status r = build_graph(sim, b);
+                if (r != PIC_OK) return r;
+            }
+            if (timing) {
+                CK(cudaGraphExecEventRecordNodeSetEvent(sim->gexec[b], sim->ev_node[b][0], ea));
+                CK(cudaGraphExecEventRecordNodeSetEvent(sim->gexec[b], sim->ev_node[b][1], eb));
+            }
+            CK(cudaGraphLaunch(sim->gexec[b], sim->stream));
+            sim->launches += sim->launches_per_step;
+        } else {
+            const int n = enqueue_step(sim, b, ea, eb, false);
+            if (n < 0) return PIC_ECUDA;
+            sim->launches += n;
+        }
+        sim->cur = 1 - b;
+        sim->step += 1;
+    }
+    return PIC_OK;
+}
+
+pic_status pic_get_fields(pic_sim* sim, int which, float* out, int on_device) {
+    if (!sim || !out) return PIC_EINVAL;
+    sim->err.clear();
+    const Geom& g = sim->g;
+    const size_t ncell = (size_t)g.nx * g.ny;
+    float* dst = on_device ? out : sim->gtmp;
+    if (which == 0 || which == 1) {
+        CK(launch_get_grid(g, sim->F[sim->cur] + 3 * which * g.cstride, 3, dst, sim->stream));
+    } else if (which == 2) {
+        CK(launch_get_grid(g, sim->J[1 - sim->cur], 3, dst, sim->stream));
+    } else if (which == 3) {
+        CK(cudaMemsetAsync(sim->rho, 0, ncell * 8, sim->stream));
+        const int32_t* offs[MAX_SPECIES];
+        for (int k = 0; k < sim->cfg.n_species; ++k) offs[k] = sim->sp[k].off[sim->cur];
+        CK(launch_rho(g, sim->sp, sim->cfg.n_species, offs, sim->rho, sim->stream));
+        std::vector<double> h(ncell);
+        CK(cudaMemcpyAsync(h.data(), sim->rho, ncell * 8, cudaMemcpyDeviceToHost, sim->stream));
+        CK(cudaStreamSynchronize(sim->stream));
+        std::vector<float> f(ncell);
+        for (size_t k = 0; k < ncell; ++k) f[k] = (float)(h[k] + sim->cfg.background);
+        CK(cudaMemcpy(out, f.data(), ncell * 4,
+                      on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+        return sync_status(sim);
+    } else {
+        return fail(sim, PIC_EINVAL, "unknown field %d", which);
+    }
+    if (!on_device)
+        CK(cudaMemcpyAsync(out, sim->gtmp, 3 * ncell * 4, cudaMemcpyDeviceToHost, sim->stream));
+    return sync_status(sim);
+}
+
+pic_status pic_get_particles(pic_sim* sim, int species, int32_t* ix, int32_t* iy, float* x,
+                             float* y, float* ux, float* uy, float* uz, int32_t* id,
+                             int64_t* tile_offset, int on_device) {
+    if (!sim) return PIC_EINVAL;
+    sim->err.clear();
+    if (species < 0 || species >= sim->cfg.n_species)
+        return fail(sim, PIC_EINVAL, "species %d out of range", species);
+    SpeciesDev& S = sim->sp[species];
+    cudaStream_t s = sim->stream;
+    const size_t b4 = 4 * (size_t)S.n;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (S.n > 0) {
+        // unpack cells into caller buffers (device) or into scratch then copy
+        int32_t* dix = on_device ? ix : (ix ? S.ocell : nullptr);
+        int32_t* diy = on_device ? iy : (iy ? S.hole : nullptr);
+        if (dix || diy) CK(launch_unpack_cells(S.cell, S.n, dix, diy, s));
+        if (!on_device && ix) CK(cudaMemcpyAsync(ix, S.ocell, b4, k, s));
+        if (!on_device && iy) CK(cudaMemcpyAsync(iy, S.hole, b4, k, s));
+        if (x) CK(cudaMemcpyAsync(x, S.x, b4, k, s));
+        if (y) CK(cudaMemcpyAsync(y, S.y, b4, k, s));
+        if (ux) CK(cudaMemcpyAsync(ux, S.ux, b4, k, s));
+        if (uy) CK(cudaMemcpyAsync(uy, S.uy, b4, k, s));
+        if (uz) CK(cudaMemcpyAsync(uz, S.uz, b4, k, s));
+        if (id && (sim->cfg.flags & PIC_TRACK_IDS)) CK(cudaMemcpyAsync(id, S.id, b4, k, s));
+    }
+    if (tile_offset) {
+        const int nt1 = sim->g.ntiles + 1;
+        int64_t* d = on_device ? tile_offset : (int64_t*)sim->rho;  // rho is scratch here
+        CK(launch_offsets_to_i64(S.off[sim->cur], nt1, d, s));
+        if (!on_device) CK(cudaMemcpyAsync(tile_offset, d, 8 * (size_t)nt1, k, s));
+    }
+    return sync_status(sim);
+}
+
+int64_t pic_num_particles(const pic_sim* sim, int species) {
+    if (!sim || species < 0 || species >= sim->cfg.n_species) return -1;
+    return sim->sp[species].n;
+}
+
+int64_t pic_num_tiles(const pic_sim* sim) { return sim ? sim->g.ntiles : -1; }
+
+pic_status pic_diagnostics(pic_sim* sim, pic_diag* out) {
+    if (!sim || !out) return PIC_EINVAL;
+    sim->err.clear();
+    const Geom& g = sim->g;
+    cudaStream_t s = sim->stream;
+    const size_t ncell = (size_t)g.nx * g.ny;
+    CK(cudaMemsetAsync(sim->rho, 0, ncell * 8, s));
+    const int32_t* offs[MAX_SPECIES];
+    for (int k = 0; k < sim->cfg.n_species; ++k) offs[k] = sim->sp[k].off[sim->cur];
+    CK(launch_rho(g, sim->sp, sim->cfg.n_species, offs, sim->rho, s));
+    CK(cudaMemsetAsync(sim->dred, 0, 8 * sizeof(double), s));
+    const bool cont = sim->rho_prev_step >= 0 && sim->rho_prev_step + 1 == sim->step;
+    CK(launch_grid_residuals(g, sim->F[sim->cur], sim->J[1 - sim->cur], sim->rho,
+                             cont ? sim->rho_prev : nullptr, sim->cfg.background, sim->dred, s));
+    double red[3];
+    CK(cudaMemcpyAsync(red, sim->dred, sizeof red, cudaMemcpyDeviceToHost, s));
+    const long long n = sim->step;
+    double he, hb, hk = NAN;
+    CK(cudaMemcpyAsync(&he, sim->hist_e + (n & (HIST - 1)), 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&hb, sim->hist_b + (n & (HIST - 1)), 8, cudaMemcpyDeviceToHost, s));
+    if (n > 0)
+        CK(cudaMemcpyAsync(&hk, sim->hist_k + ((n - 1) & (HIST - 1)), 8, cudaMemcpyDeviceToHost, s));
+    DevState h;
+    CK(cudaMemcpyAsync(&h, sim->st, sizeof h, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    memset(out, 0, sizeof *out);
+    out->step = n;
+    out->time = n * sim->cfg.dt;
+    out->w_e = he;
+    out->w_b = hb;
+    out->w_k = hk;
+    out->gauss_max = red[0];
+    out->continuity_max = cont ? red[1] : NAN;
+    out->charge_total = red[2];
+    long long lv = 0;
+    for (int k = 0; k < sim->cfg.n_species; ++k) {
+        out->n_particles[k] = sim->sp[k].n;
+        lv += h.leavers_sp[k];
+    }
+    out->leavers = n > 0 ? lv : 0;
+    out->status_bits = h.status;
+    std::swap(sim->rho, sim->rho_prev);
+    sim->rho_prev_step = n;
+    return status_from_bits(sim, h.status);
+}
+
+pic_status pic_get_history(pic_sim* sim, int64_t first, int64_t count, double* w_e, double* w_b,
+                           double* w_k) {
+    if (!sim || count < 0) return PIC_EINVAL;
+    sim->err.clear();
+    std::vector<double> he(HIST), hb(HIST), hk(HIST);
+    CK(cudaMemcpyAsync(he.data(), sim->hist_e, HIST * 8, cudaMemcpyDeviceToHost, sim->stream));
+    CK(cudaMemcpyAsync(hb.data(), sim->hist_b, HIST * 8, cudaMemcpyDeviceToHost, sim->stream));
+    CK(cudaMemcpyAsync(hk.data(), sim->hist_k, HIST * 8, cudaMemcpyDeviceToHost, sim->stream));
+    CK(cudaStreamSynchronize(sim->stream));
+    const long long n = sim->step;
+    for (int64_t k = 0; k < count; ++k) {
+        const long long lev = first + k;
+        const bool fld_ok = lev >= 0 && lev <= n && lev > n - HIST;
+        const bool kin_ok = lev >= 0 && lev < n && lev > n - HIST;
+        if (w_e) w_e[k] = fld_ok ? he[lev & (HIST - 1)] : NAN;
+        if (w_b) w_b[k] = fld_ok ? hb[lev & (HIST - 1)] : NAN;
+        if (w_k) w_k[k] = kin_ok ? hk[lev & (HIST - 1)] : NAN;
+    }
+    return PIC_OK;
+}
+
+pic_status pic_sync(pic_sim* sim) {
+    if (!sim) return PIC_EINVAL;
+    return sync_status(sim);
+}
+
+pic_status pic_clear_status(pic_sim* sim) {
+    if (!sim) return PIC_EINVAL;
+    CK(cudaStreamSynchronize(sim->stream));
+    CK(cudaMemsetAsync(&sim->st->status, 0, sizeof(unsigned), sim->stream));
+    CK(cudaStreamSynchronize(sim->stream));
+    sim->err.clear();
+    return PIC_OK;
+}
+
+pic_status pic_timing(pic_sim* sim, double* advance_ms, int64_t* advance_launches, int reset) {
+    if (!sim) return PIC_EINVAL;
+    CK(cudaStreamSynchronize(sim->stream));
+    double tot = 0.0;
+    for (size_t k = 0; k < sim->ev_used; ++k) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, sim->ev_pool[2 * k], sim->ev_pool[2 * k + 1]));
+        tot += ms;
+    }
+    if (advance_ms) *advance_ms = tot;
+    if (advance_launches) *advance_launches = (int64_t)sim->ev_used;
+    if (reset) sim->ev_used = 0;
+    return PIC_OK;
+}
+
+int64_t pic_kernel_launches(const pic_sim* sim) { return sim ? sim->launches : -1; }
+
+const char* pic_last_error(const pic_sim* sim) { return sim ? sim->err.c_str() : "null handle"; }
+
+void pic_destroy(pic_sim* sim) {
+    if (!sim) return;
+    if (sim->stream) cudaStreamSynchronize(sim->stream);
+    invalidate_graphs(sim);
+    for (int b = 0; b < 2; ++b) {
+        dfree(sim->F[b]);
+        dfree(sim->J[b]);
+        if (sim->ev_placeholder[b]) cudaEventDestroy(sim->ev_placeholder[b]);
+    }
+    for (auto ev : sim->ev_pool) cudaEventDestroy(ev);
+    dfree(sim->gtmp);
+    dfree(sim->rho);
+    dfree(sim->rho_prev);
+    dfree(sim->hist_e);
+    dfree(sim->hist_b);
+    dfree(sim->hist_k);
+    dfree(sim->dred);
+    dfree(sim->st);
+    for (int k = 0; k < sim->cfg.n_species; ++k) {
+        SpeciesDev& s = sim->sp[k];
+        free_species(s);
+        dfree(s.off[0]);
+        dfree(s.off[1]);
+        dfree(s.stay);
+        dfree(s.leave);
+        dfree(s.dirc);
+        dfree(s.evict);
+        dfree(s.cursor);
+    }
+    delete sim;
+}
+
+}  // extern "C"

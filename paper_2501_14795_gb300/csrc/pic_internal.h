@@ -1,0 +1,163 @@
+// Internal declarations shared by the host runtime (pic_host.cu) and the
+// kernel translation units.  Not part of the public ABI (include/pic.h).
+//
+// Device data layout (one simulation):
+//   * Grid arrays (E|B: 6 components, J: 3 components) are float32, each
+//     component R = ny + 3 rows of P = nx + 8 floats.  Cell (i, j) lives at
+//     row j + GY, column i + GX (GX = 4, GY = 1), so every component has guard
+//     cells i in [-4, nx+4), j in [-1, ny+2).  Guards i = -1, nx, nx+1 and
+//     j = -1, ny, ny+1 hold periodic images (update_gc_copy of Listing 3.1);
+//     the others are never written and stay zero.  The column shift of 4 makes
+//     the TMA box of a tile start on a 16-byte boundary (x multiple of 4).
+//   * E|B are double-buffered (read one, write the other each step) and so is
+//     J, because the fused Yee kernel reads neighbours across CTAs.
+//   * Particles of a species are structure-of-arrays in one contiguous range
+//     sorted by tile (§4.1): cell (int32, ix | iy << 16), x, y, ux, uy, uz
+//     (float32), optional id; tile t owns [off[t], off[t+1]) (int32 offsets,
+//     double-buffered across the re-sort).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pic {
+
+constexpr int GX = 4;            // guard columns left of cell 0
+constexpr int GY = 1;            // guard rows below cell 0
+constexpr int HIST = 1 << 16;    // energy-history ring length (time levels)
+constexpr int32_t HOLE = -1;     // cell value of a slot vacated by a leaver
+constexpr int MAX_SPECIES = 4;
+
+// device status bits (sticky)
+constexpr unsigned ST_PARTICLE = 1u;  // moved >= 1 cell, non-finite, or out of its tile
+constexpr unsigned ST_TIMEOUT = 2u;   // bounded wait ran out
+constexpr unsigned ST_SORT = 4u;      // re-sort counts inconsistent
+
+struct DevState {
+    unsigned status;
+    unsigned pad;
+    long long step;      // time level n of the current fields
+    long long leavers_sp[MAX_SPECIES];  // particles that changed tile in the last step
+    int load_bad;        // pic_load_particles validation failures
+    int pad2;
+};
+
+struct SpeciesDev {
+    // particle arrays (capacity >= n)
+    int32_t* cell;
+    float *x, *y, *ux, *uy, *uz;
+    int32_t* id;
+    // leaver / eviction staging ("out") arrays, same capacity
+    int32_t* ocell;
+    float *ox, *oy, *oux, *ouy, *ouz;
+    int32_t* oid;
+    int32_t* hole;    // positions vacated by leavers, per source tile
+    int32_t* fslot;   // fill lists: target positions ...
+    int32_t* isrc;    // ... and source indices into the out arrays
+    int32_t* off[2];  // ntiles + 1 bookmarks (tile_offset), ping-pong
+    int32_t* stay;    // per tile: particles that stayed
+    int32_t* leave;   // per tile: particles that left
+    int32_t* dirc;    // per tile x 8 directions: leavers by destination
+    int32_t* evict;   // per tile: stayers displaced by the new bookmarks
+    int32_t* cursor;  // per tile scratch for the initial load
+    int64_t n;        // particles
+    int64_t cap;      // capacity of the particle arrays
+    // per-species constants (computed in double on the host, rounded once)
+    float tem;        // (q/m) dt / 2
+    float qjx, qjy;   // qtilde dx/dt, qtilde dy/dt
+    float qjz;        // qtilde
+    double ke_w;      // kinetic-energy weight qtilde/(q/m) dx dy
+    double qtilde;
+};
+
+struct Geom {
+    int nx, ny, T, ntx, nty, ntiles;
+    int P, R;          // pitch (floats) and rows of a grid component
+    long long cstride; // R * P
+    float cx, cy;      // dt/dx, dt/dy
+    float hdt_dx, hdt_dy, dt_dx, dt_dy, dt;
+    double dx, dy, dtd;
+};
+
+// ---- parameters passed by value to the kernels ------------------------------
+struct PushSpecies {
+    const int32_t* off;
+    int32_t *cell, *id, *ocell, *oid, *hole, *stay, *leave, *dirc;
+    float *x, *y, *ux, *uy, *uz, *ox, *oy, *oux, *ouy, *ouz;
+    float tem, qjx, qjy, qjz;
+    double ke_w;
+};
+
+struct PushParams {
+    Geom g;
+    float* J;              // this step's current buffer (base of component 0)
+    int nsp;
+    int track_ids;
+    PushSpecies sp[MAX_SPECIES];
+    double* hist_k;        // kinetic-energy history ring
+    DevState* st;
+};
+
+struct SortSpecies {
+    const int32_t* off_old;
+    int32_t* off_new;
+    int32_t *cell, *id, *ocell, *oid, *hole, *fslot, *isrc, *stay, *leave, *dirc, *evict;
+    float *x, *y, *ux, *uy, *uz, *ox, *oy, *oux, *ouy, *ouz;
+    int n;
+};
+
+struct SortParams {
+    Geom g;
+    int nsp;
+    int track_ids;
+    SortSpecies sp[MAX_SPECIES];
+    double *hist_e, *hist_b, *hist_k;
+    DevState* st;
+};
+
+struct YeeParams {
+    Geom g;
+    const float* Fin;   // E|B at n (6 components)
+    float* Fout;        // E|B at n+1
+    const float* J;     // current of this step
+    float* Jnext;       // next step's current buffer: its shared ring is zeroed here
+    double *hist_e, *hist_b;
+    DevState* st;
+};
+
+// ---- launchers (defined in the kernel translation units) ---------------------
+// particle advance, fast (FMA) and strict (no contraction) builds
+cudaError_t launch_push_fast(const CUtensorMap* fmap, const PushParams& p, int threads,
+                             cudaStream_t s);
+cudaError_t launch_push_strict(const CUtensorMap* fmap, const PushParams& p, int threads,
+                               cudaStream_t s);
+
+cudaError_t launch_scan(const SortParams& p, cudaStream_t s);
+cudaError_t launch_evict(const SortParams& p, int threads, cudaStream_t s);
+cudaError_t launch_fill(const SortParams& p, int threads, cudaStream_t s);
+cudaError_t launch_yee(const YeeParams& p, cudaStream_t s);
+
+// grid utilities
+cudaError_t launch_set_grid(const Geom& g, float* F, int ncomp, const float* src, cudaStream_t s);
+cudaError_t launch_get_grid(const Geom& g, const float* F, int ncomp, float* dst, cudaStream_t s);
+cudaError_t launch_field_energy(const Geom& g, const float* F, double* out_e, double* out_b,
+                                cudaStream_t s);
+cudaError_t launch_rho(const Geom& g, const SpeciesDev* sp, int nsp, const int32_t* const* off,
+                       double* rho, cudaStream_t s);
+cudaError_t launch_grid_residuals(const Geom& g, const float* F, const float* J,
+                                  const double* rho, const double* rho_prev, double background,
+                                  double* out /* [gauss_max, cont_max, charge_sum] */,
+                                  cudaStream_t s);
+// Initial sort of a staged species into tiles.  The input is staged in the
+// out arrays: ix in ocell, iy in hole, x..uz in ox..ouz; ids (optional) in
+// `staged_ids`.  phase 0 validates and counts per tile, phase 1 scans the
+// counts into `off` and scatters into the particle arrays.
+cudaError_t launch_load(const Geom& g, SpeciesDev& sp, int track_ids, int64_t n, int32_t* off,
+                        DevState* st, cudaStream_t s, int phase, const int32_t* staged_ids);
+cudaError_t launch_unpack_cells(const int32_t* cell, int64_t n, int32_t* ix, int32_t* iy,
+                                cudaStream_t s);
+cudaError_t launch_offsets_to_i64(const int32_t* off, int64_t n, int64_t* out, cudaStream_t s);
+cudaError_t launch_hist_prime(double* hist_e, double* hist_b, double* hist_k, DevState* st,
+                              cudaStream_t s);
+
+}  // namespace pic

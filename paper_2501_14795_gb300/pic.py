@@ -1,0 +1,327 @@
+"""Thin ctypes binding of the C ABI in include/pic.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does
+nothing but convert arguments: all computation runs in libpic.so's CUDA
+kernels.  Arrays may be numpy arrays (host memory) or torch tensors (host or
+CUDA); ``on_device`` is inferred from the first array.  If libpic.so cannot be
+loaded the binding raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpic.so")
+
+PIC_MAX_SPECIES = 4
+PIC_STRICT_FP = 1
+PIC_TRACK_IDS = 2
+PIC_TIMING = 4
+PIC_NO_GRAPH = 8
+
+STATUS = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ECFL", 3: "PIC_ENOMEM", 4: "PIC_ECUDA",
+          5: "PIC_EOVERFLOW", 6: "PIC_EPARTICLE", 7: "PIC_ETIMEOUT"}
+FIELD_E, FIELD_B, FIELD_J, FIELD_RHO = 0, 1, 2, 3
+
+
+class PicError(RuntimeError):
+    def __init__(self, status: int, message: str = ""):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+
+
+class pic_species_cfg(C.Structure):
+    _fields_ = [("q_over_m", C.c_double), ("density", C.c_double), ("ppc", C.c_double)]
+
+
+class pic_config(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double), ("dy", C.c_double),
+                ("dt", C.c_double), ("tile", C.c_int), ("threads", C.c_int),
+                ("n_species", C.c_int), ("species", pic_species_cfg * PIC_MAX_SPECIES),
+                ("background", C.c_double), ("flags", C.c_uint)]
+
+
+class pic_diag(C.Structure):
+    _fields_ = [("step", C.c_int64), ("time", C.c_double), ("w_e", C.c_double),
+                ("w_b", C.c_double), ("w_k", C.c_double), ("gauss_max", C.c_double),
+                ("continuity_max", C.c_double), ("charge_total", C.c_double),
+                ("n_particles", C.c_int64 * PIC_MAX_SPECIES), ("leavers", C.c_int64),
+                ("status_bits", C.c_uint32)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "n_particles"}
+        d["n_particles"] = list(self.n_particles)
+        return d
+
+
+_lib = None
+_P = C.c_void_p
+
+
+def load_library() -> C.CDLL:
+    """Load libpic.so (built by paper_2501_14795_gb300.build).  Raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        L.pic_init.argtypes = [C.POINTER(pic_config), _P, C.POINTER(_P)]
+        L.pic_load_particles.argtypes = [_P, C.c_int, C.c_int64] + [_P] * 8 + [C.c_int]
+        L.pic_set_fields.argtypes = [_P, _P, _P, C.c_int]
+        L.pic_step.argtypes = [_P, C.c_int]
+        L.pic_get_fields.argtypes = [_P, C.c_int, _P, C.c_int]
+        L.pic_get_particles.argtypes = [_P, C.c_int] + [_P] * 9 + [C.c_int]
+        L.pic_num_particles.argtypes = [_P, C.c_int]
+        L.pic_num_particles.restype = C.c_int64
+        L.pic_num_tiles.argtypes = [_P]
+        L.pic_num_tiles.restype = C.c_int64
+        L.pic_diagnostics.argtypes = [_P, C.POINTER(pic_diag)]
+        L.pic_get_history.argtypes = [_P, C.c_int64, C.c_int64, _P, _P, _P]
+        L.pic_sync.argtypes = [_P]
+        L.pic_clear_status.argtypes = [_P]
+        L.pic_timing.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]
+        L.pic_kernel_launches.argtypes = [_P]
+        L.pic_kernel_launches.restype = C.c_int64
+        L.pic_last_error.argtypes = [_P]
+        L.pic_last_error.restype = C.c_char_p
+        L.pic_destroy.argtypes = [_P]
+        L.pic_destroy.restype = None
+        for name in ("pic_init", "pic_load_particles", "pic_set_fields", "pic_step",
+                     "pic_get_fields", "pic_get_particles", "pic_diagnostics",
+                     "pic_get_history", "pic_sync", "pic_clear_status", "pic_timing"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(h, status):
+    if status != 0:
+        msg = load_library().pic_last_error(h) if h else b""
+        raise PicError(status, (msg or b"").decode())
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype):
+    """(pointer, on_device) of a contiguous numpy array or torch tensor."""
+    if a is None:
+        return None, None
+    if _is_torch(a):
+        import torch
+        want = {np.int32: torch.int32, np.float32: torch.float32,
+                np.int64: torch.int64}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"tensor must be contiguous {want}")
+        return a.data_ptr(), a.is_cuda
+    if not isinstance(a, np.ndarray) or a.dtype != np.dtype(dtype) or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"array must be a C-contiguous numpy {np.dtype(dtype)} array")
+    return a.ctypes.data, False
+
+
+def _default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+# ------------------------------------------------------------ C entry points
+
+def pic_init(cfg: pic_config, stream=None):
+    h = _P()
+    if stream is None:
+        stream = _default_stream()
+    _check(None, load_library().pic_init(C.byref(cfg), stream, C.byref(h)))
+    return h
+
+
+def pic_load_particles(h, species, ix, iy, x, y, ux, uy, uz, id=None):
+    arrs = [(ix, np.int32), (iy, np.int32), (x, np.float32), (y, np.float32),
+            (ux, np.float32), (uy, np.float32), (uz, np.float32)]
+    ptrs = [_ptr(a, d) for a, d in arrs]
+    n = int(ix.shape[0]) if hasattr(ix, "shape") else len(ix)
+    for a, _ in arrs:
+        if int(a.shape[0]) != n:
+            raise ValueError("particle arrays differ in length")
+    dev = ptrs[0][1]
+    if any(p[1] != dev for p in ptrs):
+        raise ValueError("particle arrays must all be on the host or all on the device")
+    pid = _ptr(id, np.int32)[0] if id is not None else None
+    _check(h, load_library().pic_load_particles(h, species, n, *[p[0] for p in ptrs], pid,
+                                                int(bool(dev))))
+
+
+def pic_set_fields(h, E=None, B=None):
+    pe, de = _ptr(E, np.float32)
+    pb, db = _ptr(B, np.float32)
+    dev = de if de is not None else db
+    _check(h, load_library().pic_set_fields(h, pe, pb, int(bool(dev))))
+
+
+def pic_step(h, nsteps=1):
+    _check(h, load_library().pic_step(h, int(nsteps)))
+
+
+def pic_get_fields(h, which, out):
+    p, dev = _ptr(out, np.float32)
+    _check(h, load_library().pic_get_fields(h, int(which), p, int(bool(dev))))
+    return out
+
+
+def pic_get_particles(h, species, ix=None, iy=None, x=None, y=None, ux=None, uy=None, uz=None,
+                      id=None, tile_offset=None):
+    ptrs = [_ptr(ix, np.int32), _ptr(iy, np.int32), _ptr(x, np.float32), _ptr(y, np.float32),
+            _ptr(ux, np.float32), _ptr(uy, np.float32), _ptr(uz, np.float32),
+            _ptr(id, np.int32), _ptr(tile_offset, np.int64)]
+    devs = {p[1] for p in ptrs if p[1] is not None}
+    if len(devs) > 1:
+        raise ValueError("outputs must all be on the host or all on the device")
+    dev = devs.pop() if devs else False
+    _check(h, load_library().pic_get_particles(h, species, *[p[0] for p in ptrs], int(bool(dev))))
+
+
+def pic_num_particles(h, species):
+    return int(load_library().pic_num_particles(h, species))
+
+
+def pic_num_tiles(h):
+    return int(load_library().pic_num_tiles(h))
+
+
+def pic_diagnostics(h) -> pic_diag:
+    d = pic_diag()
+    _check(h, load_library().pic_diagnostics(h, C.byref(d)))
+    return d
+
+
+def pic_get_history(h, first, count):
+    we = np.empty(count, np.float64)
+    wb = np.empty(count, np.float64)
+    wk = np.empty(count, np.float64)
+    _check(h, load_library().pic_get_history(h, int(first), int(count), we.ctypes.data,
+                                             wb.ctypes.data, wk.ctypes.data))
+    return we, wb, wk
+
+
+def pic_sync(h):
+    _check(h, load_library().pic_sync(h))
+
+
+def pic_clear_status(h):
+    _check(h, load_library().pic_clear_status(h))
+
+
+def pic_timing(h, reset=False):
+    ms = C.c_double()
+    cnt = C.c_int64()
+    _check(h, load_library().pic_timing(h, C.byref(ms), C.byref(cnt), int(reset)))
+    return ms.value, cnt.value
+
+
+def pic_kernel_launches(h):
+    return int(load_library().pic_kernel_launches(h))
+
+
+def pic_last_error(h):
+    return (load_library().pic_last_error(h) or b"").decode()
+
+
+def pic_destroy(h):
+    load_library().pic_destroy(h)
+
+
+# ------------------------------------------------------------- conveniences
+
+def make_config(nx, ny, dx, dy, dt, species, tile=16, threads=256, background=1.0, flags=0):
+    """pic_config from (q_over_m, qtilde) pairs: qtilde = sign(q/m) n_s/ppc_s."""
+    cfg = pic_config()
+    cfg.nx, cfg.ny, cfg.dx, cfg.dy, cfg.dt = nx, ny, dx, dy, dt
+    cfg.tile, cfg.threads, cfg.background, cfg.flags = tile, threads, background, flags
+    cfg.n_species = len(species)
+    for k, (qm, qt) in enumerate(species):
+        cfg.species[k].q_over_m = qm
+        cfg.species[k].density = abs(qt)
+        cfg.species[k].ppc = 1.0
+    return cfg
+
+
+def config_for(workload, tile=None, threads=256, flags=0):
+    return make_config(workload.nx, workload.ny, workload.dx, workload.dy, workload.dt,
+                       [(s.q_over_m, s.qtilde) for s in workload.species],
+                       tile=tile or workload.tile, threads=threads,
+                       background=workload.background, flags=flags)
+
+
+class Simulation:
+    """Owner of one pic_sim handle; methods forward to the entry points above."""
+
+    def __init__(self, cfg: pic_config, stream=None):
+        self.cfg = cfg
+        self.h = pic_init(cfg, stream)
+
+    @classmethod
+    def from_workload(cls, w, tile=None, threads=256, flags=0, stream=None, device=False):
+        sim = cls(config_for(w, tile, threads, flags), stream)
+        for k, s in enumerate(w.species):
+            arrs = s.arrays()
+            if device:
+                import torch
+                arrs = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+            pic_load_particles(sim.h, k, *arrs)
+        if w.E0 is not None or w.B0 is not None:
+            E = None if w.E0 is None else np.ascontiguousarray(w.E0, np.float32).reshape(-1)
+            B = None if w.B0 is None else np.ascontiguousarray(w.B0, np.float32).reshape(-1)
+            pic_set_fields(sim.h, E, B)
+        return sim
+
+    def step(self, n=1):
+        pic_step(self.h, n)
+
+    def fields(self, which):
+        n = 3 if which in (FIELD_E, FIELD_B, FIELD_J) else 1
+        out = np.empty(n * self.cfg.nx * self.cfg.ny, np.float32)
+        pic_get_fields(self.h, which, out)
+        return out.reshape((n, self.cfg.ny, self.cfg.nx) if n == 3 else (self.cfg.ny, self.cfg.nx))
+
+    def particles(self, species=0, ids=False):
+        n = pic_num_particles(self.h, species)
+        out = dict(ix=np.empty(n, np.int32), iy=np.empty(n, np.int32), x=np.empty(n, np.float32),
+                   y=np.empty(n, np.float32), ux=np.empty(n, np.float32),
+                   uy=np.empty(n, np.float32), uz=np.empty(n, np.float32))
+        if ids:
+            out["id"] = np.empty(n, np.int32)
+        out["tile_offset"] = np.empty(pic_num_tiles(self.h) + 1, np.int64)
+        pic_get_particles(self.h, species, **out)
+        return out
+
+    def diagnostics(self):
+        return pic_diagnostics(self.h).as_dict()
+
+    def history(self, first, count):
+        return pic_get_history(self.h, first, count)
+
+    def close(self):
+        if self.h:
+            pic_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
