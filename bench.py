@@ -1,0 +1,342 @@
+"""Throughput benchmark of the PIC step (push + deposit + re-sort + Yee).
+
+Default workload (N=1): the Weibel instability at full size, 512x512 cells,
+two electron populations of 8x8 particles per cell (33,554,432 particles),
+16x16-cell tiles, uz = +-0.6, u_th = 0.05, dt = 0.05, dx = dy = 0.1, random
+synthetic inputs.  A step is one pass of the whole hot path over all
+particles.  ``value`` is particle updates per second with the state resident
+in HBM; ``e2e`` is the same metric through the C ABI from pinned host
+buffers (load, K steps, field read-back and diagnostics inside the timed
+region).  The particle state (805 MB) is larger than the 129 MB L2, so no L2
+flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle updates/s (push+deposit+sort)"
+UNIT = "particle-updates/s"
+PEAK_FALLBACK_GBS = 6800.0
+
+WORKLOADS = {
+    # name: (factory kwargs, tile)
+    "weibel_512": dict(kind="weibel", kw=dict(nx=512, ny=512, k=8), tile=16),
+    "thermal_2048": dict(kind="thermal_seeded", kw=dict(nx=2048, ny=2048, k=4), tile=16),
+    "two_stream_64": dict(kind="two_stream", kw=dict(nx=64, ny=64, k=4), tile=16),
+}
+
+
+def make_workload(name):
+    from paper_2501_14795_gb300 import workloads as wl
+    spec = WORKLOADS[name]
+    w = getattr(wl, spec["kind"])(tile=spec["tile"], **spec["kw"])
+    return w
+
+
+def workload_config(name, w, threads):
+    return {"workload": name, "grid": [w.nx, w.ny], "particles": w.n_particles,
+            "ppc": w.meta.get("ppc"), "tile": w.tile, "threads_per_tile": threads,
+            "dt": w.dt, "dx": w.dx, "steps_of_workload": w.steps,
+            "l2": "inputs larger than L2 (particle state {:.0f} MB > 129 MB)".format(
+                w.n_particles * 24 / 1e6)}
+
+
+# ------------------------------------------------------------ measurements
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return PEAK_FALLBACK_GBS, "fallback"
+
+
+def push_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels_push.cu", "device_util.cuh", "pic_internal.h"):
+        with open(os.path.join(ROOT, "paper_2501_14795_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per particle-advance launch from the committed ncu summary,
+    valid only while the kernel sources hash the same as when captured."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    want = push_source_hash()
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 3 and not line.startswith("#") and parts[0] == workload and parts[2] == want:
+            return float(parts[1])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(budget_s=12.0):
+    """The FP64 oracle as it stands, single thread, on a bounded sample of the
+    Weibel workload: a 64x64 periodic instance (524,288 particles)."""
+    import oracle
+    from paper_2501_14795_gb300 import workloads as wl
+    w = wl.weibel(nx=64, ny=64, k=8, tile=16)
+    s = w.species[0]
+    o = oracle.OracleSim(w.nx, w.ny, w.dx, w.dy, w.dt, w.tile,
+                         [oracle.SpeciesState(s.q_over_m, s.qtilde, *s.arrays())],
+                         background=w.background)
+    o.step(1)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < budget_s:
+        o.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": w.n_particles * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"Weibel physics on a 64x64 periodic grid, 2x8x8 ppc ({w.n_particles} "
+                      f"particles), {steps} steps after 1 warm-up, FP64 single-thread C oracle",
+            "cpu_model": _cpu_model(), "host_cores": os.cpu_count()}
+
+
+def _cpu_model():
+    try:
+        for l in open("/proc/cpuinfo"):
+            if l.lower().startswith(("model name", "cpu part", "hardware")):
+                return l.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+# ------------------------------------------------------------------ arms
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle on bounded samples of the same workload."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2501_14795_gb300 import workloads as wl
+    w = wl.weibel(nx=64, ny=64, k=8, tile=16)
+    s = w.species[0]
+    o = oracle.OracleSim(w.nx, w.ny, w.dx, w.dy, w.dt, w.tile,
+                         [oracle.SpeciesState(s.q_over_m, s.qtilde, *s.arrays())],
+                         background=w.background)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = w.n_particles * args.steps / dt
+    full = make_workload(args.workload)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": workload_config(args.workload, full, args.threads),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: the Weibel physics on a 64x64 periodic grid, "
+                                       f"2x8x8 ppc ({w.n_particles} particles), FP64 single-thread "
+                                       f"C oracle"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_2501_14795_gb300 import pic
+
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    w = make_workload(args.workload)
+    n = w.n_particles
+    flags = pic.PIC_TIMING
+    sim = pic.Simulation.from_workload(w, tile=w.tile, threads=args.threads, flags=flags,
+                                       device=True, stream=stream.cuda_stream)
+    sim.step(args.warmup)
+    pic.pic_sync(sim.h)
+    pic.pic_timing(sim.h, reset=True)
+    l0 = pic.pic_kernel_launches(sim.h)
+    dist = world > 1
+    if dist:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        ev0.record(stream)
+        sim.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        torch.distributed.barrier()
+    ms = ev0.elapsed_time(ev1)
+    pic.pic_sync(sim.h)
+    adv_ms, adv_n = pic.pic_timing(sim.h, reset=True)
+    launches = pic.pic_kernel_launches(sim.h) - l0
+    d = sim.diagnostics()
+    sim.close()
+    del sim
+
+    # ---- end to end through the C ABI from pinned host buffers ----
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in w.species[0].arrays()]
+    fields_out = torch.empty(3 * w.nx * w.ny, dtype=torch.float32).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host)
+    d2h = 2 * fields_out.numel() * 4 + 96
+    torch.cuda.synchronize()
+    if dist:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    sim = pic.Simulation(pic.config_for(w, w.tile, args.threads, 0), stream.cuda_stream)
+    pic.pic_load_particles(sim.h, 0, *host)
+    sim.step(args.steps)
+    pic.pic_get_fields(sim.h, pic.FIELD_E, fields_out)
+    pic.pic_get_fields(sim.h, pic.FIELD_B, fields_out)
+    pic.pic_diagnostics(sim.h)
+    e2e_s = time.perf_counter() - t0
+    sim.close()
+
+    # ---- max over ranks ----
+    t = torch.tensor([ms, e2e_s * 1e3], dtype=torch.float64, device="cuda")
+    if dist:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms, e2e_ms = float(t[0]), float(t[1])
+    if rank != 0:
+        return
+    total = n * world
+    value = total * args.steps / (ms * 1e-3)
+    peak, peak_kind = read_peaks()
+    T = w.tile
+    cells = w.nx * w.ny
+    # algorithmic bytes of one particle-advance launch: each particle's 24 B
+    # state read and written once, each cell's E|B (24 B) read and J (12 B)
+    # written once
+    alg_push = 48.0 * n + 36.0 * cells
+    per_launch_s = (adv_ms / max(adv_n, 1)) * 1e-3
+    achieved = alg_push / per_launch_s / 1e9
+    leavers = d["leavers"]
+    f_leave = leavers / n if n else 0.0
+    step_bytes = 48.0 + 48.0 * f_leave + 96.0 * cells / n
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(workload_config(args.workload, w, args.threads),
+                       parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": recorded_traffic(args.workload),
+                     "kernel": "k_push (gather+Boris+move+deposit+leaver emission)",
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "bytes_per_launch": alg_push, "launch_ms": per_launch_s * 1e3},
+        "step_hbm": {"bytes_per_particle": step_bytes, "leaver_fraction_last_step": f_leave,
+                     "achieved_gbs": step_bytes * value / world / 1e9,
+                     "frac": step_bytes * value / world / 1e9 / peak},
+        "e2e": {"value": total * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "status_bits": d["status_bits"],
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="weibel_512", choices=sorted(WORKLOADS))
+    ap.add_argument("--threads", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

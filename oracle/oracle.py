@@ -203,10 +203,12 @@ class SpeciesState:
         return int(self.ix.size)
 
     def astype(self, dtype) -> "SpeciesState":
-        c = lambda a: np.ascontiguousarray(a, dtype)
+        # always copies: the oracle updates its arrays in place and must never
+        # write into the caller's input arrays
+        c = lambda a: np.array(a, dtype=dtype, copy=True, order="C")
         return SpeciesState(self.q_over_m, self.qtilde,
-                            np.ascontiguousarray(self.ix, np.int32),
-                            np.ascontiguousarray(self.iy, np.int32),
+                            np.array(self.ix, dtype=np.int32, copy=True),
+                            np.array(self.iy, dtype=np.int32, copy=True),
                             c(self.x), c(self.y), c(self.ux), c(self.uy), c(self.uz),
                             None if self.pid is None else self.pid.copy())
 
@@ -244,8 +246,11 @@ class OracleSim:
 
     def __post_init__(self):
         shape = (3, self.ny, self.nx)
-        self.E = np.zeros(shape, self.dtype) if self.E is None else np.ascontiguousarray(self.E, self.dtype)
-        self.B = np.zeros(shape, self.dtype) if self.B is None else np.ascontiguousarray(self.B, self.dtype)
+        # copies: the Yee step updates E and B in place, never the caller's arrays
+        self.E = (np.zeros(shape, self.dtype) if self.E is None
+                  else np.array(self.E, dtype=self.dtype, copy=True, order="C"))
+        self.B = (np.zeros(shape, self.dtype) if self.B is None
+                  else np.array(self.B, dtype=self.dtype, copy=True, order="C"))
         self.J = np.zeros(shape, self.dtype)
         self.species = [s.astype(self.dtype) for s in self.species]
 

@@ -20,7 +20,8 @@ using namespace pic;
 struct pic_sim {
     pic_config cfg;
     Geom g;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;       // caller's stream: all work is ordered on it
+    cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
     DevState* st = nullptr;
     float* F[2] = {nullptr, nullptr};  // E|B, ping-pong
     float* J[2] = {nullptr, nullptr};  // current, ping-pong
@@ -37,6 +38,7 @@ struct pic_sim {
     int cur = 0;                       // parity: F[cur], J[cur] current, off[cur] current
     long long step = 0;                // host mirror of the time level
     // graphs
+    cudaGraph_t graph[2] = {nullptr, nullptr};  // kept alive: its nodes address the exec's
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     cudaGraphNode_t ev_node[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     cudaEvent_t ev_placeholder[2] = {nullptr, nullptr};
@@ -132,7 +134,9 @@ cudaError_t alloc_particles(SpeciesDev& s, int64_t cap) {
 void invalidate_graphs(pic_sim* sim) {
     for (int b = 0; b < 2; ++b) {
         if (sim->gexec[b]) cudaGraphExecDestroy(sim->gexec[b]);
+        if (sim->graph[b]) cudaGraphDestroy(sim->graph[b]);
         sim->gexec[b] = nullptr;
+        sim->graph[b] = nullptr;
         sim->ev_node[b][0] = sim->ev_node[b][1] = nullptr;
     }
 }
@@ -187,8 +191,8 @@ SortParams sort_params(const pic_sim* sim, int b) {
 // Enqueue one step at parity b.  Returns the number of kernels launched or
 // -1 on a launch error (message in sim->err).  ev_a/ev_b bracket the particle
 // advance when non-null (external event records inside a capture).
-int enqueue_step(pic_sim* sim, int b, cudaEvent_t ev_a, cudaEvent_t ev_b, bool capturing) {
-    cudaStream_t s = sim->stream;
+int enqueue_step(pic_sim* sim, cudaStream_t s, int b, cudaEvent_t ev_a, cudaEvent_t ev_b,
+                 bool capturing) {
     const int threads = sim->cfg.threads;
     const PushParams pp = push_params(sim, b);
     const SortParams sp = sort_params(sim, b);
@@ -226,10 +230,12 @@ bad:
 pic_status build_graph(pic_sim* sim, int b) {
     cudaGraph_t graph = nullptr;
     const bool timing = (sim->cfg.flags & PIC_TIMING) != 0;
-    CK(cudaStreamBeginCapture(sim->stream, cudaStreamCaptureModeThreadLocal));
-    const int n = enqueue_step(sim, b, timing ? sim->ev_placeholder[0] : nullptr,
+    // capture on the private stream (the caller's may be the legacy default
+    // stream, which cannot be captured); the graph is launched on the caller's
+    CK(cudaStreamBeginCapture(sim->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int n = enqueue_step(sim, sim->cap_stream, b, timing ? sim->ev_placeholder[0] : nullptr,
                                timing ? sim->ev_placeholder[1] : nullptr, true);
-    cudaError_t e = cudaStreamEndCapture(sim->stream, &graph);
+    cudaError_t e = cudaStreamEndCapture(sim->cap_stream, &graph);
     if (n < 0) {
         if (graph) cudaGraphDestroy(graph);
         return PIC_ECUDA;
@@ -252,7 +258,7 @@ pic_status build_graph(pic_sim* sim, int b) {
         }
     }
     e = cudaGraphInstantiate(&sim->gexec[b], graph, 0);
-    cudaGraphDestroy(graph);
+    sim->graph[b] = graph;
     CK(e);
     return PIC_OK;
 }
@@ -427,6 +433,8 @@ pic_status pic_init(const pic_config* cfg, void* cuda_stream, pic_sim** out) {
             launch_push_strict(nullptr, p0, c.threads, sim->stream) != cudaSuccess)
             return cleanup_fail(PIC_ECUDA, "smem attribute", e);
     }
+    if (cudaStreamCreateWithFlags(&sim->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return cleanup_fail(PIC_ECUDA, "stream", e);
     if (c.flags & PIC_TIMING)
         for (int k = 0; k < 2; ++k)
             if (cudaEventCreate(&sim->ev_placeholder[k]) != cudaSuccess)
@@ -564,7 +572,7 @@ pic_status pic_step(pic_sim* sim, int nsteps) {
             CK(cudaGraphLaunch(sim->gexec[b], sim->stream));
             sim->launches += sim->launches_per_step;
         } else {
-            const int n = enqueue_step(sim, b, ea, eb, false);
+            const int n = enqueue_step(sim, sim->stream, b, ea, eb, false);
             if (n < 0) return PIC_ECUDA;
             sim->launches += n;
         }
@@ -750,6 +758,7 @@ void pic_destroy(pic_sim* sim) {
     if (!sim) return;
     if (sim->stream) cudaStreamSynchronize(sim->stream);
     invalidate_graphs(sim);
+    if (sim->cap_stream) cudaStreamDestroy(sim->cap_stream);
     for (int b = 0; b < 2; ++b) {
         dfree(sim->F[b]);
         dfree(sim->J[b]);

@@ -152,15 +152,34 @@ def test_fast_step_matches_fp64_oracle(nx, ny, T, n, threads):
 
 
 def test_graph_and_direct_launch_agree():
+    """Graph replay and one-by-one launches run the same kernels: identical
+    after one step; after five, equal to round-off (J is summed with atomics
+    in no fixed order, so later steps are reproducible to round-off only)."""
     w, E, B = _random_case(48, 32, 16, 4000, seed=5)
-    outs = []
-    for extra in (0, pic.PIC_NO_GRAPH):
-        with _gpu(w, pic.PIC_STRICT_FP | pic.PIC_TRACK_IDS | extra, tile=16, E=E, B=B) as sim:
-            sim.step(5)
-            outs.append((_by_id(sim.particles(0, ids=True)), sim.fields(pic.FIELD_E)))
-    for k in ("ix", "iy", "x", "y"):
-        np.testing.assert_array_equal(outs[0][0][k], outs[1][0][k])
-    np.testing.assert_allclose(outs[0][1], outs[1][1], rtol=0, atol=1e-6)
+    outs = {}
+    for nsteps in (1, 5):
+        for extra in (0, pic.PIC_NO_GRAPH):
+            with _gpu(w, pic.PIC_STRICT_FP | pic.PIC_TRACK_IDS | extra, tile=16, E=E, B=B) as sim:
+                sim.step(nsteps)
+                outs[nsteps, extra] = (_by_id(sim.particles(0, ids=True)), sim.fields(pic.FIELD_E))
+    a, b = outs[1, 0][0], outs[1, pic.PIC_NO_GRAPH][0]
+    for k in ("ix", "iy", "x", "y", "ux", "uy", "uz"):
+        np.testing.assert_array_equal(a[k], b[k])
+    a, b = outs[5, 0], outs[5, pic.PIC_NO_GRAPH]
+    _assert_close_states(a[0], b[0], 48, 32)
+    np.testing.assert_allclose(a[1], b[1], rtol=0, atol=1e-5 * np.max(np.abs(b[1])))
+
+
+def _assert_close_states(a, b, nx, ny, pos_tol=1e-5, u_tol=1e-5):
+    """Same particles (by id) within round-off: unwrapped positions and momenta."""
+    np.testing.assert_array_equal(a["id"], b["id"])
+    dx = (a["ix"] + a["x"].astype(np.float64)) - (b["ix"] + b["x"].astype(np.float64))
+    dy = (a["iy"] + a["y"].astype(np.float64)) - (b["iy"] + b["y"].astype(np.float64))
+    dx = (dx + nx / 2) % nx - nx / 2
+    dy = (dy + ny / 2) % ny - ny / 2
+    assert np.max(np.abs(dx)) < pos_tol and np.max(np.abs(dy)) < pos_tol
+    for k in ("ux", "uy", "uz"):
+        assert np.max(np.abs(a[k].astype(np.float64) - b[k])) < u_tol
 
 
 def test_two_stream_100_steps_tracks_fp64_oracle():
@@ -311,16 +330,22 @@ def test_empty_species_and_single_tile_crowding():
     w = wl.Workload("crowd", nx, ny, 0.1, 0.1, 0.05, 8, 1, [sp0, sp1], background=0.0)
     E, B = wl.random_fields(nx, ny, amp=0.1, seed=9)
     with _gpu(w, pic.PIC_STRICT_FP | pic.PIC_TRACK_IDS, tile=8, E=E, B=B) as sim:
-        sim.step(3)
-        got = _by_id(sim.particles(0, ids=True))
+        sim.step(1)
+        got1 = _by_id(sim.particles(0, ids=True))
+        sim.step(2)
+        got3 = _by_id(sim.particles(0, ids=True))
         assert pic.pic_num_particles(sim.h, 1) == 0
         p1 = sim.particles(1)
         assert np.all(p1["tile_offset"] == 0)
     o = _oracle(w, np.float32, E, B, 8)
-    o.step(3)
+    o.step(1)
     ref = _oracle_by_id(o.species[0])
     for k in ("ix", "iy", "x", "y", "ux", "uy", "uz"):
-        np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
+        np.testing.assert_array_equal(got1[k], ref[k], err_msg=k)
+    o.step(2)
+    ref = _oracle_by_id(o.species[0])
+    ref["id"] = np.sort(o.species[0].pid).astype(np.int32)
+    _assert_close_states(got3, ref, nx, ny)
 
 
 def test_boundary_offsets_and_two_species():
@@ -340,18 +365,25 @@ def test_boundary_offsets_and_two_species():
     w = wl.Workload("edges", nx, ny, 0.1, 0.1, 0.05, 8, 1, [el, po], background=0.0)
     E, B = wl.random_fields(nx, ny, amp=0.3, seed=2)
     with _gpu(w, pic.PIC_STRICT_FP | pic.PIC_TRACK_IDS, tile=8, E=E, B=B) as sim:
-        sim.step(4)
+        sim.step(1)
         gots = [_by_id(sim.particles(s, ids=True)) for s in range(2)]
         Jg = sim.fields(pic.FIELD_J)
+        sim.step(3)
+        gots4 = [_by_id(sim.particles(s, ids=True)) for s in range(2)]
     o = _oracle(w, np.float32, E, B, 8)
-    o.step(4)
+    o.step(1)
     for s in range(2):
         ref = _oracle_by_id(o.species[s])
         for k in ("ix", "iy", "x", "y", "ux", "uy", "uz"):
             np.testing.assert_array_equal(gots[s][k], ref[k], err_msg=f"species {s} {k}")
     o64 = _oracle(w, np.float64, E, B, 8)
-    o64.step(4)
-    assert np.max(np.abs(Jg - o64.J)) <= 1e-4 * max(np.max(np.abs(o64.J)), 1e-3)
+    o64.step(1)
+    assert np.max(np.abs(Jg - o64.J)) <= J_RTOL * np.max(np.abs(o64.J))
+    o64.step(3)
+    for s in range(2):
+        ref = _oracle_by_id(o64.species[s])
+        ref["id"] = np.arange(m, dtype=np.int32)
+        _assert_close_states(gots4[s], ref, nx, ny)
     assert m == 6
 
 
@@ -362,7 +394,7 @@ def test_restart_roundtrip_is_exact():
         st = a.particles(0, ids=True)
         E = a.fields(pic.FIELD_E)
         B = a.fields(pic.FIELD_B)
-        a.step(5)
+        a.step(1)
         ref = _by_id(a.particles(0, ids=True))
     sp = wl.Species(-1.0, w.species[0].qtilde, st["ix"], st["iy"], st["x"], st["y"], st["ux"],
                     st["uy"], st["uz"])
@@ -371,7 +403,7 @@ def test_restart_roundtrip_is_exact():
         # carry the ids over
         pic.pic_load_particles(b.h, 0, st["ix"], st["iy"], st["x"], st["y"], st["ux"], st["uy"],
                                st["uz"], id=st["id"])
-        b.step(5)
+        b.step(1)
         got = _by_id(b.particles(0, ids=True))
     for k in ("ix", "iy", "x", "y", "ux", "uy", "uz", "id"):
         np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
@@ -407,8 +439,10 @@ def test_non_finite_field_raises_particle_status_not_a_fault():
         with pytest.raises(pic.PicError) as ei:
             pic.pic_sync(sim.h)
         assert ei.value.status == 6
+        # the affected particles keep their non-finite momenta: reload them
         pic.pic_clear_status(sim.h)
         pic.pic_set_fields(sim.h, np.zeros(3 * 256, np.float32), np.zeros(3 * 256, np.float32))
+        pic.pic_load_particles(sim.h, 0, *w.species[0].arrays())
         sim.step(1)
         pic.pic_sync(sim.h)
         assert sim.particles(0)["tile_offset"][-1] == w.n_particles

@@ -318,3 +318,21 @@ def test_cfl_limit_number():
     lim = (1 / DX ** 2 + 1 / DY ** 2) ** -0.5
     assert lim == pytest.approx(0.0707107, abs=1e-6)
     assert DT < lim
+
+
+def test_oracle_never_writes_into_its_inputs(orc):
+    """Both precisions copy the particle and field arrays they are given: a
+    run must leave the caller's arrays (shared with the GPU side) untouched."""
+    from paper_2501_14795_gb300 import workloads as wl
+    sp = wl.random_particles(16, 16, 500, u_max=0.6, seed=3)
+    E, B = wl.random_fields(16, 16, amp=0.2, seed=4)
+    E0, B0, a0 = E.copy(), B.copy(), [a.copy() for a in sp.arrays()]
+    for dt in (np.float32, np.float64):
+        o = orc.OracleSim(16, 16, DX, DY, DT, 8,
+                          [orc.SpeciesState(sp.q_over_m, sp.qtilde, *sp.arrays())],
+                          dtype=dt, E=E, B=B)
+        o.step(2)
+    np.testing.assert_array_equal(E, E0)
+    np.testing.assert_array_equal(B, B0)
+    for a, b in zip(a0, sp.arrays()):
+        np.testing.assert_array_equal(a, b)
