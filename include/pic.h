@@ -183,6 +183,32 @@ const char* pic_last_error(const pic_sim* sim);
 /* Free everything.  NULL is accepted. */
 void pic_destroy(pic_sim* sim);
 
+/* ---- Allocation-free tile sort ---------------------------------------------
+ * The paper has no counterpart: this entry point is for callers that cannot
+ * call cudaMalloc (host callbacks, allocator hooks, plugins whose host
+ * application owns every device allocation, processes that pre-carved all of
+ * device memory into their own pool).  It sorts n caller-owned device particle
+ * arrays (same seven arrays and validity rules as pic_load_particles) by tile
+ * into caller-owned device output arrays of n values each, and writes the
+ * (nx/tile)*(ny/tile)+1 tile_offset bookmarks (int64, device), the same
+ * counting sort pic_load_particles performs; order inside a tile is
+ * unspecified.  It allocates nothing: its scratch is a fixed device array of
+ * PIC_NOALLOC_MAX_TILES + 64 int32 (256 KB + 256 B) that every GPU loading the
+ * library holds until exit.  The first call on a device looks up that
+ * array's address (make it before any stream capture).  Calls share the
+ * array: two calls whose work overlaps on the GPU race and give wrong
+ * results.  Synchronises `cuda_stream` (a cudaStream_t, NULL = default).
+ * Returns PIC_EINVAL for a bad size or tile, more than PIC_NOALLOC_MAX_TILES
+ * tiles, or an invalid particle (outputs then unspecified); PIC_ECUDA on a
+ * CUDA error. */
+#define PIC_NOALLOC_MAX_TILES 65536
+pic_status pic_tile_sort_noalloc(int nx, int ny, int tile, int64_t n, const int32_t* ix,
+                                 const int32_t* iy, const float* x, const float* y,
+                                 const float* ux, const float* uy, const float* uz,
+                                 int32_t* ix_out, int32_t* iy_out, float* x_out, float* y_out,
+                                 float* ux_out, float* uy_out, float* uz_out,
+                                 int64_t* tile_offset, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,6 +35,7 @@ def _units():
         ("sort.o", "kernels_sort.cu", common),
         ("grid.o", "kernels_grid.cu", common),
         ("host.o", "pic_host.cu", common),
+        ("noalloc.o", "noalloc.cu", common),
     ]
 
 

@@ -90,6 +90,8 @@ def load_library() -> C.CDLL:
         L.pic_last_error.restype = C.c_char_p
         L.pic_destroy.argtypes = [_P]
         L.pic_destroy.restype = None
+        L.pic_tile_sort_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64] + [_P] * 15 + [_P]
+        L.pic_tile_sort_noalloc.restype = C.c_int
         for name in ("pic_init", "pic_load_particles", "pic_set_fields", "pic_step",
                      "pic_get_fields", "pic_get_particles", "pic_diagnostics",
                      "pic_get_history", "pic_sync", "pic_clear_status", "pic_timing"):
@@ -237,6 +239,24 @@ def pic_last_error(h):
 
 def pic_destroy(h):
     load_library().pic_destroy(h)
+
+
+def pic_tile_sort_noalloc(nx, ny, tile, ix, iy, x, y, ux, uy, uz, ix_out, iy_out, x_out,
+                          y_out, ux_out, uy_out, uz_out, tile_offset, stream=None):
+    """Allocation-free tile sort of device arrays into device arrays (see pic.h)."""
+    ins = [_ptr(ix, np.int32), _ptr(iy, np.int32)] + [_ptr(a, np.float32) for a in (x, y, ux, uy, uz)]
+    outs = [_ptr(ix_out, np.int32), _ptr(iy_out, np.int32)] + \
+        [_ptr(a, np.float32) for a in (x_out, y_out, ux_out, uy_out, uz_out)]
+    off = _ptr(tile_offset, np.int64)
+    if not all(p[1] for p in ins + outs + [off]):
+        raise ValueError("pic_tile_sort_noalloc takes device arrays only")
+    n = int(ix.shape[0])
+    if stream is None:
+        stream = _default_stream()
+    st = load_library().pic_tile_sort_noalloc(nx, ny, tile, n, *[p[0] for p in ins],
+                                              *[p[0] for p in outs], off[0], stream)
+    if st != 0:
+        raise PicError(st, "pic_tile_sort_noalloc")
 
 
 # ------------------------------------------------------------- conveniences
