@@ -34,7 +34,12 @@ PEAK_FALLBACK_GBS = 6800.0
 WORKLOADS = {
     # name: (factory kwargs, tile)
     "weibel_512": dict(kind="weibel", kw=dict(nx=512, ny=512, k=8), tile=16),
+    # smaller instance of the same physics (8.4M particles, 201 MB state > L2)
+    # for profiler captures
+    "weibel_256": dict(kind="weibel", kw=dict(nx=256, ny=256, k=8), tile=16),
     "thermal_2048": dict(kind="thermal_seeded", kw=dict(nx=2048, ny=2048, k=4), tile=16),
+    # smaller instance (16.8M particles, 403 MB state > L2) for profiler captures
+    "thermal_1024": dict(kind="thermal_seeded", kw=dict(nx=1024, ny=1024, k=4), tile=16),
     "two_stream_64": dict(kind="two_stream", kw=dict(nx=64, ny=64, k=4), tile=16),
 }
 

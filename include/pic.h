@@ -85,6 +85,8 @@ typedef struct {
     int tile;         /* T in {8, 16, 32}; 0 = 16 */
     int threads;      /* threads per tile in the particle kernels: 64..1024, multiple
                          of 32; 0 = 256 */
+    int chunk;        /* particles per CTA in the particle kernels: a tile holding more
+                         is split over several CTAs (16..1<<20); 0 = 4096 */
     int n_species;    /* 1..PIC_MAX_SPECIES */
     pic_species_cfg species[PIC_MAX_SPECIES];
     double background;/* fixed neutralising ion charge density (enters rho only) */

@@ -31,7 +31,8 @@ def _units():
               f"-I{os.path.join(ROOT, 'include')}", f"-I{CSRC}"]
     return [
         ("push_fast.o", "kernels_push.cu", common + ["-DPIC_VARIANT=fast"]),
-        ("push_strict.o", "kernels_push.cu", common + ["-DPIC_VARIANT=strict", "-fmad=false"]),
+        ("push_strict.o", "kernels_push.cu",
+         common + ["-DPIC_VARIANT=strict", "-DPIC_STRICT_BUILD", "-fmad=false"]),
         ("sort.o", "kernels_sort.cu", common),
         ("grid.o", "kernels_grid.cu", common),
         ("host.o", "pic_host.cu", common),

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(YTHREADS) k_yee(const YeeParams prm) {
                 Bout[2 * cs + o] = bz;
             }
         const int mi = i % T, mj = j % T;
-        const bool ring = mi < 2 || mi == T - 1 || mj < 2 || mj == T - 1;
+        const bool ring = prm.zero_all || mi < 2 || mi == T - 1 || mj < 2 || mj == T - 1;
         if (ring) {
             const long long o = gidx(g, i, j);
             prm.Jnext[o] = 0.f;

@@ -1,25 +1,33 @@
-// Particle advance: one CTA per tile of T x T cells (§4.1-4.2, Listing 3.1's
-// particle loop), for all species of the tile:
+// Particle advance: CTAs over the tiles of T x T cells (§4.1-4.2, the particle
+// loop of Listing 3.1), all species of a tile; a tile holding many particles
+// is split over several CTAs (blockIdx.y) that each take a slice of it.
 //   1. TMA-load the tile's E|B halo, cells [-4, T+4) x [-1, T+2), into shared
 //      memory (one 3D box over the six components, mbarrier completion);
 //   2. per particle (coalesced SoA loads): linear gather of the six staggered
-//      components (Fig. 3.1), Boris push (Eqs. 6-10), move (Eq. 11), the
-//      Villasenor-Buneman split into at most three pieces (Figs. 3.4-3.5) and
-//      the deposit of each piece's current (Eqs. 13-16 plus the time-averaged
-//      Jz) into a shared-memory J tile, cells [-1, T+2), with shared atomics;
-//   3. emit the re-sort metadata of §4.3: particles that stay in the tile are
+//      components (Fig. 3.1), Boris push (Eqs. 6-10), move (Eq. 11) and the
+//      Villasenor-Buneman split into at most three pieces (Figs. 3.4-3.5);
+//   3. deposit each piece's current (Eqs. 13-16 plus the time-averaged Jz)
+//      into a J tile, cells [-1, T+2), in shared memory: one private J tile
+//      per warp (T <= 16), so warps never contend.  Pieces of a warp that fall
+//      into few cells (quiet or cold plasmas keep neighbouring particles
+//      together) are summed across the warp by a shuffle reduce-scatter and
+//      added with plain read-add-write by 8 lanes, one cell group at a time;
+//      scattered pieces are added with atomics on the warp's own tile;
+//   4. emit the re-sort metadata of §4.3: particles that stay in the tile are
 //      written in place; particles that leave are appended (warp-ballot slots)
 //      to the tile's section of the out arrays with their old position in the
 //      hole list, and counted by destination (8 neighbours);
-//   4. flush the J tile once: plain stores to the cells no other tile's halo
-//      reaches, red.global.add to the shared ring (update_gc_add);
-//   5. FP32 kinetic energy per thread -> FP64 block sum -> one FP64 atomic.
+//   5. flush: sum the warps' J tiles; a tile taken by one CTA stores the cells
+//      no other tile's halo reaches and adds the shared ring with
+//      red.global.add (update_gc_add); a split tile adds everything;
+//   6. FP32 kinetic energy per thread -> FP64 block sum -> one FP64 atomic.
 //
-// This file is compiled twice: PIC_VARIANT=fast (FMA contraction allowed) and
-// PIC_VARIANT=strict (-fmad=false): the strict build evaluates the
-// per-particle path in exactly the operation order of the FP32 reference
-// (every expression below is written in that order), so cells, offsets and
-// momenta are reproducible bit for bit.
+// This file is compiled twice: PIC_VARIANT=fast (FMA contraction, rsqrt and
+// fast division) and PIC_VARIANT=strict (PIC_STRICT_BUILD, -fmad=false, IEEE
+// division and square root): the strict build evaluates the per-particle path
+// in exactly the operation order of the FP32 reference (every expression below
+// is written in that order), so cells, offsets and momenta are reproducible
+// bit for bit.
 #include <cuda.h>
 
 #include "device_util.cuh"
@@ -34,6 +42,8 @@
 namespace pic {
 namespace PIC_VARIANT {
 
+constexpr unsigned FULL = 0xffffffffu;
+
 template <int T>
 struct Tile {
     static constexpr int FW = T + 8;  // TMA box columns: cells -4 .. T+3
@@ -43,11 +53,17 @@ struct Tile {
     static constexpr int JW = T + 3;  // J tile: cells -1 .. T+1 on both axes
     static constexpr int JPLANE = JW * JW;
     static constexpr int JN = 3 * JPLANE;
-    static constexpr size_t OFF_BAR = ((size_t)(FLD + JN) * 4 + 15) & ~(size_t)15;
-    static constexpr size_t OFF_CNT = OFF_BAR + 16;
-    static constexpr int NCNT = MAX_SPECIES * 9 + 4;
-    static constexpr size_t OFF_RED = (OFF_CNT + NCNT * 4 + 7) & ~(size_t)7;
-    static constexpr size_t BYTES = OFF_RED + 32 * sizeof(double);
+    static constexpr bool PER_WARP = T <= 16;  // one private J tile per warp
+    static constexpr int NCNT = MAX_SPECIES * 8 + 4;
+
+    // shared-memory layout for a block of `warps` warps
+    static __host__ __device__ size_t j_tiles(int warps) { return PER_WARP ? warps : 1; }
+    static __host__ __device__ size_t off_misc(int warps) {
+        return ((size_t)FLD * 4 + j_tiles(warps) * JN * 4 + 15) & ~(size_t)15;
+    }
+    static __host__ __device__ size_t bytes(int warps) {
+        return off_misc(warps) + 16 + NCNT * 4 + 8 + 32 * sizeof(double);
+    }
 };
 
 __device__ __forceinline__ float interp(const float* F, int fw, int col, int row, float a0,
@@ -57,32 +73,118 @@ __device__ __forceinline__ float interp(const float* F, int fw, int col, int row
     return b0 * (a0 * r0[0] + a1 * r0[1]) + b1 * (a0 * r1[0] + a1 * r1[1]);
 }
 
-// Current of one straight piece inside local cell (cl, rl) of the J tile
-// (indices already shifted by the halo), local start (fx0, fy0), end (fx1, fy1),
-// time fraction frac.
-template <int JW>
-__device__ __forceinline__ void deposit_piece(float* sJx, float* sJy, float* sJz, int cl, int rl,
-                                              float fx0, float fy0, float fx1, float fy1,
-                                              float frac, float qjx, float qjy, float qvz) {
+// division used outside the bit-reproducible path: IEEE in the strict build
+__device__ __forceinline__ float qdiv(float a, float b) {
+#ifdef PIC_STRICT_BUILD
+    return a / b;
+#else
+    return __fdividef(a, b);
+#endif
+}
+
+// Current of one straight piece inside one cell, local start (fx0, fy0), end
+// (fx1, fy1), time fraction frac: v[0..1] Jx on the faces (i+1/2, j) and
+// (i+1/2, j+1) (Eqs. 13-14), v[2..3] Jy on (i, j+1/2) and (i+1, j+1/2)
+// (Eqs. 15-16), v[4..7] Jz on the nodes (i,j), (i+1,j), (i,j+1), (i+1,j+1):
+// q vz frac times the mean over the piece of each node's area weight.
+__device__ __forceinline__ void piece_current(float v[8], float fx0, float fy0, float fx1,
+                                              float fy1, float frac, float qjx, float qjy,
+                                              float qvz) {
     const float dxp = fx1 - fx0, dyp = fy1 - fy0;
     const float xm = 0.5f * (fx0 + fx1), ym = 0.5f * (fy0 + fy1);
-    const int o = rl * JW + cl;
     const float jxv = qjx * dxp, jyv = qjy * dyp;
-    atomicAdd(sJx + o, jxv * (1.f - ym));
-    atomicAdd(sJx + o + JW, jxv * ym);
-    atomicAdd(sJy + o, jyv * (1.f - xm));
-    atomicAdd(sJy + o + 1, jyv * xm);
-    // Jz: q vz frac times the mean over the piece of the area weights
+    v[0] = jxv * (1.f - ym);
+    v[1] = jxv * ym;
+    v[2] = jyv * (1.f - xm);
+    v[3] = jyv * xm;
     const float sx0 = 1.f - fx0, sx1 = 1.f - fx1;  // a = 0 weights at start / end
     const float sy0 = 1.f - fy0, sy1 = 1.f - fy1;
     const float c = qvz * frac * (1.f / 6.f);
     // W_ab = [S0x_a (2 S0y_b + S1y_b) + S1x_a (S0y_b + 2 S1y_b)] / 6
     const float ay0 = 2.f * sy0 + sy1, by0 = sy0 + 2.f * sy1;  // b = 0
     const float ay1 = 2.f * fy0 + fy1, by1 = fy0 + 2.f * fy1;  // b = 1
-    atomicAdd(sJz + o, c * (sx0 * ay0 + sx1 * by0));
-    atomicAdd(sJz + o + 1, c * (fx0 * ay0 + fx1 * by0));
-    atomicAdd(sJz + o + JW, c * (sx0 * ay1 + sx1 * by1));
-    atomicAdd(sJz + o + JW + 1, c * (fx0 * ay1 + fx1 * by1));
+    v[4] = c * (sx0 * ay0 + sx1 * by0);
+    v[5] = c * (fx0 * ay0 + fx1 * by0);
+    v[6] = c * (sx0 * ay1 + sx1 * by1);
+    v[7] = c * (fx0 * ay1 + fx1 * by1);
+}
+
+// Offset of value k of piece_current from the piece's cell in the J tile
+// (component plane k<2: x, k<4: y, else z).
+template <int JW, int JPLANE>
+__device__ __forceinline__ int value_offset(int k) {
+    const int comp = k < 2 ? 0 : (k < 4 ? 1 : 2);
+    const int d = (k == 1 || k == 6) ? JW : (k == 3 || k == 5) ? 1 : (k == 7 ? JW + 1 : 0);
+    return comp * JPLANE + d;
+}
+
+// Reduce-scatter of eight values over the warp: lane L ends with the warp
+// total of value L >> 2 (nine shuffles instead of forty for a full reduction).
+__device__ __forceinline__ float warp_reduce_scatter8(const float v[8], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float a[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = b4 ? v[i] : v[4 + i];
+        a[i] = (b4 ? v[4 + i] : v[i]) + __shfl_xor_sync(FULL, send, 16);
+    }
+    float c[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = b3 ? a[i] : a[2 + i];
+        c[i] = (b3 ? a[2 + i] : a[i]) + __shfl_xor_sync(FULL, send, 8);
+    }
+    const float send = b2 ? c[0] : c[1];
+    float d = (b2 ? c[1] : c[0]) + __shfl_xor_sync(FULL, send, 4);
+    d += __shfl_xor_sync(FULL, d, 2);
+    d += __shfl_xor_sync(FULL, d, 1);
+    return d;
+}
+
+constexpr int AGG_MAX_GROUPS = 8;
+
+// Deposit one piece per lane (has == false: nothing) into the J tile `sJw`
+// (the warp's own tile when PER_WARP, else the CTA's).  Every lane calls this.
+template <int JW, int JPLANE, bool PER_WARP>
+__device__ __forceinline__ void deposit_warp(bool has, int o, const float v[8], float* sJw,
+                                             int lane) {
+    const unsigned act = __ballot_sync(FULL, has);
+    const unsigned peers = __match_any_sync(FULL, has ? o : -1);
+    const bool lead = has && lane == __ffs(peers) - 1;
+    unsigned leaders = __ballot_sync(FULL, lead);
+    const int ng = __popc(leaders);
+    if (ng <= AGG_MAX_GROUPS && __popc(act) >= 2 * ng) {
+        // few cells: sum each cell group across the warp, 8 lanes add the totals
+        const int k = lane >> 2;
+        const int voff = value_offset<JW, JPLANE>(k);
+        while (leaders) {
+            const int l = __ffs(leaders) - 1;
+            leaders &= leaders - 1u;
+            const int ko = __shfl_sync(FULL, o, l);
+            const bool mine = has && o == ko;
+            float s[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) s[i] = mine ? v[i] : 0.f;
+            const float tot = warp_reduce_scatter8(s, lane);
+            if ((lane & 3) == 0) {
+                float* a = sJw + ko + voff;
+                if (PER_WARP)
+                    *a += tot;  // the 8 targets are distinct; one group at a time
+                else
+                    atomicAdd(a, tot);
+            }
+            if (PER_WARP) __syncwarp();
+        }
+    } else if (has) {
+        atomicAdd(sJw + o, v[0]);
+        atomicAdd(sJw + o + JW, v[1]);
+        atomicAdd(sJw + JPLANE + o, v[2]);
+        atomicAdd(sJw + JPLANE + o + 1, v[3]);
+        atomicAdd(sJw + 2 * JPLANE + o, v[4]);
+        atomicAdd(sJw + 2 * JPLANE + o + 1, v[5]);
+        atomicAdd(sJw + 2 * JPLANE + o + JW, v[6]);
+        atomicAdd(sJw + 2 * JPLANE + o + JW + 1, v[7]);
+    }
 }
 
 template <int T>
@@ -90,32 +192,36 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
                                                const PushParams prm) {
     using L = Tile<T>;
     extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = (nth + 31) >> 5;
     float* sF = reinterpret_cast<float*>(smem);
-    float* sJ = sF + L::FLD;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::OFF_BAR);
-    int* sLeave = reinterpret_cast<int*>(smem + L::OFF_CNT);  // [MAX_SPECIES]
-    int* sDir = sLeave + MAX_SPECIES;                          // [MAX_SPECIES][8]
-    double* sRed = reinterpret_cast<double*>(smem + L::OFF_RED);
+    float* sJ = sF + L::FLD;  // [j_tiles][3][JPLANE]
+    unsigned char* misc = smem + L::off_misc(nwarps);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(misc);
+    int* sDir = reinterpret_cast<int*>(misc + 16);  // [MAX_SPECIES][8]
+    double* sRed = reinterpret_cast<double*>(misc + ((16 + L::NCNT * 4 + 7) & ~7));
+    float* sJw = sJ + (L::PER_WARP ? warp * L::JN : 0);
+    const int jtiles = (int)L::j_tiles(nwarps);
 
     const Geom& g = prm.g;
-    const int t = blockIdx.x;
+    const int t = blockIdx.x;      // tile
+    const int chunk = blockIdx.y;  // slice of the tile's particles taken by this CTA
     const int tx = t % g.ntx, ty = t / g.ntx;
     const int ix0 = tx * T, iy0 = ty * T;
-    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31;
     const long long step = *((volatile long long*)&prm.st->step);
 
     if (tid == 0) {
         dev::mbar_init(bar, 1);
         dev::fence_mbar_init();
     }
-    for (int i = tid; i < L::NCNT; i += nth) sLeave[i] = 0;
+    for (int i = tid; i < L::NCNT; i += nth) sDir[i] = 0;
     __syncthreads();
     if (tid == 0) {
         dev::mbar_arrive_expect_tx(bar, L::FLD * 4);
         // box origin: column ix0 = cell ix0 - GX, row iy0 = cell iy0 - GY
         dev::tma_load_3d(sF, &fmap, ix0, iy0, 0, bar);
     }
-    for (int i = tid; i < L::JN; i += nth) sJ[i] = 0.f;
+    for (int i = tid; i < jtiles * L::JN; i += nth) sJ[i] = 0.f;
     const bool ok = dev::mbar_wait_bounded(bar, 0);
     if (__syncthreads_or(!ok)) {
         if (tid == 0) dev::set_status(prm.st, ST_TIMEOUT);
@@ -128,9 +234,6 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
     const float* sBx = sF + 3 * L::FPLANE;
     const float* sBy = sF + 4 * L::FPLANE;
     const float* sBz = sF + 5 * L::FPLANE;
-    float* sJx = sJ;
-    float* sJy = sJ + L::JPLANE;
-    float* sJz = sJ + 2 * L::JPLANE;
     const int nx = g.nx, ny = g.ny;
     const float cxs = g.cx, cys = g.cy;
     unsigned bad_bits = 0;
@@ -138,16 +241,24 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
 
     for (int s = 0; s < prm.nsp; ++s) {
         const PushSpecies& S = prm.sp[s];
-        const int p0 = S.off[t], p1 = S.off[t + 1];
+        const int p0 = S.off[t];
+        const int nt = S.off[t + 1] - p0;
+        const int len = (nt + prm.chunks - 1) / prm.chunks;
+        const int c0 = p0 + min(chunk * len, nt), c1 = p0 + min((chunk + 1) * len, nt);
         const float tem = S.tem, qjx = S.qjx, qjy = S.qjy, qjz = S.qjz;
         float ke = 0.f;
-        for (int base = p0; base < p1; base += nth) {
+        for (int base = c0; base < c1; base += nth) {
             const int p = base + tid;
-            const bool active = p < p1;
+            const bool active = p < c1;
             bool write = false;
             int dir = -1;  // -1: stays in this tile; 0..7: leaves towards that neighbour
             int ncell = 0;
             float xn = 0.f, yn = 0.f, vx = 0.f, vy = 0.f, vzm = 0.f;
+            // the move to deposit: start, end, crossings (frame of the start cell)
+            bool mv = false;
+            float mx0 = 0.f, my0 = 0.f, mx1 = 0.f, my1 = 0.f, mxb = 0.f, myb = 0.f;
+            float mtx = 2.f, mty = 2.f, mqvz = 0.f;
+            int mdi = 0, mdj = 0, mlx = 0, mly = 0;
             if (active) {
                 const int c = S.cell[p];
                 const float x = S.x[p], y = S.y[p];
@@ -176,13 +287,20 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
                     const float umx = ux + tem * ex;
                     const float umy = uy + tem * ey;
                     const float umz = uz + tem * ez;
+#ifdef PIC_STRICT_BUILD
                     const float gm = sqrtf(1.f + umx * umx + umy * umy + umz * umz);
                     const float gtem = tem / gm;
+#else
+                    const float g2 = 1.f + umx * umx + umy * umy + umz * umz;
+                    const float rgm = rsqrtf(g2);
+                    const float gtem = tem * rgm;
+                    const float gm = g2 * rgm;
+#endif
                     const float btx = gtem * bx, bty = gtem * by, btz = gtem * bz;
                     const float upx = umx + umy * btz - umz * bty;
                     const float upy = umy + umz * btx - umx * btz;
                     const float upz = umz + umx * bty - umy * btx;
-                    const float f = 2.f / (1.f + btx * btx + bty * bty + btz * btz);
+                    const float f = qdiv(2.f, 1.f + btx * btx + bty * bty + btz * btz);
                     const float sx = f * btx, sy = f * bty, sz = f * btz;
                     const float uqx = umx + upy * sz - upz * sy;
                     const float uqy = umy + upz * sx - upx * sz;
@@ -191,10 +309,14 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
                     uy = uqy + tem * ey;
                     uz = uqz + tem * ez;
                     // gamma - 1 = |u-|^2 / (gamma + 1), free of cancellation
-                    ke += (umx * umx + umy * umy + umz * umz) / (gm + 1.f);
+                    ke += qdiv(umx * umx + umy * umy + umz * umz, gm + 1.f);
                     // ---- move, Eq. 11 in cell units ----
+#ifdef PIC_STRICT_BUILD
                     const float gg = sqrtf(1.f + ux * ux + uy * uy + uz * uz);
                     const float rg = 1.f / gg;
+#else
+                    const float rg = rsqrtf(1.f + ux * ux + uy * uy + uz * uz);
+#endif
                     const float ddx = ux * rg * cxs, ddy = uy * rg * cys;
                     const float vz = uz * rg;
                     vx = ux;
@@ -220,33 +342,21 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
                             dj = 0;
                             y1 = 0.f;
                         }
-                        // ---- Villasenor-Buneman split + deposit ----
-                        const float qvz = qjz * vz;
-                        const float xbd = di > 0 ? 1.f : 0.f, ybd = dj > 0 ? 1.f : 0.f;
-                        const float tcx = di ? (xbd - x) / (x1 - x) : 2.f;
-                        const float tcy = dj ? (ybd - y) / (y1 - y) : 2.f;
-                        const float t1 = fminf(fminf(tcx, tcy), 1.f);
-                        const float t2 = fminf(fmaxf(tcx, tcy), 1.f);
-                        float ta = 0.f, xa = x, ya = y;
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const float tb = k == 0 ? t1 : (k == 1 ? t2 : 1.f);
-                            if (tb > ta) {
-                                const float xe = tb == tcx ? xbd
-                                                           : (tb == 1.f ? x1 : x + tb * (x1 - x));
-                                const float ye = tb == tcy ? ybd
-                                                           : (tb == 1.f ? y1 : y + tb * (y1 - y));
-                                const int ci = (di != 0 && tcx <= ta) ? di : 0;
-                                const int cj = (dj != 0 && tcy <= ta) ? dj : 0;
-                                deposit_piece<L::JW>(sJx, sJy, sJz, lx + ci + 1, ly + cj + 1,
-                                                     xa - (float)ci, ya - (float)cj,
-                                                     xe - (float)ci, ye - (float)cj, tb - ta, qjx,
-                                                     qjy, qvz);
-                                xa = xe;
-                                ya = ye;
-                            }
-                            ta = fmaxf(ta, tb);
-                        }
+                        // ---- Villasenor-Buneman split: crossing fractions ----
+                        mv = true;
+                        mx0 = x;
+                        my0 = y;
+                        mx1 = x1;
+                        my1 = y1;
+                        mdi = di;
+                        mdj = dj;
+                        mlx = lx;
+                        mly = ly;
+                        mqvz = qjz * vz;
+                        mxb = di > 0 ? 1.f : 0.f;
+                        myb = dj > 0 ? 1.f : 0.f;
+                        mtx = di ? qdiv(mxb - x, x1 - x) : 2.f;
+                        mty = dj ? qdiv(myb - y, y1 - y) : 2.f;
                         // ---- new cell and tile ----
                         int nix = ix + di, niy = iy + dj;
                         nix = nix < 0 ? nix + nx : (nix >= nx ? nix - nx : nix);
@@ -266,14 +376,49 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
                     }
                 }
             }
-            // ---- re-sort metadata: warp-aggregated leaver slots ----
-            const unsigned lm = __ballot_sync(0xffffffffu, dir >= 0);
+            // ---- deposit, piece by piece over the whole warp (at most three
+            // pieces per move, Figs. 3.4-3.5) ----
+            {
+                const float t1 = fminf(fminf(mtx, mty), 1.f);
+                const float t2 = fminf(fmaxf(mtx, mty), 1.f);
+                float ta = 0.f, xa = mx0, ya = my0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float tb = k == 0 ? t1 : (k == 1 ? t2 : 1.f);
+                    // a corner crossing leaves the middle piece empty: skip, do not stop
+                    const bool has = mv && tb > ta;
+                    if (__any_sync(FULL, has)) {
+                        float v[8];
+                        int o = 0;
+                        float xe = xa, ye = ya;
+                        if (has) {
+                            xe = tb == mtx ? mxb : (tb == 1.f ? mx1 : mx0 + tb * (mx1 - mx0));
+                            ye = tb == mty ? myb : (tb == 1.f ? my1 : my0 + tb * (my1 - my0));
+                            const int ci = (mdi != 0 && mtx <= ta) ? mdi : 0;
+                            const int cj = (mdj != 0 && mty <= ta) ? mdj : 0;
+                            o = (mly + cj + 1) * L::JW + (mlx + ci + 1);
+                            piece_current(v, xa - (float)ci, ya - (float)cj, xe - (float)ci,
+                                          ye - (float)cj, tb - ta, qjx, qjy, mqvz);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) v[i] = 0.f;
+                        }
+                        deposit_warp<L::JW, L::JPLANE, L::PER_WARP>(has, o, v, sJw, lane);
+                        xa = xe;
+                        ya = ye;
+                    }
+                    ta = fmaxf(ta, tb);
+                }
+            }
+            // ---- re-sort metadata: leaver slots in the tile's out section, one
+            // global atomic per warp that has leavers (shared by the tile's CTAs) ----
+            const unsigned lm = __ballot_sync(FULL, dir >= 0);
             int slot = 0;
             if (lm) {
                 const int leader = __ffs(lm) - 1;
                 int wbase = 0;
-                if (lane == leader) wbase = atomicAdd(&sLeave[s], __popc(lm));
-                wbase = __shfl_sync(0xffffffffu, wbase, leader);
+                if (lane == leader) wbase = atomicAdd(&S.leave[t], __popc(lm));
+                wbase = __shfl_sync(FULL, wbase, leader);
                 slot = wbase + __popc(lm & ((1u << lane) - 1u));
             }
             if (write) {
@@ -303,30 +448,27 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
     }
     __syncthreads();
 
-    // ---- per-tile counts for the re-sort ----
-    for (int s = 0; s < prm.nsp; ++s) {
-        const PushSpecies& S = prm.sp[s];
-        if (tid == 0) {
-            const int n = S.off[t + 1] - S.off[t];
-            S.leave[t] = sLeave[s];
-            S.stay[t] = n - sLeave[s];
-        }
-        if (tid < 8) S.dirc[t * 8 + tid] = sDir[s * 8 + tid];
-    }
+    // ---- leavers by destination, for the re-sort's counts ----
+    for (int s = 0; s < prm.nsp; ++s)
+        if (tid < 8 && sDir[s * 8 + tid]) atomicAdd(&prm.sp[s].dirc[t * 8 + tid], sDir[s * 8 + tid]);
     if (bad_bits) dev::set_status(prm.st, bad_bits);
 
     // ---- kinetic energy: FP64 block sum, one FP64 atomic ----
     const double kb = dev::block_sum(ke_tot, sRed);
     if (tid == 0 && prm.nsp > 0) atomicAdd(&prm.hist_k[step & (HIST - 1)], kb);
 
-    // ---- J flush (update_gc_add) ----
+    // ---- J flush (update_gc_add).  A tile taken by one CTA stores the cells
+    // no other tile's halo reaches and adds the shared ring; a tile split over
+    // several CTAs adds everything (the Yee kernel then clears all of J). ----
+    const bool whole = prm.chunks == 1;
     for (int idx = tid; idx < L::JN; idx += nth) {
         const int comp = idx / L::JPLANE;
         const int rem = idx - comp * L::JPLANE;
         const int r = rem / L::JW, q = rem - r * L::JW;
         const int lx = q - 1, ly = r - 1;
-        const float v = sJ[idx];
-        const bool deep = lx >= 2 && lx < T - 1 && ly >= 2 && ly < T - 1;
+        float v = 0.f;
+        for (int w = 0; w < jtiles; ++w) v += sJ[w * L::JN + idx];
+        const bool deep = whole && lx >= 2 && lx < T - 1 && ly >= 2 && ly < T - 1;
         if (!deep && v == 0.f) continue;
         int i = ix0 + lx, j = iy0 + ly;
         i = i < 0 ? i + nx : (i >= nx ? i - nx : i);
@@ -339,17 +481,17 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
     }
 }
 
-// fmap == nullptr: only set the kernel's shared-memory limit (done once per
-// process before any launch, so never during a stream capture)
+// fmap == nullptr: only set the kernel's shared-memory limit for the largest
+// block (done once per process before any launch, so never during a capture)
 template <int T>
 static cudaError_t launch_T(const CUtensorMap* fmap, const PushParams& p, int threads,
                             cudaStream_t s) {
-    const size_t bytes = Tile<T>::BYTES;
+    const size_t bytes = Tile<T>::bytes((threads + 31) / 32);
     if (!fmap)
         return cudaFuncSetAttribute(k_push<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)bytes);
+                                    (int)Tile<T>::bytes(32));
     if (p.g.ntiles == 0) return cudaSuccess;
-    k_push<T><<<p.g.ntiles, threads, bytes, s>>>(*fmap, p);
+    k_push<T><<<dim3(p.g.ntiles, p.chunks), threads, bytes, s>>>(*fmap, p);
     return cudaGetLastError();
 }
 

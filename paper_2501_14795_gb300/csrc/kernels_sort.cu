@@ -86,8 +86,11 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const SortParams prm) {
     long long myleave = 0;
     for (int t = t0; t < t1; ++t) {
         const int tx = t % g.ntx, ty = t / g.ntx;
-        int c = S.stay[t];
+        int c = S.off_old[t + 1] - S.off_old[t] - S.leave[t];  // stayers
         myleave += S.leave[t];
+        S.leave_next[t] = 0;  // counters of the next step (other parity)
+#pragma unroll
+        for (int d = 0; d < 8; ++d) S.dirc_next[t * 8 + d] = 0;
         for (int d = 0; d < 8; ++d) {
             int ddx, ddy;
             dir_delta(d, ddx, ddy);

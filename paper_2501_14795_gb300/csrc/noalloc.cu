@@ -23,7 +23,7 @@
 
 #include <mutex>
 
-#include "../../include/pic.h"
+#include "pic.h"
 #include "device_util.cuh"
 
 namespace {

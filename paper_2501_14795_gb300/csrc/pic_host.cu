@@ -8,11 +8,12 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
 
-#include "../../include/pic.h"
+#include "pic.h"
 #include "pic_internal.h"
 
 using namespace pic;
@@ -141,6 +142,19 @@ void invalidate_graphs(pic_sim* sim) {
     }
 }
 
+// CTAs per tile in the particle advance: tiles holding many particles are
+// split so that every CTA takes about kChunkParticles (the grid then has many
+// CTAs per SM and the hardware balances them); one CTA per tile otherwise.
+constexpr int kMaxChunks = 1024;
+
+int chunks_per_tile(const pic_sim* sim) {
+    int64_t nmax = 0;
+    for (int k = 0; k < sim->cfg.n_species; ++k) nmax = std::max(nmax, sim->sp[k].n);
+    const int64_t per_tile = sim->g.ntiles ? nmax / sim->g.ntiles : 0;
+    const int64_t c = (per_tile + sim->cfg.chunk - 1) / sim->cfg.chunk;
+    return (int)std::min<int64_t>(std::max<int64_t>(c, 1), kMaxChunks);
+}
+
 PushParams push_params(const pic_sim* sim, int b) {
     PushParams p;
     memset(&p, 0, sizeof p);
@@ -153,11 +167,12 @@ PushParams push_params(const pic_sim* sim, int b) {
         PushSpecies& q = p.sp[k];
         q.off = s.off[b];
         q.cell = s.cell; q.id = s.id; q.ocell = s.ocell; q.oid = s.oid; q.hole = s.hole;
-        q.stay = s.stay; q.leave = s.leave; q.dirc = s.dirc;
+        q.leave = s.leave[b]; q.dirc = s.dirc[b];
         q.x = s.x; q.y = s.y; q.ux = s.ux; q.uy = s.uy; q.uz = s.uz;
         q.ox = s.ox; q.oy = s.oy; q.oux = s.oux; q.ouy = s.ouy; q.ouz = s.ouz;
         q.tem = s.tem; q.qjx = s.qjx; q.qjy = s.qjy; q.qjz = s.qjz; q.ke_w = s.ke_w;
     }
+    p.chunks = chunks_per_tile(sim);
     p.hist_k = sim->hist_k;
     p.st = sim->st;
     return p;
@@ -175,8 +190,8 @@ SortParams sort_params(const pic_sim* sim, int b) {
         q.off_old = s.off[b];
         q.off_new = s.off[1 - b];
         q.cell = s.cell; q.id = s.id; q.ocell = s.ocell; q.oid = s.oid; q.hole = s.hole;
-        q.fslot = s.fslot; q.isrc = s.isrc; q.stay = s.stay; q.leave = s.leave;
-        q.dirc = s.dirc; q.evict = s.evict;
+        q.fslot = s.fslot; q.isrc = s.isrc; q.leave = s.leave[b]; q.dirc = s.dirc[b];
+        q.leave_next = s.leave[1 - b]; q.dirc_next = s.dirc[1 - b]; q.evict = s.evict;
         q.x = s.x; q.y = s.y; q.ux = s.ux; q.uy = s.uy; q.uz = s.uz;
         q.ox = s.ox; q.oy = s.oy; q.oux = s.oux; q.ouy = s.ouy; q.ouz = s.ouz;
         q.n = (int)s.n;
@@ -205,6 +220,7 @@ int enqueue_step(pic_sim* sim, cudaStream_t s, int b, cudaEvent_t ev_a, cudaEven
     yp.hist_e = sim->hist_e;
     yp.hist_b = sim->hist_b;
     yp.st = sim->st;
+    yp.zero_all = pp.chunks > 1;
     int n = 0;
     cudaError_t e;
     const unsigned rec = capturing ? cudaEventRecordExternal : 0u;
@@ -331,6 +347,8 @@ pic_status pic_init(const pic_config* cfg, void* cuda_stream, pic_sim** out) {
     pic_config c = *cfg;
     if (c.tile == 0) c.tile = 16;
     if (c.threads == 0) c.threads = 256;
+    if (c.chunk == 0) c.chunk = 4096;
+    if (c.chunk < 16 || c.chunk > (1 << 20)) return PIC_EINVAL;
     if (!(c.tile == 8 || c.tile == 16 || c.tile == 32)) return PIC_EINVAL;
     if (c.threads < 64 || c.threads > 1024 || c.threads % 32) return PIC_EINVAL;
     if (c.nx < 8 || c.ny < 8 || c.nx > 32768 || c.ny > 32768) return PIC_EINVAL;
@@ -404,9 +422,14 @@ pic_status pic_init(const pic_config* cfg, void* cuda_stream, pic_sim** out) {
         memset(&s, 0, sizeof s);
         if (e == cudaSuccess) e = dalloc(&s.off[0], g.ntiles + 1);
         if (e == cudaSuccess) e = dalloc(&s.off[1], g.ntiles + 1);
-        if (e == cudaSuccess) e = dalloc(&s.stay, g.ntiles);
-        if (e == cudaSuccess) e = dalloc(&s.leave, g.ntiles);
-        if (e == cudaSuccess) e = dalloc(&s.dirc, 8 * (size_t)g.ntiles);
+        for (int b = 0; b < 2; ++b) {
+            if (e == cudaSuccess) e = dalloc(&s.leave[b], g.ntiles);
+            if (e == cudaSuccess) e = dalloc(&s.dirc[b], 8 * (size_t)g.ntiles);
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(s.leave[b], 0, sizeof(int32_t) * g.ntiles, sim->stream);
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(s.dirc[b], 0, sizeof(int32_t) * 8 * g.ntiles, sim->stream);
+        }
         if (e == cudaSuccess) e = dalloc(&s.evict, g.ntiles);
         if (e == cudaSuccess) e = dalloc(&s.cursor, g.ntiles);
         for (int b = 0; b < 2 && e == cudaSuccess; ++b)
@@ -778,9 +801,10 @@ void pic_destroy(pic_sim* sim) {
         free_species(s);
         dfree(s.off[0]);
         dfree(s.off[1]);
-        dfree(s.stay);
-        dfree(s.leave);
-        dfree(s.dirc);
+        for (int b = 0; b < 2; ++b) {
+            dfree(s.leave[b]);
+            dfree(s.dirc[b]);
+        }
         dfree(s.evict);
         dfree(s.cursor);
     }

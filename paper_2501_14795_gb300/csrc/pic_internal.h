@@ -55,9 +55,8 @@ struct SpeciesDev {
     int32_t* fslot;   // fill lists: target positions ...
     int32_t* isrc;    // ... and source indices into the out arrays
     int32_t* off[2];  // ntiles + 1 bookmarks (tile_offset), ping-pong
-    int32_t* stay;    // per tile: particles that stayed
-    int32_t* leave;   // per tile: particles that left
-    int32_t* dirc;    // per tile x 8 directions: leavers by destination
+    int32_t* leave[2];  // per tile: particles that left (ping-pong; the scan clears the idle one)
+    int32_t* dirc[2];   // per tile x 8 directions: leavers by destination (ping-pong)
     int32_t* evict;   // per tile: stayers displaced by the new bookmarks
     int32_t* cursor;  // per tile scratch for the initial load
     int64_t n;        // particles
@@ -82,7 +81,7 @@ struct Geom {
 // ---- parameters passed by value to the kernels ------------------------------
 struct PushSpecies {
     const int32_t* off;
-    int32_t *cell, *id, *ocell, *oid, *hole, *stay, *leave, *dirc;
+    int32_t *cell, *id, *ocell, *oid, *hole, *leave, *dirc;
     float *x, *y, *ux, *uy, *uz, *ox, *oy, *oux, *ouy, *ouz;
     float tem, qjx, qjy, qjz;
     double ke_w;
@@ -91,6 +90,7 @@ struct PushSpecies {
 struct PushParams {
     Geom g;
     float* J;              // this step's current buffer (base of component 0)
+    int chunks;            // CTAs per tile (gridDim.y): each takes a slice of the tile's particles
     int nsp;
     int track_ids;
     PushSpecies sp[MAX_SPECIES];
@@ -101,7 +101,8 @@ struct PushParams {
 struct SortSpecies {
     const int32_t* off_old;
     int32_t* off_new;
-    int32_t *cell, *id, *ocell, *oid, *hole, *fslot, *isrc, *stay, *leave, *dirc, *evict;
+    int32_t *cell, *id, *ocell, *oid, *hole, *fslot, *isrc, *leave, *dirc, *evict;
+    int32_t *leave_next, *dirc_next;  // cleared here for the next step
     float *x, *y, *ux, *uy, *uz, *ox, *oy, *oux, *ouy, *ouz;
     int n;
 };
@@ -121,6 +122,7 @@ struct YeeParams {
     float* Fout;        // E|B at n+1
     const float* J;     // current of this step
     float* Jnext;       // next step's current buffer: its shared ring is zeroed here
+    int zero_all;       // zero all of Jnext (tiles split over several CTAs flush with atomics)
     double *hist_e, *hist_b;
     DevState* st;
 };

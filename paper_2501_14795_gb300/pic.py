@@ -40,7 +40,7 @@ class pic_species_cfg(C.Structure):
 class pic_config(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double), ("dy", C.c_double),
                 ("dt", C.c_double), ("tile", C.c_int), ("threads", C.c_int),
-                ("n_species", C.c_int), ("species", pic_species_cfg * PIC_MAX_SPECIES),
+                ("chunk", C.c_int), ("n_species", C.c_int), ("species", pic_species_cfg * PIC_MAX_SPECIES),
                 ("background", C.c_double), ("flags", C.c_uint)]
 
 
@@ -261,11 +261,13 @@ def pic_tile_sort_noalloc(nx, ny, tile, ix, iy, x, y, ux, uy, uz, ix_out, iy_out
 
 # ------------------------------------------------------------- conveniences
 
-def make_config(nx, ny, dx, dy, dt, species, tile=16, threads=256, background=1.0, flags=0):
+def make_config(nx, ny, dx, dy, dt, species, tile=16, threads=256, background=1.0, flags=0,
+                chunk=0):
     """pic_config from (q_over_m, qtilde) pairs: qtilde = sign(q/m) n_s/ppc_s."""
     cfg = pic_config()
     cfg.nx, cfg.ny, cfg.dx, cfg.dy, cfg.dt = nx, ny, dx, dy, dt
     cfg.tile, cfg.threads, cfg.background, cfg.flags = tile, threads, background, flags
+    cfg.chunk = chunk
     cfg.n_species = len(species)
     for k, (qm, qt) in enumerate(species):
         cfg.species[k].q_over_m = qm
@@ -274,11 +276,11 @@ def make_config(nx, ny, dx, dy, dt, species, tile=16, threads=256, background=1.
     return cfg
 
 
-def config_for(workload, tile=None, threads=256, flags=0):
+def config_for(workload, tile=None, threads=256, flags=0, chunk=0):
     return make_config(workload.nx, workload.ny, workload.dx, workload.dy, workload.dt,
                        [(s.q_over_m, s.qtilde) for s in workload.species],
                        tile=tile or workload.tile, threads=threads,
-                       background=workload.background, flags=flags)
+                       background=workload.background, flags=flags, chunk=chunk)
 
 
 class Simulation:
@@ -289,8 +291,9 @@ class Simulation:
         self.h = pic_init(cfg, stream)
 
     @classmethod
-    def from_workload(cls, w, tile=None, threads=256, flags=0, stream=None, device=False):
-        sim = cls(config_for(w, tile, threads, flags), stream)
+    def from_workload(cls, w, tile=None, threads=256, flags=0, stream=None, device=False,
+                      chunk=0):
+        sim = cls(config_for(w, tile, threads, flags, chunk), stream)
         for k, s in enumerate(w.species):
             arrs = s.arrays()
             if device:

@@ -43,8 +43,9 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _gpu(w, flags=pic.PIC_TRACK_IDS, tile=None, threads=256, E=None, B=None):
-    sim = pic.Simulation.from_workload(w, tile=tile, threads=threads, flags=flags, device=True)
+def _gpu(w, flags=pic.PIC_TRACK_IDS, tile=None, threads=256, E=None, B=None, chunk=0):
+    sim = pic.Simulation.from_workload(w, tile=tile, threads=threads, flags=flags, device=True,
+                                       chunk=chunk)
     if E is not None or B is not None:
         pic.pic_set_fields(sim.h, None if E is None else _dev(E.reshape(-1)),
                            None if B is None else _dev(B.reshape(-1)))
@@ -91,10 +92,13 @@ CASES = [(48, 32, 16, 5003), (64, 64, 8, 20011), (32, 64, 32, 7001), (16, 16, 8,
          (16, 32, 16, 1500)]
 
 
+@pytest.mark.parametrize("chunk", [0, 64])
 @pytest.mark.parametrize("nx,ny,T,n", CASES)
-def test_strict_step_is_bit_exact_with_fp32_oracle(nx, ny, T, n):
+def test_strict_step_is_bit_exact_with_fp32_oracle(nx, ny, T, n, chunk):
+    """chunk = 64 splits every tile over several CTAs (shared leaver counters,
+    all-atomic J flush); chunk = 0 keeps one CTA per tile at these sizes."""
     w, E, B = _random_case(nx, ny, T, n, seed=nx + ny + T)
-    with _gpu(w, pic.PIC_STRICT_FP | pic.PIC_TRACK_IDS, tile=T, E=E, B=B) as sim:
+    with _gpu(w, pic.PIC_STRICT_FP | pic.PIC_TRACK_IDS, tile=T, E=E, B=B, chunk=chunk) as sim:
         sim.step(1)
         got = sim.particles(0, ids=True)
         Jg = sim.fields(pic.FIELD_J)
@@ -125,10 +129,10 @@ def test_strict_step_is_bit_exact_with_fp32_oracle(nx, ny, T, n):
 
 
 @pytest.mark.parametrize("nx,ny,T,n", CASES[:3])
-@pytest.mark.parametrize("threads", [128, 256, 512])
-def test_fast_step_matches_fp64_oracle(nx, ny, T, n, threads):
+@pytest.mark.parametrize("threads,chunk", [(128, 0), (256, 0), (512, 0), (256, 100)])
+def test_fast_step_matches_fp64_oracle(nx, ny, T, n, threads, chunk):
     w, E, B = _random_case(nx, ny, T, n, seed=7 * nx + T)
-    with _gpu(w, pic.PIC_TRACK_IDS, tile=T, threads=threads, E=E, B=B) as sim:
+    with _gpu(w, pic.PIC_TRACK_IDS, tile=T, threads=threads, E=E, B=B, chunk=chunk) as sim:
         sim.step(1)
         got = _by_id(sim.particles(0, ids=True))
         Jg = sim.fields(pic.FIELD_J)
@@ -182,12 +186,13 @@ def _assert_close_states(a, b, nx, ny, pos_tol=1e-5, u_tol=1e-5):
         assert np.max(np.abs(a[k].astype(np.float64) - b[k])) < u_tol
 
 
-def test_two_stream_100_steps_tracks_fp64_oracle():
+@pytest.mark.parametrize("chunk", [0, 256])
+def test_two_stream_100_steps_tracks_fp64_oracle(chunk):
     """The two-stream workload (64x64, 4x4 ppc, drift +-0.2, u_th 0.1), 100
     steps: particle positions agree within 1e-4 cell and the energy histories
-    within 1e-3 of the total."""
+    within 1e-3 of the total (chunk = 256: every tile split over 16 CTAs)."""
     w = wl.two_stream()
-    with _gpu(w, pic.PIC_TRACK_IDS) as sim:
+    with _gpu(w, pic.PIC_TRACK_IDS, chunk=chunk) as sim:
         sim.step(100)
         got = _by_id(sim.particles(0, ids=True))
         he, hb, hk = sim.history(0, 101)
