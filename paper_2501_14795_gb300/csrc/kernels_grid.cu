@@ -280,9 +280,23 @@ __global__ void k_residuals(const Geom g, const float* F, const float* J, const 
 }
 
 // ------------------------------------------------------- particle load
+// The initial sort orders particles by tile (§4.1); inside a tile, where the
+// method leaves the order free, they are placed in a pseudo-random order
+// (key = tile * T^2 + a hash of the input index modulo T^2).  A warp's 32
+// particles then fall into many different cells, which keeps the shared-memory
+// conflicts of the current deposit low from the first step on (the order a
+// simulation reaches after some steps is of this kind anyway: particles keep
+// their slot when they change cell).
 // phase 0: validate the staged input (out arrays; ocell holds ix, hole holds
-//          iy on entry) and count per tile;
-// phase 1: scatter into the particle arrays at off[tile] + cursor.
+//          iy on entry) and count per cell key;
+// phase 1: scan the counts into cell offsets, take the tile bookmarks from
+//          them and scatter into the particle arrays.
+__device__ __forceinline__ int load_key(const Geom& g, int ix, int iy, int k) {
+    const int t = (iy / g.T) * g.ntx + ix / g.T;
+    const unsigned h = ((unsigned)k * 2654435761u) >> 8;  // Knuth's multiplicative hash
+    return t * g.T * g.T + (int)(h % (unsigned)(g.T * g.T));
+}
+
 __global__ void k_load_count(const Geom g, SpeciesDev sp, int n, DevState* st) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int ix = sp.ocell[k], iy = sp.hole[k];
@@ -294,17 +308,16 @@ __global__ void k_load_count(const Geom g, SpeciesDev sp, int n, DevState* st) {
             atomicAdd(&st->load_bad, 1);
             continue;
         }
-        const int t = (iy / g.T) * g.ntx + ix / g.T;
-        atomicAdd(&sp.cursor[t], 1);
+        atomicAdd(&sp.cursor[load_key(g, ix, iy, k)], 1);
     }
 }
 
 __global__ void k_load_scatter(const Geom g, SpeciesDev sp, int n, const int32_t* ids,
-                               const int32_t* off, int track) {
+                               const int32_t* celloff, int track) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int ix = sp.ocell[k], iy = sp.hole[k];
-        const int t = (iy / g.T) * g.ntx + ix / g.T;
-        const int p = off[t] + atomicAdd(&sp.cursor[t], 1);
+        const int key = load_key(g, ix, iy, k);
+        const int p = celloff[key] + atomicAdd(&sp.cursor[key], 1);
         sp.cell[p] = ix | (iy << 16);
         sp.x[p] = sp.ox[k];
         sp.y[p] = sp.oy[k];
@@ -313,6 +326,12 @@ __global__ void k_load_scatter(const Geom g, SpeciesDev sp, int n, const int32_t
         sp.uz[p] = sp.ouz[k];
         if (track) sp.id[p] = ids ? ids[k] : k;
     }
+}
+
+// tile bookmarks = offsets of each tile's first cell key
+__global__ void k_tile_from_cells(const int32_t* celloff, int ntiles, int T2, int32_t* off) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t <= ntiles; t += gridDim.x * blockDim.x)
+        off[t] = celloff[(long long)t * T2];
 }
 
 // exclusive scan of per-tile counts (single CTA)
@@ -428,22 +447,26 @@ cudaError_t launch_grid_residuals(const Geom& g, const float* F, const float* J,
 }
 
 cudaError_t launch_load(const Geom& g, SpeciesDev& sp, int track_ids, int64_t n, int32_t* off,
-                        DevState* st, cudaStream_t s, int phase, const int32_t* staged_ids) {
+                        DevState* st, cudaStream_t s, int phase, const int32_t* staged_ids,
+                        int32_t* celloff) {
     const int nn = (int)n;
+    const long long ncell = (long long)g.nx * g.ny;
     if (phase == 0) {
-        cudaError_t e = cudaMemsetAsync(sp.cursor, 0, sizeof(int32_t) * g.ntiles, s);
+        cudaError_t e = cudaMemsetAsync(sp.cursor, 0, sizeof(int32_t) * ncell, s);
         if (e != cudaSuccess) return e;
         if (nn > 0) k_load_count<<<grid_for(nn, 256), 256, 0, s>>>(g, sp, nn, st);
         return cudaGetLastError();
     }
-    // phase 1: offsets from the counts, then scatter
-    k_scan_counts<<<1, 1024, 0, s>>>(sp.cursor, g.ntiles, off);
+    // phase 1: cell offsets from the counts, tile bookmarks, then scatter
+    k_scan_counts<<<1, 1024, 0, s>>>(sp.cursor, (int)ncell, celloff);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(sp.cursor, 0, sizeof(int32_t) * g.ntiles, s);
+    k_tile_from_cells<<<grid_for(g.ntiles + 1, 256), 256, 0, s>>>(celloff, g.ntiles, g.T * g.T,
+                                                                 off);
+    e = cudaMemsetAsync(sp.cursor, 0, sizeof(int32_t) * ncell, s);
     if (e != cudaSuccess) return e;
     if (nn > 0)
-        k_load_scatter<<<grid_for(nn, 256), 256, 0, s>>>(g, sp, nn, staged_ids, off, track_ids);
+        k_load_scatter<<<grid_for(nn, 256), 256, 0, s>>>(g, sp, nn, staged_ids, celloff, track_ids);
     return cudaGetLastError();
 }
 

@@ -6,13 +6,15 @@
 //   2. per particle (coalesced SoA loads): linear gather of the six staggered
 //      components (Fig. 3.1), Boris push (Eqs. 6-10), move (Eq. 11) and the
 //      Villasenor-Buneman split into at most three pieces (Figs. 3.4-3.5);
-//   3. deposit each piece's current (Eqs. 13-16 plus the time-averaged Jz)
-//      into a J tile, cells [-1, T+2), in shared memory: one private J tile
-//      per warp (T <= 16), so warps never contend.  Pieces of a warp that fall
-//      into few cells (quiet or cold plasmas keep neighbouring particles
-//      together) are summed across the warp by a shuffle reduce-scatter and
-//      added with plain read-add-write by 8 lanes, one cell group at a time;
-//      scattered pieces are added with atomics on the warp's own tile;
+//   3. deposit each piece's current (Eqs. 13-16 plus the time-averaged Jz),
+//      computed in FP32, into a J tile, cells [-1, T+2), in shared memory:
+//      one private tile per warp (T <= 16), so warps never contend, holding
+//      exact 32-bit fixed-point sums (native integer shared atomics cost the
+//      same with up to 4 lanes on one word, float ones grow with every
+//      conflicting lane); the scale is bounded so no sum can overflow, and the
+//      tiles are converted to FP32 once, at the flush.  Pieces of a warp that
+//      fall into few cells are first summed across the warp (shuffle
+//      reduce-scatter) and added by 8 lanes, one cell run at a time;
 //   4. emit the re-sort metadata of §4.3: particles that stay in the tile are
 //      written in place; particles that leave are appended (warp-ballot slots)
 //      to the tile's section of the out arrays with their old position in the
@@ -44,7 +46,14 @@ namespace PIC_VARIANT {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-template <int T>
+constexpr int NSTAGE = 4;  // particle batches (blockDim particles each) in flight per CTA
+constexpr int PAD = 4;     // a batch is copied from a 16-byte aligned start: <= 3 extra
+
+// Shared-memory layout of one CTA (blocks of `nth` threads):
+//   [E|B halo FLD floats][J tiles: one per warp (PW) or one per CTA]
+//   [NSTAGE particle stages: 6 arrays x (nth + PAD) 32-bit words]
+//   [mbarriers: halo + one per stage][counters][FP64 reduction scratch]
+template <int T, bool PW>
 struct Tile {
     static constexpr int FW = T + 8;  // TMA box columns: cells -4 .. T+3
     static constexpr int FH = T + 3;  // TMA box rows:    cells -1 .. T+1
@@ -53,17 +62,22 @@ struct Tile {
     static constexpr int JW = T + 3;  // J tile: cells -1 .. T+1 on both axes
     static constexpr int JPLANE = JW * JW;
     static constexpr int JN = 3 * JPLANE;
-    static constexpr bool PER_WARP = T <= 16;  // one private J tile per warp
+    static constexpr bool PER_WARP = PW;
     static constexpr int NCNT = MAX_SPECIES * 8 + 4;
 
-    // shared-memory layout for a block of `warps` warps
-    static __host__ __device__ size_t j_tiles(int warps) { return PER_WARP ? warps : 1; }
-    static __host__ __device__ size_t off_misc(int warps) {
-        return ((size_t)FLD * 4 + j_tiles(warps) * JN * 4 + 15) & ~(size_t)15;
+    static __host__ __device__ size_t j_tiles(int nth) { return PW ? (nth + 31) / 32 : 1; }
+    static __host__ __device__ size_t off_stage(int nth) {
+        return ((size_t)FLD * 4 + j_tiles(nth) * JN * 4 + 15) & ~(size_t)15;
     }
-    static __host__ __device__ size_t bytes(int warps) {
-        return off_misc(warps) + 16 + NCNT * 4 + 8 + 32 * sizeof(double);
+    static __host__ __device__ size_t stage_words(int nth) { return 6 * (size_t)(nth + PAD); }
+    static __host__ __device__ size_t off_misc(int nth) {
+        return off_stage(nth) + NSTAGE * stage_words(nth) * 4;
     }
+    static __host__ __device__ size_t off_cnt(int nth) { return off_misc(nth) + 8 * (NSTAGE + 2); }
+    static __host__ __device__ size_t off_red(int nth) {
+        return (off_cnt(nth) + NCNT * 4 + 7) & ~(size_t)7;
+    }
+    static __host__ __device__ size_t bytes(int nth) { return off_red(nth) + 32 * sizeof(double); }
 };
 
 __device__ __forceinline__ float interp(const float* F, int fw, int col, int row, float a0,
@@ -143,65 +157,85 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float v[8], int lane
 
 constexpr int AGG_MAX_GROUPS = 8;
 
+// Add one value to the J tile: per-warp tiles (PER_WARP) hold exact 32-bit
+// fixed-point sums (value * qs, the CTA's scale); the CTA-wide tile holds FP32.
+template <bool PER_WARP>
+__device__ __forceinline__ void tile_add(float* a, float x, float qs) {
+    if constexpr (PER_WARP)
+        atomicAdd(reinterpret_cast<int*>(a), __float2int_rn(x * qs));
+    else
+        atomicAdd(a, x);
+}
+
 // Deposit one piece per lane (has == false: nothing) into the J tile `sJw`
 // (the warp's own tile when PER_WARP, else the CTA's).  Every lane calls this.
+// Lanes holding consecutive particles with the same piece cell form a run
+// (a run starts where the cell differs from the previous lane's); when the
+// warp has few runs, each run is summed across the warp and added by 8 lanes.
+// Runs are exact for any particle order: a cell split over several runs is
+// simply added several times.  Otherwise every lane adds its eight values.
 template <int JW, int JPLANE, bool PER_WARP>
 __device__ __forceinline__ void deposit_warp(bool has, int o, const float v[8], float* sJw,
-                                             int lane) {
+                                             int lane, float qs) {
     const unsigned act = __ballot_sync(FULL, has);
-    const unsigned peers = __match_any_sync(FULL, has ? o : -1);
-    const bool lead = has && lane == __ffs(peers) - 1;
-    unsigned leaders = __ballot_sync(FULL, lead);
-    const int ng = __popc(leaders);
+    const int prev = __shfl_up_sync(FULL, o, 1);
+    const bool head = has && (lane == 0 || prev != o || !((act >> (lane - 1)) & 1u));
+    unsigned heads = __ballot_sync(FULL, head);
+    const int ng = __popc(heads);
     if (ng <= AGG_MAX_GROUPS && __popc(act) >= 2 * ng) {
-        // few cells: sum each cell group across the warp, 8 lanes add the totals
+        // few runs: sum each run across the warp, 8 lanes add the totals
         const int k = lane >> 2;
         const int voff = value_offset<JW, JPLANE>(k);
-        while (leaders) {
-            const int l = __ffs(leaders) - 1;
-            leaders &= leaders - 1u;
+        while (heads) {
+            const int l = __ffs(heads) - 1;
+            heads &= heads - 1u;
+            const int nxt = heads ? __ffs(heads) - 1 : 32;
+            const unsigned upto = nxt == 32 ? FULL : ((1u << nxt) - 1u);
+            const unsigned run = upto & ~((1u << l) - 1u) & act;
             const int ko = __shfl_sync(FULL, o, l);
-            const bool mine = has && o == ko;
+            const bool mine = (run >> lane) & 1u;
             float s[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) s[i] = mine ? v[i] : 0.f;
             const float tot = warp_reduce_scatter8(s, lane);
             if ((lane & 3) == 0) {
                 float* a = sJw + ko + voff;
-                if (PER_WARP)
-                    *a += tot;  // the 8 targets are distinct; one group at a time
+                if constexpr (PER_WARP)  // the 8 targets are distinct; one run at a time
+                    *reinterpret_cast<int*>(a) += __float2int_rn(tot * qs);
                 else
                     atomicAdd(a, tot);
             }
-            if (PER_WARP) __syncwarp();
+            if constexpr (PER_WARP) __syncwarp();
         }
     } else if (has) {
-        atomicAdd(sJw + o, v[0]);
-        atomicAdd(sJw + o + JW, v[1]);
-        atomicAdd(sJw + JPLANE + o, v[2]);
-        atomicAdd(sJw + JPLANE + o + 1, v[3]);
-        atomicAdd(sJw + 2 * JPLANE + o, v[4]);
-        atomicAdd(sJw + 2 * JPLANE + o + 1, v[5]);
-        atomicAdd(sJw + 2 * JPLANE + o + JW, v[6]);
-        atomicAdd(sJw + 2 * JPLANE + o + JW + 1, v[7]);
+        tile_add<PER_WARP>(sJw + o, v[0], qs);
+        tile_add<PER_WARP>(sJw + o + JW, v[1], qs);
+        tile_add<PER_WARP>(sJw + JPLANE + o, v[2], qs);
+        tile_add<PER_WARP>(sJw + JPLANE + o + 1, v[3], qs);
+        tile_add<PER_WARP>(sJw + 2 * JPLANE + o, v[4], qs);
+        tile_add<PER_WARP>(sJw + 2 * JPLANE + o + 1, v[5], qs);
+        tile_add<PER_WARP>(sJw + 2 * JPLANE + o + JW, v[6], qs);
+        tile_add<PER_WARP>(sJw + 2 * JPLANE + o + JW + 1, v[7], qs);
     }
 }
 
-template <int T>
+template <int T, bool PW>
 __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorMap fmap,
                                                const PushParams prm) {
-    using L = Tile<T>;
+    using L = Tile<T, PW>;
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
-    const int nwarps = (nth + 31) >> 5;
     float* sF = reinterpret_cast<float*>(smem);
     float* sJ = sF + L::FLD;  // [j_tiles][3][JPLANE]
-    unsigned char* misc = smem + L::off_misc(nwarps);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(misc);
-    int* sDir = reinterpret_cast<int*>(misc + 16);  // [MAX_SPECIES][8]
-    double* sRed = reinterpret_cast<double*>(misc + ((16 + L::NCNT * 4 + 7) & ~7));
+    float* sStage = reinterpret_cast<float*>(smem + L::off_stage(nth));
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::off_misc(nth));
+    uint64_t* sbar = bar + 1;  // one per particle stage
+    int* sDir = reinterpret_cast<int*>(smem + L::off_cnt(nth));  // [MAX_SPECIES][8]
+    double* sRed = reinterpret_cast<double*>(smem + L::off_red(nth));
     float* sJw = sJ + (L::PER_WARP ? warp * L::JN : 0);
-    const int jtiles = (int)L::j_tiles(nwarps);
+    const int jtiles = (int)L::j_tiles(nth);
+    const int SW = nth + PAD;  // words per array per stage
+    const unsigned stage_bytes = (unsigned)L::stage_words(nth) * 4u;
 
     const Geom& g = prm.g;
     const int t = blockIdx.x;      // tile
@@ -211,7 +245,7 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
     const long long step = *((volatile long long*)&prm.st->step);
 
     if (tid == 0) {
-        dev::mbar_init(bar, 1);
+        for (int i = 0; i <= NSTAGE; ++i) dev::mbar_init(bar + i, 1);
         dev::fence_mbar_init();
     }
     for (int i = tid; i < L::NCNT; i += nth) sDir[i] = 0;
@@ -238,6 +272,20 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
     const float cxs = g.cx, cys = g.cy;
     unsigned bad_bits = 0;
     double ke_tot = 0.0;
+    unsigned gb = 0;  // particle batches taken so far (all species): stage slot and phase
+    // Fixed-point scale of the per-warp J tiles.  The current one particle
+    // gives to any one node, summed over its pieces, is at most |qtilde| (the
+    // pieces partition a move shorter than a cell per step and the weights sum
+    // to one), and a warp takes at most 32 particles per batch, so every tile
+    // sum stays below 2^30 with this scale: no overflow is possible.
+    float qbound = 0.f;
+    for (int s = 0; s < prm.nsp; ++s) {
+        const int ns = prm.sp[s].off[t + 1] - prm.sp[s].off[t];
+        const int ls = (ns + prm.chunks - 1) / prm.chunks;
+        qbound += (float)(((ls + nth - 1) / nth) * 32) * fabsf(prm.sp[s].qjz);
+    }
+    const float qscale = qbound > 0.f ? 1073741824.f / qbound : 1.f;
+    const float qinv = 1.f / qscale;
 
     for (int s = 0; s < prm.nsp; ++s) {
         const PushSpecies& S = prm.sp[s];
@@ -247,9 +295,36 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
         const int c0 = p0 + min(chunk * len, nt), c1 = p0 + min((chunk + 1) * len, nt);
         const float tem = S.tem, qjx = S.qjx, qjy = S.qjy, qjz = S.qjz;
         float ke = 0.f;
-        for (int base = c0; base < c1; base += nth) {
+        // Particle batches come in through a NSTAGE-deep pipeline of bulk copies
+        // (one per array, from the 16-byte aligned index below the batch start;
+        // the arrays are padded so the copy never leaves their allocation).
+        const int nb = (c1 - c0 + nth - 1) / nth;
+        auto issue = [&](int b, unsigned gslot) {
+            const int a4 = (c0 + b * nth) & ~3;
+            float* dst = sStage + (size_t)(gslot % NSTAGE) * L::stage_words(nth);
+            uint64_t* sb = sbar + gslot % NSTAGE;
+            const unsigned bytes = (unsigned)SW * 4u;
+            dev::mbar_arrive_expect_tx(sb, stage_bytes);
+            dev::bulk_load(dst, S.cell + a4, bytes, sb);
+            dev::bulk_load(dst + SW, S.x + a4, bytes, sb);
+            dev::bulk_load(dst + 2 * SW, S.y + a4, bytes, sb);
+            dev::bulk_load(dst + 3 * SW, S.ux + a4, bytes, sb);
+            dev::bulk_load(dst + 4 * SW, S.uy + a4, bytes, sb);
+            dev::bulk_load(dst + 5 * SW, S.uz + a4, bytes, sb);
+        };
+        if (tid == 0)
+            for (int b = 0; b < min(nb, NSTAGE - 1); ++b) issue(b, gb + b);
+        for (int b = 0; b < nb; ++b) {
+            const unsigned gcur = gb + b;
+            __syncthreads();  // every thread is done with batch b-1: its slot can be refilled
+            if (tid == 0 && b + NSTAGE - 1 < nb) issue(b + NSTAGE - 1, gcur + NSTAGE - 1);
+            const bool landed = dev::mbar_wait_bounded(sbar + gcur % NSTAGE, (gcur / NSTAGE) & 1u);
+            if (!landed) bad_bits |= ST_TIMEOUT;
+            const int base = c0 + b * nth;
+            const float* sp = sStage + (size_t)(gcur % NSTAGE) * L::stage_words(nth) +
+                              (base - (base & ~3)) + tid;
             const int p = base + tid;
-            const bool active = p < c1;
+            const bool active = p < c1 && landed;
             bool write = false;
             int dir = -1;  // -1: stays in this tile; 0..7: leaves towards that neighbour
             int ncell = 0;
@@ -260,9 +335,9 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
             float mtx = 2.f, mty = 2.f, mqvz = 0.f;
             int mdi = 0, mdj = 0, mlx = 0, mly = 0;
             if (active) {
-                const int c = S.cell[p];
-                const float x = S.x[p], y = S.y[p];
-                float ux = S.ux[p], uy = S.uy[p], uz = S.uz[p];
+                const int c = __float_as_int(sp[0]);
+                const float x = sp[SW], y = sp[2 * SW];
+                float ux = sp[3 * SW], uy = sp[4 * SW], uz = sp[5 * SW];
                 const int ix = c & 0xffff, iy = (int)((unsigned)c >> 16);
                 const int lx = ix - ix0, ly = iy - iy0;
                 if (c == HOLE || lx < 0 || lx >= T || ly < 0 || ly >= T) {
@@ -403,7 +478,7 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
 #pragma unroll
                             for (int i = 0; i < 8; ++i) v[i] = 0.f;
                         }
-                        deposit_warp<L::JW, L::JPLANE, L::PER_WARP>(has, o, v, sJw, lane);
+                        deposit_warp<L::JW, L::JPLANE, L::PER_WARP>(has, o, v, sJw, lane, qscale);
                         xa = xe;
                         ya = ye;
                     }
@@ -444,6 +519,7 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
                 }
             }
         }
+        gb += nb;
         ke_tot += (double)ke * S.ke_w;
     }
     __syncthreads();
@@ -466,8 +542,15 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
         const int rem = idx - comp * L::JPLANE;
         const int r = rem / L::JW, q = rem - r * L::JW;
         const int lx = q - 1, ly = r - 1;
-        float v = 0.f;
-        for (int w = 0; w < jtiles; ++w) v += sJ[w * L::JN + idx];
+        float v;
+        if constexpr (L::PER_WARP) {
+            long long acc = 0;
+            for (int w = 0; w < jtiles; ++w)
+                acc += reinterpret_cast<const int*>(sJ)[w * L::JN + idx];
+            v = (float)acc * qinv;
+        } else {
+            v = sJ[idx];
+        }
         const bool deep = whole && lx >= 2 && lx < T - 1 && ly >= 2 && ly < T - 1;
         if (!deep && v == 0.f) continue;
         int i = ix0 + lx, j = iy0 + ly;
@@ -481,17 +564,37 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
     }
 }
 
-// fmap == nullptr: only set the kernel's shared-memory limit for the largest
-// block (done once per process before any launch, so never during a capture)
+// Per-warp J tiles are used for T <= 16 when the CTA's shared memory allows
+// (PIC_J_PER_WARP=0 at build time turns them off).
+#ifndef PIC_J_PER_WARP
+#define PIC_J_PER_WARP 1
+#endif
+constexpr size_t SMEM_MAX = 227 * 1024;
+
+template <int T, bool PW>
+static cudaError_t set_smem_limit() {
+    size_t b = Tile<T, PW>::bytes(1024);
+    if (b > SMEM_MAX) b = SMEM_MAX;
+    return cudaFuncSetAttribute(k_push<T, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+}
+
+// fmap == nullptr: only set the kernels' shared-memory limits (done once per
+// process before any launch, so never during a stream capture)
 template <int T>
 static cudaError_t launch_T(const CUtensorMap* fmap, const PushParams& p, int threads,
                             cudaStream_t s) {
-    const size_t bytes = Tile<T>::bytes((threads + 31) / 32);
-    if (!fmap)
-        return cudaFuncSetAttribute(k_push<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)Tile<T>::bytes(32));
+    constexpr bool kPW = PIC_J_PER_WARP && T <= 16;
+    if (!fmap) {
+        cudaError_t e = set_smem_limit<T, false>();
+        if (e == cudaSuccess && kPW) e = set_smem_limit<T, kPW>();
+        return e;
+    }
     if (p.g.ntiles == 0) return cudaSuccess;
-    k_push<T><<<dim3(p.g.ntiles, p.chunks), threads, bytes, s>>>(*fmap, p);
+    const dim3 grid(p.g.ntiles, p.chunks);
+    if (kPW && Tile<T, kPW>::bytes(threads) <= SMEM_MAX)
+        k_push<T, kPW><<<grid, threads, Tile<T, kPW>::bytes(threads), s>>>(*fmap, p);
+    else
+        k_push<T, false><<<grid, threads, Tile<T, false>::bytes(threads), s>>>(*fmap, p);
     return cudaGetLastError();
 }
 

@@ -120,10 +120,15 @@ void free_species(SpeciesDev& s) {
     s.cap = 0;
 }
 
+// The particle kernels copy batches of up to 1024 particles from the 16-byte
+// aligned index at or below the batch start, so every array carries this many
+// spare elements past its capacity.
+constexpr int64_t kParticlePad = 1024 + 64;
+
 cudaError_t alloc_particles(SpeciesDev& s, int64_t cap) {
     cudaError_t e = cudaSuccess;
     auto A = [&](auto** p) {
-        if (e == cudaSuccess) e = dalloc(p, (size_t)cap);
+        if (e == cudaSuccess) e = dalloc(p, (size_t)(cap + kParticlePad));
     };
     A(&s.cell); A(&s.x); A(&s.y); A(&s.ux); A(&s.uy); A(&s.uz); A(&s.id);
     A(&s.ocell); A(&s.ox); A(&s.oy); A(&s.oux); A(&s.ouy); A(&s.ouz); A(&s.oid);
@@ -431,7 +436,7 @@ pic_status pic_init(const pic_config* cfg, void* cuda_stream, pic_sim** out) {
                 e = cudaMemsetAsync(s.dirc[b], 0, sizeof(int32_t) * 8 * g.ntiles, sim->stream);
         }
         if (e == cudaSuccess) e = dalloc(&s.evict, g.ntiles);
-        if (e == cudaSuccess) e = dalloc(&s.cursor, g.ntiles);
+        if (e == cudaSuccess) e = dalloc(&s.cursor, (size_t)c.nx * c.ny);
         for (int b = 0; b < 2 && e == cudaSuccess; ++b)
             e = cudaMemsetAsync(s.off[b], 0, sizeof(int32_t) * (g.ntiles + 1), sim->stream);
         const auto& sc = c.species[k];
@@ -517,7 +522,7 @@ pic_status pic_load_particles(pic_sim* sim, int species, int64_t n, const int32_
     if (e == cudaSuccess) e = copy_in(W.ouz, uz);
     if (e == cudaSuccess && track && id) e = copy_in(W.isrc, id);
     if (e == cudaSuccess) e = cudaMemsetAsync(&sim->st->load_bad, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = launch_load(sim->g, W, track, n, W.off[sim->cur], sim->st, s, 0, nullptr);
+    if (e == cudaSuccess) e = launch_load(sim->g, W, track, n, W.off[sim->cur], sim->st, s, 0, nullptr, nullptr);
     DevState h;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sim->st, sizeof h, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -528,8 +533,9 @@ pic_status pic_load_particles(pic_sim* sim, int species, int64_t n, const int32_
         return fail(sim, PIC_EINVAL, "%d particles with a cell outside the grid, an offset outside [0,1) or a non-finite momentum",
                     h.load_bad);
     }
+    // the FP64 charge-density buffer (2 nx*ny ints) serves as the cell-offset scratch
     e = launch_load(sim->g, W, track, n, W.off[sim->cur], sim->st, s, 1,
-                    (track && id) ? W.isrc : nullptr);
+                    (track && id) ? W.isrc : nullptr, reinterpret_cast<int32_t*>(sim->rho));
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         if (grow) free_species(W);

@@ -58,7 +58,7 @@ struct SpeciesDev {
     int32_t* leave[2];  // per tile: particles that left (ping-pong; the scan clears the idle one)
     int32_t* dirc[2];   // per tile x 8 directions: leavers by destination (ping-pong)
     int32_t* evict;   // per tile: stayers displaced by the new bookmarks
-    int32_t* cursor;  // per tile scratch for the initial load
+    int32_t* cursor;  // per cell scratch for the initial load (nx*ny)
     int64_t n;        // particles
     int64_t cap;      // capacity of the particle arrays
     // per-species constants (computed in double on the host, rounded once)
@@ -150,12 +150,15 @@ cudaError_t launch_grid_residuals(const Geom& g, const float* F, const float* J,
                                   const double* rho, const double* rho_prev, double background,
                                   double* out /* [gauss_max, cont_max, charge_sum] */,
                                   cudaStream_t s);
-// Initial sort of a staged species into tiles.  The input is staged in the
-// out arrays: ix in ocell, iy in hole, x..uz in ox..ouz; ids (optional) in
-// `staged_ids`.  phase 0 validates and counts per tile, phase 1 scans the
-// counts into `off` and scatters into the particle arrays.
+// Initial sort of a staged species into tiles, in a pseudo-random order inside
+// each tile.  The input is staged in the out arrays: ix in ocell, iy in hole,
+// x..uz in ox..ouz; ids (optional) in `staged_ids`.  phase 0 validates and
+// counts per key (sp.cursor holds nx*ny counters), phase 1 scans the counts into
+// `celloff` (nx*ny + 1 ints of scratch), writes the tile bookmarks `off` and
+// scatters into the particle arrays.
 cudaError_t launch_load(const Geom& g, SpeciesDev& sp, int track_ids, int64_t n, int32_t* off,
-                        DevState* st, cudaStream_t s, int phase, const int32_t* staged_ids);
+                        DevState* st, cudaStream_t s, int phase, const int32_t* staged_ids,
+                        int32_t* celloff);
 cudaError_t launch_unpack_cells(const int32_t* cell, int64_t n, int32_t* ix, int32_t* iy,
                                 cudaStream_t s);
 cudaError_t launch_offsets_to_i64(const int32_t* off, int64_t n, int64_t* out, cudaStream_t s);
