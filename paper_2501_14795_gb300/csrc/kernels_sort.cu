@@ -3,13 +3,14 @@
 // After the particle advance every tile t knows: stay[t] particles still in
 // place, leave[t] leavers appended to out[off_old[t] ...] with their vacated
 // positions in hole[off_old[t] ...], and dirc[t][d] leavers per destination.
-//   k_scan   (one CTA per species): new counts stay + incoming from the eight
-//            neighbours (step 1 of §4.3), exclusive scan -> off_new; also
-//            advances the step counter and primes the energy history.
-//   k_evict  (CTA per tile): stayers whose position falls outside the tile's
+//   k_count  (thread per tile): new counts = stayers + incoming from the eight
+//            neighbours (step 1 of §4.3);
+//   k_scan   (one CTA per species): exclusive scan -> off_new; also advances
+//            the step counter and primes the energy history.
+//   k_evict  (warp per tile): stayers whose position falls outside the tile's
 //            new range are displaced occupants; copy them to the tail of the
 //            tile's out section (they are re-inserted into their own tile).
-//   k_fill   (CTA per tile): target_idx = holes of t inside its new range plus
+//   k_fill   (warp per tile): target_idx = holes of t inside its new range plus
 //            the part of the new range outside the old one; source_idx =
 //            leavers of the neighbours heading to t plus t's displaced
 //            stayers (steps 2-4); then move source -> target (step 5).
@@ -36,18 +37,6 @@ __device__ __forceinline__ void dir_delta(int d, int& dx, int& dy) {
     dy = k / 3 - 1;
 }
 
-// warp-aggregated slot in a CTA counter; every lane of the warp must call it
-__device__ __forceinline__ int warp_slot(bool take, int* counter) {
-    const unsigned m = __ballot_sync(0xffffffffu, take);
-    if (!m) return 0;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(m) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(counter, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    return base + __popc(m & ((1u << lane) - 1u));
-}
-
 __device__ __forceinline__ void copy_particle(const SortSpecies& S, int from_out, int to_main,
                                               int track) {
     S.cell[to_main] = S.ocell[from_out];
@@ -61,13 +50,49 @@ __device__ __forceinline__ void copy_particle(const SortSpecies& S, int from_out
 
 constexpr int SCAN_THREADS = 1024;
 
+// Step 1 of §4.3, one thread per tile: the tile's new count = its stayers
+// (old count - leavers) + the leavers of the eight neighbours heading here;
+// kept in off_new[t] for the scan.  Also clears the idle parity's counters
+// for the next step and sums the leavers.
+__global__ void k_count(const SortParams prm) {
+    const int s = blockIdx.y;
+    const SortSpecies& S = prm.sp[s];
+    const Geom& g = prm.g;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int lv = 0;
+    if (t < g.ntiles) {
+        const int tx = t % g.ntx, ty = t / g.ntx;
+        lv = S.leave[t];
+        int c = S.off_old[t + 1] - S.off_old[t] - lv;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            int ddx, ddy;
+            dir_delta(d, ddx, ddy);
+            if ((g.ntx == 1 && ddx) || (g.nty == 1 && ddy)) continue;
+            const int sx = dev::wrapi(tx - ddx, g.ntx), sy = dev::wrapi(ty - ddy, g.nty);
+            c += S.dirc[(sy * g.ntx + sx) * 8 + d];
+        }
+        S.off_new[t] = c;
+        S.leave_next[t] = 0;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) S.dirc_next[t * 8 + d] = 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lv += __shfl_xor_sync(0xffffffffu, lv, o);
+    if ((threadIdx.x & 31) == 0 && lv)
+        atomicAdd(reinterpret_cast<unsigned long long*>(&prm.st->leavers_acc[s]),
+                  (unsigned long long)lv);
+}
+
+// In-place exclusive scan of the counts in off_new (one CTA per species),
+// 4096 tiles per round with coalesced loads; off_new[ntiles] = total, which
+// must equal the particle count.  Block 0 also advances the time level and
+// primes the history slots of level n+1.
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const SortParams prm) {
     __shared__ int sWarp[32];
-    __shared__ long long sLeavers[32];
     const int s = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (s == 0 && tid == 0) {
-        // advance the time level and prime the history slots of level n+1
         const long long n = prm.st->step + 1;
         prm.hist_e[n & (HIST - 1)] = 0.0;
         prm.hist_b[n & (HIST - 1)] = 0.0;
@@ -76,104 +101,85 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const SortParams prm) {
     }
     if (s >= prm.nsp) return;
     const SortSpecies& S = prm.sp[s];
-    const Geom& g = prm.g;
-    const int nt = g.ntiles;
-    const int per = (nt + SCAN_THREADS - 1) / SCAN_THREADS;
-    const int t0 = min(tid * per, nt), t1 = min(t0 + per, nt);
-
-    // pass 1: new count of each of my tiles (kept in off_new[t]) and their sum
-    int mysum = 0;
-    long long myleave = 0;
-    for (int t = t0; t < t1; ++t) {
-        const int tx = t % g.ntx, ty = t / g.ntx;
-        int c = S.off_old[t + 1] - S.off_old[t] - S.leave[t];  // stayers
-        myleave += S.leave[t];
-        S.leave_next[t] = 0;  // counters of the next step (other parity)
+    const int nt = prm.g.ntiles;
+    int carry = 0;
+    for (int base = 0; base < nt; base += 4 * SCAN_THREADS) {
+        const int i0 = base + 4 * tid;
+        int v[4];
 #pragma unroll
-        for (int d = 0; d < 8; ++d) S.dirc_next[t * 8 + d] = 0;
-        for (int d = 0; d < 8; ++d) {
-            int ddx, ddy;
-            dir_delta(d, ddx, ddy);
-            if (g.ntx == 1 && ddx) continue;
-            if (g.nty == 1 && ddy) continue;
-            const int sx = dev::wrapi(tx - ddx, g.ntx), sy = dev::wrapi(ty - ddy, g.nty);
-            c += S.dirc[(sy * g.ntx + sx) * 8 + d];
-        }
-        S.off_new[t] = c;
-        mysum += c;
-    }
-    // exclusive block scan of the per-thread sums
-    int incl = mysum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    long long lv = myleave;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lv += __shfl_xor_sync(0xffffffffu, lv, o);
-    if (lane == 31) sWarp[wid] = incl;
-    if (lane == 0) sLeavers[wid] = lv;
-    __syncthreads();
-    if (wid == 0) {
-        const int w = sWarp[lane];
-        int wi = w;
+        for (int k = 0; k < 4; ++k) v[k] = i0 + k < nt ? S.off_new[i0 + k] : 0;
+        const int mine = v[0] + v[1] + v[2] + v[3];
+        int incl = mine;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += v;
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
         }
-        sWarp[lane] = wi - w;  // exclusive prefix of the warp sums
-    }
-    __syncthreads();
-    // pass 2: each thread rewrites only its own tiles' entries
-    int run = sWarp[wid] + incl - mysum;
-    for (int t = t0; t < t1; ++t) {
-        const int c = S.off_new[t];
-        S.off_new[t] = run;
-        run += c;
-    }
-    if (tid == SCAN_THREADS - 1) {
-        // the last thread's running sum is the grand total
-        S.off_new[nt] = run;
-        if (run != S.n) dev::set_status(prm.st, ST_SORT);
+        if (lane == 31) sWarp[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const int w = sWarp[lane];
+            int wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += u;
+            }
+            sWarp[lane] = wi;  // inclusive prefix of the warp sums
+        }
+        __syncthreads();
+        int run = carry + (wid ? sWarp[wid - 1] : 0) + incl - mine;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (i0 + k < nt) S.off_new[i0 + k] = run;
+            run += v[k];
+        }
+        carry += sWarp[31];
+        __syncthreads();  // sWarp is rewritten by the next round
     }
     if (tid == 0) {
-        long long tot = 0;
-        for (int w = 0; w < SCAN_THREADS / 32; ++w) tot += sLeavers[w];
-        prm.st->leavers_sp[s] = tot;
+        S.off_new[nt] = carry;
+        if (carry != S.n) dev::set_status(prm.st, ST_SORT);
+        prm.st->leavers_sp[s] = prm.st->leavers_acc[s];
+        prm.st->leavers_acc[s] = 0;
     }
 }
 
-__global__ void k_evict(const SortParams prm) {
-    __shared__ int sCount;
-    const int t = blockIdx.x, s = blockIdx.y;
+// Warp-per-tile kernels: a warp takes one tile; slots come from the warp's
+// ballots (register counters), so no CTA barrier or shared atomic is needed.
+constexpr int SORT_WARPS = 4;
+
+__global__ void __launch_bounds__(32 * SORT_WARPS) k_evict(const SortParams prm) {
+    const int s = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * SORT_WARPS + (threadIdx.x >> 5);
     const SortSpecies& S = prm.sp[s];
+    if (t >= prm.g.ntiles) return;
     const int p0 = S.off_old[t], p1 = S.off_old[t + 1];
     const int r0 = S.off_new[t], r1 = S.off_new[t + 1];
     const int lv = S.leave[t];
     if (r0 < 0 || r1 < r0 || r1 > S.n || p1 - p0 < lv) {
-        if (threadIdx.x == 0) dev::set_status(prm.st, ST_SORT);
+        if (lane == 0) dev::set_status(prm.st, ST_SORT);
         return;
     }
-    if (threadIdx.x == 0) sCount = 0;
-    __syncthreads();
     // positions of the old range outside the new one: [p0, min(r0,p1)) and [max(r1,p0), p1)
     const int a1 = min(r0, p1), b0 = max(r1, p0);
     const int na = max(a1 - p0, 0), nb = max(p1 - b0, 0);
     const int tot = na + nb;
+    const unsigned lt = (1u << lane) - 1u;
+    int count = 0;
     bool overflow = false;
-    for (int base = 0; base < tot; base += blockDim.x) {
-        const int k = base + threadIdx.x;
+    for (int base = 0; base < tot; base += 32) {
+        const int k = base + lane;
         int p = -1;
         bool take = false;
         if (k < tot) {
             p = k < na ? p0 + k : b0 + (k - na);
             take = S.cell[p] != HOLE;
         }
-        const int slot = warp_slot(take, &sCount);
+        const unsigned m = __ballot_sync(0xffffffffu, take);
         if (take) {
-            const int q = p0 + lv + slot;
+            const int q = p0 + lv + count + __popc(m & lt);
             if (q < p1) {
                 S.ocell[q] = S.cell[p];
                 S.ox[q] = S.x[p];
@@ -186,31 +192,34 @@ __global__ void k_evict(const SortParams prm) {
                 overflow = true;
             }
         }
+        count += __popc(m);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) S.evict[t] = min(sCount, p1 - p0 - lv);
+    if (lane == 0) S.evict[t] = min(count, p1 - p0 - lv);
     if (overflow) dev::set_status(prm.st, ST_SORT);
 }
 
-__global__ void k_fill(const SortParams prm) {
-    __shared__ int sSrc, sTgt;
-    const int t = blockIdx.x, s = blockIdx.y;
+__global__ void __launch_bounds__(32 * SORT_WARPS) k_fill(const SortParams prm) {
+    const int s = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * SORT_WARPS + (threadIdx.x >> 5);
     const SortSpecies& S = prm.sp[s];
     const Geom& g = prm.g;
+    if (t >= g.ntiles) return;
     const int T = g.T;
     const int tx = t % g.ntx, ty = t / g.ntx;
     const int p0 = S.off_old[t], p1 = S.off_old[t + 1];
     const int r0 = S.off_new[t], r1 = S.off_new[t + 1];
     const int cap = r1 - r0;
-    if (r0 < 0 || r1 < r0 || r1 > S.n || S.leave[t] + S.evict[t] > p1 - p0) {
-        if (threadIdx.x == 0) dev::set_status(prm.st, ST_SORT);
+    const int lvt = S.leave[t], ev = S.evict[t];
+    if (r0 < 0 || r1 < r0 || r1 > S.n || lvt + ev > p1 - p0) {
+        if (lane == 0) dev::set_status(prm.st, ST_SORT);
         return;
     }
-    if (threadIdx.x == 0) {
-        sSrc = 0;
-        sTgt = 0;
-    }
-    __syncthreads();
+    // particles to place: incoming = new count - stayers, plus displaced stayers
+    const int need = cap - (p1 - p0 - lvt) + ev;
+    if (need == 0) return;
+    const unsigned lt = (1u << lane) - 1u;
+    int nsrc = 0, ntgt = 0;
     bool overflow = false;
 
     // source_idx: neighbours' leavers heading here (distinct neighbour tiles only)
@@ -227,88 +236,87 @@ __global__ void k_fill(const SortParams prm) {
     for (int k = 0; k < nnb; ++k) {
         const int nb = nbs[k];
         const int q0 = S.off_old[nb], nl = S.leave[nb];
-        for (int base = 0; base < nl; base += blockDim.x) {
-            const int i = base + threadIdx.x;
+        for (int base = 0; base < nl; base += 32) {
+            const int i = base + lane;
             const bool take = i < nl && tile_of(S.ocell[q0 + i], T, g.ntx) == t;
-            const int slot = warp_slot(take, &sSrc);
+            const unsigned m = __ballot_sync(0xffffffffu, take);
             if (take) {
+                const int slot = nsrc + __popc(m & lt);
                 if (slot < cap) S.isrc[r0 + slot] = q0 + i;
                 else overflow = true;
             }
+            nsrc += __popc(m);
         }
     }
     // ... plus this tile's displaced stayers
-    {
-        const int q0 = p0 + S.leave[t], ne = S.evict[t];
-        for (int base = 0; base < ne; base += blockDim.x) {
-            const int i = base + threadIdx.x;
-            const bool take = i < ne;
-            const int slot = warp_slot(take, &sSrc);
-            if (take) {
-                if (slot < cap) S.isrc[r0 + slot] = q0 + i;
-                else overflow = true;
-            }
+    for (int base = 0; base < ev; base += 32) {
+        const int i = base + lane;
+        if (i < ev) {
+            const int slot = nsrc + i;
+            if (slot < cap) S.isrc[r0 + slot] = p0 + lvt + i;
+            else overflow = true;
         }
     }
+    nsrc += ev;
     // target_idx: holes of this tile inside its new range ...
-    {
-        const int nl = S.leave[t];
-        for (int base = 0; base < nl; base += blockDim.x) {
-            const int i = base + threadIdx.x;
-            int h = -1;
-            if (i < nl) h = S.hole[p0 + i];
-            const bool take = i < nl && h >= r0 && h < r1;
-            const int slot = warp_slot(take, &sTgt);
-            if (take) {
-                if (slot < cap) S.fslot[r0 + slot] = h;
-                else overflow = true;
-            }
+    for (int base = 0; base < lvt; base += 32) {
+        const int i = base + lane;
+        const int h = i < lvt ? S.hole[p0 + i] : -1;
+        const bool take = i < lvt && h >= r0 && h < r1;
+        const unsigned m = __ballot_sync(0xffffffffu, take);
+        if (take) {
+            const int slot = ntgt + __popc(m & lt);
+            if (slot < cap) S.fslot[r0 + slot] = h;
+            else overflow = true;
         }
+        ntgt += __popc(m);
     }
     // ... plus the part of the new range outside the old one
     {
         const int a1 = min(p0, r1), b0 = max(p1, r0);
         const int na = max(a1 - r0, 0), nb = max(r1 - b0, 0);
         const int tot = na + nb;
-        for (int base = 0; base < tot; base += blockDim.x) {
-            const int k = base + threadIdx.x;
-            const bool take = k < tot;
-            const int slot = warp_slot(take, &sTgt);
-            if (take) {
+        for (int base = 0; base < tot; base += 32) {
+            const int k = base + lane;
+            if (k < tot) {
+                const int slot = ntgt + k;
                 const int pos = k < na ? r0 + k : b0 + (k - na);
                 if (slot < cap) S.fslot[r0 + slot] = pos;
                 else overflow = true;
             }
         }
+        ntgt += tot;
     }
-    __syncthreads();
-    const int m = sSrc;
-    if (m != sTgt || m > cap) {
-        if (threadIdx.x == 0) dev::set_status(prm.st, ST_SORT);
+    __syncwarp();
+    if (nsrc != ntgt || nsrc != need || nsrc > cap || overflow) {
+        if (lane == 0) dev::set_status(prm.st, ST_SORT);
         return;
     }
-    if (overflow) dev::set_status(prm.st, ST_SORT);
     // move source -> target
-    for (int k = threadIdx.x; k < m; k += blockDim.x)
-        copy_particle(S, S.isrc[r0 + k], S.fslot[r0 + k], prm.track_ids);
+    for (int k = lane; k < nsrc; k += 32) copy_particle(S, S.isrc[r0 + k], S.fslot[r0 + k], prm.track_ids);
 }
 
 }  // namespace
 
 cudaError_t launch_scan(const SortParams& p, cudaStream_t s) {
+    if (p.nsp > 0 && p.g.ntiles > 0) {
+        k_count<<<dim3((p.g.ntiles + 255) / 256, p.nsp), 256, 0, s>>>(p);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     k_scan<<<p.nsp > 0 ? p.nsp : 1, SCAN_THREADS, 0, s>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_evict(const SortParams& p, int threads, cudaStream_t s) {
+cudaError_t launch_evict(const SortParams& p, int, cudaStream_t s) {
     if (p.nsp == 0 || p.g.ntiles == 0) return cudaSuccess;
-    k_evict<<<dim3(p.g.ntiles, p.nsp), threads, 0, s>>>(p);
+    k_evict<<<dim3((p.g.ntiles + SORT_WARPS - 1) / SORT_WARPS, p.nsp), 32 * SORT_WARPS, 0, s>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fill(const SortParams& p, int threads, cudaStream_t s) {
+cudaError_t launch_fill(const SortParams& p, int, cudaStream_t s) {
     if (p.nsp == 0 || p.g.ntiles == 0) return cudaSuccess;
-    k_fill<<<dim3(p.g.ntiles, p.nsp), threads, 0, s>>>(p);
+    k_fill<<<dim3((p.g.ntiles + SORT_WARPS - 1) / SORT_WARPS, p.nsp), 32 * SORT_WARPS, 0, s>>>(p);
     return cudaGetLastError();
 }
 

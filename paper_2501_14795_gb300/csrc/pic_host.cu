@@ -236,7 +236,7 @@ int enqueue_step(pic_sim* sim, cudaStream_t s, int b, cudaEvent_t ev_a, cudaEven
     n += sim->g.ntiles > 0;
     if (ev_b && (e = cudaEventRecordWithFlags(ev_b, s, rec)) != cudaSuccess) goto bad;
     if ((e = launch_scan(sp, s)) != cudaSuccess) goto bad;
-    n += 1;
+    n += (sp.nsp > 0 && sim->g.ntiles > 0) ? 2 : 1;  // count + scan
     if ((e = launch_evict(sp, threads, s)) != cudaSuccess) goto bad;
     if ((e = launch_fill(sp, threads, s)) != cudaSuccess) goto bad;
     n += (sp.nsp > 0 && sim->g.ntiles > 0) ? 2 : 0;

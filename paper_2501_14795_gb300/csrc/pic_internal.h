@@ -38,6 +38,7 @@ struct DevState {
     unsigned pad;
     long long step;      // time level n of the current fields
     long long leavers_sp[MAX_SPECIES];  // particles that changed tile in the last step
+    long long leavers_acc[MAX_SPECIES]; // running sum of the current step (k_count -> k_scan)
     int load_bad;        // pic_load_particles validation failures
     int pad2;
 };

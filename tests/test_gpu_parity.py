@@ -459,4 +459,5 @@ def test_timing_events_and_launch_count():
         sim.step(10)
         ms, cnt = pic.pic_timing(sim.h, reset=True)
         assert cnt == 10 and ms > 0
-        assert pic.pic_kernel_launches(sim.h) == 50
+        # per step: advance, count, scan, evict, fill, Yee
+        assert pic.pic_kernel_launches(sim.h) == 60
