@@ -185,6 +185,70 @@ const char* pic_last_error(const pic_sim* sim);
 /* Free everything.  NULL is accepted. */
 void pic_destroy(pic_sim* sim);
 
+/* ---- Batches: many independent simulations stepped together --------------
+ * The paper steps one simulation; a batch advances many independent ones (any
+ * mix of grid sizes, particle counts and tile sizes) with one kernel per stage
+ * of Listing 3.1 for all of them: the particle advance of every member in one
+ * persistent launch per (tile size, threads) group over a work list of
+ * (member, tile, slice) items, the re-sort over all members' tiles, the field
+ * advance over all members' field tiles; each step is a captured CUDA graph.
+ * Each member computes exactly what pic_step computes for it alone. */
+typedef struct pic_batch pic_batch;
+
+/* Create n simulations with the configurations cfgs[0..n-1], all on
+ * `cuda_stream`; out[0..n-1] receive the handles (all NULL on error).  Each is
+ * an ordinary pic_sim (load particles, set fields, read diagnostics through
+ * the calls above).  Errors as pic_init, for the first failing member. */
+pic_status pic_init_batch(const pic_config* cfgs, int n, void* cuda_stream, pic_sim** out);
+
+/* Group n existing simulations into a batch stepped on `cuda_stream`.  Every
+ * member must have been created on that same stream (so single-simulation
+ * calls on a member stay ordered with the batch's steps), none may belong to
+ * another batch, and all must share the PIC_STRICT_FP setting.  The caller
+ * keeps ownership of the members and must destroy the batch before them.
+ * Returns PIC_EINVAL (message through pic_batch_last_error), PIC_ENOMEM,
+ * PIC_ECUDA. */
+pic_status pic_batch_create(pic_sim* const* members, int n, void* cuda_stream, pic_batch** out);
+
+/* Advance every member nsteps time steps (asynchronous, like pic_step).
+ * Members reloaded, re-tiled or stepped on their own since the last call are
+ * picked up (the step graphs are rebuilt). */
+pic_status pic_batch_step(pic_batch* batch, int nsteps);
+
+/* Wait for the stream; return the first member's non-OK sticky status
+ * (PIC_OK if none), its index in *member if member is non-NULL (-1 if none). */
+pic_status pic_batch_sync(pic_batch* batch, int* member);
+
+/* Number of kernels the batch has launched, and per step. */
+int64_t pic_batch_kernel_launches(const pic_batch* batch, int* per_step);
+
+const char* pic_batch_last_error(const pic_batch* batch);
+
+/* Free the batch (not its members).  NULL is accepted. */
+void pic_batch_destroy(pic_batch* batch);
+
+/* ---- Autotuner ---------------------------------------------------------------
+ * Pick the tile size T in {8, 16, 32} (those dividing nx and ny) and the
+ * threads per CTA in {64, 128, 256, 512} of the particle kernels for a loaded
+ * simulation by timing `steps` steps (CUDA events, after two warm-up steps) of
+ * each candidate on its own particles and fields.  The simulation's state
+ * (particles, fields, energy history, step count) is saved before and put
+ * back afterwards, so tuning does not advance the physics; the particles'
+ * order inside a tile may change.  The winner is applied to the simulation and
+ * cached for the process, keyed by (nx, ny, loaded particles per cell, species,
+ * PIC_STRICT_FP, device); a later call with the same key applies the cached
+ * choice without timing unless `force` is non-zero.  tile, threads and
+ * step_ms (the winner's mean step time; 0 for a cached choice) may be NULL.
+ * Synchronises.  Needs free device memory for one copy of the particles. */
+pic_status pic_autotune(pic_sim* sim, int steps, int force, int* tile, int* threads,
+                        double* step_ms);
+
+/* Change the tile size T of a loaded simulation in place (re-sorts the
+ * particles into the new tiles); `threads` > 0 also sets the threads per CTA.
+ * Synchronises.  PIC_EINVAL if T is not in {8, 16, 32} or does not divide
+ * the grid. */
+pic_status pic_set_tiling(pic_sim* sim, int tile, int threads);
+
 /* ---- Allocation-free tile sort ---------------------------------------------
  * The paper has no counterpart: this entry point is for callers that cannot
  * call cudaMalloc (host callbacks, allocator hooks, plugins whose host

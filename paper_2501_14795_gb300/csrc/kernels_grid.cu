@@ -27,13 +27,13 @@ constexpr int EW = YX + 3, EH = YY + 3;
 constexpr int BW = YX + 2, BH = YY + 2;
 constexpr int JWY = YX + 1, JHY = YY + 1;
 
-__global__ void __launch_bounds__(YTHREADS) k_yee(const YeeParams prm) {
+__device__ __forceinline__ void yee_tile(const YeeParams& prm, int bx, int by) {
     __shared__ float sE[3][EH][EW];
     __shared__ float sB[3][BH][BW];
     __shared__ float sJ[3][JHY][JWY];
     __shared__ double sRed[32];
     const Geom& g = prm.g;
-    const int i0 = blockIdx.x * YX, j0 = blockIdx.y * YY;
+    const int i0 = bx * YX, j0 = by * YY;
     const int tid = threadIdx.x;
     const long long cs = g.cstride;
     const float* Ein = prm.Fin;
@@ -137,6 +137,25 @@ __global__ void __launch_bounds__(YTHREADS) k_yee(const YeeParams prm) {
     if (tid == 0) atomicAdd(&prm.hist_e[n & (HIST - 1)], 0.5 * se * dxdy);
     const double sb = dev::block_sum((double)wb, sRed);
     if (tid == 0) atomicAdd(&prm.hist_b[n & (HIST - 1)], 0.5 * sb * dxdy);
+}
+
+__global__ void __launch_bounds__(YTHREADS) k_yee(const YeeParams prm) {
+    yee_tile(prm, blockIdx.x, blockIdx.y);
+}
+
+// batched: one CTA per field tile of the flattened tile list of all members
+__global__ void __launch_bounds__(YTHREADS) k_yee_batch(const YeeBatch b) {
+    const int gt = blockIdx.x;
+    int lo = 0, hi = b.nmembers - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.ytile_start[mid] <= gt) lo = mid;
+        else hi = mid - 1;
+    }
+    const YeeParams& P = b.members[lo];
+    const int t = gt - b.ytile_start[lo];
+    const int nbx = (P.g.nx + YX - 1) / YX;
+    yee_tile(P, t % nbx, t / nbx);
 }
 
 // -------------------------------------------------------- grid utilities
@@ -395,6 +414,14 @@ int grid_for(long long n, int threads) {
 }
 
 }  // namespace
+
+int yee_tiles(const Geom& g) { return ((g.nx + YX - 1) / YX) * ((g.ny + YY - 1) / YY); }
+
+cudaError_t launch_yee_batch(const YeeBatch& b, cudaStream_t s) {
+    if (b.nmembers == 0 || b.total_ytiles == 0) return cudaSuccess;
+    k_yee_batch<<<b.total_ytiles, YTHREADS, 0, s>>>(b);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_yee(const YeeParams& p, cudaStream_t s) {
     dim3 grid((p.g.nx + YX - 1) / YX, (p.g.ny + YY - 1) / YY);

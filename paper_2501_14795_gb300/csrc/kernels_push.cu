@@ -53,6 +53,7 @@ constexpr int PAD = 4;     // a batch is copied from a 16-byte aligned start: <=
 //   [E|B halo FLD floats][J tiles: one per warp (PW) or one per CTA]
 //   [NSTAGE particle stages: 6 arrays x (nth + PAD) 32-bit words]
 //   [mbarriers: halo + one per stage][counters][FP64 reduction scratch]
+//   [one simulation's parameters (batched launch)]
 template <int T, bool PW>
 struct Tile {
     static constexpr int FW = T + 8;  // TMA box columns: cells -4 .. T+3
@@ -77,7 +78,14 @@ struct Tile {
     static __host__ __device__ size_t off_red(int nth) {
         return (off_cnt(nth) + NCNT * 4 + 7) & ~(size_t)7;
     }
+    static __host__ __device__ size_t off_prm(int nth) {
+        return (off_red(nth) + 32 * sizeof(double) + 15) & ~(size_t)15;
+    }
     static __host__ __device__ size_t bytes(int nth) { return off_red(nth) + 32 * sizeof(double); }
+    // batched launch: one simulation's parameters, then the current item index
+    static __host__ __device__ size_t bytes_batch(int nth) {
+        return off_prm(nth) + sizeof(PushParams) + 16;
+    }
 };
 
 __device__ __forceinline__ float interp(const float* F, int fw, int col, int row, float a0,
@@ -219,9 +227,14 @@ __device__ __forceinline__ void deposit_warp(bool has, int o, const float v[8], 
     }
 }
 
+// One work item: slice `chunk` of tile t of the simulation `prm` (steps 1-6
+// above).  The caller has initialised the mbarriers (halo: bar[0], stages:
+// bar[1..NSTAGE]); fphase is the parity of the next halo phase and gb counts
+// the particle batches taken so far, both carried from item to item.
+// Returns false (after flagging the timeout) if a bounded wait ran out.
 template <int T, bool PW>
-__global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorMap fmap,
-                                               const PushParams prm) {
+__device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorMap* fmap, int t,
+                                          int chunk, unsigned& fphase, unsigned& gb) {
     using L = Tile<T, PW>;
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
@@ -238,28 +251,23 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
     const unsigned stage_bytes = (unsigned)L::stage_words(nth) * 4u;
 
     const Geom& g = prm.g;
-    const int t = blockIdx.x;      // tile
-    const int chunk = blockIdx.y;  // slice of the tile's particles taken by this CTA
     const int tx = t % g.ntx, ty = t / g.ntx;
     const int ix0 = tx * T, iy0 = ty * T;
     const long long step = *((volatile long long*)&prm.st->step);
 
-    if (tid == 0) {
-        for (int i = 0; i <= NSTAGE; ++i) dev::mbar_init(bar + i, 1);
-        dev::fence_mbar_init();
-    }
     for (int i = tid; i < L::NCNT; i += nth) sDir[i] = 0;
     __syncthreads();
     if (tid == 0) {
         dev::mbar_arrive_expect_tx(bar, L::FLD * 4);
         // box origin: column ix0 = cell ix0 - GX, row iy0 = cell iy0 - GY
-        dev::tma_load_3d(sF, &fmap, ix0, iy0, 0, bar);
+        dev::tma_load_3d(sF, fmap, ix0, iy0, 0, bar);
     }
     for (int i = tid; i < jtiles * L::JN; i += nth) sJ[i] = 0.f;
-    const bool ok = dev::mbar_wait_bounded(bar, 0);
+    const bool ok = dev::mbar_wait_bounded(bar, fphase);
+    fphase ^= 1u;
     if (__syncthreads_or(!ok)) {
         if (tid == 0) dev::set_status(prm.st, ST_TIMEOUT);
-        return;
+        return false;
     }
 
     const float* sEx = sF;
@@ -272,7 +280,6 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
     const float cxs = g.cx, cys = g.cy;
     unsigned bad_bits = 0;
     double ke_tot = 0.0;
-    unsigned gb = 0;  // particle batches taken so far (all species): stage slot and phase
     // Fixed-point scale of the per-warp J tiles.  The current one particle
     // gives to any one node, summed over its pieces, is at most |qtilde| (the
     // pieces partition a move shorter than a cell per step and the weights sum
@@ -562,6 +569,53 @@ __global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorM
         else
             atomicAdd(dst, v);
     }
+    return true;
+}
+
+__device__ __forceinline__ void init_barriers(uint64_t* bar) {
+    if (threadIdx.x == 0) {
+        for (int i = 0; i <= NSTAGE; ++i) dev::mbar_init(bar + i, 1);
+        dev::fence_mbar_init();
+    }
+}
+
+// One simulation: CTA (tile, chunk) = (blockIdx.x, blockIdx.y).
+template <int T, bool PW>
+__global__ void __launch_bounds__(1024) k_push(const __grid_constant__ CUtensorMap fmap,
+                                               const PushParams prm) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    init_barriers(reinterpret_cast<uint64_t*>(smem + Tile<T, PW>::off_misc(blockDim.x)));
+    unsigned fphase = 0, gb = 0;
+    push_item<T, PW>(prm, &fmap, blockIdx.x, blockIdx.y, fphase, gb);
+}
+
+// Many simulations in one persistent launch: each CTA takes work items
+// (member, tile, chunk) from a global counter until the list is exhausted (the
+// list is ordered costliest first, so this is greedy longest-first
+// balancing); the item's parameters are copied into shared memory and its
+// TMA descriptor is read from global memory.
+template <int T, bool PW>
+__global__ void __launch_bounds__(1024) k_push_batch(const PushBatch pb) {
+    using L = Tile<T, PW>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    init_barriers(reinterpret_cast<uint64_t*>(smem + L::off_misc(blockDim.x)));
+    PushParams* sPrm = reinterpret_cast<PushParams*>(smem + L::off_prm(blockDim.x));
+    int* sItem = reinterpret_cast<int*>(smem + L::off_prm(blockDim.x) + sizeof(PushParams));
+    unsigned fphase = 0, gb = 0;
+    while (true) {
+        __syncthreads();  // the previous item is done with shared memory
+        if (threadIdx.x == 0) *sItem = atomicAdd(pb.next, 1);
+        __syncthreads();
+        const int it = *sItem;
+        if (it >= pb.nitems) return;
+        const int4 item = pb.items[it];
+        const int4* src = reinterpret_cast<const int4*>(pb.members + item.x);
+        int4* dst = reinterpret_cast<int4*>(sPrm);
+        for (int i = threadIdx.x; i < (int)(sizeof(PushParams) / 16); i += blockDim.x)
+            dst[i] = src[i];
+        __syncthreads();
+        if (!push_item<T, PW>(*sPrm, pb.tmaps + item.x, item.y, item.z, fphase, gb)) return;
+    }
 }
 
 // Per-warp J tiles are used for T <= 16 when the CTA's shared memory allows
@@ -573,9 +627,14 @@ constexpr size_t SMEM_MAX = 227 * 1024;
 
 template <int T, bool PW>
 static cudaError_t set_smem_limit() {
-    size_t b = Tile<T, PW>::bytes(1024);
+    static_assert(sizeof(PushParams) % 16 == 0, "parameters are copied as int4");
+    size_t b = Tile<T, PW>::bytes_batch(1024);
     if (b > SMEM_MAX) b = SMEM_MAX;
-    return cudaFuncSetAttribute(k_push<T, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_push<T, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_push_batch<T, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)b);
 }
 
 // fmap == nullptr: only set the kernels' shared-memory limits (done once per
@@ -598,10 +657,56 @@ static cudaError_t launch_T(const CUtensorMap* fmap, const PushParams& p, int th
     return cudaGetLastError();
 }
 
+template <int T, bool PW>
+static cudaError_t launch_batch_TP(const PushBatch& b, int threads, int grid, cudaStream_t s) {
+    const size_t bytes = Tile<T, PW>::bytes_batch(threads);
+    if (grid <= 0) {
+        // persistent: as many CTAs as can be resident at once
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_batch<T, PW>, threads,
+                                                              bytes);
+        if (e != cudaSuccess) return e;
+        grid = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    if (grid > b.nitems) grid = b.nitems;
+    k_push_batch<T, PW><<<grid, threads, bytes, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <int T>
+static cudaError_t launch_batch_T(const PushBatch& b, int threads, int grid, cudaStream_t s) {
+    constexpr bool kPW = PIC_J_PER_WARP && T <= 16;
+    if (b.nitems == 0) return cudaSuccess;
+    if (kPW && Tile<T, kPW>::bytes_batch(threads) <= SMEM_MAX)
+        return launch_batch_TP<T, kPW>(b, threads, grid, s);
+    return launch_batch_TP<T, false>(b, threads, grid, s);
+}
+
 }  // namespace PIC_VARIANT
+
+cudaError_t PIC_CAT(launch_push_batch_, PIC_VARIANT)(const PushBatch& b, int T, int threads,
+                                                     int grid, cudaStream_t s) {
+    switch (T) {
+        case 8: return PIC_VARIANT::launch_batch_T<8>(b, threads, grid, s);
+        case 16: return PIC_VARIANT::launch_batch_T<16>(b, threads, grid, s);
+        case 32: return PIC_VARIANT::launch_batch_T<32>(b, threads, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t PIC_CAT(launch_push_, PIC_VARIANT)(const CUtensorMap* fmap, const PushParams& p,
                                                int threads, cudaStream_t s) {
+    if (!fmap) {
+        // raise the shared-memory limits of every tile size (a simulation may
+        // be re-tiled later)
+        cudaError_t e = PIC_VARIANT::launch_T<8>(nullptr, p, threads, s);
+        if (e == cudaSuccess) e = PIC_VARIANT::launch_T<16>(nullptr, p, threads, s);
+        if (e == cudaSuccess) e = PIC_VARIANT::launch_T<32>(nullptr, p, threads, s);
+        return e;
+    }
     switch (p.g.T) {
         case 8: return PIC_VARIANT::launch_T<8>(fmap, p, threads, s);
         case 16: return PIC_VARIANT::launch_T<16>(fmap, p, threads, s);

@@ -1,9 +1,8 @@
 // Tile re-sort (§4.3, the Jocksch scheme adapted to warp ballots and scans).
 //
-// After the particle advance every tile t knows: stay[t] particles still in
-// place, leave[t] leavers appended to out[off_old[t] ...] with their vacated
+// After the particle advance every tile t knows: leave[t] leavers appended to out[off_old[t] ...] with their vacated
 // positions in hole[off_old[t] ...], and dirc[t][d] leavers per destination.
-//   k_count  (thread per tile): new counts = stayers + incoming from the eight
+//   count  (thread per tile): new counts = stayers + incoming from the eight
 //            neighbours (step 1 of §4.3);
 //   k_scan   (one CTA per species): exclusive scan -> off_new; also advances
 //            the step counter and primes the energy history.
@@ -16,7 +15,9 @@
 //            stayers (steps 2-4); then move source -> target (step 5).
 // Only leavers and displaced particles move; a particle's bytes are read and
 // written once more.  No per-particle global atomics: slots come from warp
-// ballots and CTA-local counters.
+// ballots.  Every step has a single-simulation kernel and a batched one that
+// flattens the tiles of many simulations into one grid; both call the same
+// per-tile bodies.
 #include "device_util.cuh"
 #include "pic_internal.h"
 
@@ -37,6 +38,17 @@ __device__ __forceinline__ void dir_delta(int d, int& dx, int& dy) {
     dy = k / 3 - 1;
 }
 
+// member m of a batch whose items start at start[m] (start[nmembers] = total)
+__device__ __forceinline__ int find_member(const int* start, int n, int g) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 __device__ __forceinline__ void copy_particle(const SortSpecies& S, int from_out, int to_main,
                                               int track) {
     S.cell[to_main] = S.ocell[from_out];
@@ -50,33 +62,35 @@ __device__ __forceinline__ void copy_particle(const SortSpecies& S, int from_out
 
 constexpr int SCAN_THREADS = 1024;
 
-// Step 1 of §4.3, one thread per tile: the tile's new count = its stayers
+// Step 1 of §4.3 for tile t of species s: the tile's new count = its stayers
 // (old count - leavers) + the leavers of the eight neighbours heading here;
 // kept in off_new[t] for the scan.  Also clears the idle parity's counters
-// for the next step and sums the leavers.
-__global__ void k_count(const SortParams prm) {
-    const int s = blockIdx.y;
+// for the next step.  Returns the tile's leavers.
+__device__ __forceinline__ int count_tile(const SortParams& prm, int s, int t) {
     const SortSpecies& S = prm.sp[s];
     const Geom& g = prm.g;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int lv = 0;
-    if (t < g.ntiles) {
-        const int tx = t % g.ntx, ty = t / g.ntx;
-        lv = S.leave[t];
-        int c = S.off_old[t + 1] - S.off_old[t] - lv;
+    const int tx = t % g.ntx, ty = t / g.ntx;
+    const int lv = S.leave[t];
+    int c = S.off_old[t + 1] - S.off_old[t] - lv;
 #pragma unroll
-        for (int d = 0; d < 8; ++d) {
-            int ddx, ddy;
-            dir_delta(d, ddx, ddy);
-            if ((g.ntx == 1 && ddx) || (g.nty == 1 && ddy)) continue;
-            const int sx = dev::wrapi(tx - ddx, g.ntx), sy = dev::wrapi(ty - ddy, g.nty);
-            c += S.dirc[(sy * g.ntx + sx) * 8 + d];
-        }
-        S.off_new[t] = c;
-        S.leave_next[t] = 0;
-#pragma unroll
-        for (int d = 0; d < 8; ++d) S.dirc_next[t * 8 + d] = 0;
+    for (int d = 0; d < 8; ++d) {
+        int ddx, ddy;
+        dir_delta(d, ddx, ddy);
+        if ((g.ntx == 1 && ddx) || (g.nty == 1 && ddy)) continue;
+        const int sx = dev::wrapi(tx - ddx, g.ntx), sy = dev::wrapi(ty - ddy, g.nty);
+        c += S.dirc[(sy * g.ntx + sx) * 8 + d];
     }
+    S.off_new[t] = c;
+    S.leave_next[t] = 0;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) S.dirc_next[t * 8 + d] = 0;
+    return lv;
+}
+
+__global__ void k_count(const SortParams prm) {
+    const int s = blockIdx.y;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int lv = t < prm.g.ntiles ? count_tile(prm, s, t) : 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lv += __shfl_xor_sync(0xffffffffu, lv, o);
     if ((threadIdx.x & 31) == 0 && lv)
@@ -84,15 +98,28 @@ __global__ void k_count(const SortParams prm) {
                   (unsigned long long)lv);
 }
 
-// In-place exclusive scan of the counts in off_new (one CTA per species),
-// 4096 tiles per round with coalesced loads; off_new[ntiles] = total, which
-// must equal the particle count.  Block 0 also advances the time level and
-// primes the history slots of level n+1.
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan(const SortParams prm) {
+// batched: thread per tile of the flattened tile list of all members
+__global__ void k_count_batch(const SortBatch b) {
+    const int s = blockIdx.y;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gt >= b.total_tiles) return;
+    const int m = find_member(b.tile_start, b.nmembers, gt);
+    const SortParams& P = b.members[m];
+    if (s >= P.nsp) return;
+    const int lv = count_tile(P, s, gt - b.tile_start[m]);
+    if (lv)
+        atomicAdd(reinterpret_cast<unsigned long long*>(&P.st->leavers_acc[s]),
+                  (unsigned long long)lv);
+}
+
+// In-place exclusive scan of the counts in off_new of species s by the whole
+// CTA, 4096 tiles per round with coalesced loads; off_new[ntiles] = total,
+// which must equal the particle count.  With `advance`, thread 0 also moves
+// the simulation to time level n+1 and primes that level's history slots.
+__device__ __forceinline__ void scan_species(const SortParams& prm, int s, bool advance) {
     __shared__ int sWarp[32];
-    const int s = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (s == 0 && tid == 0) {
+    if (advance && tid == 0) {
         const long long n = prm.st->step + 1;
         prm.hist_e[n & (HIST - 1)] = 0.0;
         prm.hist_b[n & (HIST - 1)] = 0.0;
@@ -145,16 +172,21 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const SortParams prm) {
     }
 }
 
-// Warp-per-tile kernels: a warp takes one tile; slots come from the warp's
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan(const SortParams prm) {
+    scan_species(prm, blockIdx.x, blockIdx.x == 0);
+}
+
+// batched: CTA (member, species)
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_batch(const SortBatch b) {
+    scan_species(b.members[blockIdx.x], blockIdx.y, blockIdx.y == 0);
+}
+
+// Warp-per-tile bodies: a warp takes one tile; slots come from the warp's
 // ballots (register counters), so no CTA barrier or shared atomic is needed.
 constexpr int SORT_WARPS = 4;
 
-__global__ void __launch_bounds__(32 * SORT_WARPS) k_evict(const SortParams prm) {
-    const int s = blockIdx.y;
-    const int lane = threadIdx.x & 31;
-    const int t = blockIdx.x * SORT_WARPS + (threadIdx.x >> 5);
+__device__ __forceinline__ void evict_tile(const SortParams& prm, int s, int t, int lane) {
     const SortSpecies& S = prm.sp[s];
-    if (t >= prm.g.ntiles) return;
     const int p0 = S.off_old[t], p1 = S.off_old[t + 1];
     const int r0 = S.off_new[t], r1 = S.off_new[t + 1];
     const int lv = S.leave[t];
@@ -198,13 +230,23 @@ __global__ void __launch_bounds__(32 * SORT_WARPS) k_evict(const SortParams prm)
     if (overflow) dev::set_status(prm.st, ST_SORT);
 }
 
-__global__ void __launch_bounds__(32 * SORT_WARPS) k_fill(const SortParams prm) {
-    const int s = blockIdx.y;
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(32 * SORT_WARPS) k_evict(const SortParams prm) {
     const int t = blockIdx.x * SORT_WARPS + (threadIdx.x >> 5);
+    if (t < prm.g.ntiles) evict_tile(prm, blockIdx.y, t, threadIdx.x & 31);
+}
+
+// batched: warp per tile of the flattened tile list of all members
+__global__ void __launch_bounds__(32 * SORT_WARPS) k_evict_batch(const SortBatch b) {
+    const int gt = blockIdx.x * SORT_WARPS + (threadIdx.x >> 5);
+    if (gt >= b.total_tiles) return;
+    const int m = find_member(b.tile_start, b.nmembers, gt);
+    const SortParams& P = b.members[m];
+    if ((int)blockIdx.y < P.nsp) evict_tile(P, blockIdx.y, gt - b.tile_start[m], threadIdx.x & 31);
+}
+
+__device__ __forceinline__ void fill_tile(const SortParams& prm, int s, int t, int lane) {
     const SortSpecies& S = prm.sp[s];
     const Geom& g = prm.g;
-    if (t >= g.ntiles) return;
     const int T = g.T;
     const int tx = t % g.ntx, ty = t / g.ntx;
     const int p0 = S.off_old[t], p1 = S.off_old[t + 1];
@@ -293,7 +335,21 @@ __global__ void __launch_bounds__(32 * SORT_WARPS) k_fill(const SortParams prm) 
         return;
     }
     // move source -> target
-    for (int k = lane; k < nsrc; k += 32) copy_particle(S, S.isrc[r0 + k], S.fslot[r0 + k], prm.track_ids);
+    for (int k = lane; k < nsrc; k += 32)
+        copy_particle(S, S.isrc[r0 + k], S.fslot[r0 + k], prm.track_ids);
+}
+
+__global__ void __launch_bounds__(32 * SORT_WARPS) k_fill(const SortParams prm) {
+    const int t = blockIdx.x * SORT_WARPS + (threadIdx.x >> 5);
+    if (t < prm.g.ntiles) fill_tile(prm, blockIdx.y, t, threadIdx.x & 31);
+}
+
+__global__ void __launch_bounds__(32 * SORT_WARPS) k_fill_batch(const SortBatch b) {
+    const int gt = blockIdx.x * SORT_WARPS + (threadIdx.x >> 5);
+    if (gt >= b.total_tiles) return;
+    const int m = find_member(b.tile_start, b.nmembers, gt);
+    const SortParams& P = b.members[m];
+    if ((int)blockIdx.y < P.nsp) fill_tile(P, blockIdx.y, gt - b.tile_start[m], threadIdx.x & 31);
 }
 
 }  // namespace
@@ -317,6 +373,24 @@ cudaError_t launch_evict(const SortParams& p, int, cudaStream_t s) {
 cudaError_t launch_fill(const SortParams& p, int, cudaStream_t s) {
     if (p.nsp == 0 || p.g.ntiles == 0) return cudaSuccess;
     k_fill<<<dim3((p.g.ntiles + SORT_WARPS - 1) / SORT_WARPS, p.nsp), 32 * SORT_WARPS, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+// count, scan, evict and fill over all members of a batch (four launches)
+cudaError_t launch_sort_batch(const SortBatch& b, cudaStream_t s) {
+    if (b.nmembers == 0) return cudaSuccess;
+    const int nsp = b.max_nsp > 0 ? b.max_nsp : 1;
+    cudaError_t e;
+    if (b.total_tiles > 0) {
+        k_count_batch<<<dim3((b.total_tiles + 255) / 256, nsp), 256, 0, s>>>(b);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_scan_batch<<<dim3(b.nmembers, nsp), SCAN_THREADS, 0, s>>>(b);
+    if ((e = cudaGetLastError()) != cudaSuccess || b.total_tiles == 0) return e;
+    const dim3 grid((b.total_tiles + SORT_WARPS - 1) / SORT_WARPS, nsp);
+    k_evict_batch<<<grid, 32 * SORT_WARPS, 0, s>>>(b);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_fill_batch<<<grid, 32 * SORT_WARPS, 0, s>>>(b);
     return cudaGetLastError();
 }
 

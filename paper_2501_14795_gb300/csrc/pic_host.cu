@@ -13,44 +13,12 @@
 #include <string>
 #include <vector>
 
-#include "pic.h"
-#include "pic_internal.h"
+#include "host_internal.h"
 
 using namespace pic;
 
-struct pic_sim {
-    pic_config cfg;
-    Geom g;
-    cudaStream_t stream = nullptr;       // caller's stream: all work is ordered on it
-    cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
-    DevState* st = nullptr;
-    float* F[2] = {nullptr, nullptr};  // E|B, ping-pong
-    float* J[2] = {nullptr, nullptr};  // current, ping-pong
-    CUtensorMap fmap[2];
-    float* gtmp = nullptr;             // 3*nx*ny staging for set/get
-    double* rho = nullptr;             // nx*ny FP64 charge density (no background)
-    double* rho_prev = nullptr;
-    long long rho_prev_step = -1;
-    double* hist_e = nullptr;
-    double* hist_b = nullptr;
-    double* hist_k = nullptr;
-    double* dred = nullptr;            // small FP64 reduction outputs
-    SpeciesDev sp[MAX_SPECIES];
-    int cur = 0;                       // parity: F[cur], J[cur] current, off[cur] current
-    long long step = 0;                // host mirror of the time level
-    // graphs
-    cudaGraph_t graph[2] = {nullptr, nullptr};  // kept alive: its nodes address the exec's
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    cudaGraphNode_t ev_node[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-    cudaEvent_t ev_placeholder[2] = {nullptr, nullptr};
-    std::vector<cudaEvent_t> ev_pool;  // timing pairs
-    size_t ev_used = 0;                // pairs recorded since reset
-    long long launches = 0;
-    int launches_per_step = 0;
-    std::string err;
-};
-
-namespace {
+namespace pic {
+namespace host {
 
 pic_status fail(pic_sim* s, pic_status code, const char* fmt, ...) {
     if (s) {
@@ -64,13 +32,7 @@ pic_status fail(pic_sim* s, pic_status code, const char* fmt, ...) {
     return code;
 }
 
-#define CK(call)                                                                          \
-    do {                                                                                  \
-        cudaError_t e_ = (call);                                                          \
-        if (e_ != cudaSuccess)                                                            \
-            return fail(sim, e_ == cudaErrorMemoryAllocation ? PIC_ENOMEM : PIC_ECUDA,    \
-                        "%s failed: %s", #call, cudaGetErrorString(e_));                  \
-    } while (0)
+#define CK(call) PIC_CK(sim, call)
 
 template <class P>
 cudaError_t dalloc(P** p, size_t count) {
@@ -111,6 +73,58 @@ bool make_field_map(CUtensorMap* map, const Geom& g, float* base) {
     return r == CUDA_SUCCESS;
 }
 
+// Geometry of a configuration (tile size included).
+void set_geometry(Geom& g, const pic_config& c) {
+    g.nx = c.nx;
+    g.ny = c.ny;
+    g.T = c.tile;
+    g.ntx = c.nx / c.tile;
+    g.nty = c.ny / c.tile;
+    g.ntiles = g.ntx * g.nty;
+    g.P = c.nx + 2 * GX;
+    g.R = c.ny + 3;
+    g.cstride = (long long)g.P * g.R;
+    g.cx = (float)(c.dt / c.dx);
+    g.cy = (float)(c.dt / c.dy);
+    g.hdt_dx = (float)(0.5 * c.dt / c.dx);
+    g.hdt_dy = (float)(0.5 * c.dt / c.dy);
+    g.dt_dx = (float)(c.dt / c.dx);
+    g.dt_dy = (float)(c.dt / c.dy);
+    g.dt = (float)c.dt;
+    g.dx = c.dx;
+    g.dy = c.dy;
+    g.dtd = c.dt;
+}
+
+// Per-tile bookkeeping of a species (tile bookmarks, leaver counters by
+// destination, displaced counts), zeroed.
+cudaError_t alloc_tile_arrays(SpeciesDev& s, const Geom& g, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2; ++b) {
+        if (e == cudaSuccess) e = dalloc(&s.off[b], g.ntiles + 1);
+        if (e == cudaSuccess) e = dalloc(&s.leave[b], g.ntiles);
+        if (e == cudaSuccess) e = dalloc(&s.dirc[b], 8 * (size_t)g.ntiles);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(s.off[b], 0, sizeof(int32_t) * (g.ntiles + 1), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s.leave[b], 0, sizeof(int32_t) * g.ntiles, st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(s.dirc[b], 0, sizeof(int32_t) * 8 * g.ntiles, st);
+    }
+    if (e == cudaSuccess) e = dalloc(&s.evict, g.ntiles);
+    return e;
+}
+
+void free_tile_arrays(SpeciesDev& s) {
+    for (int b = 0; b < 2; ++b) {
+        dfree(s.off[b]);
+        dfree(s.leave[b]);
+        dfree(s.dirc[b]);
+        s.off[b] = s.leave[b] = s.dirc[b] = nullptr;
+    }
+    dfree(s.evict);
+    s.evict = nullptr;
+}
+
 void free_species(SpeciesDev& s) {
     void* ptrs[] = {s.cell, s.x,  s.y,  s.ux,   s.uy,   s.uz,    s.id,     s.ocell, s.ox,
                     s.oy,   s.oux, s.ouy, s.ouz, s.oid, s.hole, s.fslot, s.isrc};
@@ -145,6 +159,7 @@ void invalidate_graphs(pic_sim* sim) {
         sim->graph[b] = nullptr;
         sim->ev_node[b][0] = sim->ev_node[b][1] = nullptr;
     }
+    sim->gen += 1;
 }
 
 // CTAs per tile in the particle advance: tiles holding many particles are
@@ -208,15 +223,9 @@ SortParams sort_params(const pic_sim* sim, int b) {
     return p;
 }
 
-// Enqueue one step at parity b.  Returns the number of kernels launched or
-// -1 on a launch error (message in sim->err).  ev_a/ev_b bracket the particle
-// advance when non-null (external event records inside a capture).
-int enqueue_step(pic_sim* sim, cudaStream_t s, int b, cudaEvent_t ev_a, cudaEvent_t ev_b,
-                 bool capturing) {
-    const int threads = sim->cfg.threads;
-    const PushParams pp = push_params(sim, b);
-    const SortParams sp = sort_params(sim, b);
+YeeParams yee_params(const pic_sim* sim, int b, int chunks) {
     YeeParams yp;
+    memset(&yp, 0, sizeof yp);
     yp.g = sim->g;
     yp.Fin = sim->F[b];
     yp.Fout = sim->F[1 - b];
@@ -225,7 +234,19 @@ int enqueue_step(pic_sim* sim, cudaStream_t s, int b, cudaEvent_t ev_a, cudaEven
     yp.hist_e = sim->hist_e;
     yp.hist_b = sim->hist_b;
     yp.st = sim->st;
-    yp.zero_all = pp.chunks > 1;
+    yp.zero_all = chunks > 1;
+    return yp;
+}
+
+// Enqueue one step at parity b.  Returns the number of kernels launched or
+// -1 on a launch error (message in sim->err).  ev_a/ev_b bracket the particle
+// advance when non-null (external event records inside a capture).
+int enqueue_step(pic_sim* sim, cudaStream_t s, int b, cudaEvent_t ev_a, cudaEvent_t ev_b,
+                 bool capturing) {
+    const int threads = sim->cfg.threads;
+    const PushParams pp = push_params(sim, b);
+    const SortParams sp = sort_params(sim, b);
+    const YeeParams yp = yee_params(sim, b, pp.chunks);
     int n = 0;
     cudaError_t e;
     const unsigned rec = capturing ? cudaEventRecordExternal : 0u;
@@ -341,7 +362,70 @@ const void* stage_in(pic_sim* sim, const void* src, size_t bytes, void* staging,
     return staging;
 }
 
-}  // namespace
+
+pic_status retile(pic_sim* sim, int tile) {
+    const pic_config& c = sim->cfg;
+    if (!(tile == 8 || tile == 16 || tile == 32) || c.nx % tile || c.ny % tile)
+        return fail(sim, PIC_EINVAL, "tile %d does not divide the %dx%d grid", tile, c.nx, c.ny);
+    if (tile == sim->g.T) return PIC_OK;
+    cudaStream_t s = sim->stream;
+    {
+        DevState h;
+        pic_status r = read_state(sim, &h);
+        if (r != PIC_OK) return r;
+        if (h.status) return status_from_bits(sim, h.status);
+    }
+    const bool track = (c.flags & PIC_TRACK_IDS) != 0;
+    // stage every species in its out arrays, as the load path expects them
+    for (int k = 0; k < c.n_species; ++k) {
+        SpeciesDev& S = sim->sp[k];
+        if (S.n == 0) continue;
+        const size_t b4 = 4 * (size_t)S.n;
+        CK(launch_unpack_cells(S.cell, S.n, S.ocell, S.hole, s));
+        CK(cudaMemcpyAsync(S.ox, S.x, b4, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(S.oy, S.y, b4, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(S.oux, S.ux, b4, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(S.ouy, S.uy, b4, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(S.ouz, S.uz, b4, cudaMemcpyDeviceToDevice, s));
+        if (track) CK(cudaMemcpyAsync(S.isrc, S.id, b4, cudaMemcpyDeviceToDevice, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    invalidate_graphs(sim);
+    sim->cfg.tile = tile;
+    set_geometry(sim->g, sim->cfg);
+    for (int k = 0; k < c.n_species; ++k) {
+        free_tile_arrays(sim->sp[k]);
+        CK(alloc_tile_arrays(sim->sp[k], sim->g, s));
+    }
+    for (int b = 0; b < 2; ++b)
+        if (!make_field_map(&sim->fmap[b], sim->g, sim->F[b]))
+            return fail(sim, PIC_ECUDA, "cannot encode the field tensor map");
+    // the next step deposits into J[cur] with plain stores on the tiles'
+    // interiors: it must be all zero for the new tiling
+    CK(cudaMemsetAsync(sim->J[sim->cur], 0, 3 * (size_t)sim->g.cstride * 4, s));
+    CK(cudaMemsetAsync(&sim->st->load_bad, 0, sizeof(int), s));
+    DevState h;
+    for (int k = 0; k < c.n_species; ++k) {
+        SpeciesDev& S = sim->sp[k];
+        CK(launch_load(sim->g, S, track, S.n, S.off[sim->cur], sim->st, s, 0, nullptr, nullptr));
+        // the scatter trusts the validated cells: check before it runs
+        pic_status r = read_state(sim, &h);
+        if (r != PIC_OK) return r;
+        if (h.load_bad)
+            return fail(sim, PIC_EOVERFLOW, "re-tiling found %d invalid particles", h.load_bad);
+        CK(launch_load(sim->g, S, track, S.n, S.off[sim->cur], sim->st, s, 1,
+                       track ? S.isrc : nullptr, reinterpret_cast<int32_t*>(sim->rho)));
+    }
+    pic_status r = read_state(sim, &h);
+    if (r != PIC_OK) return r;
+    sim->rho_prev_step = -1;
+    return status_from_bits(sim, h.status);
+}
+
+}  // namespace host
+}  // namespace pic
+
+using namespace pic::host;
 
 extern "C" {
 
@@ -374,25 +458,7 @@ pic_status pic_init(const pic_config* cfg, void* cuda_stream, pic_sim** out) {
     sim->cfg = c;
     sim->stream = (cudaStream_t)cuda_stream;
     Geom& g = sim->g;
-    g.nx = c.nx;
-    g.ny = c.ny;
-    g.T = c.tile;
-    g.ntx = c.nx / c.tile;
-    g.nty = c.ny / c.tile;
-    g.ntiles = g.ntx * g.nty;
-    g.P = c.nx + 2 * GX;
-    g.R = c.ny + 3;
-    g.cstride = (long long)g.P * g.R;
-    g.cx = (float)(c.dt / c.dx);
-    g.cy = (float)(c.dt / c.dy);
-    g.hdt_dx = (float)(0.5 * c.dt / c.dx);
-    g.hdt_dy = (float)(0.5 * c.dt / c.dy);
-    g.dt_dx = (float)(c.dt / c.dx);
-    g.dt_dy = (float)(c.dt / c.dy);
-    g.dt = (float)c.dt;
-    g.dx = c.dx;
-    g.dy = c.dy;
-    g.dtd = c.dt;
+    set_geometry(g, c);
 
     auto cleanup_fail = [&](pic_status code, const char* what, cudaError_t e) {
         pic_destroy(sim);
@@ -425,20 +491,8 @@ pic_status pic_init(const pic_config* cfg, void* cuda_stream, pic_sim** out) {
     for (int k = 0; k < c.n_species && e == cudaSuccess; ++k) {
         SpeciesDev& s = sim->sp[k];
         memset(&s, 0, sizeof s);
-        if (e == cudaSuccess) e = dalloc(&s.off[0], g.ntiles + 1);
-        if (e == cudaSuccess) e = dalloc(&s.off[1], g.ntiles + 1);
-        for (int b = 0; b < 2; ++b) {
-            if (e == cudaSuccess) e = dalloc(&s.leave[b], g.ntiles);
-            if (e == cudaSuccess) e = dalloc(&s.dirc[b], 8 * (size_t)g.ntiles);
-            if (e == cudaSuccess)
-                e = cudaMemsetAsync(s.leave[b], 0, sizeof(int32_t) * g.ntiles, sim->stream);
-            if (e == cudaSuccess)
-                e = cudaMemsetAsync(s.dirc[b], 0, sizeof(int32_t) * 8 * g.ntiles, sim->stream);
-        }
-        if (e == cudaSuccess) e = dalloc(&s.evict, g.ntiles);
+        if (e == cudaSuccess) e = alloc_tile_arrays(s, g, sim->stream);
         if (e == cudaSuccess) e = dalloc(&s.cursor, (size_t)c.nx * c.ny);
-        for (int b = 0; b < 2 && e == cudaSuccess; ++b)
-            e = cudaMemsetAsync(s.off[b], 0, sizeof(int32_t) * (g.ntiles + 1), sim->stream);
         const auto& sc = c.species[k];
         const double qt = (sc.q_over_m > 0 ? 1.0 : -1.0) * sc.density / sc.ppc;
         s.qtilde = qt;
@@ -547,6 +601,10 @@ pic_status pic_load_particles(pic_sim* sim, int species, int64_t n, const int32_
     }
     W.n = n;
     S = W;
+    // leaver counters of the next step's parity start from zero (a restore
+    // may put the simulation back on a parity whose counters were in use)
+    CK(cudaMemsetAsync(S.leave[sim->cur], 0, sizeof(int32_t) * sim->g.ntiles, s));
+    CK(cudaMemsetAsync(S.dirc[sim->cur], 0, sizeof(int32_t) * 8 * sim->g.ntiles, s));
     invalidate_graphs(sim);
     sim->rho_prev_step = -1;
     pic_status r = refresh_level_energy(sim);
@@ -785,6 +843,7 @@ const char* pic_last_error(const pic_sim* sim) { return sim ? sim->err.c_str() :
 
 void pic_destroy(pic_sim* sim) {
     if (!sim) return;
+    if (sim->batch) batch_forget(sim->batch, sim);
     if (sim->stream) cudaStreamSynchronize(sim->stream);
     invalidate_graphs(sim);
     if (sim->cap_stream) cudaStreamDestroy(sim->cap_stream);
@@ -805,13 +864,7 @@ void pic_destroy(pic_sim* sim) {
     for (int k = 0; k < sim->cfg.n_species; ++k) {
         SpeciesDev& s = sim->sp[k];
         free_species(s);
-        dfree(s.off[0]);
-        dfree(s.off[1]);
-        for (int b = 0; b < 2; ++b) {
-            dfree(s.leave[b]);
-            dfree(s.dirc[b]);
-        }
-        dfree(s.evict);
+        free_tile_arrays(s);
         dfree(s.cursor);
     }
     delete sim;

@@ -88,7 +88,7 @@ struct PushSpecies {
     double ke_w;
 };
 
-struct PushParams {
+struct alignas(16) PushParams {
     Geom g;
     float* J;              // this step's current buffer (base of component 0)
     int chunks;            // CTAs per tile (gridDim.y): each takes a slice of the tile's particles
@@ -128,12 +128,48 @@ struct YeeParams {
     DevState* st;
 };
 
+// ---- batched launches: many simulations, one grid per kernel -----------------
+// Parameter blocks of every member live in device memory; work items are
+// flattened over the members.
+struct PushBatch {
+    const PushParams* members;  // one per member (current parity)
+    const CUtensorMap* tmaps;   // each member's E|B map (current parity), 64-byte aligned
+    const int4* items;          // (member, tile, chunk, 0), costliest first
+    int nitems;
+    int* next;                  // work-item counter, zero at launch
+};
+
+struct SortBatch {
+    const SortParams* members;
+    const int* tile_start;      // nmembers + 1 prefix of the members' tile counts
+    int nmembers;
+    int total_tiles;
+    int max_nsp;
+};
+
+struct YeeBatch {
+    const YeeParams* members;
+    const int* ytile_start;     // nmembers + 1 prefix of the members' Yee-tile counts
+    int nmembers;
+    int total_ytiles;
+};
+
 // ---- launchers (defined in the kernel translation units) ---------------------
 // particle advance, fast (FMA) and strict (no contraction) builds
 cudaError_t launch_push_fast(const CUtensorMap* fmap, const PushParams& p, int threads,
                              cudaStream_t s);
 cudaError_t launch_push_strict(const CUtensorMap* fmap, const PushParams& p, int threads,
                                cudaStream_t s);
+
+// batched particle advance; grid = number of persistent CTAs (0: all that fit at once)
+cudaError_t launch_push_batch_fast(const PushBatch& b, int T, int threads, int grid,
+                                   cudaStream_t s);
+cudaError_t launch_push_batch_strict(const PushBatch& b, int T, int threads, int grid,
+                                     cudaStream_t s);
+// batched re-sort and field advance
+cudaError_t launch_sort_batch(const SortBatch& b, cudaStream_t s);
+cudaError_t launch_yee_batch(const YeeBatch& b, cudaStream_t s);
+int yee_tiles(const Geom& g);
 
 cudaError_t launch_scan(const SortParams& p, cudaStream_t s);
 cudaError_t launch_evict(const SortParams& p, int threads, cudaStream_t s);

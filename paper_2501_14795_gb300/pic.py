@@ -92,9 +92,24 @@ def load_library() -> C.CDLL:
         L.pic_destroy.restype = None
         L.pic_tile_sort_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64] + [_P] * 15 + [_P]
         L.pic_tile_sort_noalloc.restype = C.c_int
+        L.pic_init_batch.argtypes = [C.POINTER(pic_config), C.c_int, _P, C.POINTER(_P)]
+        L.pic_batch_create.argtypes = [C.POINTER(_P), C.c_int, _P, C.POINTER(_P)]
+        L.pic_batch_step.argtypes = [_P, C.c_int]
+        L.pic_batch_sync.argtypes = [_P, C.POINTER(C.c_int)]
+        L.pic_batch_kernel_launches.argtypes = [_P, C.POINTER(C.c_int)]
+        L.pic_batch_kernel_launches.restype = C.c_int64
+        L.pic_batch_last_error.argtypes = [_P]
+        L.pic_batch_last_error.restype = C.c_char_p
+        L.pic_batch_destroy.argtypes = [_P]
+        L.pic_batch_destroy.restype = None
+        L.pic_autotune.argtypes = [_P, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_double)]
+        L.pic_set_tiling.argtypes = [_P, C.c_int, C.c_int]
         for name in ("pic_init", "pic_load_particles", "pic_set_fields", "pic_step",
                      "pic_get_fields", "pic_get_particles", "pic_diagnostics",
-                     "pic_get_history", "pic_sync", "pic_clear_status", "pic_timing"):
+                     "pic_get_history", "pic_sync", "pic_clear_status", "pic_timing",
+                     "pic_init_batch", "pic_batch_create", "pic_batch_step", "pic_batch_sync",
+                     "pic_autotune", "pic_set_tiling"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -241,6 +256,80 @@ def pic_destroy(h):
     load_library().pic_destroy(h)
 
 
+def pic_init_batch(cfgs, stream=None):
+    """n simulations on one stream; returns their handles."""
+    n = len(cfgs)
+    arr = (pic_config * n)(*cfgs)
+    out = (_P * n)()
+    if stream is None:
+        stream = _default_stream()
+    _check(None, load_library().pic_init_batch(arr, n, stream, out))
+    return [_P(v) for v in out]
+
+
+def _bcheck(b, status):
+    if status != 0:
+        msg = load_library().pic_batch_last_error(b) if b else b""
+        raise PicError(status, (msg or b"").decode())
+
+
+def pic_batch_create(members, stream=None):
+    n = len(members)
+    arr = (_P * n)(*[m.value if isinstance(m, _P) else m for m in members])
+    b = _P()
+    if stream is None:
+        stream = _default_stream()
+    st = load_library().pic_batch_create(arr, n, stream, C.byref(b))
+    if st != 0:
+        msg = ""
+        for m in members:
+            if m and pic_last_error(m):
+                msg = pic_last_error(m)
+                break
+        raise PicError(st, msg or "pic_batch_create")
+    return b
+
+
+def pic_batch_step(b, nsteps=1):
+    _bcheck(b, load_library().pic_batch_step(b, nsteps))
+
+
+def pic_batch_sync(b):
+    """Wait; raise the first failing member's status (PicError.member set)."""
+    m = C.c_int(-1)
+    st = load_library().pic_batch_sync(b, C.byref(m))
+    if st != 0:
+        e = PicError(st, (load_library().pic_batch_last_error(b) or b"").decode())
+        e.member = m.value
+        raise e
+
+
+def pic_batch_kernel_launches(b):
+    per = C.c_int(0)
+    tot = load_library().pic_batch_kernel_launches(b, C.byref(per))
+    return int(tot), per.value
+
+
+def pic_batch_last_error(b):
+    return (load_library().pic_batch_last_error(b) or b"").decode()
+
+
+def pic_batch_destroy(b):
+    load_library().pic_batch_destroy(b)
+
+
+def pic_autotune(h, steps=5, force=False):
+    """(tile, threads, step_ms) chosen for a loaded simulation (see pic.h)."""
+    t, n, ms = C.c_int(), C.c_int(), C.c_double()
+    _check(h, load_library().pic_autotune(h, steps, int(force), C.byref(t), C.byref(n),
+                                          C.byref(ms)))
+    return t.value, n.value, ms.value
+
+
+def pic_set_tiling(h, tile, threads=0):
+    _check(h, load_library().pic_set_tiling(h, tile, threads))
+
+
 def pic_tile_sort_noalloc(nx, ny, tile, ix, iy, x, y, ux, uy, uz, ix_out, iy_out, x_out,
                           y_out, ux_out, uy_out, uz_out, tile_offset, stream=None):
     """Allocation-free tile sort of device arrays into device arrays (see pic.h)."""
@@ -306,8 +395,32 @@ class Simulation:
             pic_set_fields(sim.h, E, B)
         return sim
 
+    @classmethod
+    def init_batch(cls, cfgs, stream=None):
+        """Simulations created together on one stream (pic_init_batch)."""
+        out = []
+        for cfg, h in zip(cfgs, pic_init_batch(cfgs, stream)):
+            s = cls.__new__(cls)
+            s.cfg, s.h = cfg, h
+            out.append(s)
+        return out
+
     def step(self, n=1):
         pic_step(self.h, n)
+
+    def autotune(self, steps=5, force=False):
+        t, n, ms = pic_autotune(self.h, steps, force)
+        self.cfg.tile, self.cfg.threads = t, n
+        return t, n, ms
+
+    def set_tiling(self, tile, threads=0):
+        pic_set_tiling(self.h, tile, threads)
+        self.cfg.tile = tile
+        if threads:
+            self.cfg.threads = threads
+
+    def num_tiles(self):
+        return pic_num_tiles(self.h)
 
     def fields(self, which):
         n = 3 if which in (FIELD_E, FIELD_B, FIELD_J) else 1
@@ -336,6 +449,40 @@ class Simulation:
         if self.h:
             pic_destroy(self.h)
             self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owner of a pic_batch over existing Simulation objects (kept alive here)."""
+
+    def __init__(self, sims, stream=None):
+        self.sims = list(sims)
+        self.b = pic_batch_create([s.h for s in self.sims], stream)
+
+    def step(self, n=1):
+        pic_batch_step(self.b, n)
+
+    def sync(self):
+        pic_batch_sync(self.b)
+
+    def kernel_launches(self):
+        return pic_batch_kernel_launches(self.b)
+
+    def close(self):
+        if self.b:
+            pic_batch_destroy(self.b)
+            self.b = None
 
     def __enter__(self):
         return self

@@ -67,3 +67,29 @@ def test_init_validation_without_gpu(lib):
     assert status(nx=4, tile=8) == 1
     assert status(dx=-0.1) == 1
     assert h.value is None
+
+
+def test_batch_and_tuner_entry_points_check_arguments_without_gpu(lib):
+    """Null handles and bad counts answer before any CUDA call."""
+    from paper_2501_14795_gb300 import pic
+    L = pic.load_library()
+    out = ctypes.c_void_p(1)
+    assert L.pic_batch_create(None, 2, None, ctypes.byref(out)) == 1 and out.value is None
+    members = (ctypes.c_void_p * 2)(None, None)
+    assert L.pic_batch_create(members, 0, None, ctypes.byref(out)) == 1
+    assert L.pic_batch_create(members, 2, None, ctypes.byref(out)) == 1 and out.value is None
+    assert L.pic_batch_step(None, 1) == 1
+    assert L.pic_batch_sync(None, None) == 1
+    assert L.pic_batch_kernel_launches(None, None) == -1
+    assert L.pic_batch_last_error(None) == b"null handle"
+    L.pic_batch_destroy(None)
+    assert L.pic_autotune(None, 3, 0, None, None, None) == 1
+    assert L.pic_set_tiling(None, 16, 0) == 1
+    # a batch of configurations fails on the first invalid one, all handles NULL
+    good = pic.make_config(64, 64, 0.1, 0.1, 0.05, [(-1.0, -1.0 / 16)])
+    bad = pic.make_config(64, 64, 0.1, 0.1, 0.08, [(-1.0, -1.0 / 16)])
+    cfgs = (pic.pic_config * 1)(bad)
+    hs = (ctypes.c_void_p * 1)(7)
+    assert L.pic_init_batch(cfgs, 1, None, hs) == 2 and hs[0] is None
+    assert L.pic_init_batch(None, 1, None, hs) == 1
+    del good
