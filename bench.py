@@ -334,6 +334,8 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.current_stream()
     w = make_workload(args.workload)
+    if args.tile:
+        w.tile = args.tile
     n = w.n_particles
     flags = pic.PIC_TIMING
     sim = pic.Simulation.from_workload(w, tile=w.tile, threads=args.threads, flags=flags,
@@ -435,6 +437,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="weibel_512", choices=sorted(WORKLOADS))
     ap.add_argument("--threads", type=int, default=256)
+    ap.add_argument("--tile", type=int, default=0, help="override the workload's tile size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -25,6 +25,11 @@ Parity status per function (what pins each one; the pins live in
 * Weibel growth (config with counter-streaming populations along z): parity
   only bounded, between 0.7x and 1x the cold-fluid rate (the thermal spread
   lowers the cold rate by an amount the thesis does not give).
+* ``denoiser`` (module): circular 3x3 convolution pinned by brute force and an
+  FFT correlation; its input, weight and bias gradients by adjoint identities
+  and brute force; pooling / upsampling adjoints; the whole network's gradient
+  by central finite differences; Adam by its first step and convergence on a
+  quadratic; bfloat16 rounding by hand-computed bit patterns.
 """
 from .oracle import (  # noqa: F401
     OracleSim,
