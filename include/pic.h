@@ -249,6 +249,81 @@ pic_status pic_autotune(pic_sim* sim, int steps, int force, int* tile, int* thre
  * the grid. */
 pic_status pic_set_tiling(pic_sim* sim, int tile, int threads);
 
+/* ---- Learned current denoiser -----------------------------------------------
+ * The paper smooths the deposited current with a binomial filter placed after
+ * the guard-cell reduction of J and before the field advance (Listing 3.1).
+ * The denoiser is a learned alternative for that slot: a small convolutional
+ * encoder-decoder that maps the current of a low-ppc run to that of a
+ * high-ppc run.  Architecture (3 levels, 3x3 kernels with periodic padding,
+ * ReLU, 2x2 mean pooling, nearest upsampling, additive skips s1, s2):
+ *   c1 3->32, c2 32->32 (s1), pool, c3 32->64, c4 64->64 (s2), pool,
+ *   c5 64->128, c6 128->128, up, c7 128->64 (+s2), c8 64->64, up,
+ *   c9 64->32 (+s1), c10 32->32, c11 32->3;  out = x + c11(...),
+ * with x = J / scale and the denoised current scale * out.  Activations and
+ * weights are bfloat16 on the tensor cores with FP32 accumulation; the
+ * parameters have an FP32 master copy trained with Adam (beta1 0.9, beta2
+ * 0.999, eps 1e-8) on the mean-squared error of the normalised output.
+ * Parameter vector (FP32, pic_denoiser_num_params() values): per layer in
+ * order c1..c11 the weights [ky][kx][cin][cout] (tap offset (ky-1, kx-1)),
+ * then the bias [cout].  Currents are exchanged as `batch` consecutive
+ * samples in the field layout of the header comment (3 x ny x nx FP32 each).
+ * A handle is not thread-safe; its work is ordered on `cuda_stream`, and while
+ * it is installed in a simulation it also runs on that simulation's stream. */
+typedef struct pic_denoiser pic_denoiser;
+
+int64_t pic_denoiser_num_params(void);
+
+/* nx a multiple of 64, ny of 32 (two 2x poolings onto 16x8 convolution
+ * tiles); batch_max >= 1 samples per call; scale > 0 the current
+ * normalisation.  Parameters start at zero (the network is the identity). */
+pic_status pic_denoiser_create(int nx, int ny, int batch_max, double scale, void* cuda_stream,
+                               pic_denoiser** out);
+
+/* Replace / read the parameter vector (resets the Adam moments). */
+pic_status pic_denoiser_set_params(pic_denoiser* d, const float* params, int on_device);
+pic_status pic_denoiser_get_params(pic_denoiser* d, float* params, int on_device);
+
+/* J_out = the denoised J_in (batch samples).  J_out may equal J_in.  Synchronises. */
+pic_status pic_denoiser_forward(pic_denoiser* d, const float* J_in, float* J_out, int batch,
+                                int on_device);
+
+/* Loss (mean squared error of the normalised output against J_target / scale)
+ * and, if grads is non-NULL, its gradient with respect to the parameter
+ * vector.  Synchronises. */
+pic_status pic_denoiser_grad(pic_denoiser* d, const float* J_in, const float* J_target, int batch,
+                             double* loss, float* grads, int on_device);
+
+/* pic_denoiser_grad followed by one Adam step with learning rate lr. */
+pic_status pic_denoiser_train_step(pic_denoiser* d, const float* J_in, const float* J_target,
+                                   int batch, float lr, double* loss, int on_device);
+
+/* Install d (NULL: remove) in the current-filter slot of sim: every later
+ * pic_step applies the network to J in place between the deposit and the
+ * field advance (the continuity residual of pic_diagnostics then measures the
+ * filtered current).  d must match the grid.  Simulations with a filter
+ * cannot be stepped in a batch. */
+pic_status pic_set_denoiser(pic_sim* sim, pic_denoiser* d);
+
+const char* pic_denoiser_last_error(const pic_denoiser* d);
+void pic_denoiser_destroy(pic_denoiser* d);
+
+/* Kernel-level probes on caller device buffers (bfloat16 NHWC tensors as
+ * uint16 bit patterns, channel counts padded to a multiple of 16; FP32
+ * weights [ky][kx][cin][cout]).  Synchronise `cuda_stream`.
+ *   pic_nn_conv3x3: a = bf16(relu?(conv(x) + bias)), y = bf16(a + skip) if
+ *     skip is non-NULL; cout in {32, 64, 128}; H % 8 == 0, W % 16 == 0.
+ *   pic_nn_conv3x3_dgrad: dx (FP32 NHWC, cin channels) = input gradient of
+ *     the convolution for the output gradient dz; cin in {32, 64, 128}.
+ *   pic_nn_conv3x3_wgrad: dw (FP32 [3][3][cin][cout], overwritten) = weight
+ *     gradient; W % 16 == 0. */
+pic_status pic_nn_conv3x3(const void* x, int B, int H, int W, int cin, int cout, const float* w,
+                          const float* bias, int relu, const void* skip, void* a_out, void* y_out,
+                          void* cuda_stream);
+pic_status pic_nn_conv3x3_dgrad(const void* dz, int B, int H, int W, int cin, int cout,
+                                const float* w, float* dx, void* cuda_stream);
+pic_status pic_nn_conv3x3_wgrad(const void* x, const void* dz, int B, int H, int W, int cin,
+                                int cout, float* dw, void* cuda_stream);
+
 /* ---- Allocation-free tile sort ---------------------------------------------
  * The paper has no counterpart: this entry point is for callers that cannot
  * call cudaMalloc (host callbacks, allocator hooks, plugins whose host

@@ -37,6 +37,8 @@ def _units():
         ("grid.o", "kernels_grid.cu", common),
         ("host.o", "pic_host.cu", common),
         ("batch.o", "pic_batch.cu", common),
+        ("nn.o", "nn_kernels.cu", common),
+        ("denoiser.o", "denoiser.cu", common),
         ("noalloc.o", "noalloc.cu", common),
     ]
 
@@ -66,7 +68,7 @@ def build_library(force: bool = False, verbose: bool = False, ptxas_info: bool =
         r = subprocess.run(cmd, capture_output=True, text=True)
         return obj, cmd, r
 
-    with ThreadPoolExecutor(max_workers=min(7, os.cpu_count() or 1)) as ex:
+    with ThreadPoolExecutor(max_workers=min(9, os.cpu_count() or 1)) as ex:
         results = list(ex.map(compile_one, _units()))
     for obj, cmd, r in results:
         if verbose or ptxas_info:

@@ -44,6 +44,10 @@ struct pic_sim {
     // reload or re-tiling), so that batches capturing this member rebuild
     unsigned long long gen = 0;
     pic_batch* batch = nullptr;  // batch this member belongs to, if any
+    // current filter applied to J[b] between the re-sort and the field
+    // advance; returns the kernels it launched or -1 (message in sim->err)
+    int (*jfilter)(void* ctx, pic_sim* sim, cudaStream_t s, int b) = nullptr;
+    void* jfilter_ctx = nullptr;
 };
 
 namespace pic {

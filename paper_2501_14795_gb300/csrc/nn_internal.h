@@ -1,0 +1,93 @@
+// Internal declarations of the denoiser kernels (nn_kernels.cu) shared with
+// their host runtime (denoiser.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+namespace pic {
+namespace nn {
+
+// convolution tile: 8 x 16 output pixels per CTA, one pixel row per warp
+constexpr int TH = 8, TW = 16;
+constexpr int PH = TH + 2, PW = TW + 2;
+constexpr int CONV_THREADS = 256;
+// weight gradient: pixel chunks of WG_PIX consecutive pixels of one row
+constexpr int WG_PIX = 16;
+constexpr int WG_THREADS = 256, WG_WARPS = 8;
+
+enum { EPI_ACT = 0, EPI_FINAL = 1, EPI_GRAD = 2 };
+
+struct ConvParams {
+    const __nv_bfloat16* x;  // input NHWC, channels = the kernel's CIN
+    int B, H, W;
+    const __nv_bfloat16* w;  // packed [9][cout_pad][CIN]
+    const float* bias;       // [cout] or null
+    int cout, cout_pad;
+    int epi, relu;
+    // EPI_ACT: a_out = bf16(relu(z + bias)); with skip: y_out = bf16(a + skip)
+    __nv_bfloat16* a_out;
+    const __nv_bfloat16* skip;
+    __nv_bfloat16* y_out;
+    // EPI_GRAD: g_out = z (FP32 NHWC, cout_pad channels)
+    float* g_out;
+    // EPI_FINAL: fout[o] = res[o] * rs + (z + bias) * os for c < cout, with
+    // o = b*bstride + c*cstride + offset + y*pitch + x (field layout)
+    const float* res;
+    float* fout;
+    long long bstride, cstride;
+    int pitch, offset;
+    float rs, os;
+};
+
+struct WgradParams {
+    const __nv_bfloat16* x;   // layer input NHWC (CI channels)
+    const __nv_bfloat16* dz;  // output gradient NHWC (CO channels)
+    int B, H, W;
+    int cin, cout;            // real channel counts
+    float* dw;                // += into [9][cin][cout]
+};
+
+struct LayerDesc {
+    int cin, cout;            // real channel counts
+    int cin_pad, cout_pad;    // forward GEMM: k = cin_pad (x16), n = cout_pad (x CT)
+    int dg_cin_pad, dg_cout_pad;  // input-gradient GEMM: k = cout padded to 16, n = cin (0: none)
+    long long woff;           // weights in the master vector ([9][cin][cout], then bias)
+    long long wf_off, wd_off; // packed bfloat16 arrays
+};
+
+constexpr int MAX_LAYERS = 16;
+struct PackTable {
+    int n;
+    LayerDesc layer[MAX_LAYERS];
+};
+
+// raise every kernel shape's shared-memory limit (before any graph capture)
+cudaError_t init_kernels();
+cudaError_t launch_conv(const ConvParams& p, int cin, int ct, cudaStream_t s);
+cudaError_t launch_wgrad(const WgradParams& p, int ci, int co, cudaStream_t s);
+cudaError_t launch_pack_input(const float* J, long long bstride, long long cstride, int pitch,
+                              int offset, int B, int H, int W, float inv_scale, __nv_bfloat16* out,
+                              cudaStream_t s);
+cudaError_t launch_pool_fwd(const __nv_bfloat16* in, int B, int H, int W, int C,
+                            __nv_bfloat16* out, cudaStream_t s);
+cudaError_t launch_up_fwd(const __nv_bfloat16* in, int B, int H, int W, int C, __nv_bfloat16* out,
+                          cudaStream_t s);
+cudaError_t launch_pool_back(const float* in, int B, int H, int W, int C, float* out,
+                             cudaStream_t s);
+cudaError_t launch_up_back(const float* in, int B, int H, int W, int C, float* out,
+                           cudaStream_t s);
+cudaError_t launch_relu_back(const float* dy, const float* extra, const __nv_bfloat16* a,
+                             long long npix, int C, __nv_bfloat16* dz, float* db, cudaStream_t s);
+cudaError_t launch_mse(const float* out, const float* target, long long bstride, long long cstride,
+                       int pitch, int offset, int B, int H, int W, float inv_scale,
+                       __nv_bfloat16* dz, float* db, double* loss, cudaStream_t s);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr,
+                        float b1, float b2, float eps, float c1, float c2, cudaStream_t s);
+cudaError_t launch_pack_weights(const PackTable& t, const float* master, __nv_bfloat16* wf,
+                                __nv_bfloat16* wd, cudaStream_t s);
+
+}  // namespace nn
+}  // namespace pic

@@ -1,0 +1,706 @@
+// Kernels of the learned current denoiser: a 3x3 circular-padding
+// convolutional encoder-decoder run in bfloat16 with FP32 accumulation on the
+// tensor cores (mma.sync m16n8k16, operands staged in shared memory with
+// cp.async and fed with ldmatrix), its backward pass and its Adam update.
+//
+// Tensors are NHWC bfloat16 with the channel count a multiple of 16 (the
+// 3-channel current is padded with zeros); gradients are FP32 except where
+// they enter a tensor-core product (dz, rounded to bfloat16).
+//
+//   k_conv   implicit GEMM: CTA = 8x16 output pixels x a tile of output
+//            channels; the halo patch and the CTA's weights sit in shared
+//            memory; warp = one pixel row (m16) x the channel tile.  The same
+//            kernel computes the input gradient with flipped, transposed
+//            weights (dgrad).  Epilogues: bias + ReLU (+ skip) to bfloat16,
+//            raw FP32, or the network's residual output in field layout.
+//   k_wgrad  weight gradient: per tap a (cout x cin) GEMM over all pixels,
+//            split over CTAs (FP32 atomics into the gradient).
+//   elementwise: input packing, 2x2 mean pooling / nearest upsampling and
+//            their adjoints, ReLU backward with the bias gradient, MSE loss,
+//            Adam, weight packing.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nn_internal.h"
+
+namespace pic {
+namespace nn {
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr(sdst)), "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(saddr(p)));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t r[2], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
+                 : "=r"(r[0]), "=r"(r[1])
+                 : "r"(saddr(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t r[4], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(saddr(p)));
+}
+
+// D += A (16x16, row) * B (16x8, col), bf16 in, fp32 accumulate
+__device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// ------------------------------------------------------------------ conv
+template <int CIN, int CT>
+struct ConvSmem {
+    static constexpr int CS = CIN + 8;  // row stride in elements (16 B of padding: no bank conflicts)
+    static constexpr int PATCH = PH * PW * CS;
+    static constexpr int WTS = 9 * CT * CS;
+    static constexpr size_t bytes = (size_t)(PATCH + WTS) * 2;
+};
+
+template <int CIN, int CT>
+__global__ void __launch_bounds__(CONV_THREADS) k_conv(const ConvParams p) {
+    using L = ConvSmem<CIN, CT>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    bf16* sP = reinterpret_cast<bf16*>(smem);
+    bf16* sW = sP + L::PATCH;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tilesx = p.W / TW;
+    const int ty0 = (blockIdx.x / tilesx) * TH, tx0 = (blockIdx.x % tilesx) * TW;
+    const int b = blockIdx.y, co0 = blockIdx.z * CT;
+    constexpr int CH = CIN / 8;  // 16-byte chunks per pixel
+
+    for (int i = tid; i < PH * PW * CH; i += CONV_THREADS) {
+        const int pix = i / CH, c = i - pix * CH;
+        const int r = pix / PW, q = pix - r * PW;
+        const int y = wrap(ty0 - 1 + r, p.H), x = wrap(tx0 - 1 + q, p.W);
+        cp_async16(sP + pix * L::CS + c * 8,
+                   p.x + (((size_t)b * p.H + y) * p.W + x) * CIN + c * 8);
+    }
+    for (int i = tid; i < 9 * CT * CH; i += CONV_THREADS) {
+        const int row = i / CH, c = i - row * CH;
+        const int tap = row / CT, n = row - tap * CT;
+        cp_async16(sW + row * L::CS + c * 8,
+                   p.w + ((size_t)tap * p.cout_pad + co0 + n) * CIN + c * 8);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+
+    constexpr int NT = CT / 8;
+    float acc[NT][4];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    const int r = warp;  // the warp's output pixel row inside the tile
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap - 3 * (tap / 3);
+        const bf16* pa = sP + ((r + ky) * PW + kx + (lane & 15)) * L::CS + (lane >> 4) * 8;
+        const bf16* pw = sW + tap * CT * L::CS;
+#pragma unroll
+        for (int kc = 0; kc < CIN / 16; ++kc) {
+            uint32_t a[4];
+            ldsm_x4(a, pa + kc * 16);
+            if constexpr (NT == 1) {
+                uint32_t bb[2];
+                ldsm_x2(bb, pw + (lane & 7) * L::CS + kc * 16 + ((lane >> 3) & 1) * 8);
+                mma_bf16(acc[0], a, bb[0], bb[1]);
+            } else {
+#pragma unroll
+                for (int nt = 0; nt < NT; nt += 2) {
+                    const int j = lane >> 3;
+                    uint32_t bb[4];
+                    ldsm_x4(bb, pw + (nt * 8 + (j >> 1) * 8 + (lane & 7)) * L::CS + kc * 16 +
+                                    (j & 1) * 8);
+                    mma_bf16(acc[nt], a, bb[0], bb[1]);
+                    mma_bf16(acc[nt + 1], a, bb[2], bb[3]);
+                }
+            }
+        }
+    }
+
+    // epilogue: rows g, g+8 of the warp's 16 pixels; columns 2(lane%4), +1 of each n-tile
+    const int g = lane >> 2, cq = (lane & 3) * 2;
+    const int y = ty0 + r;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int x = tx0 + g + 8 * h;
+        const size_t pix = ((size_t)b * p.H + y) * p.W + x;
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            const int co = co0 + nt * 8 + cq;
+            float v0 = acc[nt][2 * h], v1 = acc[nt][2 * h + 1];
+            if (p.epi == EPI_GRAD) {
+                *reinterpret_cast<float2*>(p.g_out + pix * p.cout_pad + co) = make_float2(v0, v1);
+                continue;
+            }
+            if (p.bias) {
+                if (co < p.cout) v0 += p.bias[co];
+                if (co + 1 < p.cout) v1 += p.bias[co + 1];
+            }
+            if (p.epi == EPI_FINAL) {
+                // residual output in field layout: out = res * rs + z * os
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int c = co + e;
+                    if (c >= p.cout) continue;
+                    const size_t o = (size_t)b * p.bstride + (size_t)c * p.cstride + p.offset +
+                                     (size_t)y * p.pitch + x;
+                    p.fout[o] = p.res[o] * p.rs + (e ? v1 : v0) * p.os;
+                }
+                continue;
+            }
+            if (p.relu) {
+                v0 = fmaxf(v0, 0.f);
+                v1 = fmaxf(v1, 0.f);
+            }
+            const __nv_bfloat162 a2 = __floats2bfloat162_rn(v0, v1);
+            *reinterpret_cast<__nv_bfloat162*>(p.a_out + pix * p.cout_pad + co) = a2;
+            if (p.skip) {
+                const __nv_bfloat162 s2 =
+                    *reinterpret_cast<const __nv_bfloat162*>(p.skip + pix * p.cout_pad + co);
+                const float2 af = __bfloat1622float2(a2), sf = __bfloat1622float2(s2);
+                *reinterpret_cast<__nv_bfloat162*>(p.y_out + pix * p.cout_pad + co) =
+                    __floats2bfloat162_rn(af.x + sf.x, af.y + sf.y);
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------- wgrad
+// dW[tap][ci][co] += sum over pixels p of x[p + tap offset][ci] * dz[p][co].
+// Per tap a GEMM with M = co, N = ci, K = pixels; CTA s takes pixel chunks
+// (WG_PIX consecutive pixels of one image row) s, s + gridDim.x, ... through a
+// two-stage cp.async pipeline.  Warps split the (CO/16) x (CI/16) blocks.
+template <int CI, int CO>
+struct WgradSmem {
+    static constexpr int XS = CI + 8, DS = CO + 8;
+    static constexpr int STAGE = WG_PIX * (XS + DS);
+    static constexpr size_t bytes = (size_t)2 * STAGE * 2;
+};
+
+template <int CI, int CO>
+__global__ void __launch_bounds__(WG_THREADS) k_wgrad(const WgradParams p) {
+    using L = WgradSmem<CI, CO>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    bf16* sbase = reinterpret_cast<bf16*>(smem);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tap = blockIdx.y, ky = tap / 3, kx = tap - 3 * (tap / 3);
+    const int chunks_per_row = p.W / WG_PIX;
+    const long long nchunks = (long long)p.B * p.H * chunks_per_row;
+    constexpr int MB = CO / 16, NB = CI / 16, NBLK = MB * NB;
+    constexpr int PER = (NBLK + WG_WARPS - 1) / WG_WARPS;  // blocks per warp
+    float acc[PER][2][4];
+#pragma unroll
+    for (int k = 0; k < PER; ++k)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) acc[k][h][0] = acc[k][h][1] = acc[k][h][2] = acc[k][h][3] = 0.f;
+
+    auto load = [&](long long c, int stage) {
+        bf16* sX = sbase + stage * L::STAGE;
+        bf16* sD = sX + WG_PIX * L::XS;
+        const int xq = (int)(c % chunks_per_row);
+        const long long rowid = c / chunks_per_row;
+        const int y = (int)(rowid % p.H), b = (int)(rowid / p.H);
+        const int x0 = xq * WG_PIX;
+        const int ys = wrap(y + ky - 1, p.H);
+        constexpr int CHX = CI / 8, CHD = CO / 8;
+        for (int i = tid; i < WG_PIX * CHX; i += WG_THREADS) {
+            const int px = i / CHX, cc = i - px * CHX;
+            const int xs = wrap(x0 + px + kx - 1, p.W);
+            cp_async16(sX + px * L::XS + cc * 8, p.x + (((size_t)b * p.H + ys) * p.W + xs) * CI + cc * 8);
+        }
+        for (int i = tid; i < WG_PIX * CHD; i += WG_THREADS) {
+            const int px = i / CHD, cc = i - px * CHD;
+            cp_async16(sD + px * L::DS + cc * 8, p.dz + (((size_t)b * p.H + y) * p.W + x0 + px) * CO + cc * 8);
+        }
+    };
+
+    long long c = blockIdx.x;
+    int stage = 0;
+    if (c < nchunks) load(c, 0);
+    cp_async_commit();
+    for (; c < nchunks; c += gridDim.x) {
+        const long long cn = c + gridDim.x;
+        if (cn < nchunks) load(cn, stage ^ 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const bf16* sX = sbase + stage * L::STAGE;
+        const bf16* sD = sX + WG_PIX * L::XS;
+#pragma unroll
+        for (int ks = 0; ks < WG_PIX / 16; ++ks) {
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                const int blk = warp + k * WG_WARPS;
+                if (blk >= NBLK) break;
+                const int mb = blk / NB, nb = blk - mb * NB;
+                const int j = lane >> 3;
+                uint32_t a[4], bb[4];
+                // A (co x px) from dz stored [px][co]: transposing load
+                ldsm_x4_t(a, sD + (ks * 16 + (j >> 1) * 8 + (lane & 7)) * L::DS + mb * 16 + (j & 1) * 8);
+                // B (px x ci) from x stored [px][ci]: transposing load, two n-tiles
+                ldsm_x4_t(bb, sX + (ks * 16 + (j & 1) * 8 + (lane & 7)) * L::XS + nb * 16 + (j >> 1) * 8);
+                mma_bf16(acc[k][0], a, bb[0], bb[1]);
+                mma_bf16(acc[k][1], a, bb[2], bb[3]);
+            }
+        }
+        __syncthreads();  // the stage is refilled next
+        stage ^= 1;
+    }
+    cp_async_wait<0>();
+    // accumulate into dW[tap][ci][co] (real channel counts)
+    const int g = lane >> 2, cq = (lane & 3) * 2;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int blk = warp + k * WG_WARPS;
+        if (blk >= NBLK) break;
+        const int mb = blk / NB, nb = blk - mb * NB;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int co = mb * 16 + g + (e >= 2 ? 8 : 0);
+                const int ci = nb * 16 + h * 8 + cq + (e & 1);
+                if (co < p.cout && ci < p.cin)
+                    atomicAdd(p.dw + ((size_t)tap * p.cin + ci) * p.cout + co, acc[k][h][e]);
+            }
+    }
+}
+
+// ----------------------------------------------------------- elementwise
+
+// field layout (3 planes) -> bfloat16 NHWC with 16 channels, scaled
+__global__ void k_pack_input(const float* J, long long bstride, long long cstride, int pitch,
+                             int offset, int B, int H, int W, float inv_scale, bf16* out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)B * H * W) return;
+    const int x = (int)(i % W);
+    const long long t = i / W;
+    const int y = (int)(t % H), b = (int)(t / H);
+    const float* s = J + b * bstride + offset + (long long)y * pitch + x;
+    __align__(16) bf16 v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(c < 3 ? s[c * cstride] * inv_scale : 0.f);
+    uint4* o = reinterpret_cast<uint4*>(out + i * 16);
+    o[0] = reinterpret_cast<const uint4*>(v)[0];
+    o[1] = reinterpret_cast<const uint4*>(v)[1];
+}
+
+// 2x2 mean pooling, bfloat16 -> bfloat16 (FP32 sum of the four)
+__global__ void k_pool_fwd(const bf16* in, int B, int H, int W, int C, bf16* out) {
+    const int G = C / 8;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int Ho = H / 2, Wo = W / 2;
+    if (i >= (long long)B * Ho * Wo * G) return;
+    const int gi = (int)(i % G);
+    const long long pix = i / G;
+    const int x = (int)(pix % Wo);
+    const long long t = pix / Wo;
+    const int y = (int)(t % Ho), b = (int)(t / Ho);
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+            const uint4 u = *reinterpret_cast<const uint4*>(
+                in + (((size_t)b * H + 2 * y + dy) * W + 2 * x + dx) * C + gi * 8);
+            const bf16* v = reinterpret_cast<const bf16*>(&u);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s[k] += __bfloat162float(v[k]);
+        }
+    __align__(16) bf16 o[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) o[k] = __float2bfloat16_rn(0.25f * s[k]);
+    *reinterpret_cast<uint4*>(out + pix * C + gi * 8) = *reinterpret_cast<const uint4*>(o);
+}
+
+// nearest 2x upsampling, bfloat16 (out has 2H x 2W)
+__global__ void k_up_fwd(const bf16* in, int B, int H, int W, int C, bf16* out) {
+    const int G = C / 8;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int Ho = 2 * H, Wo = 2 * W;
+    if (i >= (long long)B * Ho * Wo * G) return;
+    const int gi = (int)(i % G);
+    const long long pix = i / G;
+    const int x = (int)(pix % Wo);
+    const long long t = pix / Wo;
+    const int y = (int)(t % Ho), b = (int)(t / Ho);
+    *reinterpret_cast<uint4*>(out + pix * C + gi * 8) = *reinterpret_cast<const uint4*>(
+        in + (((size_t)b * H + y / 2) * W + x / 2) * C + gi * 8);
+}
+
+// adjoint of pooling: out (H x W) = in (H/2 x W/2) / 4, FP32
+__global__ void k_pool_back(const float* in, int B, int H, int W, int C, float* out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)B * H * W * C / 4) return;
+    const int G = C / 4;
+    const int gi = (int)(i % G);
+    const long long pix = i / G;
+    const int x = (int)(pix % W);
+    const long long t = pix / W;
+    const int y = (int)(t % H), b = (int)(t / H);
+    float4 v = *reinterpret_cast<const float4*>(
+        in + (((size_t)b * (H / 2) + y / 2) * (W / 2) + x / 2) * C + gi * 4);
+    v.x *= 0.25f;
+    v.y *= 0.25f;
+    v.z *= 0.25f;
+    v.w *= 0.25f;
+    *reinterpret_cast<float4*>(out + pix * C + gi * 4) = v;
+}
+
+// adjoint of upsampling: out (H x W) = sum of the 2x2 block of in (2H x 2W), FP32
+__global__ void k_up_back(const float* in, int B, int H, int W, int C, float* out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)B * H * W * C / 4) return;
+    const int G = C / 4;
+    const int gi = (int)(i % G);
+    const long long pix = i / G;
+    const int x = (int)(pix % W);
+    const long long t = pix / W;
+    const int y = (int)(t % H), b = (int)(t / H);
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+            const float4 v = *reinterpret_cast<const float4*>(
+                in + (((size_t)b * 2 * H + 2 * y + dy) * 2 * W + 2 * x + dx) * C + gi * 4);
+            s.x += v.x;
+            s.y += v.y;
+            s.z += v.z;
+            s.w += v.w;
+        }
+    *reinterpret_cast<float4*>(out + pix * C + gi * 4) = s;
+}
+
+// dz = bf16((dy + extra) * (a > 0)); db[c] += sum over pixels of the FP32 product
+__global__ void __launch_bounds__(256) k_relu_back(const float* dy, const float* extra,
+                                                   const bf16* a, long long npix, int C, bf16* dz,
+                                                   float* db) {
+    __shared__ float sdb[128];
+    for (int c = threadIdx.x; c < C; c += blockDim.x) sdb[c] = 0.f;
+    __syncthreads();
+    const int G = C / 8;
+    float part[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int myg = -1;
+    const long long total = npix * G;
+    // the grid stride is a multiple of G, so a thread keeps its channel group
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        const int gi = (int)(i % G);
+        myg = gi;
+        const long long pix = i / G;
+        const float* d = dy + pix * C + gi * 8;
+        float v[8];
+        const float4 d0 = *reinterpret_cast<const float4*>(d);
+        const float4 d1 = *reinterpret_cast<const float4*>(d + 4);
+        v[0] = d0.x; v[1] = d0.y; v[2] = d0.z; v[3] = d0.w;
+        v[4] = d1.x; v[5] = d1.y; v[6] = d1.z; v[7] = d1.w;
+        if (extra) {
+            const float4 e0 = *reinterpret_cast<const float4*>(extra + pix * C + gi * 8);
+            const float4 e1 = *reinterpret_cast<const float4*>(extra + pix * C + gi * 8 + 4);
+            v[0] += e0.x; v[1] += e0.y; v[2] += e0.z; v[3] += e0.w;
+            v[4] += e1.x; v[5] += e1.y; v[6] += e1.z; v[7] += e1.w;
+        }
+        if (a) {
+            const uint4 u = *reinterpret_cast<const uint4*>(a + pix * C + gi * 8);
+            const bf16* av = reinterpret_cast<const bf16*>(&u);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (!(__bfloat162float(av[k]) > 0.f)) v[k] = 0.f;
+        }
+        __align__(16) bf16 o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            part[k] += v[k];
+            o[k] = __float2bfloat16_rn(v[k]);
+        }
+        *reinterpret_cast<uint4*>(dz + pix * C + gi * 8) = *reinterpret_cast<const uint4*>(o);
+    }
+    if (myg >= 0)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) atomicAdd(&sdb[myg * 8 + k], part[k]);
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) atomicAdd(db + c, sdb[c]);
+}
+
+// MSE of the normalised output against the normalised target; dz11 (16
+// channels, bfloat16) = bf16(2 (out - t) / N); db11 += the FP32 gradient.
+__global__ void __launch_bounds__(256) k_mse(const float* out, const float* target,
+                                             long long bstride, long long cstride, int pitch,
+                                             int offset, int B, int H, int W, float inv_scale,
+                                             double inv_n, bf16* dz, float* db, double* loss) {
+    __shared__ double sred[8];
+    __shared__ float sdb[3];
+    if (threadIdx.x < 3) sdb[threadIdx.x] = 0.f;
+    __syncthreads();
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    float gsum[3] = {0.f, 0.f, 0.f};
+    if (i < (long long)B * H * W) {
+        const int x = (int)(i % W);
+        const long long t = i / W;
+        const int y = (int)(t % H), b = (int)(t / H);
+        const long long o = b * bstride + offset + (long long)y * pitch + x;
+        // out is the normalised network output in a dense [B][3][H][W] buffer
+        const long long od = ((long long)b * 3) * H * W + (long long)y * W + x;
+        __align__(16) bf16 v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(0.f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float d = out[od + (long long)c * H * W] - target[o + c * cstride] * inv_scale;
+            l += (double)d * d;
+            const float gr = (float)(2.0 * inv_n) * d;
+            gsum[c] = gr;
+            v[c] = __float2bfloat16_rn(gr);
+        }
+        uint4* q = reinterpret_cast<uint4*>(dz + i * 16);
+        q[0] = reinterpret_cast<const uint4*>(v)[0];
+        q[1] = reinterpret_cast<const uint4*>(v)[1];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float s = gsum[c];
+#pragma unroll
+        for (int k = 16; k > 0; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&sdb[c], s);
+    }
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) l += __shfl_xor_sync(0xffffffffu, l, k);
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sred[w];
+        atomicAdd(loss, s * inv_n);
+    }
+    if (threadIdx.x < 3) atomicAdd(db + threadIdx.x, sdb[threadIdx.x]);
+}
+
+// Adam (Kingma & Ba, Algorithm 1) on the FP32 master parameters; c1, c2 are
+// the bias corrections 1/(1 - beta^t).
+__global__ void k_adam(float* p, const float* g, float* m, float* v, long long n, float lr,
+                       float b1, float b2, float eps, float c1, float c2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+}
+
+// master FP32 weights [tap][ci][co] -> bfloat16 forward [tap][co_pad][ci_pad]
+// and input-gradient [tap'][ci_padn][co_pad16] layouts (tap' = 8 - tap)
+__global__ void k_pack_weights(const PackTable t, const float* master, bf16* wf, bf16* wd) {
+    const int l = blockIdx.y;
+    if (l >= t.n) return;
+    const LayerDesc& d = t.layer[l];
+    const long long nf = 9LL * d.cout_pad * d.cin_pad;
+    const long long nd = 9LL * d.dg_cout_pad * d.dg_cin_pad;
+    const float* w = master + d.woff;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nf + nd;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (i < nf) {
+            const int ci = (int)(i % d.cin_pad);
+            const long long r = i / d.cin_pad;
+            const int co = (int)(r % d.cout_pad), tap = (int)(r / d.cout_pad);
+            const float v = (ci < d.cin && co < d.cout) ? w[((long long)tap * d.cin + ci) * d.cout + co] : 0.f;
+            wf[d.wf_off + i] = __float2bfloat16_rn(v);
+        } else if (d.dg_cout_pad > 0) {
+            const long long k = i - nf;
+            const int co = (int)(k % d.dg_cin_pad);   // the layer's output channel (k of the dgrad GEMM)
+            const long long r = k / d.dg_cin_pad;
+            const int ci = (int)(r % d.dg_cout_pad), tp = (int)(r / d.dg_cout_pad);
+            const int tap = 8 - tp;
+            const float v = (ci < d.cin && co < d.cout) ? w[((long long)tap * d.cin + ci) * d.cout + co] : 0.f;
+            wd[d.wd_off + k] = __float2bfloat16_rn(v);
+        }
+    }
+}
+
+template <int CIN, int CT>
+cudaError_t conv_attr() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_conv<CIN, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ConvSmem<CIN, CT>::bytes);
+    done = e == cudaSuccess;
+    return e;
+}
+
+template <int CI, int CO>
+cudaError_t wgrad_attr() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)WgradSmem<CI, CO>::bytes);
+    done = e == cudaSuccess;
+    return e;
+}
+
+template <int CIN, int CT>
+cudaError_t conv_T(const ConvParams& p, cudaStream_t s) {
+    cudaError_t e = conv_attr<CIN, CT>();
+    if (e != cudaSuccess) return e;
+    const dim3 grid((p.W / TW) * (p.H / TH), p.B, p.cout_pad / CT);
+    k_conv<CIN, CT><<<grid, CONV_THREADS, ConvSmem<CIN, CT>::bytes, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int CI, int CO>
+cudaError_t wgrad_T(const WgradParams& p, int nsplit, cudaStream_t s) {
+    cudaError_t e = wgrad_attr<CI, CO>();
+    if (e != cudaSuccess) return e;
+    k_wgrad<CI, CO><<<dim3(nsplit, 9), WG_THREADS, WgradSmem<CI, CO>::bytes, s>>>(p);
+    return cudaGetLastError();
+}
+
+int blocks(long long n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+#define PIC_CONV_SHAPES(X) \
+    X(16, 32) X(16, 64) X(16, 8) X(32, 32) X(32, 64) X(32, 8) X(64, 32) X(64, 64) X(128, 32) X(128, 64)
+#define PIC_WGRAD_SHAPES(X) \
+    X(16, 32) X(32, 32) X(32, 64) X(64, 64) X(64, 128) X(128, 128) X(128, 64) X(64, 32) X(32, 16)
+
+cudaError_t init_kernels() {
+    cudaError_t e = cudaSuccess;
+#define PIC_C_ATTR(A, B) if (e == cudaSuccess) e = conv_attr<A, B>();
+#define PIC_W_ATTR(A, B) if (e == cudaSuccess) e = wgrad_attr<A, B>();
+    PIC_CONV_SHAPES(PIC_C_ATTR)
+    PIC_WGRAD_SHAPES(PIC_W_ATTR)
+#undef PIC_C_ATTR
+#undef PIC_W_ATTR
+    return e;
+}
+
+// CIN in {16, 32, 64, 128}; CT in {8, 32, 64} (cout_pad a multiple of CT)
+cudaError_t launch_conv(const ConvParams& p, int cin, int ct, cudaStream_t s) {
+    if (p.H % TH || p.W % TW || p.cout_pad % ct) return cudaErrorInvalidValue;
+#define PIC_CONV_CASE(CI, C) \
+    if (cin == CI && ct == C) return conv_T<CI, C>(p, s);
+    PIC_CONV_SHAPES(PIC_CONV_CASE)
+#undef PIC_CONV_CASE
+    return cudaErrorInvalidValue;
+}
+
+// CI = x channels, CO = dz channels (both padded to 16)
+cudaError_t launch_wgrad(const WgradParams& p, int ci, int co, cudaStream_t s) {
+    if (p.W % WG_PIX) return cudaErrorInvalidValue;
+    const long long nchunks = (long long)p.B * p.H * (p.W / WG_PIX);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int nsplit = (int)std::min<long long>(nchunks, (long long)(2 * sms + 8) / 9 * 4);
+    if (nsplit < 1) nsplit = 1;
+#define PIC_WG_CASE(A, B) \
+    if (ci == A && co == B) return wgrad_T<A, B>(p, nsplit, s);
+    PIC_WGRAD_SHAPES(PIC_WG_CASE)
+#undef PIC_WG_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_pack_input(const float* J, long long bstride, long long cstride, int pitch,
+                              int offset, int B, int H, int W, float inv_scale, __nv_bfloat16* out,
+                              cudaStream_t s) {
+    const long long n = (long long)B * H * W;
+    if (n == 0) return cudaSuccess;
+    k_pack_input<<<blocks(n, 256), 256, 0, s>>>(J, bstride, cstride, pitch, offset, B, H, W,
+                                                 inv_scale, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pool_fwd(const __nv_bfloat16* in, int B, int H, int W, int C,
+                            __nv_bfloat16* out, cudaStream_t s) {
+    const long long n = (long long)B * (H / 2) * (W / 2) * (C / 8);
+    k_pool_fwd<<<blocks(n, 256), 256, 0, s>>>(in, B, H, W, C, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_up_fwd(const __nv_bfloat16* in, int B, int H, int W, int C, __nv_bfloat16* out,
+                          cudaStream_t s) {
+    const long long n = (long long)B * (2 * H) * (2 * W) * (C / 8);
+    k_up_fwd<<<blocks(n, 256), 256, 0, s>>>(in, B, H, W, C, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pool_back(const float* in, int B, int H, int W, int C, float* out,
+                             cudaStream_t s) {
+    const long long n = (long long)B * H * W * C / 4;
+    k_pool_back<<<blocks(n, 256), 256, 0, s>>>(in, B, H, W, C, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_up_back(const float* in, int B, int H, int W, int C, float* out,
+                           cudaStream_t s) {
+    const long long n = (long long)B * H * W * C / 4;
+    k_up_back<<<blocks(n, 256), 256, 0, s>>>(in, B, H, W, C, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relu_back(const float* dy, const float* extra, const __nv_bfloat16* a,
+                             long long npix, int C, __nv_bfloat16* dz, float* db, cudaStream_t s) {
+    const int G = C / 8;
+    // threads a multiple of G: each thread keeps one channel group
+    const long long work = npix * G;
+    long long nb = std::min<long long>((work + 255) / 256, 4 * 152);
+    if (nb < 1) nb = 1;
+    k_relu_back<<<(int)nb, 256, 0, s>>>(dy, extra, a, npix, C, dz, db);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mse(const float* out, const float* target, long long bstride, long long cstride,
+                       int pitch, int offset, int B, int H, int W, float inv_scale,
+                       __nv_bfloat16* dz, float* db, double* loss, cudaStream_t s) {
+    const long long n = (long long)B * H * W;
+    const double inv_n = 1.0 / (3.0 * (double)n);
+    k_mse<<<blocks(n, 256), 256, 0, s>>>(out, target, bstride, cstride, pitch, offset, B, H, W,
+                                         inv_scale, inv_n, dz, db, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr,
+                        float b1, float b2, float eps, float c1, float c2, cudaStream_t s) {
+    k_adam<<<blocks(n, 256), 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_weights(const PackTable& t, const float* master, __nv_bfloat16* wf,
+                                __nv_bfloat16* wd, cudaStream_t s) {
+    k_pack_weights<<<dim3(64, t.n), 256, 0, s>>>(t, master, wf, wd);
+    return cudaGetLastError();
+}
+
+}  // namespace nn
+}  // namespace pic

@@ -539,6 +539,8 @@ pic_status pic_batch_create(pic_sim* const* members, int n, void* cuda_stream, p
             why = "member listed twice";
         else if (k > 0 && ((sim->cfg.flags ^ members[0]->cfg.flags) & PIC_STRICT_FP))
             why = "members differ in PIC_STRICT_FP";
+        else if (sim->jfilter)
+            why = "member has a current filter installed";
         if (!why.empty()) {
             if (sim) fail(sim, PIC_EINVAL, "pic_batch_create: %s", why.c_str());
             delete batch;
@@ -573,6 +575,9 @@ pic_status pic_batch_step(pic_batch* batch, int nsteps) {
     if (nsteps < 0) return bfail(batch, PIC_EINVAL, "negative step count");
     batch->err.clear();
     if (batch->m.empty()) return PIC_OK;
+    for (pic_sim* sim : batch->m)
+        if (sim->jfilter)
+            return bfail(batch, PIC_EINVAL, "a member has a current filter installed");
     for (int k = 0; k < nsteps; ++k) {
         if (stale(batch)) {
             pic_status r = prepare(batch);

@@ -261,6 +261,13 @@ int enqueue_step(pic_sim* sim, cudaStream_t s, int b, cudaEvent_t ev_a, cudaEven
     if ((e = launch_evict(sp, threads, s)) != cudaSuccess) goto bad;
     if ((e = launch_fill(sp, threads, s)) != cudaSuccess) goto bad;
     n += (sp.nsp > 0 && sim->g.ntiles > 0) ? 2 : 0;
+    if (sim->jfilter) {
+        // the current-filter slot of Listing 3.1: after the deposit and its
+        // guard-cell reduction, before the field advance
+        const int k = sim->jfilter(sim->jfilter_ctx, sim, s, b);
+        if (k < 0) return -1;
+        n += k;
+    }
     if ((e = launch_yee(yp, s)) != cudaSuccess) goto bad;
     n += 1;
     return n;

@@ -105,11 +105,34 @@ def load_library() -> C.CDLL:
         L.pic_autotune.argtypes = [_P, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                    C.POINTER(C.c_double)]
         L.pic_set_tiling.argtypes = [_P, C.c_int, C.c_int]
+        L.pic_denoiser_num_params.argtypes = []
+        L.pic_denoiser_num_params.restype = C.c_int64
+        L.pic_denoiser_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, _P, C.POINTER(_P)]
+        L.pic_denoiser_set_params.argtypes = [_P, _P, C.c_int]
+        L.pic_denoiser_get_params.argtypes = [_P, _P, C.c_int]
+        L.pic_denoiser_forward.argtypes = [_P, _P, _P, C.c_int, C.c_int]
+        L.pic_denoiser_grad.argtypes = [_P, _P, _P, C.c_int, C.POINTER(C.c_double), _P, C.c_int]
+        L.pic_denoiser_train_step.argtypes = [_P, _P, _P, C.c_int, C.c_float,
+                                              C.POINTER(C.c_double), C.c_int]
+        L.pic_set_denoiser.argtypes = [_P, _P]
+        L.pic_denoiser_last_error.argtypes = [_P]
+        L.pic_denoiser_last_error.restype = C.c_char_p
+        L.pic_denoiser_destroy.argtypes = [_P]
+        L.pic_denoiser_destroy.restype = None
+        L.pic_nn_conv3x3.argtypes = [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P,
+                                     C.c_int, _P, _P, _P, _P]
+        L.pic_nn_conv3x3_dgrad.argtypes = [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P,
+                                           _P, _P]
+        L.pic_nn_conv3x3_wgrad.argtypes = [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                           _P, _P]
         for name in ("pic_init", "pic_load_particles", "pic_set_fields", "pic_step",
                      "pic_get_fields", "pic_get_particles", "pic_diagnostics",
                      "pic_get_history", "pic_sync", "pic_clear_status", "pic_timing",
                      "pic_init_batch", "pic_batch_create", "pic_batch_step", "pic_batch_sync",
-                     "pic_autotune", "pic_set_tiling"):
+                     "pic_autotune", "pic_set_tiling", "pic_denoiser_create",
+                     "pic_denoiser_set_params", "pic_denoiser_get_params", "pic_denoiser_forward",
+                     "pic_denoiser_grad", "pic_denoiser_train_step", "pic_set_denoiser",
+                     "pic_nn_conv3x3", "pic_nn_conv3x3_dgrad", "pic_nn_conv3x3_wgrad"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -330,6 +353,118 @@ def pic_set_tiling(h, tile, threads=0):
     _check(h, load_library().pic_set_tiling(h, tile, threads))
 
 
+# ------------------------------------------------------------ denoiser
+
+def _dcheck(d, status):
+    if status != 0:
+        msg = load_library().pic_denoiser_last_error(d) if d else b""
+        raise PicError(status, (msg or b"").decode())
+
+
+def pic_denoiser_num_params():
+    return int(load_library().pic_denoiser_num_params())
+
+
+def pic_denoiser_create(nx, ny, batch_max, scale, stream=None):
+    d = _P()
+    if stream is None:
+        stream = _default_stream()
+    st = load_library().pic_denoiser_create(nx, ny, batch_max, float(scale), stream, C.byref(d))
+    if st != 0:
+        raise PicError(st, "pic_denoiser_create")
+    return d
+
+
+def pic_denoiser_set_params(d, params):
+    p, dev = _ptr(params, np.float32)
+    _dcheck(d, load_library().pic_denoiser_set_params(d, p, int(dev)))
+
+
+def pic_denoiser_get_params(d, out):
+    p, dev = _ptr(out, np.float32)
+    _dcheck(d, load_library().pic_denoiser_get_params(d, p, int(dev)))
+
+
+def _same_place(*arrs):
+    ptrs = [_ptr(a, np.float32) for a in arrs if a is not None]
+    devs = {dv for _, dv in ptrs}
+    if len(devs) != 1:
+        raise ValueError("buffers must all be on the host or all on the device")
+    return [p for p, _ in ptrs], devs.pop()
+
+
+def pic_denoiser_forward(d, J_in, J_out, batch):
+    (pi, po), dev = _same_place(J_in, J_out)
+    _dcheck(d, load_library().pic_denoiser_forward(d, pi, po, batch, int(dev)))
+
+
+def pic_denoiser_grad(d, J_in, J_target, batch, grads=None):
+    ptrs, dev = _same_place(J_in, J_target, grads)
+    loss = C.c_double()
+    _dcheck(d, load_library().pic_denoiser_grad(d, ptrs[0], ptrs[1], batch, C.byref(loss),
+                                                ptrs[2] if grads is not None else None, int(dev)))
+    return loss.value
+
+
+def pic_denoiser_train_step(d, J_in, J_target, batch, lr):
+    (pi, pt), dev = _same_place(J_in, J_target)
+    loss = C.c_double()
+    _dcheck(d, load_library().pic_denoiser_train_step(d, pi, pt, batch, float(lr),
+                                                      C.byref(loss), int(dev)))
+    return loss.value
+
+
+def pic_set_denoiser(h, d):
+    _check(h, load_library().pic_set_denoiser(h, d))
+
+
+def pic_denoiser_destroy(d):
+    load_library().pic_denoiser_destroy(d)
+
+
+def _dptr(t):
+    """device pointer of a contiguous torch CUDA tensor (any dtype)."""
+    if t is None:
+        return None
+    if not (_is_torch(t) and t.is_cuda and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def pic_nn_conv3x3(x, w, bias, a_out, relu=True, skip=None, y_out=None, stream=None):
+    """x, skip, a_out, y_out: bfloat16 NHWC CUDA tensors; w [3,3,cin,cout], bias FP32."""
+    B, H, W, _ = x.shape
+    cin, cout = int(w.shape[2]), int(w.shape[3])
+    if stream is None:
+        stream = _default_stream()
+    st = load_library().pic_nn_conv3x3(_dptr(x), B, H, W, cin, cout, _dptr(w), _dptr(bias),
+                                       int(relu), _dptr(skip), _dptr(a_out), _dptr(y_out), stream)
+    if st != 0:
+        raise PicError(st, "pic_nn_conv3x3")
+
+
+def pic_nn_conv3x3_dgrad(dz, w, dx, stream=None):
+    B, H, W, _ = dz.shape
+    cin, cout = int(w.shape[2]), int(w.shape[3])
+    if stream is None:
+        stream = _default_stream()
+    st = load_library().pic_nn_conv3x3_dgrad(_dptr(dz), B, H, W, cin, cout, _dptr(w), _dptr(dx),
+                                             stream)
+    if st != 0:
+        raise PicError(st, "pic_nn_conv3x3_dgrad")
+
+
+def pic_nn_conv3x3_wgrad(x, dz, dw, stream=None):
+    B, H, W, _ = x.shape
+    cin, cout = int(dw.shape[2]), int(dw.shape[3])
+    if stream is None:
+        stream = _default_stream()
+    st = load_library().pic_nn_conv3x3_wgrad(_dptr(x), _dptr(dz), B, H, W, cin, cout, _dptr(dw),
+                                             stream)
+    if st != 0:
+        raise PicError(st, "pic_nn_conv3x3_wgrad")
+
+
 def pic_tile_sort_noalloc(nx, ny, tile, ix, iy, x, y, ux, uy, uz, ix_out, iy_out, x_out,
                           y_out, ux_out, uy_out, uz_out, tile_offset, stream=None):
     """Allocation-free tile sort of device arrays into device arrays (see pic.h)."""
@@ -483,6 +618,58 @@ class Batch:
         if self.b:
             pic_batch_destroy(self.b)
             self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Denoiser:
+    """Owner of a pic_denoiser handle."""
+
+    def __init__(self, nx, ny, batch_max=1, scale=1.0, stream=None):
+        self.nx, self.ny, self.batch_max, self.scale = nx, ny, batch_max, scale
+        self.d = pic_denoiser_create(nx, ny, batch_max, scale, stream)
+
+    @staticmethod
+    def num_params():
+        return pic_denoiser_num_params()
+
+    def set_params(self, flat):
+        pic_denoiser_set_params(self.d, flat)
+
+    def params(self):
+        out = np.empty(self.num_params(), np.float32)
+        pic_denoiser_get_params(self.d, out)
+        return out
+
+    def forward(self, J_in, J_out=None):
+        batch = J_in.shape[0] if J_in.ndim == 4 else 1
+        if J_out is None:
+            J_out = np.empty_like(J_in)
+        pic_denoiser_forward(self.d, J_in, J_out, batch)
+        return J_out
+
+    def grad(self, J_in, J_target, grads=None):
+        batch = J_in.shape[0] if J_in.ndim == 4 else 1
+        return pic_denoiser_grad(self.d, J_in, J_target, batch, grads)
+
+    def train_step(self, J_in, J_target, lr):
+        batch = J_in.shape[0] if J_in.ndim == 4 else 1
+        return pic_denoiser_train_step(self.d, J_in, J_target, batch, lr)
+
+    def close(self):
+        if self.d:
+            pic_denoiser_destroy(self.d)
+            self.d = None
 
     def __enter__(self):
         return self
