@@ -45,6 +45,10 @@ WORKLOADS = {
     # ppc from {4,16,64}, drift U[0.1,0.5], u_th 0.05, per-simulation seeds)
     # stepped as one batch; tiles and threads autotuned per (grid, ppc)
     "batched_64": dict(kind="batch", kw=dict(members=64), tile=0),
+    # learned current denoiser: 256x256 two-stream draws, 2,000 training pairs
+    # (64 ppc vs its 1/16 subsample), the denoised 4-ppc run against 64 ppc
+    "denoiser": dict(kind="denoiser", kw=dict(nx=256, ny=256, pairs_per_draw=200, draws=10,
+                                              iters=4000, batch=16), tile=16),
 }
 
 
@@ -327,6 +331,115 @@ def run_batched(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_denoiser(args, rank, world, local_rank):
+    """Learned denoiser: pairs from 64-ppc runs, training on the GPU, then true
+    4-ppc runs with the network in the current-filter slot against plain 64-ppc
+    and 4-ppc runs of the same draws (growth rate, field-energy history, step
+    time)."""
+    import torch
+    from paper_2501_14795_gb300 import denoise as dn
+    from paper_2501_14795_gb300 import pic
+
+    torch.cuda.set_device(local_rank)
+    kw = WORKLOADS["denoiser"]["kw"]
+    nx, ny, B = kw["nx"], kw["ny"], kw["batch"]
+    t0 = time.perf_counter()
+    every = max(1, 600 // kw["pairs_per_draw"])
+    Jn, Jc = dn.make_pairs(dn.draws(kw["draws"]), nx, ny, steps=600, every=every)
+    pair_s = time.perf_counter() - t0
+    n_pairs = int(Jn.shape[0])
+    Vn, Vc = dn.make_pairs(dn.draws(2, offset=400), nx, ny, steps=600, every=20)
+    scale = float(Jc.pow(2).mean().sqrt())
+    net = pic.Denoiser(nx, ny, B, scale)
+    net.set_params(dn.init_params(dn.SEED_DENOISER + 999))
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    ev0.record(stream)
+    losses = dn.train(net, Jn, Jc, kw["iters"], B, lr=1e-3, lr_min=5e-5, seed=11)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = ev0.elapsed_time(ev1)
+    raw, den = dn.mse_gain(net, Vn, Vc, B)
+    del Jn, Jc
+    # forward pass alone, one sample (the in-loop use)
+    x = Vn[:1].contiguous()
+    o = torch.empty_like(x)
+    for _ in range(3):
+        pic.pic_denoiser_forward(net.d, x, o, 1)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    nf = 50
+    for _ in range(nf):
+        pic.pic_denoiser_forward(net.d, x, o, 1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = ev0.elapsed_time(ev1) / nf
+
+    steps = args.steps
+    results = []
+    for d in dn.draws(3, offset=500):
+        theory = dn.kinetic_growth_rate(d.drift, d.u_th, nx * 0.1)
+        row = {"seed": d.seed, "drift": d.drift, "u_th": d.u_th, "theory_gamma": theory,
+               "eligible": theory > 0.05}
+        runs = {}
+        for name, k, use in (("ppc64", 8, False), ("ppc4", 2, False), ("ppc4_denoised", 2, True)):
+            w = dn.workload(d, nx, ny, k, steps)
+            we, _, diag, spec = dn.field_energy_run(w, steps, net if use else None, modes=True)
+            _, ms, _, _ = dn.field_energy_run(w, steps, net if use else None)
+            runs[name] = (we, spec, ms, diag)
+        m = int(np.argmax(runs["ppc64"][1][:, 1:].max(axis=0))) + 1
+        lw64 = np.log(np.maximum(runs["ppc64"][0][1:], 1e-300))   # W_E(0) = 0
+        for name, (we, spec, ms, diag) in runs.items():
+            gm, _ = dn.mode_growth_rate(spec, 0.05, m)
+            ge, _ = dn.growth_rate(we, 0.05)
+            row[name] = {"gamma_mode": gm, "gamma_WE": ge, "ms_per_step": ms,
+                         "W_E_max": float(we.max()),
+                         "lnWE_rms_diff_vs_64": float(np.sqrt(np.mean(
+                             (np.log(np.maximum(we[1:], 1e-300)) - lw64) ** 2))),
+                         "continuity_max": diag["continuity_max"]}
+        row["mode"] = m
+        g64 = row["ppc64"]["gamma_mode"]
+        for name in ("ppc4", "ppc4_denoised"):
+            row[name]["gamma_mode_rel_err"] = abs(row[name]["gamma_mode"] - g64) / g64
+        results.append(row)
+    ms64 = float(np.mean([r["ppc64"]["ms_per_step"] for r in results]))
+    msnn = float(np.mean([r["ppc4_denoised"]["ms_per_step"] for r in results]))
+    ms4 = float(np.mean([r["ppc4"]["ms_per_step"] for r in results]))
+    flops = dn.forward_flops(nx, ny)
+    peak = None
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        peak = float(json.load(open(p))["bf16_tflops"])
+    achieved = flops / (fwd_ms * 1e-3) / 1e12
+    train_tflops = 3 * flops * B * kw["iters"] / (train_ms * 1e-3) / 1e12
+    if rank != 0:
+        return
+    elig = [r for r in results if r["eligible"]]
+    line = {
+        "metric": "denoised 4-ppc vs 64-ppc", "value": ms64 / msnn,
+        "unit": "x (64-ppc step time / denoised 4-ppc step time)", "n_gpus": world,
+        "steps": steps, "warmup": 2, "ms_per_step": msnn, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (network) / f32 (PIC)",
+        "data": "synthetic",
+        "config": {"workload": "denoiser", "grid": [nx, ny], "train_pairs": n_pairs,
+                   "iters": kw["iters"], "batch": B, "scale": scale},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "kernel": "denoiser forward, one 256x256 sample (all launches)",
+                     "flops_per_launch": flops, "launch_ms": fwd_ms,
+                     "peak_source": "measured bf16_tflops" if peak else None},
+        "training": {"pair_gen_s": pair_s, "train_ms": train_ms,
+                     "train_tflops": train_tflops, "loss_first": losses[0],
+                     "loss_last50": float(np.mean(losses[-50:]))},
+        "validation_mse": {"raw_4ppc": raw, "denoised": den, "ratio": den / raw},
+        "step_ms": {"ppc64": ms64, "ppc4": ms4, "ppc4_denoised": msnn},
+        "growth": results,
+        "growth_within_5pct": [r["ppc4_denoised"]["gamma_mode_rel_err"] < 0.05 for r in elig],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_2501_14795_gb300 import pic
@@ -455,6 +568,8 @@ def main():
     try:
         if args.workload == "batched_64":
             run_batched(args, rank, world, local_rank)
+        elif args.workload == "denoiser":
+            run_denoiser(args, rank, world, local_rank)
         else:
             run_gpu(args, rank, world, local_rank)
     finally:

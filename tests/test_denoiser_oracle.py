@@ -209,3 +209,14 @@ def test_adam_converges_on_a_quadratic():
         g = {"x": 2 * a * (p["x"] - c)}
         p = opt.step(p, g)
     np.testing.assert_allclose(p["x"], c, atol=1e-3)
+
+
+def test_library_parameter_layout_and_init_match_the_oracle():
+    """The library's flat parameter vector (layer order, [ky][kx][cin][cout]
+    weights then biases) and its seeded initialisation recipe agree with the
+    oracle's, so parameters pass between them unchanged."""
+    from paper_2501_14795_gb300 import denoise as dn
+    assert dn.LAYERS == [(ci, co, lv) for _, ci, co, lv, _, _ in D.LAYERS]
+    np.testing.assert_array_equal(dn.init_params(5), D.flatten(D.init_params(5)).astype(np.float32))
+    assert dn.forward_flops(256, 256) == sum(2.0 * 65536 / 4 ** lv * 9 * ci * co
+                                              for _, ci, co, lv, _, _ in D.LAYERS)
