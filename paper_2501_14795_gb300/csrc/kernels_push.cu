@@ -8,13 +8,11 @@
 //      Villasenor-Buneman split into at most three pieces (Figs. 3.4-3.5);
 //   3. deposit each piece's current (Eqs. 13-16 plus the time-averaged Jz),
 //      computed in FP32, into a J tile, cells [-1, T+2), in shared memory:
-//      one private tile per warp (T <= 16), so warps never contend, holding
-//      exact 32-bit fixed-point sums (native integer shared atomics cost the
-//      same with up to 4 lanes on one word, float ones grow with every
-//      conflicting lane); the scale is bounded so no sum can overflow, and the
-//      tiles are converted to FP32 once, at the flush.  Pieces of a warp that
-//      fall into few cells are first summed across the warp (shuffle
-//      reduce-scatter) and added by 8 lanes, one cell run at a time;
+//      one tile per pair of warps (T <= 16), holding exact 32-bit fixed-point
+//      sums (native integer shared atomics cost the same with up to 4 lanes on
+//      one word, float ones grow with every conflicting lane); the scale is
+//      bounded so no sum can overflow, and the tiles are converted to FP32
+//      once, at the flush;
 //   4. emit the re-sort metadata of §4.3: particles that stay in the tile are
 //      written in place; particles that leave are appended (warp-ballot slots)
 //      to the tile's section of the out arrays with their old position in the
@@ -46,8 +44,26 @@ namespace PIC_VARIANT {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-constexpr int NSTAGE = 4;  // particle batches (blockDim particles each) in flight per CTA
+// build-time tuning knobs
+#ifndef PIC_NSTAGE
+#define PIC_NSTAGE 4
+#endif
+// Two warps share a fixed-point J tile (half the shared memory of per-warp
+// tiles: more CTAs per SM; integer atomics of different warps on one word
+// only queue, they do not fail), and the run aggregation is off: with the
+// pseudo-random order inside a tile a warp's particles almost never share
+// cells, so looking for runs costs more than it saves (measured on GB300:
+// -17 % particle-advance time for the two together on the 512^2 Weibel case).
+#ifndef PIC_WARPS_PER_JTILE
+#define PIC_WARPS_PER_JTILE 2
+#endif
+#ifndef PIC_AGGREGATE
+#define PIC_AGGREGATE 0
+#endif
+constexpr int NSTAGE = PIC_NSTAGE;  // particle batches (blockDim particles each) in flight per CTA
 constexpr int PAD = 4;     // a batch is copied from a 16-byte aligned start: <= 3 extra
+// warps sharing one fixed-point J tile (per-warp tiles: 1)
+constexpr int WPT = PIC_WARPS_PER_JTILE;
 
 // Shared-memory layout of one CTA (blocks of `nth` threads):
 //   [E|B halo FLD floats][J tiles: one per warp (PW) or one per CTA]
@@ -66,7 +82,7 @@ struct Tile {
     static constexpr bool PER_WARP = PW;
     static constexpr int NCNT = MAX_SPECIES * 8 + 4;
 
-    static __host__ __device__ size_t j_tiles(int nth) { return PW ? (nth + 31) / 32 : 1; }
+    static __host__ __device__ size_t j_tiles(int nth) { return PW ? ((nth + 31) / 32 + WPT - 1) / WPT : 1; }
     static __host__ __device__ size_t off_stage(int nth) {
         return ((size_t)FLD * 4 + j_tiles(nth) * JN * 4 + 15) & ~(size_t)15;
     }
@@ -190,7 +206,7 @@ __device__ __forceinline__ void deposit_warp(bool has, int o, const float v[8], 
     const bool head = has && (lane == 0 || prev != o || !((act >> (lane - 1)) & 1u));
     unsigned heads = __ballot_sync(FULL, head);
     const int ng = __popc(heads);
-    if (ng <= AGG_MAX_GROUPS && __popc(act) >= 2 * ng) {
+    if (PIC_AGGREGATE && ng <= AGG_MAX_GROUPS && __popc(act) >= 2 * ng) {
         // few runs: sum each run across the warp, 8 lanes add the totals
         const int k = lane >> 2;
         const int voff = value_offset<JW, JPLANE>(k);
@@ -208,12 +224,14 @@ __device__ __forceinline__ void deposit_warp(bool has, int o, const float v[8], 
             const float tot = warp_reduce_scatter8(s, lane);
             if ((lane & 3) == 0) {
                 float* a = sJw + ko + voff;
-                if constexpr (PER_WARP)  // the 8 targets are distinct; one run at a time
+                if constexpr (PER_WARP && WPT == 1)  // the 8 targets are distinct; one run at a time
                     *reinterpret_cast<int*>(a) += __float2int_rn(tot * qs);
+                else if constexpr (PER_WARP)
+                    atomicAdd(reinterpret_cast<int*>(a), __float2int_rn(tot * qs));
                 else
                     atomicAdd(a, tot);
             }
-            if constexpr (PER_WARP) __syncwarp();
+            if constexpr (PER_WARP && WPT == 1) __syncwarp();
         }
     } else if (has) {
         tile_add<PER_WARP>(sJw + o, v[0], qs);
@@ -245,7 +263,7 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
     uint64_t* sbar = bar + 1;  // one per particle stage
     int* sDir = reinterpret_cast<int*>(smem + L::off_cnt(nth));  // [MAX_SPECIES][8]
     double* sRed = reinterpret_cast<double*>(smem + L::off_red(nth));
-    float* sJw = sJ + (L::PER_WARP ? warp * L::JN : 0);
+    float* sJw = sJ + (L::PER_WARP ? (warp / WPT) * L::JN : 0);
     const int jtiles = (int)L::j_tiles(nth);
     const int SW = nth + PAD;  // words per array per stage
     const unsigned stage_bytes = (unsigned)L::stage_words(nth) * 4u;
@@ -280,16 +298,17 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
     const float cxs = g.cx, cys = g.cy;
     unsigned bad_bits = 0;
     double ke_tot = 0.0;
-    // Fixed-point scale of the per-warp J tiles.  The current one particle
-    // gives to any one node, summed over its pieces, is at most |qtilde| (the
-    // pieces partition a move shorter than a cell per step and the weights sum
-    // to one), and a warp takes at most 32 particles per batch, so every tile
-    // sum stays below 2^30 with this scale: no overflow is possible.
+    // Fixed-point scale of the J tiles.  The current one particle gives to
+    // any one node, summed over its pieces, is at most |qtilde| (the pieces
+    // partition a move shorter than a cell per step and the weights sum to
+    // one), and the WPT warps of a tile take at most 32 particles each per
+    // batch, so every tile sum stays below 2^30 with this scale: no overflow
+    // is possible.
     float qbound = 0.f;
     for (int s = 0; s < prm.nsp; ++s) {
         const int ns = prm.sp[s].off[t + 1] - prm.sp[s].off[t];
         const int ls = (ns + prm.chunks - 1) / prm.chunks;
-        qbound += (float)(((ls + nth - 1) / nth) * 32) * fabsf(prm.sp[s].qjz);
+        qbound += (float)(((ls + nth - 1) / nth) * 32 * WPT) * fabsf(prm.sp[s].qjz);
     }
     const float qscale = qbound > 0.f ? 1073741824.f / qbound : 1.f;
     const float qinv = 1.f / qscale;
