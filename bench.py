@@ -37,6 +37,8 @@ WORKLOADS = {
     # smaller instance of the same physics (8.4M particles, 201 MB state > L2)
     # for profiler captures
     "weibel_256": dict(kind="weibel", kw=dict(nx=256, ny=256, k=8), tile=16),
+    # L2-resident instance (2.1M particles, 50 MB state < L2): compute-bound reference
+    "weibel_128": dict(kind="weibel", kw=dict(nx=128, ny=128, k=8), tile=16),
     "thermal_2048": dict(kind="thermal_seeded", kw=dict(nx=2048, ny=2048, k=4), tile=16),
     # smaller instance (16.8M particles, 403 MB state > L2) for profiler captures
     "thermal_1024": dict(kind="thermal_seeded", kw=dict(nx=1024, ny=1024, k=4), tile=16),

@@ -181,12 +181,13 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float v[8], int lane
 
 constexpr int AGG_MAX_GROUPS = 8;
 
-// Add one value to the J tile: per-warp tiles (PER_WARP) hold exact 32-bit
-// fixed-point sums (value * qs, the CTA's scale); the CTA-wide tile holds FP32.
+// Add one value to the J tile: the fixed-point tiles (PER_WARP) hold exact
+// 32-bit sums of values already multiplied by the CTA's scale; the CTA-wide
+// tile holds FP32.
 template <bool PER_WARP>
-__device__ __forceinline__ void tile_add(float* a, float x, float qs) {
+__device__ __forceinline__ void tile_add(float* a, float x) {
     if constexpr (PER_WARP)
-        atomicAdd(reinterpret_cast<int*>(a), __float2int_rn(x * qs));
+        atomicAdd(reinterpret_cast<int*>(a), __float2int_rn(x));
     else
         atomicAdd(a, x);
 }
@@ -200,12 +201,16 @@ __device__ __forceinline__ void tile_add(float* a, float x, float qs) {
 // simply added several times.  Otherwise every lane adds its eight values.
 template <int JW, int JPLANE, bool PER_WARP>
 __device__ __forceinline__ void deposit_warp(bool has, int o, const float v[8], float* sJw,
-                                             int lane, float qs) {
-    const unsigned act = __ballot_sync(FULL, has);
-    const int prev = __shfl_up_sync(FULL, o, 1);
-    const bool head = has && (lane == 0 || prev != o || !((act >> (lane - 1)) & 1u));
-    unsigned heads = __ballot_sync(FULL, head);
-    const int ng = __popc(heads);
+                                             int lane) {
+    unsigned act = 0, heads = 0;
+    int ng = AGG_MAX_GROUPS + 1;
+    if constexpr (PIC_AGGREGATE) {
+        act = __ballot_sync(FULL, has);
+        const int prev = __shfl_up_sync(FULL, o, 1);
+        const bool head = has && (lane == 0 || prev != o || !((act >> (lane - 1)) & 1u));
+        heads = __ballot_sync(FULL, head);
+        ng = __popc(heads);
+    }
     if (PIC_AGGREGATE && ng <= AGG_MAX_GROUPS && __popc(act) >= 2 * ng) {
         // few runs: sum each run across the warp, 8 lanes add the totals
         const int k = lane >> 2;
@@ -225,23 +230,23 @@ __device__ __forceinline__ void deposit_warp(bool has, int o, const float v[8], 
             if ((lane & 3) == 0) {
                 float* a = sJw + ko + voff;
                 if constexpr (PER_WARP && WPT == 1)  // the 8 targets are distinct; one run at a time
-                    *reinterpret_cast<int*>(a) += __float2int_rn(tot * qs);
+                    *reinterpret_cast<int*>(a) += __float2int_rn(tot);
                 else if constexpr (PER_WARP)
-                    atomicAdd(reinterpret_cast<int*>(a), __float2int_rn(tot * qs));
+                    atomicAdd(reinterpret_cast<int*>(a), __float2int_rn(tot));
                 else
                     atomicAdd(a, tot);
             }
             if constexpr (PER_WARP && WPT == 1) __syncwarp();
         }
     } else if (has) {
-        tile_add<PER_WARP>(sJw + o, v[0], qs);
-        tile_add<PER_WARP>(sJw + o + JW, v[1], qs);
-        tile_add<PER_WARP>(sJw + JPLANE + o, v[2], qs);
-        tile_add<PER_WARP>(sJw + JPLANE + o + 1, v[3], qs);
-        tile_add<PER_WARP>(sJw + 2 * JPLANE + o, v[4], qs);
-        tile_add<PER_WARP>(sJw + 2 * JPLANE + o + 1, v[5], qs);
-        tile_add<PER_WARP>(sJw + 2 * JPLANE + o + JW, v[6], qs);
-        tile_add<PER_WARP>(sJw + 2 * JPLANE + o + JW + 1, v[7], qs);
+        tile_add<PER_WARP>(sJw + o, v[0]);
+        tile_add<PER_WARP>(sJw + o + JW, v[1]);
+        tile_add<PER_WARP>(sJw + JPLANE + o, v[2]);
+        tile_add<PER_WARP>(sJw + JPLANE + o + 1, v[3]);
+        tile_add<PER_WARP>(sJw + 2 * JPLANE + o, v[4]);
+        tile_add<PER_WARP>(sJw + 2 * JPLANE + o + 1, v[5]);
+        tile_add<PER_WARP>(sJw + 2 * JPLANE + o + JW, v[6]);
+        tile_add<PER_WARP>(sJw + 2 * JPLANE + o + JW + 1, v[7]);
     }
 }
 
@@ -319,7 +324,9 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
         const int nt = S.off[t + 1] - p0;
         const int len = (nt + prm.chunks - 1) / prm.chunks;
         const int c0 = p0 + min(chunk * len, nt), c1 = p0 + min((chunk + 1) * len, nt);
-        const float tem = S.tem, qjx = S.qjx, qjy = S.qjy, qjz = S.qjz;
+        // current constants, times the fixed-point scale for the integer tiles
+        const float dsc = L::PER_WARP ? qscale : 1.f;
+        const float tem = S.tem, qjx = S.qjx * dsc, qjy = S.qjy * dsc, qjz = S.qjz * dsc;
         float ke = 0.f;
         // Particle batches come in through a NSTAGE-deep pipeline of bulk copies
         // (one per array, from the 16-byte aligned index below the batch start;
@@ -373,11 +380,12 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
                     // ---- gather (Fig. 3.1 staggering) ----
                     const float wx1 = x, wx0 = 1.f - x, wy1 = y, wy0 = 1.f - y;
                     const float xh = x + 0.5f, yh = y + 0.5f;
-                    const float fhx = floorf(xh), fhy = floorf(yh);
-                    const float hx1 = xh - fhx, hx0 = 1.f - hx1;
-                    const float hy1 = yh - fhy, hy0 = 1.f - hy1;
-                    const int cn = lx + GX, ch = lx + (int)fhx - 1 + GX;
-                    const int rn = ly + GY, rh = ly + (int)fhy - 1 + GY;
+                    // floor(xh) for xh in [0.5, 1.5]
+                    const bool xup = xh >= 1.f, yup = yh >= 1.f;
+                    const float hx1 = xh - (xup ? 1.f : 0.f), hx0 = 1.f - hx1;
+                    const float hy1 = yh - (yup ? 1.f : 0.f), hy0 = 1.f - hy1;
+                    const int cn = lx + GX, ch = cn - (xup ? 0 : 1);
+                    const int rn = ly + GY, rh = rn - (yup ? 0 : 1);
                     const float ex = interp(sEx, L::FW, ch, rn, hx0, hx1, wy0, wy1);
                     const float ey = interp(sEy, L::FW, cn, rh, wx0, wx1, hy0, hy1);
                     const float ez = interp(sEz, L::FW, cn, rn, wx0, wx1, wy0, wy1);
@@ -504,7 +512,7 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
 #pragma unroll
                             for (int i = 0; i < 8; ++i) v[i] = 0.f;
                         }
-                        deposit_warp<L::JW, L::JPLANE, L::PER_WARP>(has, o, v, sJw, lane, qscale);
+                        deposit_warp<L::JW, L::JPLANE, L::PER_WARP>(has, o, v, sJw, lane);
                         xa = xe;
                         ya = ye;
                     }
