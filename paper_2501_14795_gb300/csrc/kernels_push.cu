@@ -3,6 +3,9 @@
 // is split over several CTAs (blockIdx.y) that each take a slice of it.
 //   1. TMA-load the tile's E|B halo, cells [-4, T+4) x [-1, T+2), into shared
 //      memory (one 3D box over the six components, mbarrier completion);
+//      particles come in batches of blockDim through NSTAGE stages of bulk
+//      copies; warps move through the batches independently and the last
+//      warp done with a stage issues its refill;
 //   2. per particle (coalesced SoA loads): linear gather of the six staggered
 //      components (Fig. 3.1), Boris push (Eqs. 6-10), move (Eq. 11) and the
 //      Villasenor-Buneman split into at most three pieces (Figs. 3.4-3.5);
@@ -80,7 +83,8 @@ struct Tile {
     static constexpr int JPLANE = JW * JW;
     static constexpr int JN = 3 * JPLANE;
     static constexpr bool PER_WARP = PW;
-    static constexpr int NCNT = MAX_SPECIES * 8 + 4;
+    // leavers by destination per species, then one release counter per stage
+    static constexpr int NCNT = MAX_SPECIES * 8 + NSTAGE;
 
     static __host__ __device__ size_t j_tiles(int nth) { return PW ? ((nth + 31) / 32 + WPT - 1) / WPT : 1; }
     static __host__ __device__ size_t off_stage(int nth) {
@@ -267,6 +271,8 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::off_misc(nth));
     uint64_t* sbar = bar + 1;  // one per particle stage
     int* sDir = reinterpret_cast<int*>(smem + L::off_cnt(nth));  // [MAX_SPECIES][8]
+    int* sFree = sDir + MAX_SPECIES * 8;  // [NSTAGE]: warps done with the stage's batch
+    const int nwarps = nth >> 5;
     double* sRed = reinterpret_cast<double*>(smem + L::off_red(nth));
     float* sJw = sJ + (L::PER_WARP ? (warp / WPT) * L::JN : 0);
     const int jtiles = (int)L::j_tiles(nth);
@@ -345,12 +351,13 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
             dev::bulk_load(dst + 4 * SW, S.uy + a4, bytes, sb);
             dev::bulk_load(dst + 5 * SW, S.uz + a4, bytes, sb);
         };
+        // Warps run through the batches independently: the last warp to be
+        // done with a stage refills it (no CTA barrier per batch).
+        __syncthreads();  // every warp is done with the previous species' stages
         if (tid == 0)
-            for (int b = 0; b < min(nb, NSTAGE - 1); ++b) issue(b, gb + b);
+            for (int b = 0; b < min(nb, NSTAGE); ++b) issue(b, gb + b);
         for (int b = 0; b < nb; ++b) {
             const unsigned gcur = gb + b;
-            __syncthreads();  // every thread is done with batch b-1: its slot can be refilled
-            if (tid == 0 && b + NSTAGE - 1 < nb) issue(b + NSTAGE - 1, gcur + NSTAGE - 1);
             const bool landed = dev::mbar_wait_bounded(sbar + gcur % NSTAGE, (gcur / NSTAGE) & 1u);
             if (!landed) bad_bits |= ST_TIMEOUT;
             const int base = c0 + b * nth;
@@ -550,6 +557,19 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
                     S.hole[q] = p;
                     S.cell[p] = HOLE;
                     atomicAdd(&sDir[s * 8 + dir], 1);
+                }
+            }
+            // ---- release the stage; the last warp refills it ----
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                const int st = (int)(gcur % NSTAGE);
+                if (atomicAdd(&sFree[st], 1) == nwarps - 1) {
+                    atomicExch(&sFree[st], 0);
+                    if (b + NSTAGE < nb) {
+                        dev::fence_proxy_async_smem();  // our reads before the async overwrite
+                        issue(b + NSTAGE, gcur + NSTAGE);
+                    }
                 }
             }
         }
