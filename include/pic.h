@@ -315,7 +315,7 @@ void pic_denoiser_destroy(pic_denoiser* d);
  *   pic_nn_conv3x3_dgrad: dx (FP32 NHWC, cin channels) = input gradient of
  *     the convolution for the output gradient dz; cin in {32, 64, 128}.
  *   pic_nn_conv3x3_wgrad: dw (FP32 [3][3][cin][cout], overwritten) = weight
- *     gradient; W % 16 == 0. */
+ *     gradient; B*H*W a multiple of 64. */
 pic_status pic_nn_conv3x3(const void* x, int B, int H, int W, int cin, int cout, const float* w,
                           const float* bias, int relu, const void* skip, void* a_out, void* y_out,
                           void* cuda_stream);

@@ -38,6 +38,7 @@ def _units():
         ("host.o", "pic_host.cu", common),
         ("batch.o", "pic_batch.cu", common),
         ("nn.o", "nn_kernels.cu", common),
+        ("nn_tc.o", "nn_tc.cu", common),
         ("denoiser.o", "denoiser.cu", common),
         ("noalloc.o", "noalloc.cu", common),
     ]
@@ -68,7 +69,7 @@ def build_library(force: bool = False, verbose: bool = False, ptxas_info: bool =
         r = subprocess.run(cmd, capture_output=True, text=True)
         return obj, cmd, r
 
-    with ThreadPoolExecutor(max_workers=min(9, os.cpu_count() or 1)) as ex:
+    with ThreadPoolExecutor(max_workers=min(10, os.cpu_count() or 1)) as ex:
         results = list(ex.map(compile_one, _units()))
     for obj, cmd, r in results:
         if verbose or ptxas_info:

@@ -62,12 +62,14 @@ struct pic_denoiser {
     // activations (Bmax samples)
     bf16* xin = nullptr;
     bf16* a[NL] = {};
-    bf16 *y7 = nullptr, *y9 = nullptr, *p1 = nullptr, *p2 = nullptr, *u1 = nullptr, *u2 = nullptr;
+    bf16 *y7 = nullptr, *y9 = nullptr, *p1 = nullptr, *p2 = nullptr;
     float* out = nullptr;  // normalised output, dense [B][3][H][W]
     // gradients
     bf16* dz = nullptr;
     float *G0 = nullptr, *G1 = nullptr, *S1 = nullptr, *S2 = nullptr;
     double* dloss = nullptr;
+    unsigned* status = nullptr;      // device word: bit 2 = a bounded wait in a kernel ran out
+    unsigned* cur_status = nullptr;  // where the next launches report (own word or a simulation's)
     // host-buffer staging
     float *stage_in = nullptr, *stage_t = nullptr;
     std::vector<void*> allocs;
@@ -146,11 +148,19 @@ int dims(const pic_denoiser* d, int level, int* H, int* W) {
     return 0;
 }
 
+// Output-channel tile for a launch: 64 when the grid is large enough to fill
+// the GPU twice over, else 32 (more, smaller CTAs for small layers).
+int ctile_for(int cout, long long tiles) {
+    const int t = ctile(cout);
+    if (t == 64 && tiles * ((cout + 63) / 64) < 2 * 152) return 32;
+    return t;
+}
+
 cudaError_t conv(pic_denoiser* d, int l, int B, const bf16* x, int epi, bf16* a_out,
                  const bf16* skip, bf16* y_out, float* g_out, cudaStream_t s,
                  const float* res = nullptr, float* fout = nullptr, long long bstride = 0,
                  long long cstride = 0, int pitch = 0, int offset = 0, float rs = 0.f,
-                 float os = 0.f) {
+                 float os = 0.f, int up = 0) {
     const LayerDesc& L = d->tab.layer[l];
     ConvParams p;
     memset(&p, 0, sizeof p);
@@ -160,13 +170,16 @@ cudaError_t conv(pic_denoiser* d, int l, int B, const bf16* x, int epi, bf16* a_
     p.B = B;
     p.H = H;
     p.W = W;
+    p.up = up;
     p.epi = epi;
+    p.status = d->cur_status;
+    const long long tiles = (long long)B * (H / TH) * (W / TW);
     if (epi == EPI_GRAD) {
         p.w = d->wd + L.wd_off;
         p.cout = L.cin;
         p.cout_pad = L.dg_cout_pad;
         p.g_out = g_out;
-        return launch_conv(p, L.dg_cin_pad, ctile(L.cin), s);
+        return launch_conv(p, L.dg_cin_pad, ctile_for(L.cin, tiles), s);
     }
     p.w = d->wf + L.wf_off;
     p.bias = d->master + d->boff[l];
@@ -184,7 +197,7 @@ cudaError_t conv(pic_denoiser* d, int l, int B, const bf16* x, int epi, bf16* a_
     p.offset = offset;
     p.rs = rs;
     p.os = os;
-    return launch_conv(p, L.cin_pad, ctile(L.cout), s);
+    return launch_conv(p, L.cin_pad, ctile_for(L.cout, tiles), s);
 }
 
 // Forward pass of B samples given in field layout (J, with the layout
@@ -194,7 +207,7 @@ int forward(pic_denoiser* d, int B, const float* J, long long bstride, long long
             int pitch, int offset, float* fout, float rs, float os, cudaStream_t s) {
     cudaError_t e;
     int n = 0;
-    const int H0 = d->H, W0 = d->W, H1 = H0 / 2, W1 = W0 / 2, H2 = H0 / 4, W2 = W0 / 4;
+    const int H0 = d->H, W0 = d->W, H1 = H0 / 2, W1 = W0 / 2;
 #define FW(call)                                                                    \
     do {                                                                            \
         if ((e = (call)) != cudaSuccess) {                                          \
@@ -213,11 +226,12 @@ int forward(pic_denoiser* d, int B, const float* J, long long bstride, long long
     FW(launch_pool_fwd(d->a[3], B, H1, W1, 64, d->p2, s));
     FW(conv(d, 4, B, d->p2, EPI_ACT, d->a[4], nullptr, nullptr, nullptr, s));
     FW(conv(d, 5, B, d->a[4], EPI_ACT, d->a[5], nullptr, nullptr, nullptr, s));
-    FW(launch_up_fwd(d->a[5], B, H2, W2, 128, d->u1, s));
-    FW(conv(d, 6, B, d->u1, EPI_ACT, d->a[6], d->a[3], d->y7, nullptr, s));
+    // c7 and c9 read the coarser level through the fused 2x upsampling
+    FW(conv(d, 6, B, d->a[5], EPI_ACT, d->a[6], d->a[3], d->y7, nullptr, s, nullptr, nullptr, 0,
+            0, 0, 0, 0.f, 0.f, 1));
     FW(conv(d, 7, B, d->y7, EPI_ACT, d->a[7], nullptr, nullptr, nullptr, s));
-    FW(launch_up_fwd(d->a[7], B, H1, W1, 64, d->u2, s));
-    FW(conv(d, 8, B, d->u2, EPI_ACT, d->a[8], d->a[1], d->y9, nullptr, s));
+    FW(conv(d, 8, B, d->a[7], EPI_ACT, d->a[8], d->a[1], d->y9, nullptr, s, nullptr, nullptr, 0,
+            0, 0, 0, 0.f, 0.f, 1));
     FW(conv(d, 9, B, d->y9, EPI_ACT, d->a[9], nullptr, nullptr, nullptr, s));
     FW(conv(d, 10, B, d->a[9], EPI_FINAL, nullptr, nullptr, nullptr, nullptr, s, J, fout, bstride,
             cstride, pitch, offset, rs, os));
@@ -232,7 +246,7 @@ int backward(pic_denoiser* d, int B, const float* target, cudaStream_t s) {
     const int H0 = d->H, W0 = d->W, H1 = H0 / 2, W1 = W0 / 2, H2 = H0 / 4, W2 = W0 / 4;
     const long long P0 = (long long)B * H0 * W0, P1 = P0 / 4, P2 = P0 / 16;
     const long long HW = (long long)H0 * W0;
-    auto wg = [&](int l, const bf16* x) -> cudaError_t {
+    auto wg = [&](int l, const bf16* x, int up = 0) -> cudaError_t {
         const LayerDesc& L = d->tab.layer[l];
         int H, W;
         dims(d, kLayers[l].level, &H, &W);
@@ -242,6 +256,7 @@ int backward(pic_denoiser* d, int B, const float* target, cudaStream_t s) {
         p.B = B;
         p.H = H;
         p.W = W;
+        p.up = up;
         p.cin = L.cin;
         p.cout = L.cout;
         p.dw = d->grad + L.woff;
@@ -261,7 +276,7 @@ int backward(pic_denoiser* d, int B, const float* target, cudaStream_t s) {
     FW(conv(d, 9, B, d->dz, EPI_GRAD, nullptr, nullptr, nullptr, d->S1, s));        // dy9 (= ds1)
     // c9 (+s1)
     FW(launch_relu_back(d->S1, nullptr, d->a[8], P0, 32, d->dz, db(8), s));
-    FW(wg(8, d->u2));
+    FW(wg(8, d->a[7], 1));
     FW(conv(d, 8, B, d->dz, EPI_GRAD, nullptr, nullptr, nullptr, d->G0, s));        // du2
     FW(launch_up_back(d->G0, B, H1, W1, 64, d->G1, s));                              // dy8
     // c8
@@ -270,7 +285,7 @@ int backward(pic_denoiser* d, int B, const float* target, cudaStream_t s) {
     FW(conv(d, 7, B, d->dz, EPI_GRAD, nullptr, nullptr, nullptr, d->S2, s));        // dy7 (= ds2)
     // c7 (+s2)
     FW(launch_relu_back(d->S2, nullptr, d->a[6], P1, 64, d->dz, db(6), s));
-    FW(wg(6, d->u1));
+    FW(wg(6, d->a[5], 1));
     FW(conv(d, 6, B, d->dz, EPI_GRAD, nullptr, nullptr, nullptr, d->G0, s));        // du1
     FW(launch_up_back(d->G0, B, H2, W2, 128, d->G1, s));                             // dy6
     // c6
@@ -319,6 +334,17 @@ const float* stage(pic_denoiser* d, const float* src, float* buf, size_t count, 
     return buf;
 }
 
+// the device status word after a synchronisation: a bounded wait that ran out
+pic_status check_status(pic_denoiser* d) {
+    unsigned h = 0;
+    DCK(cudaMemcpy(&h, d->status, sizeof h, cudaMemcpyDeviceToHost));
+    if (h) {
+        DCK(cudaMemset(d->status, 0, sizeof(unsigned)));
+        return dfail(d, PIC_ETIMEOUT, "a bounded wait in a tensor-core kernel ran out");
+    }
+    return PIC_OK;
+}
+
 pic_status run_grad(pic_denoiser* d, const float* J_in, const float* J_t, int batch, int on_device,
                     double* loss) {
     if (batch < 1 || batch > d->Bmax) return dfail(d, PIC_EINVAL, "batch %d not in 1..%d", batch, d->Bmax);
@@ -338,15 +364,17 @@ pic_status run_grad(pic_denoiser* d, const float* J_in, const float* J_t, int ba
         DCK(cudaMemcpyAsync(loss, d->dloss, sizeof(double), cudaMemcpyDeviceToHost, d->stream));
     }
     DCK(cudaStreamSynchronize(d->stream));
-    return PIC_OK;
+    return check_status(d);
 }
 
 // the current-filter hook: the network applied to J[b] in place
 int filter_hook(void* ctx, pic_sim* sim, cudaStream_t s, int b) {
     pic_denoiser* d = static_cast<pic_denoiser*>(ctx);
     const Geom& g = sim->g;
+    d->cur_status = &sim->st->status;  // timeouts show in the simulation's status (ST_TIMEOUT)
     const int k = forward(d, 1, sim->J[b], 3 * g.cstride, g.cstride, g.P, GY * g.P + GX, sim->J[b],
                           1.f, (float)d->scale, s);
+    d->cur_status = d->status;
     if (k < 0) sim->err = d->err;
     return k;
 }
@@ -354,11 +382,18 @@ int filter_hook(void* ctx, pic_sim* sim, cudaStream_t s, int b) {
 // Pack random-access probe weights ([9][cin][cout] FP32, device) for one layer shape.
 struct Probe {
     bf16 *wf = nullptr, *wd = nullptr;
-    float* bias0 = nullptr;
+    unsigned* st = nullptr;
+    // synchronise; a bounded wait that ran out gives PIC_ETIMEOUT
+    pic_status finish(cudaStream_t s) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;
+        unsigned h = 0;
+        if (cudaMemcpy(&h, st, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return PIC_ECUDA;
+        return h ? PIC_ETIMEOUT : PIC_OK;
+    }
     ~Probe() {
         cudaFree(wf);
         cudaFree(wd);
-        cudaFree(bias0);
+        cudaFree(st);
     }
 };
 
@@ -406,8 +441,6 @@ pic_status pic_denoiser_create(int nx, int ny, int batch_max, double scale, void
     A(&d->y9, P0 * 32);
     A(&d->p1, P1 * 32);
     A(&d->p2, P2 * 64);
-    A(&d->u1, P1 * 128);
-    A(&d->u2, P0 * 64);
     A(&d->out, P0 * 3);
     A(&d->dz, P0 * 32);
     A(&d->G0, P0 * 64);
@@ -415,10 +448,13 @@ pic_status pic_denoiser_create(int nx, int ny, int batch_max, double scale, void
     A(&d->S1, P0 * 32);
     A(&d->S2, P1 * 64);
     A(&d->dloss, 1);
+    A(&d->status, 1);
     A(&d->stage_in, P0 * 3);
     A(&d->stage_t, P0 * 3);
     // shared-memory limits of every kernel shape, set before any graph capture
     if (e == cudaSuccess) e = init_kernels();
+    if (e == cudaSuccess) e = cudaMemsetAsync(d->status, 0, sizeof(unsigned), d->stream);
+    d->cur_status = d->status;
     if (e == cudaSuccess) e = cudaMemsetAsync(d->master, 0, sizeof(float) * d->np, d->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d->m, 0, sizeof(float) * d->np, d->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d->v, 0, sizeof(float) * d->np, d->stream);
@@ -472,7 +508,7 @@ pic_status pic_denoiser_forward(pic_denoiser* d, const float* J_in, float* J_out
     if (!on_device)
         DCK(cudaMemcpyAsync(J_out, o, cnt * 4, cudaMemcpyDeviceToHost, d->stream));
     DCK(cudaStreamSynchronize(d->stream));
-    return PIC_OK;
+    return check_status(d);
 }
 
 pic_status pic_denoiser_grad(pic_denoiser* d, const float* J_in, const float* J_target, int batch,
@@ -554,8 +590,11 @@ pic_status pic_nn_conv3x3(const void* x, int B, int H, int W, int cin, int cout,
     Probe pr;
     if (cudaMalloc((void**)&pr.wf, 2 * 9LL * cout_pad * cin_pad) != cudaSuccess) return PIC_ENOMEM;
     if (launch_pack_weights(t, w, pr.wf, nullptr, s) != cudaSuccess) return PIC_ECUDA;
+    if (cudaMalloc((void**)&pr.st, sizeof(unsigned)) != cudaSuccess) return PIC_ENOMEM;
+    if (cudaMemsetAsync(pr.st, 0, sizeof(unsigned), s) != cudaSuccess) return PIC_ECUDA;
     ConvParams p;
     memset(&p, 0, sizeof p);
+    p.status = pr.st;
     p.x = (const bf16*)x;
     p.B = B;
     p.H = H;
@@ -570,7 +609,7 @@ pic_status pic_nn_conv3x3(const void* x, int B, int H, int W, int cin, int cout,
     p.skip = (const bf16*)skip;
     p.y_out = (bf16*)y_out;
     if (launch_conv(p, cin_pad, ct, s) != cudaSuccess) return PIC_ECUDA;
-    return cudaStreamSynchronize(s) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+    return pr.finish(s);
 }
 
 pic_status pic_nn_conv3x3_dgrad(const void* dz, int B, int H, int W, int cin, int cout,
@@ -593,8 +632,11 @@ pic_status pic_nn_conv3x3_dgrad(const void* dz, int B, int H, int W, int cin, in
     if (cudaMalloc((void**)&pr.wd, 2 * 9LL * L.dg_cout_pad * L.dg_cin_pad) != cudaSuccess)
         return PIC_ENOMEM;
     if (launch_pack_weights(t, w, nullptr, pr.wd, s) != cudaSuccess) return PIC_ECUDA;
+    if (cudaMalloc((void**)&pr.st, sizeof(unsigned)) != cudaSuccess) return PIC_ENOMEM;
+    if (cudaMemsetAsync(pr.st, 0, sizeof(unsigned), s) != cudaSuccess) return PIC_ECUDA;
     ConvParams p;
     memset(&p, 0, sizeof p);
+    p.status = pr.st;
     p.x = (const bf16*)dz;
     p.B = B;
     p.H = H;
@@ -605,14 +647,14 @@ pic_status pic_nn_conv3x3_dgrad(const void* dz, int B, int H, int W, int cin, in
     p.epi = EPI_GRAD;
     p.g_out = dx;
     if (launch_conv(p, L.dg_cin_pad, ctile(cin), s) != cudaSuccess) return PIC_ECUDA;
-    return cudaStreamSynchronize(s) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+    return pr.finish(s);
 }
 
 pic_status pic_nn_conv3x3_wgrad(const void* x, const void* dz, int B, int H, int W, int cin,
                                 int cout, float* dw, void* cuda_stream) {
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    if (!x || !dz || !dw || B < 1 || H < 1 || W % WG_PIX || cin < 1 || cin > 128 || cout < 1 ||
-        cout > 128)
+    if (!x || !dz || !dw || B < 1 || H < 1 || W < 16 || ((long long)B * H * W) % WG_PIX ||
+        cin < 1 || cin > 128 || cout < 1 || cout > 128)
         return PIC_EINVAL;
     WgradParams p;
     p.x = (const bf16*)x;
@@ -620,6 +662,7 @@ pic_status pic_nn_conv3x3_wgrad(const void* x, const void* dz, int B, int H, int
     p.B = B;
     p.H = H;
     p.W = W;
+    p.up = 0;
     p.cin = cin;
     p.cout = cout;
     p.dw = dw;

@@ -14,15 +14,17 @@ namespace nn {
 constexpr int TH = 8, TW = 16;
 constexpr int PH = TH + 2, PW = TW + 2;
 constexpr int CONV_THREADS = 256;
-// weight gradient: pixel chunks of WG_PIX consecutive pixels of one row
-constexpr int WG_PIX = 16;
+// weight gradient: chunks of WG_PIX consecutive pixels (flattened b, y, x)
+// through a WG_STAGES-deep pipeline
+constexpr int WG_PIX = 64, WG_STAGES = 3;
 constexpr int WG_THREADS = 256, WG_WARPS = 8;
 
 enum { EPI_ACT = 0, EPI_FINAL = 1, EPI_GRAD = 2 };
 
 struct ConvParams {
     const __nv_bfloat16* x;  // input NHWC, channels = the kernel's CIN
-    int B, H, W;
+    int B, H, W;             // output (and, without up, input) size
+    int up;                  // x is H/2 x W/2, read at (y/2, x/2): fused 2x upsampling
     const __nv_bfloat16* w;  // packed [9][cout_pad][CIN]
     const float* bias;       // [cout] or null
     int cout, cout_pad;
@@ -40,12 +42,14 @@ struct ConvParams {
     long long bstride, cstride;
     int pitch, offset;
     float rs, os;
+    unsigned* status;        // tensor-core path: bit 2 set when a bounded wait ran out (may be null)
 };
 
 struct WgradParams {
     const __nv_bfloat16* x;   // layer input NHWC (CI channels)
     const __nv_bfloat16* dz;  // output gradient NHWC (CO channels)
-    int B, H, W;
+    int B, H, W;              // output size
+    int up;                   // x is H/2 x W/2, read at (y/2, x/2)
     int cin, cout;            // real channel counts
     float* dw;                // += into [9][cin][cout]
 };
@@ -66,7 +70,12 @@ struct PackTable {
 
 // raise every kernel shape's shared-memory limit (before any graph capture)
 cudaError_t init_kernels();
+// mma.sync implicit GEMM (any shape of the network), or the tcgen05 kernel
+// (nn_tc.cu) when the row length is a multiple of 128 and the shape is built
 cudaError_t launch_conv(const ConvParams& p, int cin, int ct, cudaStream_t s);
+bool conv_tc_supported(const ConvParams& p, int cin);
+cudaError_t launch_conv_tc(const ConvParams& p, int cin, cudaStream_t s);
+cudaError_t init_tc_kernels();
 cudaError_t launch_wgrad(const WgradParams& p, int ci, int co, cudaStream_t s);
 cudaError_t launch_pack_input(const float* J, long long bstride, long long cstride, int pitch,
                               int offset, int B, int H, int W, float inv_scale, __nv_bfloat16* out,

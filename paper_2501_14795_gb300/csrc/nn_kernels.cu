@@ -96,12 +96,16 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv(const ConvParams p) {
     const int b = blockIdx.y, co0 = blockIdx.z * CT;
     constexpr int CH = CIN / 8;  // 16-byte chunks per pixel
 
+    // input pixel (y, x); with p.up the input is the half-resolution tensor
+    // read at (y/2, x/2): nearest 2x upsampling fused into the load
+    const int sh = p.up ? 1 : 0;
+    const int Hi = p.H >> sh, Wi = p.W >> sh;
     for (int i = tid; i < PH * PW * CH; i += CONV_THREADS) {
         const int pix = i / CH, c = i - pix * CH;
         const int r = pix / PW, q = pix - r * PW;
-        const int y = wrap(ty0 - 1 + r, p.H), x = wrap(tx0 - 1 + q, p.W);
+        const int y = wrap(ty0 - 1 + r, p.H) >> sh, x = wrap(tx0 - 1 + q, p.W) >> sh;
         cp_async16(sP + pix * L::CS + c * 8,
-                   p.x + (((size_t)b * p.H + y) * p.W + x) * CIN + c * 8);
+                   p.x + (((size_t)b * Hi + y) * Wi + x) * CIN + c * 8);
     }
     for (int i = tid; i < 9 * CT * CH; i += CONV_THREADS) {
         const int row = i / CH, c = i - row * CH;
@@ -195,14 +199,17 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv(const ConvParams p) {
 
 // ----------------------------------------------------------------- wgrad
 // dW[tap][ci][co] += sum over pixels p of x[p + tap offset][ci] * dz[p][co].
-// Per tap a GEMM with M = co, N = ci, K = pixels; CTA s takes pixel chunks
-// (WG_PIX consecutive pixels of one image row) s, s + gridDim.x, ... through a
-// two-stage cp.async pipeline.  Warps split the (CO/16) x (CI/16) blocks.
+// Per tap a GEMM with M = co, N = ci, K = pixels: CTA (s, tap) takes the
+// chunks of WG_PIX consecutive pixels (flattened b, y, x order) s, s +
+// gridDim.x, ... through a WG_STAGES-deep cp.async pipeline.  The warps split
+// the (CO/16) x (CI/16) output blocks and, when there are fewer blocks than
+// warps, the 16-pixel k-steps of a chunk as well.  With p.up the input is the
+// half-resolution tensor read at (y/2, x/2) (fused nearest upsampling).
 template <int CI, int CO>
 struct WgradSmem {
     static constexpr int XS = CI + 8, DS = CO + 8;
     static constexpr int STAGE = WG_PIX * (XS + DS);
-    static constexpr size_t bytes = (size_t)2 * STAGE * 2;
+    static constexpr size_t bytes = (size_t)WG_STAGES * STAGE * 2;
 };
 
 template <int CI, int CO>
@@ -212,10 +219,16 @@ __global__ void __launch_bounds__(WG_THREADS) k_wgrad(const WgradParams p) {
     bf16* sbase = reinterpret_cast<bf16*>(smem);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tap = blockIdx.y, ky = tap / 3, kx = tap - 3 * (tap / 3);
-    const int chunks_per_row = p.W / WG_PIX;
-    const long long nchunks = (long long)p.B * p.H * chunks_per_row;
+    const long long HW = (long long)p.H * p.W;
+    const long long nchunks = (long long)p.B * HW / WG_PIX;
+    const int sh = p.up ? 1 : 0;
+    const int Hi = p.H >> sh, Wi = p.W >> sh;
     constexpr int MB = CO / 16, NB = CI / 16, NBLK = MB * NB;
-    constexpr int PER = (NBLK + WG_WARPS - 1) / WG_WARPS;  // blocks per warp
+    constexpr bool SPLITK = NBLK < WG_WARPS;
+    constexpr int KS = SPLITK ? WG_WARPS / NBLK : 1;                  // k-step phases
+    constexpr int PER = SPLITK ? 1 : (NBLK + WG_WARPS - 1) / WG_WARPS;  // blocks per warp
+    const int blk0 = SPLITK ? warp % NBLK : warp;
+    const int kph = SPLITK ? warp / NBLK : 0;
     float acc[PER][2][4];
 #pragma unroll
     for (int k = 0; k < PER; ++k)
@@ -225,43 +238,56 @@ __global__ void __launch_bounds__(WG_THREADS) k_wgrad(const WgradParams p) {
     auto load = [&](long long c, int stage) {
         bf16* sX = sbase + stage * L::STAGE;
         bf16* sD = sX + WG_PIX * L::XS;
-        const int xq = (int)(c % chunks_per_row);
-        const long long rowid = c / chunks_per_row;
-        const int y = (int)(rowid % p.H), b = (int)(rowid / p.H);
-        const int x0 = xq * WG_PIX;
-        const int ys = wrap(y + ky - 1, p.H);
+        const long long pix0 = c * WG_PIX;
+        // the chunk's first pixel (b0, y0, x0), once; the chunk spans < 64 / 16 + 1 rows
+        const int b0 = (int)(pix0 / HW);
+        const int rem0 = (int)(pix0 - (long long)b0 * HW);
+        const int y0 = rem0 / p.W, x0 = rem0 - y0 * p.W;
         constexpr int CHX = CI / 8, CHD = CO / 8;
         for (int i = tid; i < WG_PIX * CHX; i += WG_THREADS) {
             const int px = i / CHX, cc = i - px * CHX;
-            const int xs = wrap(x0 + px + kx - 1, p.W);
-            cp_async16(sX + px * L::XS + cc * 8, p.x + (((size_t)b * p.H + ys) * p.W + xs) * CI + cc * 8);
+            int x = x0 + px, y = y0, b = b0;
+            while (x >= p.W) {  // at most WG_PIX / 16 times (W >= 16)
+                x -= p.W;
+                if (++y == p.H) {
+                    y = 0;
+                    ++b;
+                }
+            }
+            const int ys = wrap(y + ky - 1, p.H) >> sh, xs = wrap(x + kx - 1, p.W) >> sh;
+            cp_async16(sX + px * L::XS + cc * 8, p.x + (((size_t)b * Hi + ys) * Wi + xs) * CI + cc * 8);
         }
         for (int i = tid; i < WG_PIX * CHD; i += WG_THREADS) {
             const int px = i / CHD, cc = i - px * CHD;
-            cp_async16(sD + px * L::DS + cc * 8, p.dz + (((size_t)b * p.H + y) * p.W + x0 + px) * CO + cc * 8);
+            cp_async16(sD + px * L::DS + cc * 8, p.dz + (size_t)(pix0 + px) * CO + cc * 8);
         }
     };
 
-    long long c = blockIdx.x;
-    int stage = 0;
-    if (c < nchunks) load(c, 0);
-    cp_async_commit();
-    for (; c < nchunks; c += gridDim.x) {
-        const long long cn = c + gridDim.x;
-        if (cn < nchunks) load(cn, stage ^ 1);
+    const long long c0 = blockIdx.x;
+    const long long ns = gridDim.x;
+    // prefetch WG_STAGES - 1 chunks
+#pragma unroll
+    for (int k = 0; k < WG_STAGES - 1; ++k) {
+        if (c0 + k * ns < nchunks) load(c0 + k * ns, k);
         cp_async_commit();
-        cp_async_wait<1>();
+    }
+    int stage = 0;
+    for (long long c = c0; c < nchunks; c += ns) {
+        const long long cn = c + (WG_STAGES - 1) * ns;
+        if (cn < nchunks) load(cn, (stage + WG_STAGES - 1) % WG_STAGES);
+        cp_async_commit();
+        cp_async_wait<WG_STAGES - 1>();  // the chunk of this iteration has landed
         __syncthreads();
         const bf16* sX = sbase + stage * L::STAGE;
         const bf16* sD = sX + WG_PIX * L::XS;
+        const int j = lane >> 3;
 #pragma unroll
-        for (int ks = 0; ks < WG_PIX / 16; ++ks) {
+        for (int ks = kph; ks < WG_PIX / 16; ks += KS) {
 #pragma unroll
             for (int k = 0; k < PER; ++k) {
-                const int blk = warp + k * WG_WARPS;
+                const int blk = blk0 + k * WG_WARPS;
                 if (blk >= NBLK) break;
                 const int mb = blk / NB, nb = blk - mb * NB;
-                const int j = lane >> 3;
                 uint32_t a[4], bb[4];
                 // A (co x px) from dz stored [px][co]: transposing load
                 ldsm_x4_t(a, sD + (ks * 16 + (j >> 1) * 8 + (lane & 7)) * L::DS + mb * 16 + (j & 1) * 8);
@@ -271,15 +297,15 @@ __global__ void __launch_bounds__(WG_THREADS) k_wgrad(const WgradParams p) {
                 mma_bf16(acc[k][1], a, bb[2], bb[3]);
             }
         }
-        __syncthreads();  // the stage is refilled next
-        stage ^= 1;
+        __syncthreads();  // the stage is refilled by a later iteration
+        stage = (stage + 1) % WG_STAGES;
     }
     cp_async_wait<0>();
     // accumulate into dW[tap][ci][co] (real channel counts)
     const int g = lane >> 2, cq = (lane & 3) * 2;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-        const int blk = warp + k * WG_WARPS;
+        const int blk = blk0 + k * WG_WARPS;
         if (blk >= NBLK) break;
         const int mb = blk / NB, nb = blk - mb * NB;
 #pragma unroll
@@ -595,7 +621,7 @@ int blocks(long long n, int t) { return (int)((n + t - 1) / t); }
     X(16, 32) X(32, 32) X(32, 64) X(64, 64) X(64, 128) X(128, 128) X(128, 64) X(64, 32) X(32, 16)
 
 cudaError_t init_kernels() {
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = init_tc_kernels();
 #define PIC_C_ATTR(A, B) if (e == cudaSuccess) e = conv_attr<A, B>();
 #define PIC_W_ATTR(A, B) if (e == cudaSuccess) e = wgrad_attr<A, B>();
     PIC_CONV_SHAPES(PIC_C_ATTR)
@@ -608,6 +634,7 @@ cudaError_t init_kernels() {
 // CIN in {16, 32, 64, 128}; CT in {8, 32, 64} (cout_pad a multiple of CT)
 cudaError_t launch_conv(const ConvParams& p, int cin, int ct, cudaStream_t s) {
     if (p.H % TH || p.W % TW || p.cout_pad % ct) return cudaErrorInvalidValue;
+    if (conv_tc_supported(p, cin)) return launch_conv_tc(p, cin, s);
 #define PIC_CONV_CASE(CI, C) \
     if (cin == CI && ct == C) return conv_T<CI, C>(p, s);
     PIC_CONV_SHAPES(PIC_CONV_CASE)
@@ -617,13 +644,14 @@ cudaError_t launch_conv(const ConvParams& p, int cin, int ct, cudaStream_t s) {
 
 // CI = x channels, CO = dz channels (both padded to 16)
 cudaError_t launch_wgrad(const WgradParams& p, int ci, int co, cudaStream_t s) {
-    if (p.W % WG_PIX) return cudaErrorInvalidValue;
-    const long long nchunks = (long long)p.B * p.H * (p.W / WG_PIX);
+    const long long npix = (long long)p.B * p.H * p.W;
+    if (npix % WG_PIX || p.W < 16 || (p.up && (p.H % 2 || p.W % 2))) return cudaErrorInvalidValue;
+    const long long nchunks = npix / WG_PIX;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int nsplit = (int)std::min<long long>(nchunks, (long long)(2 * sms + 8) / 9 * 4);
-    if (nsplit < 1) nsplit = 1;
+    // about four CTAs per SM over the nine taps
+    int nsplit = (int)std::min<long long>(nchunks, std::max(1, 4 * sms / 9));
 #define PIC_WG_CASE(A, B) \
     if (ci == A && co == B) return wgrad_T<A, B>(p, nsplit, s);
     PIC_WGRAD_SHAPES(PIC_WG_CASE)

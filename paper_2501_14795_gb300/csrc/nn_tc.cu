@@ -1,0 +1,294 @@
+// 3x3 circular convolution on the 5th-generation tensor cores (tcgen05):
+// the implicit GEMM D[pixels x cout] = sum over taps and input channels of
+// X[shifted pixel][cin] * W[tap][cout][cin], bfloat16 operands in shared
+// memory, FP32 accumulator in tensor memory (TMEM).
+//
+// CTA = one segment of M = 128 consecutive output pixels of one image row x
+// all NT output channels.  Shared memory holds the 3 x (M + 2) input patch
+// (the segment's rows y-1..y+1 with the circular halo) and the weights of all
+// nine taps, both in the K-major canonical layout without swizzle: 8 x 16 B
+// core matrices, an operand's 8-row groups 128 B apart (SBO) and its 8-column
+// k-groups one "plane" apart (LBO).  For tap (ky, kx) the A operand is simply
+// the patch row ky starting at column kx, so each tap is a plain descriptor
+// offset and no im2col copy exists.  One thread issues the 9 x cin/16
+// tcgen05.mma (M = 128, N = NT, K = 16) into one TMEM accumulator and commits
+// them to an mbarrier; each warp then reads its 32 TMEM lanes (pixels) and
+// runs the same epilogues as the mma.sync kernel (bias + ReLU (+ skip) to
+// bfloat16, raw FP32, residual output in field layout).
+//
+// Every wait is bounded; on a timeout the kernel flags it in the status word,
+// frees its TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nn_internal.h"
+
+namespace pic {
+namespace nn {
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int TC_M = 128;             // pixels per CTA (one row segment)
+constexpr int TC_THREADS = 128;       // 4 warps: one per 32 TMEM lanes
+constexpr int TC_PW = TC_M + 2;       // patch row length (halo)
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr(sdst)), "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// shared-memory matrix descriptor: K-major, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo & 0x3FFFF) >> 4) << 16) |
+           ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+template <int CIN, int NT>
+struct TcSmem {
+    static constexpr int KG = CIN / 8;                        // k-groups
+    static constexpr int PPLANE = 3 * TC_PW * 16;             // bytes of one k-group of the patch
+    static constexpr int WPLANE = NT * 16;                    // bytes of one k-group of one tap
+    static constexpr int WTAP = KG * WPLANE;
+    static constexpr size_t off_w = (size_t)KG * PPLANE;
+    static constexpr size_t off_bar = (off_w + 9 * WTAP + 15) & ~(size_t)15;
+    static constexpr size_t bytes = off_bar + 16 + 16;
+    static constexpr int TMEM_COLS = NT < 32 ? 32 : NT;
+};
+
+template <int CIN, int NT>
+__global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
+    using L = TcSmem<CIN, NT>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sP = smem;
+    unsigned char* sW = smem + L::off_w;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::off_bar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::off_bar + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int segs = p.W / TC_M;
+    const int x0 = (blockIdx.x % segs) * TC_M;
+    const int y = (blockIdx.x / segs) % p.H;
+    const int b = blockIdx.x / (segs * p.H);
+    const int sh = p.up ? 1 : 0;
+    const int Hi = p.H >> sh, Wi = p.W >> sh;
+
+    // patch: rows y-1..y+1, columns x0-1..x0+M, k-group planes of 16 B per pixel
+    for (int i = tid; i < 3 * TC_PW * L::KG; i += TC_THREADS) {
+        const int pix = i / L::KG, kg = i - pix * L::KG;
+        const int r = pix / TC_PW, q = pix - r * TC_PW;
+        const int ys = wrap(y - 1 + r, p.H) >> sh, xs = wrap(x0 - 1 + q, p.W) >> sh;
+        cp_async16(sP + kg * L::PPLANE + pix * 16,
+                   p.x + (((size_t)b * Hi + ys) * Wi + xs) * CIN + kg * 8);
+    }
+    // weights of the nine taps: packed [tap][cout_pad][CIN] -> [tap][kg][n][8]
+    for (int i = tid; i < 9 * NT * L::KG; i += TC_THREADS) {
+        const int kg = i % L::KG;
+        const int rn = i / L::KG;
+        const int n = rn % NT, tap = rn / NT;
+        unsigned char* dst = sW + tap * L::WTAP + kg * L::WPLANE + n * 16;
+        if (n < p.cout_pad)
+            cp_async16(dst, p.w + ((size_t)tap * p.cout_pad + n) * CIN + kg * 8);
+        else
+            *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         saddr(tslot)),
+                     "r"(L::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // the generic-proxy writes above must be visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    // D f32 (bits 4-5), A and B bf16 (7-9, 10-12), both K-major, N >> 3 at 17, M >> 4 at 24
+    constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
+                               ((uint32_t)(TC_M >> 4) << 24);
+    if (tid == 0) {
+        const uint32_t pa = saddr(sP), pw = saddr(sW);
+#pragma unroll 1
+        for (int tap = 0; tap < 9; ++tap) {
+            const int ky = tap / 3, kx = tap - 3 * (tap / 3);
+#pragma unroll
+            for (int kc = 0; kc < CIN / 16; ++kc) {
+                const uint64_t ad = smem_desc(pa + (2 * kc) * L::PPLANE + (ky * TC_PW + kx) * 16,
+                                              L::PPLANE, 128);
+                const uint64_t bd = smem_desc(pw + tap * L::WTAP + (2 * kc) * L::WPLANE,
+                                              L::WPLANE, 128);
+                const uint32_t acc = (tap | kc) != 0;
+                asm volatile(
+                    "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                saddr(bar)));
+    }
+    // bounded wait for the accumulator
+    bool ok = false;
+    {
+        const long long t0 = clock64();
+        while (true) {
+            uint32_t done;
+            asm volatile(
+                "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], 0;\n\t"
+                "selp.u32 %0, 1, 0, q;\n\t}"
+                : "=r"(done)
+                : "r"(saddr(bar))
+                : "memory");
+            if (done) {
+                ok = true;
+                break;
+            }
+            if (clock64() - t0 > 2000000000LL) break;
+            __nanosleep(64);
+        }
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok) {
+        if (tid == 0 && p.status) atomicOr(p.status, 2u);  // a bounded wait ran out
+    } else {
+        // warp w holds TMEM lanes 32w..32w+31: pixel x0 + 32w + lane, all NT columns
+        const int x = x0 + 32 * warp + lane;
+        const size_t pix = ((size_t)b * p.H + y) * p.W + x;
+#pragma unroll 1
+        for (int c0 = 0; c0 < NT; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+                "%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                  "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                  "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (c0 >= p.cout_pad) continue;
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+            if (p.epi == EPI_GRAD) {
+                float4* o = reinterpret_cast<float4*>(p.g_out + pix * p.cout_pad + c0);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                continue;
+            }
+            if (p.bias) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (c0 + j < p.cout) v[j] += p.bias[c0 + j];
+            }
+            if (p.epi == EPI_FINAL) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int c = c0 + j;
+                    if (c >= p.cout) continue;
+                    const size_t o = (size_t)b * p.bstride + (size_t)c * p.cstride + p.offset +
+                                     (size_t)y * p.pitch + x;
+                    p.fout[o] = p.res[o] * p.rs + v[j] * p.os;
+                }
+                continue;
+            }
+            if (p.relu) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
+            }
+            __align__(16) __nv_bfloat162 a2[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) a2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+            uint4* ao = reinterpret_cast<uint4*>(p.a_out + pix * p.cout_pad + c0);
+            ao[0] = reinterpret_cast<const uint4*>(a2)[0];
+            ao[1] = reinterpret_cast<const uint4*>(a2)[1];
+            if (p.skip) {
+                const uint4* sk = reinterpret_cast<const uint4*>(p.skip + pix * p.cout_pad + c0);
+                __align__(16) uint4 sv[2] = {sk[0], sk[1]};
+                const __nv_bfloat162* s2 = reinterpret_cast<const __nv_bfloat162*>(sv);
+                __align__(16) __nv_bfloat162 y2[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float2 af = __bfloat1622float2(a2[j]), sf = __bfloat1622float2(s2[j]);
+                    y2[j] = __floats2bfloat162_rn(af.x + sf.x, af.y + sf.y);
+                }
+                uint4* yo = reinterpret_cast<uint4*>(p.y_out + pix * p.cout_pad + c0);
+                yo[0] = reinterpret_cast<const uint4*>(y2)[0];
+                yo[1] = reinterpret_cast<const uint4*>(y2)[1];
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(L::TMEM_COLS));
+}
+
+template <int CIN, int NT>
+cudaError_t conv_tc_T(const ConvParams& p, cudaStream_t s) {
+    using L = TcSmem<CIN, NT>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<CIN, NT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)L::bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int grid = p.B * p.H * (p.W / TC_M);
+    k_conv_tc<CIN, NT><<<grid, TC_THREADS, L::bytes, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// the (CIN, N) shapes built for the tensor-core path (shared memory <= 200 KB)
+#define PIC_TC_SHAPES(X) X(16, 32) X(32, 32) X(32, 64) X(64, 32) X(64, 64) X(64, 128) X(32, 16)
+
+bool conv_tc_supported(const ConvParams& p, int cin) {
+    if (p.W % TC_M || p.cout_pad > 128) return false;
+    const int nt = p.cout_pad <= 16 ? 16 : (p.cout_pad <= 32 ? 32 : (p.cout_pad <= 64 ? 64 : 128));
+#define PIC_TC_HAS(A, B) if (cin == A && nt == B) return true;
+    PIC_TC_SHAPES(PIC_TC_HAS)
+#undef PIC_TC_HAS
+    return false;
+}
+
+cudaError_t launch_conv_tc(const ConvParams& p, int cin, cudaStream_t s) {
+    const int nt = p.cout_pad <= 16 ? 16 : (p.cout_pad <= 32 ? 32 : (p.cout_pad <= 64 ? 64 : 128));
+#define PIC_TC_CASE(A, B) \
+    if (cin == A && nt == B) return conv_tc_T<A, B>(p, s);
+    PIC_TC_SHAPES(PIC_TC_CASE)
+#undef PIC_TC_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t init_tc_kernels() {
+    cudaError_t e = cudaSuccess;
+#define PIC_TC_ATTR(A, B)                                                                    \
+    if (e == cudaSuccess)                                                                    \
+        e = cudaFuncSetAttribute(k_conv_tc<A, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)TcSmem<A, B>::bytes);
+    PIC_TC_SHAPES(PIC_TC_ATTR)
+#undef PIC_TC_ATTR
+    return e;
+}
+
+}  // namespace nn
+}  // namespace pic

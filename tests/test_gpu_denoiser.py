@@ -59,14 +59,18 @@ def _pad(x, c):
     return out
 
 
+# rows of 32 run on the mma.sync kernel, rows of 128 on the tcgen05 kernel
+SHAPES = [(2, 16, 32), (1, 8, 128)]
+
+
+@pytest.mark.parametrize("B,H,W", SHAPES)
 @pytest.mark.parametrize("cin,cout,relu,skip", [(3, 32, True, False), (32, 32, True, True),
                                                  (32, 64, True, False), (64, 128, True, False),
                                                  (128, 128, True, False), (128, 64, True, True),
-                                                 (64, 32, False, False)])
-def test_conv_forward_matches_oracle(cin, cout, relu, skip):
+                                                 (64, 32, False, False), (64, 64, True, True)])
+def test_conv_forward_matches_oracle(cin, cout, relu, skip, B, H, W):
     import torch
     rng = _rng(cin * 1000 + cout)
-    B, H, W = 2, 16, 32
     x = D.bf16(rng.standard_normal((B, H, W, cin)))
     w = rng.uniform(-1, 1, (3, 3, cin, cout)) * np.sqrt(3.0 / (9 * cin))
     b = rng.uniform(-0.1, 0.1, cout)
@@ -88,12 +92,12 @@ def test_conv_forward_matches_oracle(cin, cout, relu, skip):
         np.testing.assert_array_equal(_np(y), ref_y)
 
 
+@pytest.mark.parametrize("B,H,W", SHAPES)
 @pytest.mark.parametrize("cin,cout", [(32, 3), (32, 32), (32, 64), (64, 64), (64, 128),
                                       (128, 128), (128, 64)])
-def test_conv_input_gradient_matches_oracle(cin, cout):
+def test_conv_input_gradient_matches_oracle(cin, cout, B, H, W):
     import torch
     rng = _rng(cin * 7 + cout)
-    B, H, W = 2, 16, 32
     dz = D.bf16(rng.standard_normal((B, H, W, cout)))
     w = rng.uniform(-1, 1, (3, 3, cin, cout)) * 0.1
     dx = torch.empty((B, H, W, cin), dtype=torch.float32, device="cuda")
@@ -148,8 +152,9 @@ def _nhwc(J):
     return np.transpose(J, (0, 2, 3, 1)).astype(np.float64)
 
 
-def test_network_loss_and_gradients_match_oracle():
-    B, ny, nx, scale = 2, 32, 64, 0.5
+@pytest.mark.parametrize("ny,nx", [(32, 64), (32, 256)])
+def test_network_loss_and_gradients_match_oracle(ny, nx):
+    B, scale = 2, 0.5
     Jn, Jc = _currents(5, B, ny, nx)
     p = _params(41)
     flat = _flat32(p)
