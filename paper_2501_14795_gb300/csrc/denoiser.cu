@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -70,6 +71,7 @@ struct pic_denoiser {
     double* dloss = nullptr;
     unsigned* status = nullptr;      // device word: bit 2 = a bounded wait in a kernel ran out
     unsigned* cur_status = nullptr;  // where the next launches report (own word or a simulation's)
+    int force_tc = 0;                // PIC_DENOISER_TC=always: tensor-core path whenever possible
     // host-buffer staging
     float *stage_in = nullptr, *stage_t = nullptr;
     std::vector<void*> allocs;
@@ -173,6 +175,7 @@ cudaError_t conv(pic_denoiser* d, int l, int B, const bf16* x, int epi, bf16* a_
     p.up = up;
     p.epi = epi;
     p.status = d->cur_status;
+    p.force_tc = d->force_tc;
     const long long tiles = (long long)B * (H / TH) * (W / TW);
     if (epi == EPI_GRAD) {
         p.w = d->wd + L.wd_off;
@@ -422,6 +425,7 @@ pic_status pic_denoiser_create(int nx, int ny, int batch_max, double scale, void
     d->Bmax = batch_max;
     d->scale = scale;
     d->stream = (cudaStream_t)cuda_stream;
+    if (const char* v = getenv("PIC_DENOISER_TC")) d->force_tc = strcmp(v, "always") == 0;
     build_table(d);
     const long long P1 = P0 / 4, P2 = P0 / 16;
     cudaError_t e = cudaSuccess;
@@ -595,6 +599,7 @@ pic_status pic_nn_conv3x3(const void* x, int B, int H, int W, int cin, int cout,
     ConvParams p;
     memset(&p, 0, sizeof p);
     p.status = pr.st;
+    p.force_tc = 1;  // a probe exercises the tensor-core kernel whenever the shape allows
     p.x = (const bf16*)x;
     p.B = B;
     p.H = H;
@@ -637,6 +642,7 @@ pic_status pic_nn_conv3x3_dgrad(const void* dz, int B, int H, int W, int cin, in
     ConvParams p;
     memset(&p, 0, sizeof p);
     p.status = pr.st;
+    p.force_tc = 1;
     p.x = (const bf16*)dz;
     p.B = B;
     p.H = H;

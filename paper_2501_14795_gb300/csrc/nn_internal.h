@@ -43,6 +43,7 @@ struct ConvParams {
     int pitch, offset;
     float rs, os;
     unsigned* status;        // tensor-core path: bit 2 set when a bounded wait ran out (may be null)
+    int force_tc;            // take the tensor-core path whenever the shape allows (tests)
 };
 
 struct WgradParams {

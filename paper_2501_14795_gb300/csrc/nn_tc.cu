@@ -3,10 +3,10 @@
 // X[shifted pixel][cin] * W[tap][cout][cin], bfloat16 operands in shared
 // memory, FP32 accumulator in tensor memory (TMEM).
 //
-// CTA = one segment of M = 128 consecutive output pixels of one image row x
-// all NT output channels.  Shared memory holds the 3 x (M + 2) input patch
-// (the segment's rows y-1..y+1 with the circular halo) and the weights of all
-// nine taps, both in the K-major canonical layout without swizzle: 8 x 16 B
+// Work unit = one segment of M = 128 consecutive output pixels of one image
+// row x all NT output channels; persistent CTAs run through the segments.
+// Shared memory holds two 3 x (M + 2) input patches (a segment's rows
+// y-1..y+1 with the circular halo) and the weights of all nine taps, both in the K-major canonical layout without swizzle: 8 x 16 B
 // core matrices, an operand's 8-row groups 128 B apart (SBO) and its 8-column
 // k-groups one "plane" apart (LBO).  For tap (ky, kx) the A operand is simply
 // the patch row ky starting at column kx, so each tap is a plain descriptor
@@ -31,9 +31,11 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int TC_M = 128;             // pixels per CTA (one row segment)
-constexpr int TC_THREADS = 128;       // 4 warps: one per 32 TMEM lanes
+constexpr int TC_M = 128;             // pixels of one row segment (MMA M)
+constexpr int TC_R = 2;               // rows per work unit: one accumulator each
+constexpr int TC_THREADS = 256;       // 8 warps: two per 32 TMEM lanes (column halves)
 constexpr int TC_PW = TC_M + 2;       // patch row length (halo)
+constexpr int TC_PR = TC_R + 2;       // patch rows
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -53,39 +55,150 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 template <int CIN, int NT>
 struct TcSmem {
     static constexpr int KG = CIN / 8;                        // k-groups
-    static constexpr int PPLANE = 3 * TC_PW * 16;             // bytes of one k-group of the patch
+    static constexpr int PPLANE = TC_PR * TC_PW * 16;         // bytes of one k-group of a patch
+    static constexpr int PATCH = KG * PPLANE;                 // bytes of one patch
     static constexpr int WPLANE = NT * 16;                    // bytes of one k-group of one tap
     static constexpr int WTAP = KG * WPLANE;
-    static constexpr size_t off_w = (size_t)KG * PPLANE;
+    static constexpr size_t off_w = 2 * (size_t)PATCH;        // two patches, then the weights
     static constexpr size_t off_bar = (off_w + 9 * WTAP + 15) & ~(size_t)15;
-    static constexpr size_t bytes = off_bar + 16 + 16;
-    static constexpr int TMEM_COLS = NT < 32 ? 32 : NT;
+    static constexpr size_t bytes = off_bar + 32;             // 2 mbarriers + TMEM slot
+    static constexpr int NTC = NT < 32 ? 32 : NT;             // TMEM columns of one row's accumulator
+    static constexpr int TMEM_COLS = 2 * TC_R * NTC;          // two work units in flight
 };
 
+// wait for phase `parity` of an mbarrier, about a second at most
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, q;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > 2000000000LL) return false;
+        __nanosleep(64);
+    }
+}
+
+// patch of work unit `seg` (rows y0-1..y0+R, columns x0-1..x0+M, circular)
+// into k-group planes of 16 B per pixel; a thread takes whole pixels (their
+// CIN channels are contiguous in memory)
+template <int CIN, int NT>
+__device__ __forceinline__ void load_patch(const ConvParams& p, unsigned char* sP, int seg, int tid) {
+    using L = TcSmem<CIN, NT>;
+    const int segs = p.W / TC_M, rows = p.H / TC_R;
+    const int x0 = (seg % segs) * TC_M;
+    const int y0 = ((seg / segs) % rows) * TC_R;
+    const int b = seg / (segs * rows);
+    const int sh = p.up ? 1 : 0;
+    const int Hi = p.H >> sh, Wi = p.W >> sh;
+    for (int pix = tid; pix < TC_PR * TC_PW; pix += TC_THREADS) {
+        const int r = pix / TC_PW, q = pix - r * TC_PW;
+        const int ys = wrap(y0 - 1 + r, p.H) >> sh, xs = wrap(x0 - 1 + q, p.W) >> sh;
+        const bf16* src = p.x + (((size_t)b * Hi + ys) * Wi + xs) * CIN;
+        unsigned char* dst = sP + pix * 16;
+#pragma unroll
+        for (int kg = 0; kg < L::KG; ++kg) cp_async16(dst + kg * L::PPLANE, src + kg * 8);
+    }
+}
+
+// the epilogues on one accumulator (row rr of unit seg): TMEM lane = pixel
+// x0 + lane of the row, column = output channel
+template <int NT>
+__device__ __forceinline__ void epilogue(const ConvParams& p, uint32_t acc, int seg, int rr,
+                                         int warp, int lane) {
+    // warps w and w + 4 read TMEM lanes 32 (w % 4)..+31: the first and the
+    // second half of the 16-column chunks
+    const int lg = warp & 3, half = warp >> 2;
+    const int segs = p.W / TC_M, rows = p.H / TC_R;
+    const int x = (seg % segs) * TC_M + 32 * lg + lane;
+    const int y = ((seg / segs) % rows) * TC_R + rr;
+    const int b = seg / (segs * rows);
+    const size_t pix = ((size_t)b * p.H + y) * p.W + x;
+#pragma unroll 1
+    for (int c0 = 16 * half; c0 < NT; c0 += 32) {
+        uint32_t r[16];
+        const uint32_t taddr = acc + ((uint32_t)(32 * lg) << 16) + c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+            "%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+              "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+              "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (c0 >= p.cout_pad) continue;
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+        if (p.epi == EPI_GRAD) {
+            float4* o = reinterpret_cast<float4*>(p.g_out + pix * p.cout_pad + c0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            continue;
+        }
+        if (p.bias) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (c0 + j < p.cout) v[j] += p.bias[c0 + j];
+        }
+        if (p.epi == EPI_FINAL) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int c = c0 + j;
+                if (c >= p.cout) continue;
+                const size_t o = (size_t)b * p.bstride + (size_t)c * p.cstride + p.offset +
+                                 (size_t)y * p.pitch + x;
+                p.fout[o] = p.res[o] * p.rs + v[j] * p.os;
+            }
+            continue;
+        }
+        if (p.relu) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
+        }
+        __align__(16) __nv_bfloat162 a2[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        uint4* ao = reinterpret_cast<uint4*>(p.a_out + pix * p.cout_pad + c0);
+        ao[0] = reinterpret_cast<const uint4*>(a2)[0];
+        ao[1] = reinterpret_cast<const uint4*>(a2)[1];
+        if (p.skip) {
+            const uint4* sk = reinterpret_cast<const uint4*>(p.skip + pix * p.cout_pad + c0);
+            __align__(16) uint4 sv[2] = {sk[0], sk[1]};
+            const __nv_bfloat162* s2 = reinterpret_cast<const __nv_bfloat162*>(sv);
+            __align__(16) __nv_bfloat162 y2[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float2 af = __bfloat1622float2(a2[j]), sf = __bfloat1622float2(s2[j]);
+                y2[j] = __floats2bfloat162_rn(af.x + sf.x, af.y + sf.y);
+            }
+            uint4* yo = reinterpret_cast<uint4*>(p.y_out + pix * p.cout_pad + c0);
+            yo[0] = reinterpret_cast<const uint4*>(y2)[0];
+            yo[1] = reinterpret_cast<const uint4*>(y2)[1];
+        }
+    }
+}
+
+// Persistent: the CTA keeps the nine taps' weights in shared memory and runs
+// through segments blockIdx.x, blockIdx.x + gridDim.x, ...  Two patches and
+// two TMEM accumulators: while the tensor cores work on segment i, the CTA
+// stores segment i-1's results and loads segment i+1's patch.
 template <int CIN, int NT>
 __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
     using L = TcSmem<CIN, NT>;
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sP = smem;
     unsigned char* sW = smem + L::off_w;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::off_bar);
+    const uint32_t bar0 = saddr(smem + L::off_bar);           // mbarriers of accumulators 0, 1
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::off_bar + 16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int segs = p.W / TC_M;
-    const int x0 = (blockIdx.x % segs) * TC_M;
-    const int y = (blockIdx.x / segs) % p.H;
-    const int b = blockIdx.x / (segs * p.H);
-    const int sh = p.up ? 1 : 0;
-    const int Hi = p.H >> sh, Wi = p.W >> sh;
+    const int nseg = p.B * (p.H / TC_R) * (p.W / TC_M);
+    if ((int)blockIdx.x >= nseg) return;
 
-    // patch: rows y-1..y+1, columns x0-1..x0+M, k-group planes of 16 B per pixel
-    for (int i = tid; i < 3 * TC_PW * L::KG; i += TC_THREADS) {
-        const int pix = i / L::KG, kg = i - pix * L::KG;
-        const int r = pix / TC_PW, q = pix - r * TC_PW;
-        const int ys = wrap(y - 1 + r, p.H) >> sh, xs = wrap(x0 - 1 + q, p.W) >> sh;
-        cp_async16(sP + kg * L::PPLANE + pix * 16,
-                   p.x + (((size_t)b * Hi + ys) * Wi + xs) * CIN + kg * 8);
-    }
     // weights of the nine taps: packed [tap][cout_pad][CIN] -> [tap][kg][n][8]
     for (int i = tid; i < 9 * NT * L::KG; i += TC_THREADS) {
         const int kg = i % L::KG;
@@ -97,9 +210,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
         else
             *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
     }
+    load_patch<CIN, NT>(p, smem, blockIdx.x, tid);
     asm volatile("cp.async.commit_group;" ::: "memory");
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -108,9 +223,6 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
                      "r"(L::TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    // the generic-proxy writes above must be visible to the tensor cores
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -119,119 +231,68 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
     // D f32 (bits 4-5), A and B bf16 (7-9, 10-12), both K-major, N >> 3 at 17, M >> 4 at 24
     constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
                                ((uint32_t)(TC_M >> 4) << 24);
-    if (tid == 0) {
-        const uint32_t pa = saddr(sP), pw = saddr(sW);
+    bool ok = true;
+    int i = 0, prev = -1;
+    for (int seg = blockIdx.x; seg < nseg; seg += gridDim.x, ++i) {
+        const int buf = i & 1;
+        // this segment's patch (and, the first time, the weights) has landed
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint32_t pa = saddr(smem + buf * L::PATCH), pw = saddr(sW);
 #pragma unroll 1
-        for (int tap = 0; tap < 9; ++tap) {
-            const int ky = tap / 3, kx = tap - 3 * (tap / 3);
+            for (int tap = 0; tap < 9; ++tap) {
+                const int ky = tap / 3, kx = tap - 3 * (tap / 3);
 #pragma unroll
-            for (int kc = 0; kc < CIN / 16; ++kc) {
-                const uint64_t ad = smem_desc(pa + (2 * kc) * L::PPLANE + (ky * TC_PW + kx) * 16,
-                                              L::PPLANE, 128);
-                const uint64_t bd = smem_desc(pw + tap * L::WTAP + (2 * kc) * L::WPLANE,
-                                              L::WPLANE, 128);
-                const uint32_t acc = (tap | kc) != 0;
-                asm volatile(
-                    "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-            }
-        }
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                saddr(bar)));
-    }
-    // bounded wait for the accumulator
-    bool ok = false;
-    {
-        const long long t0 = clock64();
-        while (true) {
-            uint32_t done;
-            asm volatile(
-                "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], 0;\n\t"
-                "selp.u32 %0, 1, 0, q;\n\t}"
-                : "=r"(done)
-                : "r"(saddr(bar))
-                : "memory");
-            if (done) {
-                ok = true;
-                break;
-            }
-            if (clock64() - t0 > 2000000000LL) break;
-            __nanosleep(64);
-        }
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!ok) {
-        if (tid == 0 && p.status) atomicOr(p.status, 2u);  // a bounded wait ran out
-    } else {
-        // warp w holds TMEM lanes 32w..32w+31: pixel x0 + 32w + lane, all NT columns
-        const int x = x0 + 32 * warp + lane;
-        const size_t pix = ((size_t)b * p.H + y) * p.W + x;
-#pragma unroll 1
-        for (int c0 = 0; c0 < NT; c0 += 16) {
-            uint32_t r[16];
-            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
-                "%12,%13,%14,%15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                  "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                  "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (c0 >= p.cout_pad) continue;
-            float v[16];
+                for (int kc = 0; kc < CIN / 16; ++kc) {
+                    const uint64_t bd =
+                        smem_desc(pw + tap * L::WTAP + (2 * kc) * L::WPLANE, L::WPLANE, 128);
+                    const uint32_t accum = (tap | kc) != 0;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-            if (p.epi == EPI_GRAD) {
-                float4* o = reinterpret_cast<float4*>(p.g_out + pix * p.cout_pad + c0);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-                continue;
-            }
-            if (p.bias) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (c0 + j < p.cout) v[j] += p.bias[c0 + j];
-            }
-            if (p.epi == EPI_FINAL) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int c = c0 + j;
-                    if (c >= p.cout) continue;
-                    const size_t o = (size_t)b * p.bstride + (size_t)c * p.cstride + p.offset +
-                                     (size_t)y * p.pitch + x;
-                    p.fout[o] = p.res[o] * p.rs + v[j] * p.os;
+                    for (int rr = 0; rr < TC_R; ++rr) {
+                        const uint32_t acc = tmem + (buf * TC_R + rr) * L::NTC;
+                        const uint64_t ad = smem_desc(
+                            pa + (2 * kc) * L::PPLANE + ((rr + ky) * TC_PW + kx) * 16, L::PPLANE, 128);
+                        asm volatile(
+                            "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(acc),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                    }
                 }
-                continue;
             }
-            if (p.relu) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
-            }
-            __align__(16) __nv_bfloat162 a2[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) a2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-            uint4* ao = reinterpret_cast<uint4*>(p.a_out + pix * p.cout_pad + c0);
-            ao[0] = reinterpret_cast<const uint4*>(a2)[0];
-            ao[1] = reinterpret_cast<const uint4*>(a2)[1];
-            if (p.skip) {
-                const uint4* sk = reinterpret_cast<const uint4*>(p.skip + pix * p.cout_pad + c0);
-                __align__(16) uint4 sv[2] = {sk[0], sk[1]};
-                const __nv_bfloat162* s2 = reinterpret_cast<const __nv_bfloat162*>(sv);
-                __align__(16) __nv_bfloat162 y2[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float2 af = __bfloat1622float2(a2[j]), sf = __bfloat1622float2(s2[j]);
-                    y2[j] = __floats2bfloat162_rn(af.x + sf.x, af.y + sf.y);
-                }
-                uint4* yo = reinterpret_cast<uint4*>(p.y_out + pix * p.cout_pad + c0);
-                yo[0] = reinterpret_cast<const uint4*>(y2)[0];
-                yo[1] = reinterpret_cast<const uint4*>(y2)[1];
-            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    bar0 + 8 * buf));
         }
+        // the previous segment's results, while the tensor cores run this one
+        if (prev >= 0) {
+            const int pb = (i - 1) & 1;
+            if (ok && !wait_bar(bar0 + 8 * pb, ((i - 1) >> 1) & 1)) ok = false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (ok)
+                for (int rr = 0; rr < TC_R; ++rr)
+                    epilogue<NT>(p, tmem + (pb * TC_R + rr) * L::NTC, prev, rr, warp, lane);
+        }
+        // the next segment's patch goes where the previous segment's was
+        // (its MMAs are complete: waited just above)
+        const int nxt = seg + gridDim.x;
+        if (nxt < nseg) load_patch<CIN, NT>(p, smem + (buf ^ 1) * L::PATCH, nxt, tid);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        prev = seg;
     }
+    if (prev >= 0) {
+        const int pb = (i - 1) & 1;
+        if (ok && !wait_bar(bar0 + 8 * pb, ((i - 1) >> 1) & 1)) ok = false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok)
+            for (int rr = 0; rr < TC_R; ++rr)
+                epilogue<NT>(p, tmem + (pb * TC_R + rr) * L::NTC, prev, rr, warp, lane);
+    }
+    if (!ok && tid == 0 && p.status) atomicOr(p.status, 2u);  // a bounded wait ran out
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -240,29 +301,62 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
                      "r"(L::TMEM_COLS));
 }
 
+// Persistent grid size of a shape: CTAs resident at once (shared memory and
+// 512 TMEM columns per SM); also raises the shared-memory limit.  Called once
+// per shape before any graph capture (init_tc_kernels).
+template <int CIN, int NT>
+int& tc_grid_cap() {
+    static int cap = 0;
+    return cap;
+}
+
+template <int CIN, int NT>
+cudaError_t tc_prepare() {
+    using L = TcSmem<CIN, NT>;
+    if (tc_grid_cap<CIN, NT>()) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<CIN, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, smem = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    if ((e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) !=
+        cudaSuccess)
+        return e;
+    // resident CTAs: shared memory (plus the 1 KB the system keeps per CTA),
+    // TMEM columns, threads
+    int per = smem / (int)(L::bytes + 1024);
+    per = per < 1 ? 1 : per;
+    if (per * L::TMEM_COLS > 512) per = 512 / L::TMEM_COLS;
+    if (per * TC_THREADS > 2048) per = 2048 / TC_THREADS;
+    tc_grid_cap<CIN, NT>() = sms * per;
+    return cudaSuccess;
+}
+
 template <int CIN, int NT>
 cudaError_t conv_tc_T(const ConvParams& p, cudaStream_t s) {
     using L = TcSmem<CIN, NT>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<CIN, NT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)L::bytes);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    const int grid = p.B * p.H * (p.W / TC_M);
+    cudaError_t e = tc_prepare<CIN, NT>();
+    if (e != cudaSuccess) return e;
+    const int nseg = p.B * (p.H / TC_R) * (p.W / TC_M);
+    const int cap = tc_grid_cap<CIN, NT>();
+    const int grid = nseg < cap ? nseg : cap;
     k_conv_tc<CIN, NT><<<grid, TC_THREADS, L::bytes, s>>>(p);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-// the (CIN, N) shapes built for the tensor-core path (shared memory <= 200 KB)
-#define PIC_TC_SHAPES(X) X(16, 32) X(32, 32) X(32, 64) X(64, 32) X(64, 64) X(64, 128) X(32, 16)
+// the (CIN, N) shapes built for the tensor-core path (two patches and nine
+// taps of weights within 227 KB of shared memory)
+#define PIC_TC_SHAPES(X) X(16, 32) X(32, 32) X(32, 64) X(64, 32) X(64, 64) X(32, 16)
 
 bool conv_tc_supported(const ConvParams& p, int cin) {
-    if (p.W % TC_M || p.cout_pad > 128) return false;
+    if (p.W % TC_M || p.H % TC_R || p.cout_pad > 128) return false;
+    // small problems (a few hundred work units) finish sooner on the mma.sync
+    // kernel, whose CTAs do not each stage all nine taps of weights
+    if ((long long)p.B * (p.H / TC_R) * (p.W / TC_M) < 600 && !p.force_tc) return false;
     const int nt = p.cout_pad <= 16 ? 16 : (p.cout_pad <= 32 ? 32 : (p.cout_pad <= 64 ? 64 : 128));
 #define PIC_TC_HAS(A, B) if (cin == A && nt == B) return true;
     PIC_TC_SHAPES(PIC_TC_HAS)
@@ -281,12 +375,10 @@ cudaError_t launch_conv_tc(const ConvParams& p, int cin, cudaStream_t s) {
 
 cudaError_t init_tc_kernels() {
     cudaError_t e = cudaSuccess;
-#define PIC_TC_ATTR(A, B)                                                                    \
-    if (e == cudaSuccess)                                                                    \
-        e = cudaFuncSetAttribute(k_conv_tc<A, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)TcSmem<A, B>::bytes);
-    PIC_TC_SHAPES(PIC_TC_ATTR)
-#undef PIC_TC_ATTR
+#define PIC_TC_PREP(A, B) \
+    if (e == cudaSuccess) e = tc_prepare<A, B>();
+    PIC_TC_SHAPES(PIC_TC_PREP)
+#undef PIC_TC_PREP
     return e;
 }
 
