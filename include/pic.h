@@ -134,6 +134,14 @@ pic_status pic_set_fields(pic_sim* sim, const float* E, const float* B, int on_d
  * window).  Asynchronous: enqueues the work on the stream and returns. */
 pic_status pic_step(pic_sim* sim, int nsteps);
 
+/* The current filter of Listing 3.1 (applied after the guard-cell reduction
+ * of J and before the field advance): `passes` passes (0 = off, at most 64)
+ * of the binomial stencil (1/4, 1/2, 1/4) along x and then along y on each
+ * component's periodic lattice; each pass multiplies the Fourier mode
+ * (kx, ky) by cos^2(kx dx/2) cos^2(ky dy/2).  Replaces an installed denoiser
+ * (and pic_set_denoiser replaces it).  Synchronises. */
+pic_status pic_set_binomial_filter(pic_sim* sim, int passes);
+
 /* Copy a grid quantity into the caller's buffer: which = 0 E, 1 B (3*nx*ny
  * values each, at time level n), 2 J (the current deposited by the last step,
  * at n-1/2, 3*nx*ny values), 3 rho (nx*ny values at nodes, including the

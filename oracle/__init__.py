@@ -22,6 +22,9 @@ Parity status per function (what pins each one; the pins live in
 * ``orc_rho``      pinned: the weights of each particle sum to its charge; a
   uniform lattice gives a uniform density.
 * ``orc_tile_sort`` pinned: equal to numpy's stable argsort by tile id.
+* ``binomial_filter`` pinned: the closed-form response cos^2(k dx/2) cos^2(k dy/2)
+  per pass on single Fourier modes, exact conservation of the sum (k = 0), the
+  Nyquist mode removed, brute-force 3x3 stencil (1 2 1)(1 2 1)/16.
 * Weibel growth (config with counter-streaming populations along z): parity
   only bounded, between 0.7x and 1x the cold-fluid rate (the thermal spread
   lowers the cold rate by an amount the thesis does not give).
@@ -41,6 +44,7 @@ from .oracle import (  # noqa: F401
     deposit_move,
     advance,
     yee,
+    binomial_filter,
     rho_nodes,
     tile_sort,
     field_energy,

@@ -135,6 +135,19 @@ def advance(sp: "SpeciesState", E, B, J, dx, dy, dt):
     return st, ke.value
 
 
+def binomial_filter(J, passes=1):
+    """The current filter of the time loop (Listing 3.1, after the guard-cell
+    reduction of J, before the field advance): the binomial stencil
+    (1/4, 1/2, 1/4) along x and then along y on each component's own periodic
+    lattice, `passes` times.  Each pass multiplies a Fourier mode (kx, ky) by
+    cos^2(kx dx / 2) cos^2(ky dy / 2)."""
+    J = np.array(J, dtype=np.float64, copy=True)
+    for _ in range(passes):
+        J = 0.25 * np.roll(J, 1, axis=2) + 0.5 * J + 0.25 * np.roll(J, -1, axis=2)
+        J = 0.25 * np.roll(J, 1, axis=1) + 0.5 * J + 0.25 * np.roll(J, -1, axis=1)
+    return J
+
+
 def yee(E, B, J, dx, dy, dt):
     _, ny, nx = E.shape
     getattr(lib(), "orc_yee" + _sfx(E.dtype))(nx, ny, dx, dy, dt, _ptr(E), _ptr(B), _ptr(J))
@@ -240,6 +253,7 @@ class OracleSim:
     E: np.ndarray = None
     B: np.ndarray = None
     J: np.ndarray = None
+    filter_passes: int = 0          # binomial current filter (0: off)
     step_count: int = 0
     status: int = 0
     ke_history: list = field(default_factory=list)
@@ -267,6 +281,8 @@ class OracleSim:
                 self.status |= st
                 ke += self.kinetic_energy_of(sp, g)
             self.ke_history.append(ke)
+            if self.filter_passes:
+                self.J[...] = binomial_filter(self.J, self.filter_passes)
             yee(self.E, self.B, self.J, self.dx, self.dy, self.dt)
             if sort:
                 self.sort()

@@ -558,6 +558,7 @@ pic_status pic_set_denoiser(pic_sim* sim, pic_denoiser* d) {
     PIC_CK(sim, cudaStreamSynchronize(sim->stream));
     sim->jfilter = d ? filter_hook : nullptr;
     sim->jfilter_ctx = d;
+    sim->binomial_passes = 0;
     invalidate_graphs(sim);
     return PIC_OK;
 }

@@ -48,6 +48,7 @@ struct pic_sim {
     // advance; returns the kernels it launched or -1 (message in sim->err)
     int (*jfilter)(void* ctx, pic_sim* sim, cudaStream_t s, int b) = nullptr;
     void* jfilter_ctx = nullptr;
+    int binomial_passes = 0;  // the binomial filter's passes when it is the installed filter
 };
 
 namespace pic {

@@ -158,6 +158,36 @@ __global__ void __launch_bounds__(YTHREADS) k_yee_batch(const YeeBatch b) {
     yee_tile(P, t % nbx, t / nbx);
 }
 
+// ------------------------------------------------------ binomial filter
+// The current filter of Listing 3.1: (1/4, 1/2, 1/4) along x, then along y,
+// on each component's periodic lattice.  x pass: J (grid layout) -> dense
+// scratch [3][ny][nx]; y pass: scratch -> J (interior; the guard images of J
+// are never read).
+__global__ void k_binom_x(const Geom g, const float* J, float* tmp) {
+    const long long n = 3LL * g.nx * g.ny;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = (int)(k % g.nx);
+    const long long r = k / g.nx;
+    const int j = (int)(r % g.ny), c = (int)(r / g.ny);
+    const float* row = J + c * g.cstride + (long long)(j + GY) * g.P + GX;
+    const float l = row[i == 0 ? g.nx - 1 : i - 1], m = row[i], rr = row[i == g.nx - 1 ? 0 : i + 1];
+    tmp[k] = 0.25f * l + 0.5f * m + 0.25f * rr;
+}
+
+__global__ void k_binom_y(const Geom g, const float* tmp, float* J) {
+    const long long n = 3LL * g.nx * g.ny;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = (int)(k % g.nx);
+    const long long r = k / g.nx;
+    const int j = (int)(r % g.ny), c = (int)(r / g.ny);
+    const float* col = tmp + (long long)c * g.ny * g.nx + i;
+    const float u = col[(long long)(j == 0 ? g.ny - 1 : j - 1) * g.nx], m = col[(long long)j * g.nx],
+                d = col[(long long)(j == g.ny - 1 ? 0 : j + 1) * g.nx];
+    J[c * g.cstride + (long long)(j + GY) * g.P + i + GX] = 0.25f * u + 0.5f * m + 0.25f * d;
+}
+
 // -------------------------------------------------------- grid utilities
 // src is component-major (c, j, i) with nx*ny values per component; writes
 // the interior and the periodic images.
@@ -414,6 +444,15 @@ int grid_for(long long n, int threads) {
 }
 
 }  // namespace
+
+cudaError_t launch_binomial(const Geom& g, float* J, float* tmp, cudaStream_t s) {
+    const long long n = 3LL * g.nx * g.ny;
+    k_binom_x<<<grid_for(n, 256), 256, 0, s>>>(g, J, tmp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_binom_y<<<grid_for(n, 256), 256, 0, s>>>(g, tmp, J);
+    return cudaGetLastError();
+}
 
 int yee_tiles(const Geom& g) { return ((g.nx + YX - 1) / YX) * ((g.ny + YY - 1) / YY); }
 

@@ -370,6 +370,18 @@ const void* stage_in(pic_sim* sim, const void* src, size_t bytes, void* staging,
 }
 
 
+// the binomial filter in the current-filter slot
+int binomial_hook(void*, pic_sim* sim, cudaStream_t s, int b) {
+    for (int k = 0; k < sim->binomial_passes; ++k) {
+        cudaError_t e = launch_binomial(sim->g, sim->J[b], sim->gtmp, s);
+        if (e != cudaSuccess) {
+            sim->err = std::string("binomial filter launch failed: ") + cudaGetErrorString(e);
+            return -1;
+        }
+    }
+    return 2 * sim->binomial_passes;
+}
+
 pic_status retile(pic_sim* sim, int tile) {
     const pic_config& c = sim->cfg;
     if (!(tile == 8 || tile == 16 || tile == 32) || c.nx % tile || c.ny % tile)
@@ -673,6 +685,18 @@ pic_status pic_step(pic_sim* sim, int nsteps) {
         sim->cur = 1 - b;
         sim->step += 1;
     }
+    return PIC_OK;
+}
+
+pic_status pic_set_binomial_filter(pic_sim* sim, int passes) {
+    if (!sim) return PIC_EINVAL;
+    sim->err.clear();
+    if (passes < 0 || passes > 64) return fail(sim, PIC_EINVAL, "passes %d not in 0..64", passes);
+    CK(cudaStreamSynchronize(sim->stream));
+    sim->binomial_passes = passes;
+    sim->jfilter = passes ? binomial_hook : nullptr;
+    sim->jfilter_ctx = nullptr;
+    invalidate_graphs(sim);
     return PIC_OK;
 }
 

@@ -171,6 +171,8 @@ cudaError_t launch_sort_batch(const SortBatch& b, cudaStream_t s);
 cudaError_t launch_yee_batch(const YeeBatch& b, cudaStream_t s);
 int yee_tiles(const Geom& g);
 
+// one pass of the binomial current filter on J (tmp: 3 nx ny floats); 2 kernels
+cudaError_t launch_binomial(const Geom& g, float* J, float* tmp, cudaStream_t s);
 cudaError_t launch_scan(const SortParams& p, cudaStream_t s);
 cudaError_t launch_evict(const SortParams& p, int threads, cudaStream_t s);
 cudaError_t launch_fill(const SortParams& p, int threads, cudaStream_t s);

@@ -115,6 +115,7 @@ def load_library() -> C.CDLL:
         L.pic_denoiser_train_step.argtypes = [_P, _P, _P, C.c_int, C.c_float,
                                               C.POINTER(C.c_double), C.c_int]
         L.pic_set_denoiser.argtypes = [_P, _P]
+        L.pic_set_binomial_filter.argtypes = [_P, C.c_int]
         L.pic_denoiser_last_error.argtypes = [_P]
         L.pic_denoiser_last_error.restype = C.c_char_p
         L.pic_denoiser_destroy.argtypes = [_P]
@@ -132,7 +133,8 @@ def load_library() -> C.CDLL:
                      "pic_autotune", "pic_set_tiling", "pic_denoiser_create",
                      "pic_denoiser_set_params", "pic_denoiser_get_params", "pic_denoiser_forward",
                      "pic_denoiser_grad", "pic_denoiser_train_step", "pic_set_denoiser",
-                     "pic_nn_conv3x3", "pic_nn_conv3x3_dgrad", "pic_nn_conv3x3_wgrad"):
+                     "pic_nn_conv3x3", "pic_nn_conv3x3_dgrad", "pic_nn_conv3x3_wgrad",
+                     "pic_set_binomial_filter"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -416,6 +418,10 @@ def pic_denoiser_train_step(d, J_in, J_target, batch, lr):
 
 def pic_set_denoiser(h, d):
     _check(h, load_library().pic_set_denoiser(h, d))
+
+
+def pic_set_binomial_filter(h, passes):
+    _check(h, load_library().pic_set_binomial_filter(h, int(passes)))
 
 
 def pic_denoiser_destroy(d):

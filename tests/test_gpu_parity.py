@@ -461,3 +461,30 @@ def test_timing_events_and_launch_count():
         assert cnt == 10 and ms > 0
         # per step: advance, count, scan, evict, fill, Yee
         assert pic.pic_kernel_launches(sim.h) == 60
+
+
+@pytest.mark.parametrize("passes", [1, 3])
+def test_binomial_filter_matches_oracle(passes):
+    """The current filter slot with the binomial filter: J after the filter,
+    E and B after the field advance against the FP64 oracle with the same
+    filter; 20 more steps keep the energies together."""
+    w, E, B = _random_case(64, 32, 16, 9000, seed=77)
+    with _gpu(w, pic.PIC_TRACK_IDS, tile=16, E=E, B=B) as sim:
+        pic.pic_set_binomial_filter(sim.h, passes)
+        sim.step(1)
+        Jg = sim.fields(pic.FIELD_J)
+        Eg = sim.fields(pic.FIELD_E)
+        Bg = sim.fields(pic.FIELD_B)
+        sim.step(20)
+        d = sim.diagnostics()
+    o = _oracle(w, np.float64, E, B, 16)
+    o.filter_passes = passes
+    o.step(1)
+    assert np.abs(Jg - o.J).max() <= J_RTOL * np.abs(o.J).max()
+    assert np.abs(Eg - o.E).max() <= F_RTOL * np.abs(o.E).max()
+    assert np.abs(Bg - o.B).max() <= F_RTOL * np.abs(o.B).max()
+    o.step(20)
+    assert d["status_bits"] == 0
+    we, wb = o.energies()
+    assert d["w_e"] == pytest.approx(we, rel=2e-3)
+    assert d["w_b"] == pytest.approx(wb, rel=2e-3)

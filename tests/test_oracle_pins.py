@@ -336,3 +336,37 @@ def test_oracle_never_writes_into_its_inputs(orc):
     np.testing.assert_array_equal(B, B0)
     for a, b in zip(a0, sp.arrays()):
         np.testing.assert_array_equal(a, b)
+
+
+from oracle import binomial_filter  # noqa: E402
+
+
+def test_binomial_filter_closed_form_response():
+    """One pass multiplies the mode (mx, my) by cos^2(pi mx/nx) cos^2(pi my/ny);
+    the sum is kept (k = 0) and the Nyquist mode in x is removed."""
+    nx, ny = 16, 12
+    y, x = np.mgrid[0:ny, 0:nx]
+    for mx, my, passes in ((1, 0, 1), (3, 2, 1), (2, 5, 3), (0, 0, 2)):
+        f = np.cos(2 * np.pi * (mx * x / nx + my * y / ny) + 0.3)
+        J = np.stack([f, 2 * f, -f])
+        got = binomial_filter(J, passes)
+        gain = (np.cos(np.pi * mx / nx) ** 2 * np.cos(np.pi * my / ny) ** 2) ** passes
+        np.testing.assert_allclose(got, gain * J, atol=1e-12)
+    rng = np.random.Generator(np.random.PCG64(5))
+    J = rng.standard_normal((3, ny, nx))
+    assert abs(binomial_filter(J, 2).sum() - J.sum()) < 1e-12
+    nyq = np.cos(np.pi * x)[None].repeat(3, 0)
+    assert np.max(np.abs(binomial_filter(nyq, 1))) < 1e-12
+
+
+def test_binomial_filter_is_the_3x3_stencil():
+    rng = np.random.Generator(np.random.PCG64(6))
+    J = rng.standard_normal((3, 7, 9))
+    w = np.array([1.0, 2.0, 1.0]) / 4
+    want = np.zeros_like(J)
+    for c in range(3):
+        for j in range(7):
+            for i in range(9):
+                want[c, j, i] = sum(w[a] * w[b] * J[c, (j + b - 1) % 7, (i + a - 1) % 9]
+                                    for a in range(3) for b in range(3))
+    np.testing.assert_allclose(binomial_filter(J, 1), want, atol=1e-13)
