@@ -40,6 +40,9 @@ WORKLOADS = {
     # L2-resident instance (2.1M particles, 50 MB state < L2): compute-bound reference
     "weibel_128": dict(kind="weibel", kw=dict(nx=128, ny=128, k=8), tile=16),
     "thermal_2048": dict(kind="thermal_seeded", kw=dict(nx=2048, ny=2048, k=4), tile=16),
+    # the thesis's own Weibel shape: electrons and positrons, 10x10 ppc each,
+    # 512^2 (26.2M per species; the thesis has 25M per species on 500^2)
+    "weibel_pair_512": dict(kind="weibel_pair", kw=dict(nx=512, ny=512, k=10), tile=16),
     # smaller instance (16.8M particles, 403 MB state > L2) for profiler captures
     "thermal_1024": dict(kind="thermal_seeded", kw=dict(nx=1024, ny=1024, k=4), tile=16),
     "two_stream_64": dict(kind="two_stream", kw=dict(nx=64, ny=64, k=4), tile=16),
@@ -385,10 +388,12 @@ def run_denoiser(args, rank, world, local_rank):
         row = {"seed": d.seed, "drift": d.drift, "u_th": d.u_th, "theory_gamma": theory,
                "eligible": theory > 0.05}
         runs = {}
-        for name, k, use in (("ppc64", 8, False), ("ppc4", 2, False), ("ppc4_denoised", 2, True)):
+        for name, k, use, binom in (("ppc64", 8, False, 0), ("ppc4", 2, False, 0),
+                                    ("ppc4_denoised", 2, True, 0), ("ppc4_binomial", 2, False, 1)):
             w = dn.workload(d, nx, ny, k, steps)
-            we, _, diag, spec = dn.field_energy_run(w, steps, net if use else None, modes=True)
-            _, ms, _, _ = dn.field_energy_run(w, steps, net if use else None)
+            we, _, diag, spec = dn.field_energy_run(w, steps, net if use else None, modes=True,
+                                                     binomial=binom)
+            _, ms, _, _ = dn.field_energy_run(w, steps, net if use else None, binomial=binom)
             runs[name] = (we, spec, ms, diag)
         m = int(np.argmax(runs["ppc64"][1][:, 1:].max(axis=0))) + 1
         lw64 = np.log(np.maximum(runs["ppc64"][0][1:], 1e-300))   # W_E(0) = 0
@@ -402,11 +407,12 @@ def run_denoiser(args, rank, world, local_rank):
                          "continuity_max": diag["continuity_max"]}
         row["mode"] = m
         g64 = row["ppc64"]["gamma_mode"]
-        for name in ("ppc4", "ppc4_denoised"):
+        for name in ("ppc4", "ppc4_denoised", "ppc4_binomial"):
             row[name]["gamma_mode_rel_err"] = abs(row[name]["gamma_mode"] - g64) / g64
         results.append(row)
     ms64 = float(np.mean([r["ppc64"]["ms_per_step"] for r in results]))
     msnn = float(np.mean([r["ppc4_denoised"]["ms_per_step"] for r in results]))
+    msbin = float(np.mean([r["ppc4_binomial"]["ms_per_step"] for r in results]))
     ms4 = float(np.mean([r["ppc4"]["ms_per_step"] for r in results]))
     flops = dn.forward_flops(nx, ny)
     peak = None
@@ -435,9 +441,11 @@ def run_denoiser(args, rank, world, local_rank):
                      "train_tflops": train_tflops, "loss_first": losses[0],
                      "loss_last50": float(np.mean(losses[-50:]))},
         "validation_mse": {"raw_4ppc": raw, "denoised": den, "ratio": den / raw},
-        "step_ms": {"ppc64": ms64, "ppc4": ms4, "ppc4_denoised": msnn},
+        "step_ms": {"ppc64": ms64, "ppc4": ms4, "ppc4_denoised": msnn, "ppc4_binomial": msbin},
         "growth": results,
         "growth_within_5pct": [r["ppc4_denoised"]["gamma_mode_rel_err"] < 0.05 for r in elig],
+        "growth_within_5pct_binomial": [r["ppc4_binomial"]["gamma_mode_rel_err"] < 0.05
+                                        for r in elig],
     }
     print(json.dumps(line), flush=True)
 
@@ -481,16 +489,18 @@ def run_gpu(args, rank, world, local_rank):
     del sim
 
     # ---- end to end through the C ABI from pinned host buffers ----
-    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in w.species[0].arrays()]
+    host = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in sp.arrays()]
+            for sp in w.species]
     fields_out = torch.empty(3 * w.nx * w.ny, dtype=torch.float32).pin_memory()
-    h2d = sum(t.numel() * t.element_size() for t in host)
+    h2d = sum(t.numel() * t.element_size() for h in host for t in h)
     d2h = 2 * fields_out.numel() * 4 + 96
     torch.cuda.synchronize()
     if dist:
         torch.distributed.barrier()
     t0 = time.perf_counter()
     sim = pic.Simulation(pic.config_for(w, w.tile, args.threads, 0), stream.cuda_stream)
-    pic.pic_load_particles(sim.h, 0, *host)
+    for k, h in enumerate(host):
+        pic.pic_load_particles(sim.h, k, *h)
     sim.step(args.steps)
     pic.pic_get_fields(sim.h, pic.FIELD_E, fields_out)
     pic.pic_get_fields(sim.h, pic.FIELD_B, fields_out)

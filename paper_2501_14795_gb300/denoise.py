@@ -165,8 +165,10 @@ def mse_gain(net: pic.Denoiser, Jn, Jc, batch):
     return raw / Jn.numel(), den / Jn.numel()
 
 
-def field_energy_run(w, steps, net=None, stream=None, modes=False):
-    """W_E(t) history (t = 0..steps) of a run, its mean step time (ms, CUDA
+def field_energy_run(w, steps, net=None, stream=None, modes=False, binomial=0):
+    """W_E(t) history (t = 0..steps) of a run (with the denoiser `net` or
+    `binomial` passes of the binomial filter in the current-filter slot), its
+    mean step time (ms, CUDA
     events around the stepping; None with modes=True, whose per-step field
     reads would be timed too) and the diagnostics of one further step (with
     its current's continuity residual); with modes=True also |E_x(m)|^2 of the
@@ -176,6 +178,8 @@ def field_energy_run(w, steps, net=None, stream=None, modes=False):
     try:
         if net is not None:
             pic.pic_set_denoiser(sim.h, net.d)
+        elif binomial:
+            pic.pic_set_binomial_filter(sim.h, binomial)
         spec = None
         if modes:
             E = torch.empty((3, w.ny, w.nx), dtype=torch.float32, device="cuda")
@@ -213,51 +217,60 @@ def _continuity_diag(sim):
     return sim.diagnostics()
 
 
-def mode_growth_rate(power, dt, m, floor_steps=20, lo=1.0, hi=1.5):
-    """Growth rate of Fourier mode m from its power history (|E_m|^2 at steps
-    1..): the least-squares slope of ln|E_m| between lo e-folds above its
-    early noise level (median of the first floor_steps steps) and hi e-folds
-    below its first maximum."""
-    lp = 0.5 * np.log(np.maximum(power[:, m], 1e-300))
-    ks = int(np.argmax(lp))
-    floor = float(np.median(lp[:floor_steps]))
-    top = lp[ks]
-    idx = [j for j in range(ks + 1) if floor + lo <= lp[j] <= top - hi]
-    if len(idx) < 5:
-        return float("nan"), (None, None)
-    # the last contiguous run of qualifying steps before the maximum
-    run = [idx[-1]]
-    for j in reversed(idx[:-1]):
-        if j == run[-1] - 1:
-            run.append(j)
+def _smooth(v, w):
+    if w <= 1:
+        return v
+    k = np.ones(w) / w
+    pad = np.concatenate([np.full(w // 2, v[0]), v, np.full(w - 1 - w // 2, v[-1])])
+    return np.convolve(pad, k, mode="valid")
+
+
+def _fit_window(lv, floor_steps, lo, hi, smooth):
+    """Indices of the exponential-growth stretch of a log-amplitude history:
+    the longest contiguous run, before the (smoothed) global maximum, where the
+    smoothed value lies between lo above the early noise level (median of the
+    first floor_steps values) and hi below the maximum."""
+    ls = _smooth(lv, smooth)
+    ks = int(np.argmax(ls))
+    floor = float(np.median(ls[:floor_steps]))
+    top = float(ls[ks])
+    ok = [(floor + lo <= ls[j] <= top - hi) for j in range(ks + 1)]
+    best, cur = (0, -1), None
+    for j, o in enumerate(ok):
+        if o:
+            cur = (cur[0], j) if cur else (j, j)
+            if cur[1] - cur[0] > best[1] - best[0]:
+                best = cur
         else:
-            break
-    j0, j1 = min(run), max(run)
+            cur = None
+    return best
+
+
+def mode_growth_rate(power, dt, m, floor_steps=20, lo=1.5, hi=1.0, smooth=9, band=1):
+    """Growth rate of the field amplitude in the band of Fourier modes
+    m-band..m+band (power |E_m|^2 at steps 1..): least-squares slope of
+    ln|E| over the longest stretch between lo e-folds above the early noise
+    level and hi e-folds below the saturation maximum (smoothed over `smooth`
+    steps to place the window)."""
+    lo_m, hi_m = max(1, m - band), min(power.shape[1] - 1, m + band)
+    lv = 0.5 * np.log(np.maximum(power[:, lo_m:hi_m + 1].sum(axis=1), 1e-300))
+    j0, j1 = _fit_window(lv, floor_steps, lo, hi, smooth)
     if j1 - j0 < 5:
         return float("nan"), (j0, j1)
     t = (np.arange(j0, j1 + 1) + 1) * dt
-    return float(np.polyfit(t, lp[j0:j1 + 1], 1)[0]), (j0, j1)
+    return float(np.polyfit(t, lv[j0:j1 + 1], 1)[0]), (j0, j1)
 
 
-def growth_rate(we, dt, lo=4.0, hi=1.0):
-    """Field-amplitude growth rate from W_E(t): the least-squares slope of
-    ln W_E / 2 over the last stretch before the first maximum where ln W_E is
-    between (max - lo) and (max - hi)."""
-    lw = np.log(np.maximum(we, 1e-300))
-    # first maximum: the saturation of the instability
-    ks = int(np.argmax(lw))
-    top = lw[ks]
-    j1 = ks
-    while j1 > 0 and lw[j1] > top - hi:
-        j1 -= 1
-    j0 = j1
-    while j0 > 0 and lw[j0] > top - lo:
-        j0 -= 1
+def growth_rate(we, dt, floor_steps=20, lo=1.5, hi=1.0, smooth=9):
+    """Field-amplitude growth rate from the field-energy history W_E(t) (t = 0,
+    dt, ...): the slope of ln W_E / 2 over the same window as
+    mode_growth_rate."""
+    lv = 0.5 * np.log(np.maximum(np.asarray(we[1:], np.float64), 1e-300))
+    j0, j1 = _fit_window(lv, floor_steps, lo, hi, smooth)
     if j1 - j0 < 5:
         return float("nan"), (j0, j1)
-    t = np.arange(j0, j1 + 1) * dt
-    slope = np.polyfit(t, lw[j0:j1 + 1], 1)[0]
-    return 0.5 * slope, (j0, j1)
+    t = (np.arange(j0, j1 + 1) + 1) * dt
+    return float(np.polyfit(t, lv[j0:j1 + 1], 1)[0]), (j0, j1)
 
 
 def kinetic_growth_rate(drift, u_th, L, m_max=None):

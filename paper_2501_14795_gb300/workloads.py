@@ -138,6 +138,27 @@ def weibel(nx=512, ny=512, k=8, u_drift=0.6, u_th=0.05, dx=0.1, dy=0.1, dt=0.05,
                     meta=dict(ppc=2 * k2, u_th=u_th, u_drift=u_drift, seed=seed))
 
 
+def weibel_pair(nx=512, ny=512, k=10, u_drift=0.6, u_th=0.05, dx=0.1, dy=0.1, dt=0.05,
+                tile=16, steps=500, seed=SEED_BASE + 6) -> Workload:
+    """The thesis's own Weibel shape (§5.1): electrons and positrons, k x k per
+    cell each (k = 10: 26.2M per species on 512^2, the thesis's 25M per species
+    on 500^2 cells rounded to a tile-divisible grid), density 1 each, electrons
+    drifting +u_drift and positrons -u_drift along z, thermal spread u_th; a
+    neutral pair plasma, no fixed background."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ix, iy, x, y, _, _ = lattice(nx, ny, k)
+    n = ix.size
+    sps = []
+    for qm, drift in ((-1.0, u_drift), (1.0, -u_drift)):
+        ux = _maxwellian(rng, n, u_th)
+        uy = _maxwellian(rng, n, u_th)
+        uz = _maxwellian(rng, n, u_th) + drift
+        sps.append(Species(qm, qm / (k * k), ix.copy(), iy.copy(), x.copy(), y.copy(), _f32(ux),
+                           _f32(uy), _f32(uz)))
+    return Workload("weibel_pair", nx, ny, dx, dy, dt, tile, steps, sps, background=0.0,
+                    meta=dict(ppc=2 * k * k, u_th=u_th, u_drift=u_drift, seed=seed))
+
+
 def thermal_seeded(nx=2048, ny=2048, k=4, u_th=0.2, amp=1e-3, mode=1, dx=0.1, dy=0.1,
                    dt=0.05, tile=16, steps=200, seed=SEED_BASE + 3) -> Workload:
     """Thermal electrons on fixed ions with a seeded longitudinal mode:

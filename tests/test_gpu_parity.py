@@ -488,3 +488,24 @@ def test_binomial_filter_matches_oracle(passes):
     we, wb = o.energies()
     assert d["w_e"] == pytest.approx(we, rel=2e-3)
     assert d["w_b"] == pytest.approx(wb, rel=2e-3)
+
+
+def test_electron_positron_weibel_follows_the_oracle():
+    """Two mobile species of opposite charge (the thesis's Weibel shape) on a
+    small grid: 10 steps against the FP64 oracle; the pair plasma stays
+    neutral and charge-conserving."""
+    w = wl.weibel_pair(nx=64, ny=64, k=4, tile=16)
+    with _gpu(w, 0) as sim:
+        sim.diagnostics()
+        sim.step(10)
+        d = sim.diagnostics()
+        sim.step(1)
+        d2 = sim.diagnostics()
+    o = _oracle(w, np.float64)
+    o.step(10)
+    we, wb = o.energies()
+    assert d["status_bits"] == 0 and d["n_particles"][:2] == [w.species[0].n, w.species[1].n]
+    assert d["w_e"] == pytest.approx(we, rel=1e-3, abs=1e-9)
+    assert d["w_k"] == pytest.approx(o.ke_history[-1], rel=1e-5)
+    assert abs(d["charge_total"]) < 1e-9
+    assert d2["continuity_max"] < 1e-4
