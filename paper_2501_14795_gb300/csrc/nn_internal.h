@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <utility>
 
 namespace pic {
 namespace nn {
@@ -73,6 +74,28 @@ struct PackTable {
 cudaError_t init_kernels();
 // mma.sync implicit GEMM (any shape of the network), or the tcgen05 kernel
 // (nn_tc.cu) when the row length is a multiple of 128 and the shape is built
+// Programmatic dependent launch: the kernel may start before the previous
+// kernel in the stream has finished; it must call pdl_wait() before touching
+// anything that kernel writes (pdl_trigger() lets the next kernel start).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 cudaError_t launch_conv(const ConvParams& p, int cin, int ct, cudaStream_t s);
 bool conv_tc_supported(const ConvParams& p, int cin);
 cudaError_t launch_conv_tc(const ConvParams& p, int cin, cudaStream_t s);

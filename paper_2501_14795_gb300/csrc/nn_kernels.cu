@@ -76,6 +76,10 @@ __device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], uint32
 __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 // ------------------------------------------------------------------ conv
+// Launched as programmatic dependents (PDL): a CTA stages its weights, which
+// no earlier kernel of the forward pass writes, before waiting for the
+// previous kernel, and lets the next kernel start staging once its own
+// products are issued.
 template <int CIN, int CT>
 struct ConvSmem {
     static constexpr int CS = CIN + 8;  // row stride in elements (16 B of padding: no bank conflicts)
@@ -100,18 +104,19 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv(const ConvParams p) {
     // read at (y/2, x/2): nearest 2x upsampling fused into the load
     const int sh = p.up ? 1 : 0;
     const int Hi = p.H >> sh, Wi = p.W >> sh;
+    for (int i = tid; i < 9 * CT * CH; i += CONV_THREADS) {
+        const int row = i / CH, c = i - row * CH;
+        const int tap = row / CT, n = row - tap * CT;
+        cp_async16(sW + row * L::CS + c * 8,
+                   p.w + ((size_t)tap * p.cout_pad + co0 + n) * CIN + c * 8);
+    }
+    pdl_wait();  // the input is the previous kernel's output
     for (int i = tid; i < PH * PW * CH; i += CONV_THREADS) {
         const int pix = i / CH, c = i - pix * CH;
         const int r = pix / PW, q = pix - r * PW;
         const int y = wrap(ty0 - 1 + r, p.H) >> sh, x = wrap(tx0 - 1 + q, p.W) >> sh;
         cp_async16(sP + pix * L::CS + c * 8,
                    p.x + (((size_t)b * Hi + y) * Wi + x) * CIN + c * 8);
-    }
-    for (int i = tid; i < 9 * CT * CH; i += CONV_THREADS) {
-        const int row = i / CH, c = i - row * CH;
-        const int tap = row / CT, n = row - tap * CT;
-        cp_async16(sW + row * L::CS + c * 8,
-                   p.w + ((size_t)tap * p.cout_pad + co0 + n) * CIN + c * 8);
     }
     cp_async_commit();
     cp_async_wait<0>();
@@ -149,6 +154,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv(const ConvParams p) {
         }
     }
 
+    pdl_trigger();
     // epilogue: rows g, g+8 of the warp's 16 pixels; columns 2(lane%4), +1 of each n-tile
     const int g = lane >> 2, cq = (lane & 3) * 2;
     const int y = ty0 + r;
@@ -325,6 +331,8 @@ __global__ void __launch_bounds__(WG_THREADS) k_wgrad(const WgradParams p) {
 // field layout (3 planes) -> bfloat16 NHWC with 16 channels, scaled
 __global__ void k_pack_input(const float* J, long long bstride, long long cstride, int pitch,
                              int offset, int B, int H, int W, float inv_scale, bf16* out) {
+    pdl_wait();
+    pdl_trigger();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)B * H * W) return;
     const int x = (int)(i % W);
@@ -341,6 +349,8 @@ __global__ void k_pack_input(const float* J, long long bstride, long long cstrid
 
 // 2x2 mean pooling, bfloat16 -> bfloat16 (FP32 sum of the four)
 __global__ void k_pool_fwd(const bf16* in, int B, int H, int W, int C, bf16* out) {
+    pdl_wait();
+    pdl_trigger();
     const int G = C / 8;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int Ho = H / 2, Wo = W / 2;
@@ -599,8 +609,7 @@ cudaError_t conv_T(const ConvParams& p, cudaStream_t s) {
     cudaError_t e = conv_attr<CIN, CT>();
     if (e != cudaSuccess) return e;
     const dim3 grid((p.W / TW) * (p.H / TH), p.B, p.cout_pad / CT);
-    k_conv<CIN, CT><<<grid, CONV_THREADS, ConvSmem<CIN, CT>::bytes, s>>>(p);
-    return cudaGetLastError();
+    return launch_pdl(k_conv<CIN, CT>, grid, dim3(CONV_THREADS), ConvSmem<CIN, CT>::bytes, s, p);
 }
 
 template <int CI, int CO>
@@ -664,16 +673,14 @@ cudaError_t launch_pack_input(const float* J, long long bstride, long long cstri
                               cudaStream_t s) {
     const long long n = (long long)B * H * W;
     if (n == 0) return cudaSuccess;
-    k_pack_input<<<blocks(n, 256), 256, 0, s>>>(J, bstride, cstride, pitch, offset, B, H, W,
-                                                 inv_scale, out);
-    return cudaGetLastError();
+    return launch_pdl(k_pack_input, dim3(blocks(n, 256)), dim3(256), 0, s, J, bstride, cstride,
+                      pitch, offset, B, H, W, inv_scale, out);
 }
 
 cudaError_t launch_pool_fwd(const __nv_bfloat16* in, int B, int H, int W, int C,
                             __nv_bfloat16* out, cudaStream_t s) {
     const long long n = (long long)B * (H / 2) * (W / 2) * (C / 8);
-    k_pool_fwd<<<blocks(n, 256), 256, 0, s>>>(in, B, H, W, C, out);
-    return cudaGetLastError();
+    return launch_pdl(k_pool_fwd, dim3(blocks(n, 256)), dim3(256), 0, s, in, B, H, W, C, out);
 }
 
 cudaError_t launch_up_fwd(const __nv_bfloat16* in, int B, int H, int W, int C, __nv_bfloat16* out,

@@ -210,6 +210,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
         else
             *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
     }
+    pdl_wait();  // the input is the previous kernel's output
+    pdl_trigger();
     load_patch<CIN, NT>(p, smem, blockIdx.x, tid);
     asm volatile("cp.async.commit_group;" ::: "memory");
     if (tid == 0) {
@@ -342,8 +344,7 @@ cudaError_t conv_tc_T(const ConvParams& p, cudaStream_t s) {
     const int nseg = p.B * (p.H / TC_R) * (p.W / TC_M);
     const int cap = tc_grid_cap<CIN, NT>();
     const int grid = nseg < cap ? nseg : cap;
-    k_conv_tc<CIN, NT><<<grid, TC_THREADS, L::bytes, s>>>(p);
-    return cudaGetLastError();
+    return launch_pdl(k_conv_tc<CIN, NT>, dim3(grid), dim3(TC_THREADS), L::bytes, s, p);
 }
 
 }  // namespace
