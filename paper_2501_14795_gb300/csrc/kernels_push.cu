@@ -63,6 +63,10 @@ constexpr unsigned FULL = 0xffffffffu;
 #ifndef PIC_AGGREGATE
 #define PIC_AGGREGATE 0
 #endif
+// J tiles of the warp groups: exact 32-bit fixed point (1) or FP32 (0)
+#ifndef PIC_J_FIXED
+#define PIC_J_FIXED 1
+#endif
 constexpr int NSTAGE = PIC_NSTAGE;  // particle batches (blockDim particles each) in flight per CTA
 constexpr int PAD = 4;     // a batch is copied from a 16-byte aligned start: <= 3 extra
 // warps sharing one fixed-point J tile (per-warp tiles: 1)
@@ -190,7 +194,7 @@ constexpr int AGG_MAX_GROUPS = 8;
 // tile holds FP32.
 template <bool PER_WARP>
 __device__ __forceinline__ void tile_add(float* a, float x) {
-    if constexpr (PER_WARP)
+    if constexpr (PER_WARP && PIC_J_FIXED)
         atomicAdd(reinterpret_cast<int*>(a), __float2int_rn(x));
     else
         atomicAdd(a, x);
@@ -331,7 +335,7 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
         const int len = (nt + prm.chunks - 1) / prm.chunks;
         const int c0 = p0 + min(chunk * len, nt), c1 = p0 + min((chunk + 1) * len, nt);
         // current constants, times the fixed-point scale for the integer tiles
-        const float dsc = L::PER_WARP ? qscale : 1.f;
+        const float dsc = (L::PER_WARP && PIC_J_FIXED) ? qscale : 1.f;
         const float tem = S.tem, qjx = S.qjx * dsc, qjy = S.qjy * dsc, qjz = S.qjz * dsc;
         float ke = 0.f;
         // Particle batches come in through a NSTAGE-deep pipeline of bulk copies
@@ -597,11 +601,14 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
         const int r = rem / L::JW, q = rem - r * L::JW;
         const int lx = q - 1, ly = r - 1;
         float v;
-        if constexpr (L::PER_WARP) {
+        if constexpr (L::PER_WARP && PIC_J_FIXED) {
             long long acc = 0;
             for (int w = 0; w < jtiles; ++w)
                 acc += reinterpret_cast<const int*>(sJ)[w * L::JN + idx];
             v = (float)acc * qinv;
+        } else if constexpr (L::PER_WARP) {
+            v = 0.f;
+            for (int w = 0; w < jtiles; ++w) v += sJ[w * L::JN + idx];
         } else {
             v = sJ[idx];
         }
