@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <utility>
 
 namespace pic {
@@ -80,6 +81,18 @@ cudaError_t init_kernels();
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
 
+// Programmatic dependent launch is off unless PIC_NN_PDL=1 in the
+// environment: measured on GB300 inside the step graph of a 256^2 run the
+// denoiser took ~10 us longer with it (the early dependents' CTAs compete
+// with the tail of the running layer).
+inline bool pdl_enabled() {
+    static const int on = [] {
+        const char* v = getenv("PIC_NN_PDL");
+        return (v && v[0] == '1') ? 1 : 0;
+    }();
+    return on != 0;
+}
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
                        cudaStream_t s, Args&&... args) {
@@ -92,7 +105,7 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
