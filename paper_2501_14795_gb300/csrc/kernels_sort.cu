@@ -264,31 +264,61 @@ __device__ __forceinline__ void fill_tile(const SortParams& prm, int s, int t, i
     int nsrc = 0, ntgt = 0;
     bool overflow = false;
 
-    // source_idx: neighbours' leavers heading here (distinct neighbour tiles only)
-    int nbs[8];
-    int nnb = 0;
-    for (int d = 0; d < 8; ++d) {
+    // source_idx: neighbours' leavers heading here.  Lanes 0-7 take the eight
+    // neighbour tiles (a neighbour that is t itself or repeats a lower lane's,
+    // on grids one or two tiles across, is dropped); their leaver lists are
+    // scanned as one concatenated list, so the loads of a chunk do not wait
+    // for the previous chunk.
+    int nb = -1, q0 = 0, nl = 0;
+    if (lane < 8) {
         int ddx, ddy;
-        dir_delta(d, ddx, ddy);
-        const int nb = dev::wrapi(ty + ddy, g.nty) * g.ntx + dev::wrapi(tx + ddx, g.ntx);
-        bool dup = nb == t;
-        for (int k = 0; k < nnb; ++k) dup |= nbs[k] == nb;
-        if (!dup) nbs[nnb++] = nb;
+        dir_delta(lane, ddx, ddy);
+        nb = dev::wrapi(ty + ddy, g.nty) * g.ntx + dev::wrapi(tx + ddx, g.ntx);
     }
-    for (int k = 0; k < nnb; ++k) {
-        const int nb = nbs[k];
-        const int q0 = S.off_old[nb], nl = S.leave[nb];
-        for (int base = 0; base < nl; base += 32) {
-            const int i = base + lane;
-            const bool take = i < nl && tile_of(S.ocell[q0 + i], T, g.ntx) == t;
-            const unsigned m = __ballot_sync(0xffffffffu, take);
-            if (take) {
-                const int slot = nsrc + __popc(m & lt);
-                if (slot < cap) S.isrc[r0 + slot] = q0 + i;
-                else overflow = true;
-            }
-            nsrc += __popc(m);
+    bool keep = lane < 8 && nb != t;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const int o = __shfl_sync(0xffffffffu, nb, k);
+        if (k < lane && o == nb) keep = false;
+    }
+    if (keep) {
+        q0 = S.off_old[nb];
+        nl = S.leave[nb];
+    }
+    int pre = nl;  // inclusive prefix over lanes 0-7
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, pre, 7);
+    int ex[8], qq[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        ex[k] = __shfl_sync(0xffffffffu, pre - nl, k);
+        qq[k] = __shfl_sync(0xffffffffu, q0, k);
+    }
+    for (int base = 0; base < total; base += 32) {
+        const int e = base + lane;
+        bool take = false;
+        int src = 0;
+        if (e < total) {
+            // the list holding e: the last one starting at or before it (lists
+            // of length 0 share their start with the next one)
+            int k = 0;
+#pragma unroll
+            for (int j = 1; j < 8; ++j)
+                if (ex[j] <= e) k = j;
+            src = qq[k] + (e - ex[k]);
+            take = tile_of(S.ocell[src], T, g.ntx) == t;
         }
+        const unsigned m = __ballot_sync(0xffffffffu, take);
+        if (take) {
+            const int slot = nsrc + __popc(m & lt);
+            if (slot < cap) S.isrc[r0 + slot] = src;
+            else overflow = true;
+        }
+        nsrc += __popc(m);
     }
     // ... plus this tile's displaced stayers
     for (int base = 0; base < ev; base += 32) {
