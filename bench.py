@@ -410,6 +410,21 @@ def run_denoiser(args, rank, world, local_rank):
         for name in ("ppc4", "ppc4_denoised", "ppc4_binomial"):
             row[name]["gamma_mode_rel_err"] = abs(row[name]["gamma_mode"] - g64) / g64
         results.append(row)
+    # the same trained network on larger grids (it is translation invariant):
+    # step times of 64 ppc, 4 ppc and denoised 4 ppc
+    by_grid = {}
+    d0 = dn.draws(1, offset=500)[0]
+    for side in (512, 1024):
+        big = pic.Denoiser(side, side, 1, scale)
+        big.set_params(net.params())
+        row = {}
+        for name, k, use in (("ppc64", 8, False), ("ppc4", 2, False), ("ppc4_denoised", 2, True)):
+            w = dn.workload(d0, side, side, k, 60)
+            _, ms, _, _ = dn.field_energy_run(w, 60, big if use else None)
+            row[name] = ms
+        row["speedup"] = row["ppc64"] / row["ppc4_denoised"]
+        by_grid[f"{side}x{side}"] = row
+        big.close()
     ms64 = float(np.mean([r["ppc64"]["ms_per_step"] for r in results]))
     msnn = float(np.mean([r["ppc4_denoised"]["ms_per_step"] for r in results]))
     msbin = float(np.mean([r["ppc4_binomial"]["ms_per_step"] for r in results]))
@@ -442,6 +457,7 @@ def run_denoiser(args, rank, world, local_rank):
                      "loss_last50": float(np.mean(losses[-50:]))},
         "validation_mse": {"raw_4ppc": raw, "denoised": den, "ratio": den / raw},
         "step_ms": {"ppc64": ms64, "ppc4": ms4, "ppc4_denoised": msnn, "ppc4_binomial": msbin},
+        "speedup_by_grid": by_grid,
         "growth": results,
         "growth_within_5pct": [r["ppc4_denoised"]["gamma_mode_rel_err"] < 0.05 for r in elig],
         "growth_within_5pct_binomial": [r["ppc4_binomial"]["gamma_mode_rel_err"] < 0.05
