@@ -60,7 +60,8 @@ struct TcSmem {
     static constexpr int WPLANE = NT * 16;                    // bytes of one k-group of one tap
     static constexpr int WTAP = KG * WPLANE;
     static constexpr size_t off_w = 2 * (size_t)PATCH;        // two patches, then the weights
-    static constexpr size_t off_bar = (off_w + 9 * WTAP + 15) & ~(size_t)15;
+    static constexpr size_t off_bias = off_w + 9 * WTAP;       // NT floats
+    static constexpr size_t off_bar = (off_bias + NT * 4 + 15) & ~(size_t)15;
     static constexpr size_t bytes = off_bar + 32;             // 2 mbarriers + TMEM slot
     static constexpr int NTC = NT < 32 ? 32 : NT;             // TMEM columns of one row's accumulator
     static constexpr int TMEM_COLS = 2 * TC_R * NTC;          // two work units in flight
@@ -108,8 +109,8 @@ __device__ __forceinline__ void load_patch(const ConvParams& p, unsigned char* s
 // the epilogues on one accumulator (row rr of unit seg): TMEM lane = pixel
 // x0 + lane of the row, column = output channel
 template <int NT>
-__device__ __forceinline__ void epilogue(const ConvParams& p, uint32_t acc, int seg, int rr,
-                                         int warp, int lane) {
+__device__ __forceinline__ void epilogue(const ConvParams& p, const float* sBias, uint32_t acc,
+                                         int seg, int rr, int warp, int lane) {
     // warps w and w + 4 read TMEM lanes 32 (w % 4)..+31: the first and the
     // second half of the 16-column chunks
     const int lg = warp & 3, half = warp >> 2;
@@ -141,11 +142,8 @@ __device__ __forceinline__ void epilogue(const ConvParams& p, uint32_t acc, int 
                 o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
             continue;
         }
-        if (p.bias) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-                if (c0 + j < p.cout) v[j] += p.bias[c0 + j];
-        }
+        for (int j = 0; j < 16; ++j) v[j] += sBias[c0 + j];  // zero past cout and without bias
         if (p.epi == EPI_FINAL) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
@@ -193,6 +191,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
     using L = TcSmem<CIN, NT>;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sW = smem + L::off_w;
+    float* sBias = reinterpret_cast<float*>(smem + L::off_bias);
     const uint32_t bar0 = saddr(smem + L::off_bar);           // mbarriers of accumulators 0, 1
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::off_bar + 16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -210,6 +209,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
         else
             *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
     }
+    for (int c = tid; c < NT; c += TC_THREADS)
+        sBias[c] = (p.bias && c < p.cout && p.epi != EPI_GRAD) ? p.bias[c] : 0.f;
     pdl_wait();  // the input is the previous kernel's output
     pdl_trigger();
     load_patch<CIN, NT>(p, smem, blockIdx.x, tid);
@@ -269,20 +270,22 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     bar0 + 8 * buf));
         }
-        // the previous segment's results, while the tensor cores run this one
+        // once the previous unit's products are complete, its patch buffer
+        // takes the next unit's patch, and its results are stored while the
+        // tensor cores run this unit
         if (prev >= 0) {
             const int pb = (i - 1) & 1;
             if (ok && !wait_bar(bar0 + 8 * pb, ((i - 1) >> 1) & 1)) ok = false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (ok)
-                for (int rr = 0; rr < TC_R; ++rr)
-                    epilogue<NT>(p, tmem + (pb * TC_R + rr) * L::NTC, prev, rr, warp, lane);
         }
-        // the next segment's patch goes where the previous segment's was
-        // (its MMAs are complete: waited just above)
         const int nxt = seg + gridDim.x;
         if (nxt < nseg) load_patch<CIN, NT>(p, smem + (buf ^ 1) * L::PATCH, nxt, tid);
         asm volatile("cp.async.commit_group;" ::: "memory");
+        if (prev >= 0 && ok) {
+            const int pb = (i - 1) & 1;
+            for (int rr = 0; rr < TC_R; ++rr)
+                epilogue<NT>(p, sBias, tmem + (pb * TC_R + rr) * L::NTC, prev, rr, warp, lane);
+        }
         prev = seg;
     }
     if (prev >= 0) {
@@ -291,7 +294,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (ok)
             for (int rr = 0; rr < TC_R; ++rr)
-                epilogue<NT>(p, tmem + (pb * TC_R + rr) * L::NTC, prev, rr, warp, lane);
+                epilogue<NT>(p, sBias, tmem + (pb * TC_R + rr) * L::NTC, prev, rr, warp, lane);
     }
     if (!ok && tid == 0 && p.status) atomicOr(p.status, 2u);  // a bounded wait ran out
     asm volatile("cp.async.wait_group 0;" ::: "memory");
