@@ -7,9 +7,10 @@
 // 3-channel current is padded with zeros); gradients are FP32 except where
 // they enter a tensor-core product (dz, rounded to bfloat16).
 //
-//   k_conv   implicit GEMM: CTA = 8x16 output pixels x a tile of output
-//            channels; the halo patch and the CTA's weights sit in shared
-//            memory; warp = one pixel row (m16) x the channel tile.  The same
+//   k_conv   implicit GEMM, persistent: a CTA keeps a tile of output
+//            channels' weights in shared memory and runs through 8x16-pixel
+//            tiles with a double-buffered halo patch; warp = one pixel row
+//            (m16) x the channel tile.  The same
 //            kernel computes the input gradient with flipped, transposed
 //            weights (dgrad).  Epilogues: bias + ReLU (+ skip) to bfloat16,
 //            raw FP32, or the network's residual output in field layout.
@@ -85,25 +86,42 @@ struct ConvSmem {
     static constexpr int CS = CIN + 8;  // row stride in elements (16 B of padding: no bank conflicts)
     static constexpr int PATCH = PH * PW * CS;
     static constexpr int WTS = 9 * CT * CS;
-    static constexpr size_t bytes = (size_t)(PATCH + WTS) * 2;
+    // the CTA's weights, then two patches
+    static constexpr size_t bytes = (size_t)(WTS + 2 * PATCH) * 2;
 };
 
+// Persistent: CTA (blockIdx.x, blockIdx.z) keeps the weights of output
+// channels [z CT, z CT + CT) in shared memory and runs through the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ... of all images; the next tile's
+// patch is copied in while the current one is computed.
 template <int CIN, int CT>
 __global__ void __launch_bounds__(CONV_THREADS) k_conv(const ConvParams p) {
     using L = ConvSmem<CIN, CT>;
     extern __shared__ __align__(16) unsigned char smem[];
-    bf16* sP = reinterpret_cast<bf16*>(smem);
-    bf16* sW = sP + L::PATCH;
+    bf16* sW = reinterpret_cast<bf16*>(smem);
+    bf16* sP0 = sW + L::WTS;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tilesx = p.W / TW;
-    const int ty0 = (blockIdx.x / tilesx) * TH, tx0 = (blockIdx.x % tilesx) * TW;
-    const int b = blockIdx.y, co0 = blockIdx.z * CT;
+    const int tilesx = p.W / TW, tiles_img = tilesx * (p.H / TH);
+    const int ntiles = p.B * tiles_img;
+    const int co0 = blockIdx.z * CT;
     constexpr int CH = CIN / 8;  // 16-byte chunks per pixel
-
     // input pixel (y, x); with p.up the input is the half-resolution tensor
     // read at (y/2, x/2): nearest 2x upsampling fused into the load
     const int sh = p.up ? 1 : 0;
     const int Hi = p.H >> sh, Wi = p.W >> sh;
+
+    auto load_patch = [&](int tile, bf16* sP) {
+        const int b = tile / tiles_img, tl = tile - b * tiles_img;
+        const int ty0 = (tl / tilesx) * TH, tx0 = (tl % tilesx) * TW;
+        for (int i = tid; i < PH * PW * CH; i += CONV_THREADS) {
+            const int pix = i / CH, c = i - pix * CH;
+            const int r = pix / PW, q = pix - r * PW;
+            const int y = wrap(ty0 - 1 + r, p.H) >> sh, x = wrap(tx0 - 1 + q, p.W) >> sh;
+            cp_async16(sP + pix * L::CS + c * 8,
+                       p.x + (((size_t)b * Hi + y) * Wi + x) * CIN + c * 8);
+        }
+    };
+
     for (int i = tid; i < 9 * CT * CH; i += CONV_THREADS) {
         const int row = i / CH, c = i - row * CH;
         const int tap = row / CT, n = row - tap * CT;
@@ -111,96 +129,101 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv(const ConvParams p) {
                    p.w + ((size_t)tap * p.cout_pad + co0 + n) * CIN + c * 8);
     }
     pdl_wait();  // the input is the previous kernel's output
-    for (int i = tid; i < PH * PW * CH; i += CONV_THREADS) {
-        const int pix = i / CH, c = i - pix * CH;
-        const int r = pix / PW, q = pix - r * PW;
-        const int y = wrap(ty0 - 1 + r, p.H) >> sh, x = wrap(tx0 - 1 + q, p.W) >> sh;
-        cp_async16(sP + pix * L::CS + c * 8,
-                   p.x + (((size_t)b * Hi + y) * Wi + x) * CIN + c * 8);
-    }
+    if ((int)blockIdx.x < ntiles) load_patch(blockIdx.x, sP0);
     cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
 
     constexpr int NT = CT / 8;
-    float acc[NT][4];
-#pragma unroll
-    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
     const int r = warp;  // the warp's output pixel row inside the tile
-#pragma unroll 1
-    for (int tap = 0; tap < 9; ++tap) {
-        const int ky = tap / 3, kx = tap - 3 * (tap / 3);
-        const bf16* pa = sP + ((r + ky) * PW + kx + (lane & 15)) * L::CS + (lane >> 4) * 8;
-        const bf16* pw = sW + tap * CT * L::CS;
-#pragma unroll
-        for (int kc = 0; kc < CIN / 16; ++kc) {
-            uint32_t a[4];
-            ldsm_x4(a, pa + kc * 16);
-            if constexpr (NT == 1) {
-                uint32_t bb[2];
-                ldsm_x2(bb, pw + (lane & 7) * L::CS + kc * 16 + ((lane >> 3) & 1) * 8);
-                mma_bf16(acc[0], a, bb[0], bb[1]);
-            } else {
-#pragma unroll
-                for (int nt = 0; nt < NT; nt += 2) {
-                    const int j = lane >> 3;
-                    uint32_t bb[4];
-                    ldsm_x4(bb, pw + (nt * 8 + (j >> 1) * 8 + (lane & 7)) * L::CS + kc * 16 +
-                                    (j & 1) * 8);
-                    mma_bf16(acc[nt], a, bb[0], bb[1]);
-                    mma_bf16(acc[nt + 1], a, bb[2], bb[3]);
-                }
-            }
-        }
-    }
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        bf16* sP = sP0 + (it & 1) * L::PATCH;
+        cp_async_wait<0>();
+        __syncthreads();  // this tile's patch is in; every warp is done with the other buffer
+        const int nxt = tile + gridDim.x;
+        if (nxt < ntiles) load_patch(nxt, sP0 + ((it + 1) & 1) * L::PATCH);
+        cp_async_commit();
 
-    pdl_trigger();
-    // epilogue: rows g, g+8 of the warp's 16 pixels; columns 2(lane%4), +1 of each n-tile
-    const int g = lane >> 2, cq = (lane & 3) * 2;
-    const int y = ty0 + r;
+        float acc[NT][4];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int x = tx0 + g + 8 * h;
-        const size_t pix = ((size_t)b * p.H + y) * p.W + x;
+        for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+#pragma unroll 1
+        for (int tap = 0; tap < 9; ++tap) {
+            const int ky = tap / 3, kx = tap - 3 * (tap / 3);
+            const bf16* pa = sP + ((r + ky) * PW + kx + (lane & 15)) * L::CS + (lane >> 4) * 8;
+            const bf16* pw = sW + tap * CT * L::CS;
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            const int co = co0 + nt * 8 + cq;
-            float v0 = acc[nt][2 * h], v1 = acc[nt][2 * h + 1];
-            if (p.epi == EPI_GRAD) {
-                *reinterpret_cast<float2*>(p.g_out + pix * p.cout_pad + co) = make_float2(v0, v1);
-                continue;
-            }
-            if (p.bias) {
-                if (co < p.cout) v0 += p.bias[co];
-                if (co + 1 < p.cout) v1 += p.bias[co + 1];
-            }
-            if (p.epi == EPI_FINAL) {
-                // residual output in field layout: out = res * rs + z * os
+            for (int kc = 0; kc < CIN / 16; ++kc) {
+                uint32_t a[4];
+                ldsm_x4(a, pa + kc * 16);
+                if constexpr (NT == 1) {
+                    uint32_t bb[2];
+                    ldsm_x2(bb, pw + (lane & 7) * L::CS + kc * 16 + ((lane >> 3) & 1) * 8);
+                    mma_bf16(acc[0], a, bb[0], bb[1]);
+                } else {
 #pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int c = co + e;
-                    if (c >= p.cout) continue;
-                    const size_t o = (size_t)b * p.bstride + (size_t)c * p.cstride + p.offset +
-                                     (size_t)y * p.pitch + x;
-                    p.fout[o] = p.res[o] * p.rs + (e ? v1 : v0) * p.os;
+                    for (int nt = 0; nt < NT; nt += 2) {
+                        const int j = lane >> 3;
+                        uint32_t bb[4];
+                        ldsm_x4(bb, pw + (nt * 8 + (j >> 1) * 8 + (lane & 7)) * L::CS + kc * 16 +
+                                        (j & 1) * 8);
+                        mma_bf16(acc[nt], a, bb[0], bb[1]);
+                        mma_bf16(acc[nt + 1], a, bb[2], bb[3]);
+                    }
                 }
-                continue;
             }
-            if (p.relu) {
-                v0 = fmaxf(v0, 0.f);
-                v1 = fmaxf(v1, 0.f);
-            }
-            const __nv_bfloat162 a2 = __floats2bfloat162_rn(v0, v1);
-            *reinterpret_cast<__nv_bfloat162*>(p.a_out + pix * p.cout_pad + co) = a2;
-            if (p.skip) {
-                const __nv_bfloat162 s2 =
-                    *reinterpret_cast<const __nv_bfloat162*>(p.skip + pix * p.cout_pad + co);
-                const float2 af = __bfloat1622float2(a2), sf = __bfloat1622float2(s2);
-                *reinterpret_cast<__nv_bfloat162*>(p.y_out + pix * p.cout_pad + co) =
-                    __floats2bfloat162_rn(af.x + sf.x, af.y + sf.y);
+        }
+        if (tile + gridDim.x >= ntiles) pdl_trigger();
+
+        // epilogue: rows g, g+8 of the warp's 16 pixels; columns 2(lane%4), +1 of each n-tile
+        const int b = tile / tiles_img, tl = tile - b * tiles_img;
+        const int ty0 = (tl / tilesx) * TH, tx0 = (tl % tilesx) * TW;
+        const int g = lane >> 2, cq = (lane & 3) * 2;
+        const int y = ty0 + r;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int x = tx0 + g + 8 * h;
+            const size_t pix = ((size_t)b * p.H + y) * p.W + x;
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                const int co = co0 + nt * 8 + cq;
+                float v0 = acc[nt][2 * h], v1 = acc[nt][2 * h + 1];
+                if (p.epi == EPI_GRAD) {
+                    *reinterpret_cast<float2*>(p.g_out + pix * p.cout_pad + co) = make_float2(v0, v1);
+                    continue;
+                }
+                if (p.bias) {
+                    if (co < p.cout) v0 += p.bias[co];
+                    if (co + 1 < p.cout) v1 += p.bias[co + 1];
+                }
+                if (p.epi == EPI_FINAL) {
+                    // residual output in field layout: out = res * rs + z * os
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int c = co + e;
+                        if (c >= p.cout) continue;
+                        const size_t o = (size_t)b * p.bstride + (size_t)c * p.cstride + p.offset +
+                                         (size_t)y * p.pitch + x;
+                        p.fout[o] = p.res[o] * p.rs + (e ? v1 : v0) * p.os;
+                    }
+                    continue;
+                }
+                if (p.relu) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                const __nv_bfloat162 a2 = __floats2bfloat162_rn(v0, v1);
+                *reinterpret_cast<__nv_bfloat162*>(p.a_out + pix * p.cout_pad + co) = a2;
+                if (p.skip) {
+                    const __nv_bfloat162 s2 =
+                        *reinterpret_cast<const __nv_bfloat162*>(p.skip + pix * p.cout_pad + co);
+                    const float2 af = __bfloat1622float2(a2), sf = __bfloat1622float2(s2);
+                    *reinterpret_cast<__nv_bfloat162*>(p.y_out + pix * p.cout_pad + co) =
+                        __floats2bfloat162_rn(af.x + sf.x, af.y + sf.y);
+                }
             }
         }
     }
+    cp_async_wait<0>();
 }
 
 // ----------------------------------------------------------------- wgrad
@@ -608,7 +631,25 @@ template <int CIN, int CT>
 cudaError_t conv_T(const ConvParams& p, cudaStream_t s) {
     cudaError_t e = conv_attr<CIN, CT>();
     if (e != cudaSuccess) return e;
-    const dim3 grid((p.W / TW) * (p.H / TH), p.B, p.cout_pad / CT);
+    static int per_sm = 0, sms = 0;
+    if (!per_sm) {
+        int dev = 0, smem = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return e;
+        if ((e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) !=
+            cudaSuccess)
+            return e;
+        per_sm = smem / (int)(ConvSmem<CIN, CT>::bytes + 1024);
+        if (per_sm < 1) per_sm = 1;
+        if (per_sm * CONV_THREADS > 2048) per_sm = 2048 / CONV_THREADS;
+    }
+    const int ntiles = p.B * (p.W / TW) * (p.H / TH), zt = p.cout_pad / CT;
+    // resident CTAs shared by the output-channel tiles
+    int gx = (sms * per_sm + zt - 1) / zt;
+    if (gx > ntiles) gx = ntiles;
+    if (gx < 1) gx = 1;
+    const dim3 grid(gx, 1, zt);
     return launch_pdl(k_conv<CIN, CT>, grid, dim3(CONV_THREADS), ConvSmem<CIN, CT>::bytes, s, p);
 }
 
@@ -625,7 +666,7 @@ int blocks(long long n, int t) { return (int)((n + t - 1) / t); }
 }  // namespace
 
 #define PIC_CONV_SHAPES(X) \
-    X(16, 32) X(16, 64) X(16, 8) X(32, 32) X(32, 64) X(32, 8) X(64, 32) X(64, 64) X(128, 32) X(128, 64)
+    X(16, 32) X(16, 64) X(16, 8) X(32, 32) X(32, 64) X(32, 8) X(64, 32) X(64, 64) X(128, 32)
 #define PIC_WGRAD_SHAPES(X) \
     X(16, 32) X(32, 32) X(32, 64) X(64, 64) X(64, 128) X(128, 128) X(128, 64) X(64, 32) X(32, 16)
 
@@ -640,10 +681,13 @@ cudaError_t init_kernels() {
     return e;
 }
 
-// CIN in {16, 32, 64, 128}; CT in {8, 32, 64} (cout_pad a multiple of CT)
+// CIN in {16, 32, 64, 128}; CT in {8, 32, 64} (cout_pad a multiple of CT).
+// CIN = 128 always runs with CT = 32: 64 channels' weights and two patches
+// would not fit in shared memory.
 cudaError_t launch_conv(const ConvParams& p, int cin, int ct, cudaStream_t s) {
     if (p.H % TH || p.W % TW || p.cout_pad % ct) return cudaErrorInvalidValue;
     if (conv_tc_supported(p, cin)) return launch_conv_tc(p, cin, s);
+    if (cin == 128 && ct == 64) ct = 32;
 #define PIC_CONV_CASE(CI, C) \
     if (cin == CI && ct == C) return conv_T<CI, C>(p, s);
     PIC_CONV_SHAPES(PIC_CONV_CASE)
