@@ -83,7 +83,7 @@ typedef struct {
     int nx, ny;       /* cells; multiples of tile, 8 <= n <= 32768 */
     double dx, dy, dt;/* dt must satisfy Eq. 1: dt < (1/dx^2 + 1/dy^2)^-1/2 */
     int tile;         /* T in {8, 16, 32}; 0 = 16 */
-    int threads;      /* threads per tile in the particle kernels: 64..1024, multiple
+    int threads;      /* threads per tile in the particle kernels: 64..512, multiple
                          of 32; 0 = 256 */
     int chunk;        /* particles per CTA in the particle kernels: a tile holding more
                          is split over several CTAs (16..1<<20); 0 = 4096 */

@@ -417,8 +417,8 @@ extern "C" {
 pic_status pic_set_tiling(pic_sim* sim, int tile, int threads) {
     if (!sim) return PIC_EINVAL;
     sim->err.clear();
-    if (threads != 0 && (threads < 64 || threads > 1024 || threads % 32))
-        return fail(sim, PIC_EINVAL, "threads %d not in 64..1024 or not a multiple of 32", threads);
+    if (threads != 0 && (threads < 64 || threads > 512 || threads % 32))
+        return fail(sim, PIC_EINVAL, "threads %d not in 64..512 or not a multiple of 32", threads);
     pic_status r = retile(sim, tile);
     if (r != PIC_OK) return r;
     if (threads > 0 && threads != sim->cfg.threads) {

@@ -458,7 +458,7 @@ pic_status pic_init(const pic_config* cfg, void* cuda_stream, pic_sim** out) {
     if (c.chunk == 0) c.chunk = 4096;
     if (c.chunk < 16 || c.chunk > (1 << 20)) return PIC_EINVAL;
     if (!(c.tile == 8 || c.tile == 16 || c.tile == 32)) return PIC_EINVAL;
-    if (c.threads < 64 || c.threads > 1024 || c.threads % 32) return PIC_EINVAL;
+    if (c.threads < 64 || c.threads > 512 || c.threads % 32) return PIC_EINVAL;
     if (c.nx < 8 || c.ny < 8 || c.nx > 32768 || c.ny > 32768) return PIC_EINVAL;
     if (c.nx % c.tile || c.ny % c.tile) return PIC_EINVAL;
     if (c.n_species < 1 || c.n_species > PIC_MAX_SPECIES) return PIC_EINVAL;
