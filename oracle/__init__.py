@@ -28,6 +28,14 @@ Parity status per function (what pins each one; the pins live in
 * Weibel growth (config with counter-streaming populations along z): parity
   only bounded, between 0.7x and 1x the cold-fluid rate (the thermal spread
   lowers the cold rate by an amount the thesis does not give).
+* ``window`` (module: moving window, injection, lasers; readings in its
+  docstring): the window position pinned against exact rational arithmetic;
+  shift, removal and injection together pinned by the exact invariance of a
+  cold plasma at rest (with a part-filled edge column); the open box's
+  dropped current by additivity; the plane pulse by the Yee scheme's own group
+  velocity and energy conservation (fixed box and moving window); the Gaussian
+  beam by its diffraction down to the waist at the focus; the polarisation by
+  the rotated pulse and B = x_hat x E.
 * ``denoiser`` (module): circular 3x3 convolution pinned by brute force and an
   FFT correlation; its input, weight and bias gradients by adjoint identities
   and brute force; pooling / upsampling adjoints; the whole network's gradient

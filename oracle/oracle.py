@@ -62,15 +62,15 @@ _D = C.c_double
 
 def _declare(L):
     for sfx, real in (("_f64", C.c_double), ("_f32", C.c_float)):
-        getattr(L, "orc_gather" + sfx).argtypes = [_I, _I, _P, _P, _I, _I, real, real, _P, _P]
+        getattr(L, "orc_gather" + sfx).argtypes = [_I, _I, _I, _P, _P, _I, _I, real, real, _P, _P]
         getattr(L, "orc_gather" + sfx).restype = None
         getattr(L, "orc_boris" + sfx).argtypes = [_P, _P, _P, real]
         getattr(L, "orc_boris" + sfx).restype = real
-        getattr(L, "orc_deposit_move" + sfx).argtypes = [_I, _I, _P, _I, _I, real, real, real, real, real, real, real]
+        getattr(L, "orc_deposit_move" + sfx).argtypes = [_I, _I, _I, _P, _I, _I, real, real, real, real, real, real, real]
         getattr(L, "orc_deposit_move" + sfx).restype = None
-        getattr(L, "orc_advance" + sfx).argtypes = [_I, _I, _D, _D, _D, _D, _D, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+        getattr(L, "orc_advance" + sfx).argtypes = [_I, _I, _I, _D, _D, _D, _D, _D, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
         getattr(L, "orc_advance" + sfx).restype = _I
-        getattr(L, "orc_yee" + sfx).argtypes = [_I, _I, _D, _D, _D, _P, _P, _P]
+        getattr(L, "orc_yee" + sfx).argtypes = [_I, _I, _I, _D, _D, _D, _P, _P, _P]
         getattr(L, "orc_yee" + sfx).restype = None
         getattr(L, "orc_rho" + sfx).argtypes = [_I, _I, _D, _I64, _P, _P, _P, _P, _P]
         getattr(L, "orc_rho" + sfx).restype = None
@@ -94,15 +94,16 @@ def _ptr(a: np.ndarray):
 
 # ---------------------------------------------------------------- primitives
 
-def gather(E, B, ix, iy, x, y):
-    """Fields at one particle (Fig. 3.1 staggering). E, B: (3, ny, nx)."""
+def gather(E, B, ix, iy, x, y, open_x=False):
+    """Fields at one particle (Fig. 3.1 staggering). E, B: (3, ny, nx); with
+    open_x the fields are zero outside the box along x."""
     E = np.ascontiguousarray(E)
     B = np.ascontiguousarray(B, dtype=E.dtype)
     _, ny, nx = E.shape
     real = E.dtype.type
     Ep = np.zeros(3, E.dtype)
     Bp = np.zeros(3, E.dtype)
-    getattr(lib(), "orc_gather" + _sfx(E.dtype))(nx, ny, _ptr(E), _ptr(B), int(ix), int(iy),
+    getattr(lib(), "orc_gather" + _sfx(E.dtype))(nx, ny, int(bool(open_x)), _ptr(E), _ptr(B), int(ix), int(iy),
                                                   real(x), real(y), _ptr(Ep), _ptr(Bp))
     return Ep, Bp
 
@@ -116,22 +117,30 @@ def boris(u, Ep, Bp, tem):
     return u, float(g)
 
 
-def deposit_move(J, ix, iy, x0, y0, x1, y1, qjx, qjy, qvz):
-    """Add the current of one straight move (cell frame of (ix, iy)) into J."""
+def deposit_move(J, ix, iy, x0, y0, x1, y1, qjx, qjy, qvz, open_x=False):
+    """Add the current of one straight move (cell frame of (ix, iy)) into J
+    (with open_x, current falling outside the box along x is dropped)."""
     _, ny, nx = J.shape
     r = J.dtype.type
     getattr(lib(), "orc_deposit_move" + _sfx(J.dtype))(
-        nx, ny, _ptr(J), int(ix), int(iy), r(x0), r(y0), r(x1), r(y1), r(qjx), r(qjy), r(qvz))
+        nx, ny, int(bool(open_x)), _ptr(J), int(ix), int(iy), r(x0), r(y0), r(x1), r(y1),
+        r(qjx), r(qjy), r(qvz))
 
 
-def advance(sp: "SpeciesState", E, B, J, dx, dy, dt):
-    """Particle loop of Listing 3.1 for one species; returns (status, sum(gamma-1))."""
+def advance(sp: "SpeciesState", E, B, J, dx, dy, dt, open_x=False):
+    """Particle loop of Listing 3.1 for one species; returns (status,
+    sum(gamma-1)).  With open_x, particles that left the box along x are
+    removed from ``sp`` afterwards."""
     _, ny, nx = E.shape
     ke = C.c_double(0.0)
+    gone = np.zeros(sp.n, np.uint8) if open_x else None
     st = getattr(lib(), "orc_advance" + _sfx(E.dtype))(
-        nx, ny, dx, dy, dt, sp.q_over_m, sp.qtilde, sp.n,
+        nx, ny, int(bool(open_x)), dx, dy, dt, sp.q_over_m, sp.qtilde, sp.n,
         _ptr(sp.ix), _ptr(sp.iy), _ptr(sp.x), _ptr(sp.y),
-        _ptr(sp.ux), _ptr(sp.uy), _ptr(sp.uz), _ptr(E), _ptr(B), _ptr(J), C.byref(ke))
+        _ptr(sp.ux), _ptr(sp.uy), _ptr(sp.uz), _ptr(E), _ptr(B), _ptr(J),
+        None if gone is None else _ptr(gone), C.byref(ke))
+    if open_x and gone.any():
+        sp.keep(gone == 0)
     return st, ke.value
 
 
@@ -148,9 +157,10 @@ def binomial_filter(J, passes=1):
     return J
 
 
-def yee(E, B, J, dx, dy, dt):
+def yee(E, B, J, dx, dy, dt, open_x=False):
     _, ny, nx = E.shape
-    getattr(lib(), "orc_yee" + _sfx(E.dtype))(nx, ny, dx, dy, dt, _ptr(E), _ptr(B), _ptr(J))
+    getattr(lib(), "orc_yee" + _sfx(E.dtype))(nx, ny, int(bool(open_x)), dx, dy, dt,
+                                              _ptr(E), _ptr(B), _ptr(J))
 
 
 def rho_nodes(nx, ny, species, dtype=np.float64, background=0.0):
@@ -231,15 +241,31 @@ class SpeciesState:
         if self.pid is not None:
             self.pid = np.ascontiguousarray(self.pid[perm])
 
+    def keep(self, mask):
+        """Drop the particles where mask is False."""
+        self.permute(np.nonzero(mask)[0])
+
+    def append(self, ix, iy, x, y, ux, uy, uz, pid=None):
+        for name, v in (("ix", ix), ("iy", iy), ("x", x), ("y", y), ("ux", ux), ("uy", uy),
+                        ("uz", uz)):
+            a = getattr(self, name)
+            setattr(self, name, np.ascontiguousarray(np.concatenate([a, np.asarray(v, a.dtype)])))
+        if self.pid is not None:
+            extra = np.full(len(ix), -1, self.pid.dtype) if pid is None else pid
+            self.pid = np.concatenate([self.pid, extra])
+
 
 @dataclass
 class OracleSim:
-    """Plain serial PIC following Listing 3.1 (no filter, no moving window).
+    """Plain serial PIC following Listing 3.1.
 
     E, B, J are (3, ny, nx) arrays at the Yee locations of Fig. 3.1.  Each step:
-    zero J; for each species push every particle and deposit its current; Yee
-    B/2, E, B/2; then re-sort each species by tile (stable counting sort, §4.3).
-    ``background`` is the fixed neutralising ion density added to rho.
+    zero J; for each species push every particle and deposit its current; the
+    optional binomial filter; Yee B/2, E, B/2; with the moving window (``window``
+    set: the box is open along x) the window shift of ``oracle.window``; then
+    re-sort each species by tile (stable counting sort, §4.3).  ``background``
+    is the fixed neutralising ion density added to rho.  ``window`` is None or
+    a list with one ``oracle.window.Inject`` (or None) per species.
     """
     nx: int
     ny: int
@@ -254,6 +280,8 @@ class OracleSim:
     B: np.ndarray = None
     J: np.ndarray = None
     filter_passes: int = 0          # binomial current filter (0: off)
+    window: list | None = None      # moving window: injection per species
+    moves: int = 0                  # cells the window has moved
     step_count: int = 0
     status: int = 0
     ke_history: list = field(default_factory=list)
@@ -273,20 +301,25 @@ class OracleSim:
         return gsum * (sp.qtilde / sp.q_over_m) * self.dx * self.dy
 
     def step(self, nsteps: int = 1, sort: bool = True):
+        open_x = self.window is not None
         for _ in range(nsteps):
             self.J[...] = 0
             ke = 0.0
             for sp in self.species:
-                st, g = advance(sp, self.E, self.B, self.J, self.dx, self.dy, self.dt)
+                st, g = advance(sp, self.E, self.B, self.J, self.dx, self.dy, self.dt, open_x)
                 self.status |= st
                 ke += self.kinetic_energy_of(sp, g)
             self.ke_history.append(ke)
             if self.filter_passes:
                 self.J[...] = binomial_filter(self.J, self.filter_passes)
-            yee(self.E, self.B, self.J, self.dx, self.dy, self.dt)
+            yee(self.E, self.B, self.J, self.dx, self.dy, self.dt, open_x)
+            self.step_count += 1
+            if open_x:
+                from . import window as W
+                if W.window_moves(self.step_count, self.dt, self.dx) > self.moves:
+                    W.shift_window(self)
             if sort:
                 self.sort()
-            self.step_count += 1
 
     def sort(self):
         for sp in self.species:

@@ -23,7 +23,10 @@
  *   Bx (i, j+1/2)   By (i+1/2, j)   Bz (i+1/2, j+1/2)
  *   J is co-located with E, rho sits on nodes.  A field array holds its three
  *   components one after the other, each ny rows of nx values (row = j), with
- *   every index taken modulo nx, ny (periodic box).
+ *   every index taken modulo nx, ny (periodic box).  With open_x != 0 (the box
+ *   of the moving window, the last steps of Listing 3.1) the box is open along
+ *   x instead: E and B are zero outside 0 <= i < nx, current deposited outside
+ *   is dropped and particles whose cell leaves 0 <= ix < nx are flagged gone.
  */
 #include <math.h>
 #include <stdint.h>
@@ -63,21 +66,27 @@ static int wrap(int i, int n) {
  * columns (i0, i0+1) and rows (j0, j0+1) with weights (a0, a1) along x and
  * (b0, b1) along y (§3.1: "interpolate linearly ... from the cell where the
  * particle is located and all its adjacent cells"). */
-static REAL interp(const REAL *F, int nx, int ny, int i0, int j0, REAL a0,
-                   REAL a1, REAL b0, REAL b1) {
-    int i1 = wrap(i0 + 1, nx), j1 = wrap(j0 + 1, ny);
-    i0 = wrap(i0, nx);
-    j0 = wrap(j0, ny);
-    return b0 * (a0 * F[(size_t)j0 * nx + i0] + a1 * F[(size_t)j0 * nx + i1]) +
-           b1 * (a0 * F[(size_t)j1 * nx + i0] + a1 * F[(size_t)j1 * nx + i1]);
+/* value of one component at column i, row j: periodic, or zero outside the
+ * box along x when open_x */
+static REAL at(const REAL *F, int nx, int ny, int open_x, int i, int j) {
+    if (open_x && (i < 0 || i >= nx)) return R(0);
+    return F[(size_t)wrap(j, ny) * nx + wrap(i, nx)];
+}
+
+static REAL interp(const REAL *F, int nx, int ny, int open_x, int i0, int j0,
+                   REAL a0, REAL a1, REAL b0, REAL b1) {
+    return b0 * (a0 * at(F, nx, ny, open_x, i0, j0) +
+                 a1 * at(F, nx, ny, open_x, i0 + 1, j0)) +
+           b1 * (a0 * at(F, nx, ny, open_x, i0, j0 + 1) +
+                 a1 * at(F, nx, ny, open_x, i0 + 1, j0 + 1));
 }
 
 /* Field at a particle (§3.1, Fig. 3.1).  A component sampled on nodes along
  * an axis takes the weights (1-x, x) on cells (ix, ix+1); a component sampled
  * half a cell up takes xh = x + 1/2, columns ix + floor(xh) - 1 and +1, with
  * weights (1-w, w), w = xh - floor(xh). */
-void FN(orc_gather)(int nx, int ny, const REAL *E, const REAL *B, int ix,
-                    int iy, REAL x, REAL y, REAL *Ep, REAL *Bp) {
+void FN(orc_gather)(int nx, int ny, int open_x, const REAL *E, const REAL *B,
+                    int ix, int iy, REAL x, REAL y, REAL *Ep, REAL *Bp) {
     size_t nc = (size_t)nx * ny;
     REAL wx1 = x, wx0 = R(1) - x;
     REAL wy1 = y, wy0 = R(1) - y;
@@ -87,12 +96,12 @@ void FN(orc_gather)(int nx, int ny, const REAL *E, const REAL *B, int ix,
     REAL hy1 = yh - fhy, hy0 = R(1) - hy1;
     int ihx = ix + (int)fhx - 1, ihy = iy + (int)fhy - 1;
 
-    Ep[0] = interp(E + 0 * nc, nx, ny, ihx, iy, hx0, hx1, wy0, wy1);
-    Ep[1] = interp(E + 1 * nc, nx, ny, ix, ihy, wx0, wx1, hy0, hy1);
-    Ep[2] = interp(E + 2 * nc, nx, ny, ix, iy, wx0, wx1, wy0, wy1);
-    Bp[0] = interp(B + 0 * nc, nx, ny, ix, ihy, wx0, wx1, hy0, hy1);
-    Bp[1] = interp(B + 1 * nc, nx, ny, ihx, iy, hx0, hx1, wy0, wy1);
-    Bp[2] = interp(B + 2 * nc, nx, ny, ihx, ihy, hx0, hx1, hy0, hy1);
+    Ep[0] = interp(E + 0 * nc, nx, ny, open_x, ihx, iy, hx0, hx1, wy0, wy1);
+    Ep[1] = interp(E + 1 * nc, nx, ny, open_x, ix, ihy, wx0, wx1, hy0, hy1);
+    Ep[2] = interp(E + 2 * nc, nx, ny, open_x, ix, iy, wx0, wx1, wy0, wy1);
+    Bp[0] = interp(B + 0 * nc, nx, ny, open_x, ix, ihy, wx0, wx1, hy0, hy1);
+    Bp[1] = interp(B + 1 * nc, nx, ny, open_x, ihx, iy, hx0, hx1, wy0, wy1);
+    Bp[2] = interp(B + 2 * nc, nx, ny, open_x, ihx, ihy, hx0, hx1, hy0, hy1);
 }
 
 /* Boris push, Eqs. 6-10, with tem = (q/m) dt / 2.  gamma_t of Eq. 10 is taken
@@ -126,28 +135,32 @@ REAL FN(orc_boris)(REAL *u, const REAL *Ep, const REAL *Bp, REAL tem) {
  * ym the mid-point of the sub-move).  Jz (not in the thesis, which works in the
  * plane) is q v_z times the time average of the area weight of each corner
  * node along the sub-move. */
-static void deposit_piece(REAL *J, int nx, int ny, int ci, int cj, REAL xa,
-                          REAL ya, REAL xb, REAL yb, REAL f, REAL qjx,
-                          REAL qjy, REAL qvz) {
+/* add v to component C at column i, row j: periodic, or dropped outside the
+ * box along x when open_x */
+static void add_at(REAL *C, int nx, int ny, int open_x, int i, int j, REAL v) {
+    if (open_x && (i < 0 || i >= nx)) return;
+    C[(size_t)wrap(j, ny) * nx + wrap(i, nx)] += v;
+}
+
+static void deposit_piece(REAL *J, int nx, int ny, int open_x, int ci, int cj,
+                          REAL xa, REAL ya, REAL xb, REAL yb, REAL f,
+                          REAL qjx, REAL qjy, REAL qvz) {
     size_t nc = (size_t)nx * ny;
     REAL *Jx = J, *Jy = J + nc, *Jz = J + 2 * nc;
     REAL ddx = xb - xa, ddy = yb - ya;
     REAL xm = R(0.5) * (xa + xb), ym = R(0.5) * (ya + yb);
-    int i0 = wrap(ci, nx), i1 = wrap(ci + 1, nx);
-    int j0 = wrap(cj, ny), j1 = wrap(cj + 1, ny);
-    Jx[(size_t)j0 * nx + i0] += qjx * ddx * (R(1) - ym);
-    Jx[(size_t)j1 * nx + i0] += qjx * ddx * ym;
-    Jy[(size_t)j0 * nx + i0] += qjy * ddy * (R(1) - xm);
-    Jy[(size_t)j0 * nx + i1] += qjy * ddy * xm;
+    add_at(Jx, nx, ny, open_x, ci, cj, qjx * ddx * (R(1) - ym));
+    add_at(Jx, nx, ny, open_x, ci, cj + 1, qjx * ddx * ym);
+    add_at(Jy, nx, ny, open_x, ci, cj, qjy * ddy * (R(1) - xm));
+    add_at(Jy, nx, ny, open_x, ci + 1, cj, qjy * ddy * xm);
 
     REAL s0x[2] = {R(1) - xa, xa}, s1x[2] = {R(1) - xb, xb};
     REAL s0y[2] = {R(1) - ya, ya}, s1y[2] = {R(1) - yb, yb};
-    int ii[2] = {i0, i1}, jj[2] = {j0, j1};
     for (int b = 0; b < 2; ++b)
         for (int a = 0; a < 2; ++a) {
             REAL w = (s0x[a] * s0y[b] + s1x[a] * s1y[b]) / R(3) +
                      (s0x[a] * s1y[b] + s1x[a] * s0y[b]) / R(6);
-            Jz[(size_t)jj[b] * nx + ii[a]] += qvz * f * w;
+            add_at(Jz, nx, ny, open_x, ci + a, cj + b, qvz * f * w);
         }
 }
 
@@ -156,9 +169,9 @@ static void deposit_piece(REAL *J, int nx, int ny, int ci, int cj, REAL xa,
  * move is cut where it crosses x = 0 or 1 and y = 0 or 1 into at most three
  * sub-moves that each stay inside one cell (the 4-, 7- and 10-boundary cases
  * of Figs. 3.4-3.5). */
-void FN(orc_deposit_move)(int nx, int ny, REAL *J, int ix, int iy, REAL x0,
-                          REAL y0, REAL x1, REAL y1, REAL qjx, REAL qjy,
-                          REAL qvz) {
+void FN(orc_deposit_move)(int nx, int ny, int open_x, REAL *J, int ix, int iy,
+                          REAL x0, REAL y0, REAL x1, REAL y1, REAL qjx,
+                          REAL qjy, REAL qvz) {
     int di = (x1 >= R(1)) - (x1 < R(0));
     int dj = (y1 >= R(1)) - (y1 < R(0));
     REAL xbd = di > 0 ? R(1) : R(0), ybd = dj > 0 ? R(1) : R(0);
@@ -188,7 +201,7 @@ void FN(orc_deposit_move)(int nx, int ny, REAL *J, int ix, int iy, REAL x0,
         REAL ya = (ta == ty) ? ybd : y0 + ta * (y1 - y0);
         REAL xb = (tb == tx) ? xbd : (tb == R(1) ? x1 : x0 + tb * (x1 - x0));
         REAL yb = (tb == ty) ? ybd : (tb == R(1) ? y1 : y0 + tb * (y1 - y0));
-        deposit_piece(J, nx, ny, ix + cx, iy + cy, xa - (REAL)cx,
+        deposit_piece(J, nx, ny, open_x, ix + cx, iy + cy, xa - (REAL)cx,
                       ya - (REAL)cy, xb - (REAL)cx, yb - (REAL)cy, tb - ta,
                       qjx, qjy, qvz);
     }
@@ -201,12 +214,15 @@ void FN(orc_deposit_move)(int nx, int ny, REAL *J, int ix, int iy, REAL x0,
  * update_gc_add).  ke_sum receives sum(gamma(u-) - 1) in double.  Returns
  * ORC_EPARTICLE if a particle tried to move one cell or more in a step (the
  * Courant condition of Eq. 1 rules that out); such a particle is left where it
- * was, with its new momentum, and deposits nothing. */
-int FN(orc_advance)(int nx, int ny, double dx, double dy, double dt,
+ * was, with its new momentum, and deposits nothing.  With open_x, gone[p] is
+ * set to 1 for a particle whose new cell lies outside 0 <= ix < nx (it has
+ * left the box; the caller removes it), else 0; its cell index is then left
+ * unwrapped. */
+int FN(orc_advance)(int nx, int ny, int open_x, double dx, double dy, double dt,
                     double q_over_m, double qtilde, int64_t n, int32_t *ix,
                     int32_t *iy, REAL *x, REAL *y, REAL *ux, REAL *uy,
                     REAL *uz, const REAL *E, const REAL *B, REAL *J,
-                    double *ke_sum) {
+                    uint8_t *gone, double *ke_sum) {
     REAL tem = (REAL)(0.5 * q_over_m * dt);
     REAL cx = (REAL)(dt / dx), cy = (REAL)(dt / dy);
     REAL qjx = (REAL)(qtilde * dx / dt), qjy = (REAL)(qtilde * dy / dt);
@@ -215,7 +231,8 @@ int FN(orc_advance)(int nx, int ny, double dx, double dy, double dt,
     double ke = 0.0;
     for (int64_t p = 0; p < n; ++p) {
         REAL Ep[3], Bp[3], u[3] = {ux[p], uy[p], uz[p]};
-        FN(orc_gather)(nx, ny, E, B, ix[p], iy[p], x[p], y[p], Ep, Bp);
+        FN(orc_gather)(nx, ny, open_x, E, B, ix[p], iy[p], x[p], y[p], Ep, Bp);
+        if (gone) gone[p] = 0;
         REAL gm = FN(orc_boris)(u, Ep, Bp, tem);
         ke += (double)gm - 1.0;
         ux[p] = u[0];
@@ -248,11 +265,16 @@ int FN(orc_advance)(int nx, int ny, double dx, double dy, double dt,
             dj = 0;
             y1 = R(0);
         }
-        FN(orc_deposit_move)(nx, ny, J, ix[p], iy[p], x0, y0, x1, y1, qjx,
-                             qjy, qjz * vz);
+        FN(orc_deposit_move)(nx, ny, open_x, J, ix[p], iy[p], x0, y0, x1, y1,
+                             qjx, qjy, qjz * vz);
         x[p] = xn;
         y[p] = yn;
-        ix[p] = wrap(ix[p] + di, nx);
+        if (open_x) {
+            ix[p] = ix[p] + di;
+            if (ix[p] < 0 || ix[p] >= nx) gone[p] = 1;
+        } else {
+            ix[p] = wrap(ix[p] + di, nx);
+        }
         iy[p] = wrap(iy[p] + dj, ny);
     }
     *ke_sum = ke;
@@ -260,8 +282,10 @@ int FN(orc_advance)(int nx, int ny, double dx, double dy, double dt,
 }
 
 /* Yee advance of Listing 3.1 (§3.1, Eqs. 19-20 on the staggered grid of
- * Fig. 3.1): B by dt/2, E by dt with J, B by dt/2.  Periodic. */
-static void yee_b(int nx, int ny, REAL *E, REAL *B, REAL hdt_dx,
+ * Fig. 3.1): B by dt/2, E by dt with J, B by dt/2.  Periodic, or with zero
+ * fields outside the box along x when open_x.  The x-neighbours are read
+ * through at() with the row index unwrapped; the values read are the same. */
+static void yee_b(int nx, int ny, int open_x, REAL *E, REAL *B, REAL hdt_dx,
                   REAL hdt_dy) {
     size_t nc = (size_t)nx * ny;
     REAL *Ex = E, *Ey = E + nc, *Ez = E + 2 * nc;
@@ -269,18 +293,19 @@ static void yee_b(int nx, int ny, REAL *E, REAL *B, REAL hdt_dx,
     for (int j = 0; j < ny; ++j) {
         int jp = wrap(j + 1, ny);
         for (int i = 0; i < nx; ++i) {
-            int ip = wrap(i + 1, nx);
             size_t c = (size_t)j * nx + i;
-            size_t cxp = (size_t)j * nx + ip, cyp = (size_t)jp * nx + i;
+            size_t cyp = (size_t)jp * nx + i;
+            REAL ez_xp = at(Ez, nx, ny, open_x, i + 1, j);
+            REAL ey_xp = at(Ey, nx, ny, open_x, i + 1, j);
             Bx[c] -= hdt_dy * (Ez[cyp] - Ez[c]);
-            By[c] += hdt_dx * (Ez[cxp] - Ez[c]);
-            Bz[c] -= hdt_dx * (Ey[cxp] - Ey[c]) - hdt_dy * (Ex[cyp] - Ex[c]);
+            By[c] += hdt_dx * (ez_xp - Ez[c]);
+            Bz[c] -= hdt_dx * (ey_xp - Ey[c]) - hdt_dy * (Ex[cyp] - Ex[c]);
         }
     }
 }
 
-static void yee_e(int nx, int ny, REAL *E, const REAL *B, const REAL *J,
-                  REAL dt, REAL dt_dx, REAL dt_dy) {
+static void yee_e(int nx, int ny, int open_x, REAL *E, const REAL *B,
+                  const REAL *J, REAL dt, REAL dt_dx, REAL dt_dy) {
     size_t nc = (size_t)nx * ny;
     REAL *Ex = E, *Ey = E + nc, *Ez = E + 2 * nc;
     const REAL *Bx = B, *By = B + nc, *Bz = B + 2 * nc;
@@ -288,23 +313,24 @@ static void yee_e(int nx, int ny, REAL *E, const REAL *B, const REAL *J,
     for (int j = 0; j < ny; ++j) {
         int jm = wrap(j - 1, ny);
         for (int i = 0; i < nx; ++i) {
-            int im = wrap(i - 1, nx);
             size_t c = (size_t)j * nx + i;
-            size_t cxm = (size_t)j * nx + im, cym = (size_t)jm * nx + i;
+            size_t cym = (size_t)jm * nx + i;
+            REAL bz_xm = at(Bz, nx, ny, open_x, i - 1, j);
+            REAL by_xm = at(By, nx, ny, open_x, i - 1, j);
             Ex[c] += dt_dy * (Bz[c] - Bz[cym]) - dt * Jx[c];
-            Ey[c] += -dt_dx * (Bz[c] - Bz[cxm]) - dt * Jy[c];
-            Ez[c] += dt_dx * (By[c] - By[cxm]) - dt_dy * (Bx[c] - Bx[cym]) -
+            Ey[c] += -dt_dx * (Bz[c] - bz_xm) - dt * Jy[c];
+            Ez[c] += dt_dx * (By[c] - by_xm) - dt_dy * (Bx[c] - Bx[cym]) -
                      dt * Jz[c];
         }
     }
 }
 
-void FN(orc_yee)(int nx, int ny, double dx, double dy, double dt, REAL *E,
-                 REAL *B, const REAL *J) {
+void FN(orc_yee)(int nx, int ny, int open_x, double dx, double dy, double dt,
+                 REAL *E, REAL *B, const REAL *J) {
     REAL hdt_dx = (REAL)(0.5 * dt / dx), hdt_dy = (REAL)(0.5 * dt / dy);
-    yee_b(nx, ny, E, B, hdt_dx, hdt_dy);
-    yee_e(nx, ny, E, B, J, (REAL)dt, (REAL)(dt / dx), (REAL)(dt / dy));
-    yee_b(nx, ny, E, B, hdt_dx, hdt_dy);
+    yee_b(nx, ny, open_x, E, B, hdt_dx, hdt_dy);
+    yee_e(nx, ny, open_x, E, B, J, (REAL)dt, (REAL)(dt / dx), (REAL)(dt / dy));
+    yee_b(nx, ny, open_x, E, B, hdt_dx, hdt_dy);
 }
 
 /* Charge density on the nodes by area weighting (Fig. 3.3): a particle gives
