@@ -99,13 +99,16 @@ typedef struct {
     double w_e, w_b;       /* field energies 1/2 sum(E^2) dx dy, 1/2 sum(B^2) dx dy at n (FP64 sums) */
     double w_k;            /* kinetic energy sum (gamma(u-) - 1) m n_s/ppc dx dy of the last
                               particle push, i.e. at time level n-1 (NaN before the first step) */
-    double gauss_max;      /* max over nodes of |div E - rho| at n (FP64), rho including the background */
+    double gauss_max;      /* max over nodes of |div E - rho| at n (FP64), rho including the background
+                              (NaN with the moving window) */
     double continuity_max; /* max over nodes of |(rho^n - rho^(n-1))/dt + div J^(n-1/2)| if the previous
-                              pic_diagnostics call was at n-1 and no state was loaded since, else NaN */
+                              pic_diagnostics call was at n-1 and no state was loaded since, else NaN
+                              (always NaN with the moving window) */
     double charge_total;   /* sum over nodes of rho dx dy (FP64) */
     int64_t n_particles[PIC_MAX_SPECIES];
     int64_t leavers;       /* particles that changed tile in the last step (all species) */
     uint32_t status_bits;  /* sticky device status: 1 = particle, 2 = timeout, 4 = re-sort */
+    int64_t window_moves;  /* cells the moving window has moved (0 without it) */
 } pic_diag;
 
 /* Create a simulation.  Validates the configuration (Eq. 1 for dt, tile
@@ -130,8 +133,9 @@ pic_status pic_load_particles(pic_sim* sim, int species, int64_t n, const int32_
  * current time level.  Either pointer may be NULL to leave that field as is. */
 pic_status pic_set_fields(pic_sim* sim, const float* E, const float* B, int on_device);
 
-/* Advance nsteps >= 0 time steps (Listing 3.1 without filter or moving
- * window).  Asynchronous: enqueues the work on the stream and returns. */
+/* Advance nsteps >= 0 time steps (Listing 3.1, with the current filter and
+ * the moving window when they are set).  Asynchronous: enqueues the work on
+ * the stream and returns. */
 pic_status pic_step(pic_sim* sim, int nsteps);
 
 /* The current filter of Listing 3.1 (applied after the guard-cell reduction
@@ -141,6 +145,66 @@ pic_status pic_step(pic_sim* sim, int nsteps);
  * (kx, ky) by cos^2(kx dx/2) cos^2(ky dy/2).  Replaces an installed denoiser
  * (and pic_set_denoiser replaces it).  Synchronises. */
 pic_status pic_set_binomial_filter(pic_sim* sim, int passes);
+
+/* ---- Moving window and lasers (the steps around the loop of Listing 3.1) ----
+ * With the moving window the simulation box follows the plasma at the speed of
+ * light (§3.2): after k steps it has moved M(k) = floor(k dt/dx + 1e-9) cells,
+ * and a step whose M grows ends, after the field update, with the three
+ * window steps of Listing 3.1: E and B shift one cell left (the new last
+ * column is zero), the particles shift one cell left (those leaving the box
+ * are removed), and new particles are inserted in the last column.  The box
+ * is then open along x: E and B are zero outside 0 <= i < nx, current
+ * deposited outside is dropped, and a particle leaving through either x edge
+ * is removed (y stays periodic).  Particle counts change: pic_get_particles
+ * and pic_diagnostics report the current ones.  Injection per species: a
+ * cold k x k lattice per cell at offsets ((a+1/2)/k, (b+1/2)/k) with momentum
+ * (ux, uy, uz), keeping the particles at physical x = (g + (a+1/2)/k) dx >=
+ * x_start, g the column's global cell index (a step density profile); k = 0
+ * injects nothing.  Each injected particle carries the species' charge
+ * density qtilde, so the injected density is k*k*|qtilde| (the species'
+ * density when k*k = ppc); injected particles carry id -1.  The filters of
+ * the current-filter slot and batches are periodic and refuse a moving window. */
+typedef struct {
+    int k;            /* injected lattice k x k per cell (0..64), 0 = none */
+    double x_start;   /* plasma at physical x >= x_start */
+    float ux, uy, uz; /* momentum of the injected (cold) particles */
+    int64_t capacity; /* particle slots to reserve for the species (>= any count reached;
+                         the loaded count if larger); exceeding it stops the re-sort with
+                         PIC_EOVERFLOW */
+} pic_inject;
+
+/* Turn the moving window on.  `inject` holds n_species entries (NULL: no
+ * injection).  Must be called before any particles are loaded.  Zeroes the x
+ * guard cells of E and B.  PIC_EINVAL if particles are loaded, a filter is
+ * installed, the simulation is in a batch or a parameter is out of range. */
+pic_status pic_set_moving_window(pic_sim* sim, const pic_inject* inject);
+
+#define PIC_LASER_PLANE 0
+#define PIC_LASER_GAUSSIAN 1
+
+/* A laser pulse moving towards +x (§3.2, lasers of the input file).  Field
+ * envelope sin^2(pi xi / (2 fwhm)) for 0 <= xi = start - x <= 2 fwhm (full
+ * width at half maximum fwhm), carrier cos(omega0 (x - start)), peak field
+ * a0 omega0; E at angle `polarization` from y towards z (Ey = cos f, Ez = sin
+ * f) and B = x_hat x E (By = -sin f, Bz = cos f), each at its Yee location.
+ * Gaussian: the paraxial beam of two dimensions with waist W0 at x = focus on
+ * y = axis: amplitude sqrt(W0/W(z)) exp(-r^2/W(z)^2), W(z) = W0 sqrt(1 +
+ * (z/zR)^2), zR = omega0 W0^2/2, extra phase omega0 r^2 z/(2(z^2 + zR^2)) -
+ * atan(z/zR)/2, z = x - focus, r = y - axis.  x is physical (the window's
+ * position included). */
+typedef struct {
+    int type;            /* PIC_LASER_PLANE or PIC_LASER_GAUSSIAN */
+    double start;        /* x of the pulse front */
+    double fwhm;         /* > 0 */
+    double a0;           /* normalised vector potential */
+    double omega0;       /* carrier frequency (= wavenumber, c = 1), > 0 */
+    double polarization; /* radians */
+    double W0, focus, axis; /* Gaussian only; W0 > 0 */
+} pic_laser;
+
+/* Add a laser pulse to the current E and B (computed in FP64 on the device,
+ * added in FP32).  Synchronises. */
+pic_status pic_add_laser(pic_sim* sim, const pic_laser* laser);
 
 /* Copy a grid quantity into the caller's buffer: which = 0 E, 1 B (3*nx*ny
  * values each, at time level n), 2 J (the current deposited by the last step,
@@ -157,7 +221,8 @@ pic_status pic_get_particles(pic_sim* sim, int species, int32_t* ix, int32_t* iy
                              float* y, float* ux, float* uy, float* uz, int32_t* id,
                              int64_t* tile_offset, int on_device);
 
-/* Number of particles of a species (host value, no synchronisation). */
+/* Number of particles of a species (host value, no synchronisation; with the
+ * moving window the count as of the last synchronising call). */
 int64_t pic_num_particles(const pic_sim* sim, int species);
 
 /* Number of tiles (nx/T)*(ny/T). */
@@ -174,7 +239,8 @@ pic_status pic_diagnostics(pic_sim* sim, pic_diag* out);
 pic_status pic_get_history(pic_sim* sim, int64_t first, int64_t count, double* w_e,
                            double* w_b, double* w_k);
 
-/* Wait for the stream; return the sticky device status as a pic_status. */
+/* Wait for the stream; return the sticky device status as a pic_status (with
+ * the moving window also refreshes the particle counts). */
 pic_status pic_sync(pic_sim* sim);
 
 /* Clear the sticky device status bits. */

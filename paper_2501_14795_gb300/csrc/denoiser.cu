@@ -555,6 +555,8 @@ pic_status pic_set_denoiser(pic_sim* sim, pic_denoiser* d) {
     if (d && (d->H != sim->cfg.ny || d->W != sim->cfg.nx))
         return fail(sim, PIC_EINVAL, "denoiser grid %dx%d differs from the simulation's %dx%d",
                     d->W, d->H, sim->cfg.nx, sim->cfg.ny);
+    if (d && sim->window)
+        return fail(sim, PIC_EINVAL, "the denoiser pads periodically: not with the moving window");
     PIC_CK(sim, cudaStreamSynchronize(sim->stream));
     sim->jfilter = d ? filter_hook : nullptr;
     sim->jfilter_ctx = d;

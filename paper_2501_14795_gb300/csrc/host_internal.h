@@ -49,6 +49,7 @@ struct pic_sim {
     int (*jfilter)(void* ctx, pic_sim* sim, cudaStream_t s, int b) = nullptr;
     void* jfilter_ctx = nullptr;
     int binomial_passes = 0;  // the binomial filter's passes when it is the installed filter
+    int window = 0;           // moving window on (box open along x)
 };
 
 namespace pic {
@@ -69,6 +70,9 @@ void batch_forget(pic_batch* batch, pic_sim* sim);
 // re-sorted into the new tiles (device to device), the tile bookkeeping and the
 // TMA descriptors are rebuilt and the next step's J buffer is cleared.
 pic_status retile(pic_sim* sim, int tile);
+// Moving window: copy the device particle counts into the host mirrors
+// (synchronises); no-op for a fixed box.
+pic_status refresh_counts(pic_sim* sim);
 
 }  // namespace host
 }  // namespace pic

@@ -21,7 +21,11 @@ __device__ __forceinline__ long long gidx(const Geom& g, int i, int j) {
 // n+1 is written with its periodic images (update_gc_copy), the field
 // energies of level n+1 are summed in FP64, and the shared ring of the next
 // step's J buffer (cells a neighbouring particle tile's halo reaches) is
-// zeroed.
+// zeroed.  With the moving window (open box along x) the fields outside
+// 0 <= i < nx stay zero through the three sub-steps, the x guards are written
+// as zeros, and on a step that shifts the window every value is written one
+// column to the left (the last column becoming zero): the shift of E and B at
+// the end of Listing 3.1 costs no extra pass.
 constexpr int YX = 32, YY = 16, YTHREADS = 256;
 constexpr int EW = YX + 3, EH = YY + 3;
 constexpr int BW = YX + 2, BH = YY + 2;
@@ -68,9 +72,14 @@ __device__ __forceinline__ void yee_tile(const YeeParams& prm, int bx, int by) {
     __syncthreads();
 
     const float hx = g.hdt_dx, hy = g.hdt_dy;
+    const bool open = g.open_x != 0;
     // B half step on [-1, YX+1) x [-1, YY+1): local (q, r) <-> cell (i0-1+q, j0-1+r)
     for (int k = tid; k < BW * BH; k += YTHREADS) {
         const int r = k / BW, q = k - r * BW;
+        if (open && (i0 - 1 + q < 0 || i0 - 1 + q >= g.nx)) {  // outside the open box
+            sB[0][r][q] = sB[1][r][q] = sB[2][r][q] = 0.f;
+            continue;
+        }
         sB[0][r][q] -= hy * (sE[2][r + 1][q] - sE[2][r][q]);
         sB[1][r][q] += hx * (sE[2][r][q + 1] - sE[2][r][q]);
         sB[2][r][q] -= hx * (sE[1][r][q + 1] - sE[1][r][q]) - hy * (sE[0][r + 1][q] - sE[0][r][q]);
@@ -81,6 +90,10 @@ __device__ __forceinline__ void yee_tile(const YeeParams& prm, int bx, int by) {
     for (int k = tid; k < JWY * JHY; k += YTHREADS) {
         const int r = k / JWY, q = k - r * JWY;
         const int e = q + 1, f = r + 1;
+        if (open && i0 + q >= g.nx) {
+            sE[0][f][e] = sE[1][f][e] = sE[2][f][e] = 0.f;
+            continue;
+        }
         sE[0][f][e] += dty * (sB[2][f][e] - sB[2][f - 1][e]) - dt * sJ[0][r][q];
         sE[1][f][e] += -dtx * (sB[2][f][e] - sB[2][f][e - 1]) - dt * sJ[1][r][q];
         sE[2][f][e] += dtx * (sB[1][f][e] - sB[1][f][e - 1]) -
@@ -92,6 +105,7 @@ __device__ __forceinline__ void yee_tile(const YeeParams& prm, int bx, int by) {
     float* Eout = prm.Fout;
     float* Bout = prm.Fout + 3 * cs;
     const int T = g.T;
+    const int wshift = open ? *((volatile int*)&prm.st->win_shift) : 0;
     for (int k = tid; k < YX * YY; k += YTHREADS) {
         const int r = k / YX, q = k - r * YX;
         const int i = i0 + q, j = j0 + r;
@@ -105,23 +119,48 @@ __device__ __forceinline__ void yee_tile(const YeeParams& prm, int bx, int by) {
         we += ex * ex + ey * ey + ez * ez;
         wb += bx * bx + by * by + bz * bz;
         // images: i' in {i, i+nx if i<2, i-nx if i==nx-1}, same for j
-        int ii[2], jj[2], ni = 1, nj = 1;
-        ii[0] = i;
+        int jj[2], nj = 1;
         jj[0] = j;
-        if (i < 2) ii[ni++] = i + g.nx;
-        else if (i == g.nx - 1) ii[ni++] = -1;
         if (j < 2) jj[nj++] = j + g.ny;
         else if (j == g.ny - 1) jj[nj++] = -1;
-        for (int a = 0; a < ni; ++a)
+        if (!open) {
+            int ii[2], ni = 1;
+            ii[0] = i;
+            if (i < 2) ii[ni++] = i + g.nx;
+            else if (i == g.nx - 1) ii[ni++] = -1;
+            for (int a = 0; a < ni; ++a)
+                for (int b = 0; b < nj; ++b) {
+                    const long long o = gidx(g, ii[a], jj[b]);
+                    Eout[o] = ex;
+                    Eout[cs + o] = ey;
+                    Eout[2 * cs + o] = ez;
+                    Bout[o] = bx;
+                    Bout[cs + o] = by;
+                    Bout[2 * cs + o] = bz;
+                }
+        } else {
+            // open box: the value goes to column d = i - shift; the guard
+            // columns (and, on a shift, the new last column) get zeros
+            const int d = i - wshift;
             for (int b = 0; b < nj; ++b) {
-                const long long o = gidx(g, ii[a], jj[b]);
-                Eout[o] = ex;
-                Eout[cs + o] = ey;
-                Eout[2 * cs + o] = ez;
-                Bout[o] = bx;
-                Bout[cs + o] = by;
-                Bout[2 * cs + o] = bz;
+                if (d >= 0) {
+                    const long long o = gidx(g, d, jj[b]);
+                    Eout[o] = ex;
+                    Eout[cs + o] = ey;
+                    Eout[2 * cs + o] = ez;
+                    Bout[o] = bx;
+                    Bout[cs + o] = by;
+                    Bout[2 * cs + o] = bz;
+                }
+                const int z0 = d == 0 ? -1 : (i == g.nx - 1 ? d + 1 : 1);
+                const int z1 = i == g.nx - 1 ? g.nx + 1 : (d == 0 ? -1 : 0);
+                for (int zc = z0; zc <= z1; ++zc) {
+                    const long long o = gidx(g, zc, jj[b]);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) Eout[c * cs + o] = Bout[c * cs + o] = 0.f;
+                }
             }
+        }
         const int mi = i % T, mj = j % T;
         const bool ring = prm.zero_all || mi < 2 || mi == T - 1 || mj < 2 || mj == T - 1;
         if (ring) {
@@ -202,12 +241,80 @@ __global__ void k_set_grid(const Geom g, float* F, int ncomp, const float* src) 
         int ii[2], jj[2], ni = 1, nj = 1;
         ii[0] = i;
         jj[0] = j;
-        if (i < 2) ii[ni++] = i + g.nx;
-        else if (i == g.nx - 1) ii[ni++] = -1;
+        if (!g.open_x) {  // an open box keeps zero x guards
+            if (i < 2) ii[ni++] = i + g.nx;
+            else if (i == g.nx - 1) ii[ni++] = -1;
+        }
         if (j < 2) jj[nj++] = j + g.ny;
         else if (j == g.ny - 1) jj[nj++] = -1;
         for (int a = 0; a < ni; ++a)
             for (int b = 0; b < nj; ++b) F[c * g.cstride + gidx(g, ii[a], jj[b])] = v;
+    }
+}
+
+// zero the x guard columns -1, nx, nx+1 (rows -1 .. ny+1) of ncomp components
+__global__ void k_zero_x_guards(const Geom g, float* F, int ncomp) {
+    const int rows = g.ny + 3;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncomp * rows * 3;
+         k += gridDim.x * blockDim.x) {
+        const int c = k / (rows * 3), r = (k / 3) % rows, q = k % 3;
+        const int i = q == 0 ? -1 : g.nx + q - 1;
+        F[c * g.cstride + gidx(g, i, r - 1)] = 0.f;
+    }
+}
+
+// ------------------------------------------------------------------ lasers
+// Field of a laser pulse at physical (x, y) before polarisation (§3.2: plane
+// and Gaussian lasers in the initial fields): envelope sin^2(pi xi / 2 fwhm)
+// for 0 <= xi = start - x <= 2 fwhm, carrier cos(omega0 (x - start)), peak
+// a0 omega0; the Gaussian beam is the paraxial beam of two dimensions with
+// waist W0 at x = focus on y = axis.  FP64.
+__device__ double laser_value(const LaserDev& l, double x, double y) {
+    const double L = 2.0 * l.fwhm, xi = l.start - x;
+    if (!(xi >= 0.0 && xi <= L)) return 0.0;
+    const double se = sin(M_PI * xi / L);
+    double v = l.a0 * l.omega0 * se * se;
+    double phase = l.omega0 * (x - l.start);
+    if (l.type == 1) {
+        const double z = x - l.focus, r = y - l.axis;
+        const double zR = 0.5 * l.omega0 * l.W0 * l.W0;
+        const double W = l.W0 * sqrt(1.0 + (z / zR) * (z / zR));
+        v *= sqrt(l.W0 / W) * exp(-(r / W) * (r / W));
+        phase += 0.5 * l.omega0 * r * r * (z / (z * z + zR * zR)) - 0.5 * atan(z / zR);
+    }
+    return v * cos(phase);
+}
+
+// Adds the pulse to Ey (i, j+1/2), Ez (i, j), By (i+1/2, j), Bz (i+1/2, j+1/2)
+// and refreshes those values' guard images (periodic box) -- an open box
+// keeps its zero x guards.
+__global__ void k_add_laser(const Geom g, float* F, const LaserDev l, const DevState* st) {
+    const long long n = (long long)g.nx * g.ny;
+    const double x0 = (double)st->win_moves * g.dx;
+    const double cp = cos(l.polarization), sp = sin(l.polarization);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < 4 * n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(k / n);
+        const long long r = k - c * n;
+        const int j = (int)(r / g.nx), i = (int)(r - (long long)j * g.nx);
+        const bool hx = c >= 2, hy = c == 0 || c == 3;  // half-cell offsets of Ey, Ez, By, Bz
+        const double x = x0 + ((double)i + (hx ? 0.5 : 0.0)) * g.dx;
+        const double y = ((double)j + (hy ? 0.5 : 0.0)) * g.dy;
+        const double pol = c == 0 ? cp : (c == 1 ? sp : (c == 2 ? -sp : cp));
+        const int comp = c == 0 ? 1 : (c == 1 ? 2 : (c == 2 ? 4 : 5));  // Ey Ez By Bz
+        float* C = F + comp * g.cstride;
+        const float v = C[gidx(g, i, j)] + (float)(pol * laser_value(l, x, y));
+        int ii[2], jj[2], ni = 1, nj = 1;
+        ii[0] = i;
+        jj[0] = j;
+        if (!g.open_x) {
+            if (i < 2) ii[ni++] = i + g.nx;
+            else if (i == g.nx - 1) ii[ni++] = -1;
+        }
+        if (j < 2) jj[nj++] = j + g.ny;
+        else if (j == g.ny - 1) jj[nj++] = -1;
+        for (int a = 0; a < ni; ++a)
+            for (int b = 0; b < nj; ++b) C[gidx(g, ii[a], jj[b])] = v;
     }
 }
 
@@ -471,6 +578,17 @@ cudaError_t launch_yee(const YeeParams& p, cudaStream_t s) {
 cudaError_t launch_set_grid(const Geom& g, float* F, int ncomp, const float* src,
                             cudaStream_t s) {
     k_set_grid<<<grid_for((long long)g.nx * g.ny * ncomp, 256), 256, 0, s>>>(g, F, ncomp, src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_x_guards(const Geom& g, float* F, int ncomp, cudaStream_t s) {
+    k_zero_x_guards<<<grid_for((long long)ncomp * (g.ny + 3) * 3, 256), 256, 0, s>>>(g, F, ncomp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_laser(const Geom& g, float* F, const LaserDev& l, const DevState* st,
+                             cudaStream_t s) {
+    k_add_laser<<<grid_for(4LL * g.nx * g.ny, 256), 256, 0, s>>>(g, F, l, st);
     return cudaGetLastError();
 }
 

@@ -293,6 +293,9 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
     const int tx = t % g.ntx, ty = t / g.ntx;
     const int ix0 = tx * T, iy0 = ty * T;
     const long long step = *((volatile long long*)&prm.st->step);
+    // moving window (open box along x): cells are written in the frame of the
+    // window after this step's shift; particles leaving the box are removed
+    const int wshift = g.open_x ? window_shift(step, g) : 0;
 
     for (int i = tid; i < L::NCNT; i += nth) sDir[i] = 0;
     __syncthreads();
@@ -484,18 +487,24 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
                         mtx = di ? qdiv(mxb - x, x1 - x) : 2.f;
                         mty = dj ? qdiv(myb - y, y1 - y) : 2.f;
                         // ---- new cell and tile ----
-                        int nix = ix + di, niy = iy + dj;
-                        nix = nix < 0 ? nix + nx : (nix >= nx ? nix - nx : nix);
+                        int nix = ix + di - wshift, niy = iy + dj;
+                        bool gone = false;
+                        if (g.open_x)  // left the box (before or by the shift)
+                            gone = nix < 0 || nix >= nx - wshift;
+                        else
+                            nix = nix < 0 ? nix + nx : (nix >= nx ? nix - nx : nix);
                         niy = niy < 0 ? niy + ny : (niy >= ny ? niy - ny : niy);
                         ncell = nix | (niy << 16);
                         xn = xnn;
                         yn = ynn;
-                        const int nlx = lx + di, nly = ly + dj;
+                        const int nlx = lx + di - wshift, nly = ly + dj;
                         int dtx = nlx < 0 ? -1 : (nlx >= T ? 1 : 0);
                         int dty = nly < 0 ? -1 : (nly >= T ? 1 : 0);
                         if (g.ntx == 1) dtx = 0;
                         if (g.nty == 1) dty = 0;
-                        if (dtx | dty) {
+                        if (gone) {
+                            dir = 8;  // removed: a leaver with no destination
+                        } else if (dtx | dty) {
                             const int d = (dty + 1) * 3 + (dtx + 1);
                             dir = d < 4 ? d : d - 1;
                         }
@@ -552,6 +561,12 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
                 if (lane == leader) wbase = atomicAdd(&S.leave[t], __popc(lm));
                 wbase = __shfl_sync(FULL, wbase, leader);
                 slot = wbase + __popc(lm & ((1u << lane) - 1u));
+                if (g.open_x) {
+                    const unsigned rm = __ballot_sync(FULL, dir == 8);
+                    if (rm && lane == leader)
+                        atomicAdd(reinterpret_cast<unsigned long long*>(&prm.st->removed[s]),
+                                  (unsigned long long)__popc(rm));
+                }
             }
             if (write) {
                 if (dir < 0) {
@@ -563,7 +578,7 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
                     S.uz[p] = vzm;
                 } else {
                     const int q = p0 + slot;
-                    S.ocell[q] = ncell;
+                    S.ocell[q] = dir == 8 ? HOLE : ncell;  // a removed particle goes nowhere
                     S.ox[q] = xn;
                     S.oy[q] = yn;
                     S.oux[q] = vx;
@@ -572,7 +587,7 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
                     if (prm.track_ids) S.oid[q] = S.id[p];
                     S.hole[q] = p;
                     S.cell[p] = HOLE;
-                    atomicAdd(&sDir[s * 8 + dir], 1);
+                    if (dir < 8) atomicAdd(&sDir[s * 8 + dir], 1);
                 }
             }
             // ---- release the stage; the last warp refills it ----
@@ -627,6 +642,7 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
         const bool deep = whole && lx >= 2 && lx < T - 1 && ly >= 2 && ly < T - 1;
         if (!deep && v == 0.f) continue;
         int i = ix0 + lx, j = iy0 + ly;
+        if (g.open_x && (i < 0 || i >= nx)) continue;  // outside the open box: dropped
         i = i < 0 ? i + nx : (i >= nx ? i - nx : i);
         j = j < 0 ? j + ny : (j >= ny ? j - ny : j);
         float* dst = prm.J + comp * g.cstride + (long long)(j + GY) * g.P + (i + GX);
@@ -651,6 +667,13 @@ __global__ void __launch_bounds__(MAX_PUSH_THREADS, 1) k_push(const __grid_const
                                                const PushParams prm) {
     extern __shared__ __align__(128) unsigned char smem[];
     init_barriers(reinterpret_cast<uint64_t*>(smem + Tile<T, PW>::off_misc(blockDim.x)));
+    if (prm.g.open_x && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        // the window decision of this step, for the re-sort and field kernels
+        // that follow (no CTA of this launch reads them)
+        const int w = window_shift(*((volatile long long*)&prm.st->step), prm.g);
+        prm.st->win_shift = w;
+        prm.st->win_moves += w;
+    }
     unsigned fphase = 0, gb = 0;
     push_item<T, PW>(prm, &fmap, blockIdx.x, blockIdx.y, fphase, gb);
 }

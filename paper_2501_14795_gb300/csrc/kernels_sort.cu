@@ -49,6 +49,43 @@ __device__ __forceinline__ int find_member(const int* start, int n, int g) {
     return lo;
 }
 
+// Moving-window injection into tile t this step: particles per tile row of
+// cells (k * kept lattice columns), the first kept lattice column and the
+// tile's total (0 unless the window shifted this step and t is in the last
+// tile column).
+struct Injection {
+    int per_row, a0, total;
+};
+__device__ __forceinline__ Injection injection(const SortParams& prm, const SortSpecies& S, int t) {
+    Injection r{0, 0, 0};
+    const Geom& g = prm.g;
+    if (!g.open_x || S.inj_k == 0 || t % g.ntx != g.ntx - 1) return r;
+    if (!*((volatile int*)&prm.st->win_shift)) return r;
+    const long long gcol = *((volatile long long*)&prm.st->win_moves) + g.nx - 1;
+    r.a0 = inject_first(gcol, S.inj_k, S.inj_x0, g.dx);
+    r.per_row = S.inj_k * (S.inj_k - r.a0);
+    r.total = r.per_row * g.T;
+    return r;
+}
+
+// Write injected particle m of tile t (rows of cells, then lattice rows b,
+// then kept lattice columns a) at slot `to`.
+__device__ __forceinline__ void inject_particle(const SortParams& prm, const SortSpecies& S,
+                                                int t, const Injection& inj, int m, int to) {
+    const Geom& g = prm.g;
+    const int k = S.inj_k, na = k - inj.a0;
+    const int r = m / inj.per_row, rem = m - r * inj.per_row;
+    const int b = rem / na, a = inj.a0 + rem % na;
+    const int iy = (t / g.ntx) * g.T + r;
+    S.cell[to] = (g.nx - 1) | (iy << 16);
+    S.x[to] = (float)(((double)a + 0.5) / (double)k);
+    S.y[to] = (float)(((double)b + 0.5) / (double)k);
+    S.ux[to] = S.inj_u[0];
+    S.uy[to] = S.inj_u[1];
+    S.uz[to] = S.inj_u[2];
+    if (prm.track_ids) S.id[to] = -1;
+}
+
 __device__ __forceinline__ void copy_particle(const SortSpecies& S, int from_out, int to_main,
                                               int track) {
     S.cell[to_main] = S.ocell[from_out];
@@ -80,6 +117,7 @@ __device__ __forceinline__ int count_tile(const SortParams& prm, int s, int t) {
         const int sx = dev::wrapi(tx - ddx, g.ntx), sy = dev::wrapi(ty - ddy, g.nty);
         c += S.dirc[(sy * g.ntx + sx) * 8 + d];
     }
+    c += injection(prm, S, t).total;
     S.off_new[t] = c;
     S.leave_next[t] = 0;
 #pragma unroll
@@ -164,9 +202,31 @@ __device__ __forceinline__ void scan_species(const SortParams& prm, int s, bool 
         carry += sWarp[31];
         __syncthreads();  // sWarp is rewritten by the next round
     }
+    __shared__ int sBad;
+    const int lim = prm.g.open_x ? S.cap : S.n;
     if (tid == 0) {
         S.off_new[nt] = carry;
-        if (carry != S.n) dev::set_status(prm.st, ST_SORT);
+        bool bad;
+        if (prm.g.open_x) {
+            // the count changes by the removed and injected particles
+            const Injection inj = injection(prm, S, prm.g.ntx - 1);
+            const long long want =
+                prm.st->np[s] - prm.st->removed[s] + (long long)inj.total * prm.g.nty;
+            bad = carry != want || carry > S.cap;
+            prm.st->np[s] = min(carry, S.cap);
+            prm.st->removed[s] = 0;
+        } else {
+            bad = carry != S.n;
+        }
+        if (bad) dev::set_status(prm.st, ST_SORT);
+        sBad = bad;
+    }
+    __syncthreads();
+    // inconsistent counts: the bookmarks are clamped to the arrays so that no
+    // later kernel reads or writes outside them (the sticky status stops the run)
+    if (sBad)
+        for (int i = tid; i <= nt; i += SCAN_THREADS) S.off_new[i] = min(S.off_new[i], lim);
+    if (tid == 0) {
         prm.st->leavers_sp[s] = prm.st->leavers_acc[s];
         prm.st->leavers_acc[s] = 0;
     }
@@ -190,7 +250,8 @@ __device__ __forceinline__ void evict_tile(const SortParams& prm, int s, int t, 
     const int p0 = S.off_old[t], p1 = S.off_old[t + 1];
     const int r0 = S.off_new[t], r1 = S.off_new[t + 1];
     const int lv = S.leave[t];
-    if (r0 < 0 || r1 < r0 || r1 > S.n || p1 - p0 < lv) {
+    const int lim = prm.g.open_x ? S.cap : S.n;
+    if (r0 < 0 || r1 < r0 || r1 > lim || p1 - p0 < lv) {
         if (lane == 0) dev::set_status(prm.st, ST_SORT);
         return;
     }
@@ -253,7 +314,8 @@ __device__ __forceinline__ void fill_tile(const SortParams& prm, int s, int t, i
     const int r0 = S.off_new[t], r1 = S.off_new[t + 1];
     const int cap = r1 - r0;
     const int lvt = S.leave[t], ev = S.evict[t];
-    if (r0 < 0 || r1 < r0 || r1 > S.n || lvt + ev > p1 - p0) {
+    const int lim = g.open_x ? S.cap : S.n;
+    if (r0 < 0 || r1 < r0 || r1 > lim || lvt + ev > p1 - p0) {
         if (lane == 0) dev::set_status(prm.st, ST_SORT);
         return;
     }
@@ -330,6 +392,17 @@ __device__ __forceinline__ void fill_tile(const SortParams& prm, int s, int t, i
         }
     }
     nsrc += ev;
+    // ... plus the particles the moving window injects here (negative: -1 - m)
+    const Injection inj = injection(prm, S, t);
+    for (int base = 0; base < inj.total; base += 32) {
+        const int i = base + lane;
+        if (i < inj.total) {
+            const int slot = nsrc + i;
+            if (slot < cap) S.isrc[r0 + slot] = -1 - i;
+            else overflow = true;
+        }
+    }
+    nsrc += inj.total;
     // target_idx: holes of this tile inside its new range ...
     for (int base = 0; base < lvt; base += 32) {
         const int i = base + lane;
@@ -365,8 +438,11 @@ __device__ __forceinline__ void fill_tile(const SortParams& prm, int s, int t, i
         return;
     }
     // move source -> target
-    for (int k = lane; k < nsrc; k += 32)
-        copy_particle(S, S.isrc[r0 + k], S.fslot[r0 + k], prm.track_ids);
+    for (int k = lane; k < nsrc; k += 32) {
+        const int src = S.isrc[r0 + k];
+        if (src >= 0) copy_particle(S, src, S.fslot[r0 + k], prm.track_ids);
+        else inject_particle(prm, S, t, inj, -1 - src, S.fslot[r0 + k]);
+    }
 }
 
 __global__ void __launch_bounds__(32 * SORT_WARPS) k_fill(const SortParams prm) {

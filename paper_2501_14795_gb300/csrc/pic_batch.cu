@@ -433,6 +433,10 @@ pic_status pic_autotune(pic_sim* sim, int steps, int force, int* tile, int* thre
     if (!sim) return PIC_EINVAL;
     sim->err.clear();
     if (steps < 1) return fail(sim, PIC_EINVAL, "steps must be >= 1");
+    {
+        pic_status r = refresh_counts(sim);
+        if (r != PIC_OK) return r;
+    }
     int dev = 0;
     PIC_CK(sim, cudaGetDevice(&dev));
     // particles per cell as loaded (all species)
@@ -541,6 +545,8 @@ pic_status pic_batch_create(pic_sim* const* members, int n, void* cuda_stream, p
             why = "members differ in PIC_STRICT_FP";
         else if (sim->jfilter)
             why = "member has a current filter installed";
+        else if (sim->window)
+            why = "member has a moving window";
         if (!why.empty()) {
             if (sim) fail(sim, PIC_EINVAL, "pic_batch_create: %s", why.c_str());
             delete batch;
@@ -575,9 +581,11 @@ pic_status pic_batch_step(pic_batch* batch, int nsteps) {
     if (nsteps < 0) return bfail(batch, PIC_EINVAL, "negative step count");
     batch->err.clear();
     if (batch->m.empty()) return PIC_OK;
-    for (pic_sim* sim : batch->m)
+    for (pic_sim* sim : batch->m) {
         if (sim->jfilter)
             return bfail(batch, PIC_EINVAL, "a member has a current filter installed");
+        if (sim->window) return bfail(batch, PIC_EINVAL, "a member has a moving window");
+    }
     for (int k = 0; k < nsteps; ++k) {
         if (stale(batch)) {
             pic_status r = prepare(batch);

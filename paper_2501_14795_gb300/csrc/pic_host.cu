@@ -94,6 +94,8 @@ void set_geometry(Geom& g, const pic_config& c) {
     g.dx = c.dx;
     g.dy = c.dy;
     g.dtd = c.dt;
+    g.open_x = 0;
+    g.pad_g = 0;
 }
 
 // Per-tile bookkeeping of a species (tile bookmarks, leaver counters by
@@ -215,6 +217,12 @@ SortParams sort_params(const pic_sim* sim, int b) {
         q.x = s.x; q.y = s.y; q.ux = s.ux; q.uy = s.uy; q.uz = s.uz;
         q.ox = s.ox; q.oy = s.oy; q.oux = s.oux; q.ouy = s.ouy; q.ouz = s.ouz;
         q.n = (int)s.n;
+        q.cap = (int)std::min<int64_t>(s.cap, 0x7fffffff);
+        q.inj_k = s.inj_k;
+        q.inj_u[0] = s.inj_u[0];
+        q.inj_u[1] = s.inj_u[1];
+        q.inj_u[2] = s.inj_u[2];
+        q.inj_x0 = s.inj_x0;
     }
     p.hist_e = sim->hist_e;
     p.hist_b = sim->hist_b;
@@ -348,6 +356,15 @@ pic_status sync_status(pic_sim* sim) {
     return status_from_bits(sim, h.status);
 }
 
+pic_status refresh_counts(pic_sim* sim) {
+    if (!sim->window) return PIC_OK;
+    DevState h;
+    pic_status r = read_state(sim, &h);
+    if (r != PIC_OK) return r;
+    for (int k = 0; k < sim->cfg.n_species; ++k) sim->sp[k].n = h.np[k];
+    return PIC_OK;
+}
+
 // zero the history slots of the current level and record the field energy
 pic_status refresh_level_energy(pic_sim* sim) {
     CK(launch_hist_prime(sim->hist_e, sim->hist_b, sim->hist_k, sim->st, sim->stream));
@@ -389,6 +406,10 @@ pic_status retile(pic_sim* sim, int tile) {
     if (tile == sim->g.T) return PIC_OK;
     cudaStream_t s = sim->stream;
     {
+        pic_status r = refresh_counts(sim);
+        if (r != PIC_OK) return r;
+    }
+    {
         DevState h;
         pic_status r = read_state(sim, &h);
         if (r != PIC_OK) return r;
@@ -412,6 +433,7 @@ pic_status retile(pic_sim* sim, int tile) {
     invalidate_graphs(sim);
     sim->cfg.tile = tile;
     set_geometry(sim->g, sim->cfg);
+    sim->g.open_x = sim->window;
     for (int k = 0; k < c.n_species; ++k) {
         free_tile_arrays(sim->sp[k]);
         CK(alloc_tile_arrays(sim->sp[k], sim->g, s));
@@ -563,7 +585,10 @@ pic_status pic_load_particles(pic_sim* sim, int species, int64_t n, const int32_
     const bool track = (sim->cfg.flags & PIC_TRACK_IDS) != 0;
     // stage into the out arrays of a (possibly new) allocation
     SpeciesDev W = S;
-    const bool grow = n > S.cap;
+    const int64_t need = sim->window ? std::max<int64_t>(n, S.want_cap) : n;
+    if (need > 0x7fffffffLL)
+        return fail(sim, PIC_EINVAL, "capacity %lld above 2^31-1", (long long)need);
+    const bool grow = need > S.cap;
     if (grow) {
         SpeciesDev fresh = S;
         fresh.cell = fresh.id = fresh.ocell = fresh.oid = fresh.hole = fresh.fslot = fresh.isrc =
@@ -571,10 +596,10 @@ pic_status pic_load_particles(pic_sim* sim, int species, int64_t n, const int32_
         fresh.x = fresh.y = fresh.ux = fresh.uy = fresh.uz = nullptr;
         fresh.ox = fresh.oy = fresh.oux = fresh.ouy = fresh.ouz = nullptr;
         fresh.cap = 0;
-        cudaError_t e = alloc_particles(fresh, n);
+        cudaError_t e = alloc_particles(fresh, need);
         if (e != cudaSuccess) {
             free_species(fresh);
-            return fail(sim, PIC_ENOMEM, "cannot allocate %lld particles", (long long)n);
+            return fail(sim, PIC_ENOMEM, "cannot allocate %lld particles", (long long)need);
         }
         W = fresh;
     }
@@ -624,6 +649,12 @@ pic_status pic_load_particles(pic_sim* sim, int species, int64_t n, const int32_
     // may put the simulation back on a parity whose counters were in use)
     CK(cudaMemsetAsync(S.leave[sim->cur], 0, sizeof(int32_t) * sim->g.ntiles, s));
     CK(cudaMemsetAsync(S.dirc[sim->cur], 0, sizeof(int32_t) * 8 * sim->g.ntiles, s));
+    {
+        const long long np = n;  // the device count (it changes with the moving window)
+        CK(cudaMemcpyAsync(&sim->st->np[species], &np, sizeof np, cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(&sim->st->removed[species], 0, sizeof(long long), s));
+        CK(cudaStreamSynchronize(s));
+    }
     invalidate_graphs(sim);
     sim->rho_prev_step = -1;
     pic_status r = refresh_level_energy(sim);
@@ -646,6 +677,7 @@ pic_status pic_set_fields(pic_sim* sim, const float* E, const float* B, int on_d
                            sim->stream));
         CK(cudaStreamSynchronize(sim->stream));
     }
+    if (sim->window) CK(launch_zero_x_guards(sim->g, sim->F[sim->cur], 6, sim->stream));
     sim->rho_prev_step = -1;
     pic_status r = refresh_level_energy(sim);
     if (r != PIC_OK) return r;
@@ -692,6 +724,8 @@ pic_status pic_set_binomial_filter(pic_sim* sim, int passes) {
     if (!sim) return PIC_EINVAL;
     sim->err.clear();
     if (passes < 0 || passes > 64) return fail(sim, PIC_EINVAL, "passes %d not in 0..64", passes);
+    if (passes && sim->window)
+        return fail(sim, PIC_EINVAL, "the binomial filter is periodic: not with the moving window");
     CK(cudaStreamSynchronize(sim->stream));
     sim->binomial_passes = passes;
     sim->jfilter = passes ? binomial_hook : nullptr;
@@ -738,6 +772,10 @@ pic_status pic_get_particles(pic_sim* sim, int species, int32_t* ix, int32_t* iy
     sim->err.clear();
     if (species < 0 || species >= sim->cfg.n_species)
         return fail(sim, PIC_EINVAL, "species %d out of range", species);
+    {
+        pic_status r = refresh_counts(sim);
+        if (r != PIC_OK) return r;
+    }
     SpeciesDev& S = sim->sp[species];
     cudaStream_t s = sim->stream;
     const size_t b4 = 4 * (size_t)S.n;
@@ -803,11 +841,15 @@ pic_status pic_diagnostics(pic_sim* sim, pic_diag* out) {
     out->w_e = he;
     out->w_b = hb;
     out->w_k = hk;
-    out->gauss_max = red[0];
-    out->continuity_max = cont ? red[1] : NAN;
+    // the moving window's open box, removal and injection make the periodic
+    // Gauss and continuity residuals meaningless: not reported
+    out->gauss_max = sim->window ? NAN : red[0];
+    out->continuity_max = (cont && !sim->window) ? red[1] : NAN;
     out->charge_total = red[2];
+    out->window_moves = sim->window ? h.win_moves : 0;
     long long lv = 0;
     for (int k = 0; k < sim->cfg.n_species; ++k) {
+        if (sim->window) sim->sp[k].n = h.np[k];
         out->n_particles[k] = sim->sp[k].n;
         lv += h.leavers_sp[k];
     }
@@ -839,8 +881,77 @@ pic_status pic_get_history(pic_sim* sim, int64_t first, int64_t count, double* w
     return PIC_OK;
 }
 
+pic_status pic_set_moving_window(pic_sim* sim, const pic_inject* inject) {
+    if (!sim) return PIC_EINVAL;
+    sim->err.clear();
+    if (sim->batch) return fail(sim, PIC_EINVAL, "a batch member cannot have a moving window");
+    if (sim->jfilter)
+        return fail(sim, PIC_EINVAL, "the current filters are periodic: not with the moving window");
+    for (int k = 0; k < sim->cfg.n_species; ++k)
+        if (sim->sp[k].n > 0)
+            return fail(sim, PIC_EINVAL, "set the moving window before loading particles");
+    for (int k = 0; inject && k < sim->cfg.n_species; ++k) {
+        const pic_inject& q = inject[k];
+        if (q.k < 0 || q.k > 64 || q.capacity < 0 || q.capacity > 0x7fffffffLL ||
+            !std::isfinite(q.x_start) || !std::isfinite(q.ux) || !std::isfinite(q.uy) ||
+            !std::isfinite(q.uz))
+            return fail(sim, PIC_EINVAL, "bad injection parameters for species %d", k);
+    }
+    CK(cudaStreamSynchronize(sim->stream));
+    sim->window = 1;
+    sim->g.open_x = 1;
+    for (int k = 0; k < sim->cfg.n_species; ++k) {
+        SpeciesDev& S = sim->sp[k];
+        const pic_inject* q = inject ? &inject[k] : nullptr;
+        S.inj_k = q ? q->k : 0;
+        S.inj_u[0] = q ? q->ux : 0.f;
+        S.inj_u[1] = q ? q->uy : 0.f;
+        S.inj_u[2] = q ? q->uz : 0.f;
+        S.inj_x0 = q ? q->x_start : 0.0;
+        S.want_cap = q ? q->capacity : 0;
+    }
+    for (int b = 0; b < 2; ++b) CK(launch_zero_x_guards(sim->g, sim->F[b], 6, sim->stream));
+    CK(cudaMemsetAsync(&sim->st->win_moves, 0, sizeof(long long), sim->stream));
+    CK(cudaMemsetAsync(&sim->st->win_shift, 0, sizeof(int), sim->stream));
+    invalidate_graphs(sim);
+    pic_status r = refresh_level_energy(sim);
+    if (r != PIC_OK) return r;
+    CK(cudaStreamSynchronize(sim->stream));
+    return PIC_OK;
+}
+
+pic_status pic_add_laser(pic_sim* sim, const pic_laser* laser) {
+    if (!sim || !laser) return PIC_EINVAL;
+    sim->err.clear();
+    const pic_laser& l = *laser;
+    if (!(l.type == PIC_LASER_PLANE || l.type == PIC_LASER_GAUSSIAN) || !(l.fwhm > 0) ||
+        !(l.omega0 > 0) || !std::isfinite(l.a0) || !std::isfinite(l.start) ||
+        !std::isfinite(l.polarization) ||
+        (l.type == PIC_LASER_GAUSSIAN &&
+         (!(l.W0 > 0) || !std::isfinite(l.focus) || !std::isfinite(l.axis))))
+        return fail(sim, PIC_EINVAL, "bad laser parameters");
+    LaserDev d;
+    d.type = l.type == PIC_LASER_GAUSSIAN ? 1 : 0;
+    d.start = l.start;
+    d.fwhm = l.fwhm;
+    d.a0 = l.a0;
+    d.omega0 = l.omega0;
+    d.polarization = l.polarization;
+    d.W0 = l.W0;
+    d.focus = l.focus;
+    d.axis = l.axis;
+    CK(launch_add_laser(sim->g, sim->F[sim->cur], d, sim->st, sim->stream));
+    sim->rho_prev_step = -1;
+    pic_status r = refresh_level_energy(sim);
+    if (r != PIC_OK) return r;
+    CK(cudaStreamSynchronize(sim->stream));
+    return sync_status(sim);
+}
+
 pic_status pic_sync(pic_sim* sim) {
     if (!sim) return PIC_EINVAL;
+    pic_status r = refresh_counts(sim);
+    if (r != PIC_OK) return r;
     return sync_status(sim);
 }
 

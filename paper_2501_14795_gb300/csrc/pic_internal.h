@@ -7,7 +7,8 @@
 //     row j + GY, column i + GX (GX = 4, GY = 1), so every component has guard
 //     cells i in [-4, nx+4), j in [-1, ny+2).  Guards i = -1, nx, nx+1 and
 //     j = -1, ny, ny+1 hold periodic images (update_gc_copy of Listing 3.1);
-//     the others are never written and stay zero.  The column shift of 4 makes
+//     the others are never written and stay zero.  With the moving window the
+//     box is open along x and the guards i = -1, nx, nx+1 hold zeros instead.  The column shift of 4 makes
 //     the TMA box of a tile start on a 16-byte boundary (x multiple of 4).
 //   * E|B are double-buffered (read one, write the other each step) and so is
 //     J, because the fused Yee kernel reads neighbours across CTAs.
@@ -40,7 +41,10 @@ struct DevState {
     long long leavers_sp[MAX_SPECIES];  // particles that changed tile in the last step
     long long leavers_acc[MAX_SPECIES]; // running sum of the current step (k_count -> k_scan)
     int load_bad;        // pic_load_particles validation failures
-    int pad2;
+    int win_shift;       // moving window: 1 if the step being taken shifts it (set by the push)
+    long long win_moves; // moving window: cells moved so far (after the step's shift)
+    long long np[MAX_SPECIES];       // particles per species (moving window: changes)
+    long long removed[MAX_SPECIES];  // particles that left the open box this step
 };
 
 struct SpeciesDev {
@@ -68,6 +72,11 @@ struct SpeciesDev {
     float qjz;        // qtilde
     double ke_w;      // kinetic-energy weight qtilde/(q/m) dx dy
     double qtilde;
+    // moving-window injection (inj_k = 0: none) and requested capacity
+    int inj_k;
+    float inj_u[3];
+    double inj_x0;
+    int64_t want_cap;
 };
 
 struct Geom {
@@ -77,7 +86,39 @@ struct Geom {
     float cx, cy;      // dt/dx, dt/dy
     float hdt_dx, hdt_dy, dt_dx, dt_dy, dt;
     double dx, dy, dtd;
+    int open_x;        // moving window: box open along x (else periodic)
+    int pad_g;
 };
+
+// Moving window (the last steps of Listing 3.1; the window moves at c = 1).
+// Cells moved after k steps, M(k) = floor(k dt / dx + 1e-9), in IEEE double
+// with the operation order of the host and the tests.
+__host__ __device__ inline long long window_moves(long long k, double dt, double dx) {
+#ifdef __CUDA_ARCH__
+    return (long long)floor(__dadd_rn(__ddiv_rn(__dmul_rn((double)k, dt), dx), 1e-9));
+#else
+    return (long long)floor((double)k * dt / dx + 1e-9);
+#endif
+}
+// 1 if the step from time level n to n+1 ends with a shift of the window
+__host__ __device__ inline int window_shift(long long n, const Geom& g) {
+    return (int)(window_moves(n + 1, g.dtd, g.dx) - window_moves(n, g.dtd, g.dx));
+}
+// Injection into the new last column (global cell index gcol) of a moving
+// window: lattice sub-indices a >= first of a k x k lattice keep the
+// particles at physical x = (gcol + (a + 1/2)/k) dx >= x0 (a step profile).
+// Returns the first kept a (k if none).
+__host__ __device__ inline int inject_first(long long gcol, int k, double x0, double dx) {
+    int a = 0;
+#ifdef __CUDA_ARCH__
+    while (a < k && __dmul_rn(__dadd_rn((double)gcol, __ddiv_rn(__dadd_rn((double)a, 0.5), (double)k)),
+                              dx) < x0)
+        ++a;
+#else
+    while (a < k && ((double)gcol + ((double)a + 0.5) / (double)k) * dx < x0) ++a;
+#endif
+    return a;
+}
 
 // ---- parameters passed by value to the kernels ------------------------------
 struct PushSpecies {
@@ -105,7 +146,13 @@ struct SortSpecies {
     int32_t *cell, *id, *ocell, *oid, *hole, *fslot, *isrc, *leave, *dirc, *evict;
     int32_t *leave_next, *dirc_next;  // cleared here for the next step
     float *x, *y, *ux, *uy, *uz, *ox, *oy, *oux, *ouy, *ouz;
-    int n;
+    int n;       // particles (fixed count; with the moving window see DevState::np)
+    int cap;     // capacity of the particle arrays
+    // moving-window injection (inj_k = 0: none): k x k cold lattice per cell at
+    // physical x >= inj_x0 with momentum inj_u
+    int inj_k;
+    float inj_u[3];
+    double inj_x0;
 };
 
 struct SortParams {
@@ -203,5 +250,17 @@ cudaError_t launch_unpack_cells(const int32_t* cell, int64_t n, int32_t* ix, int
 cudaError_t launch_offsets_to_i64(const int32_t* off, int64_t n, int64_t* out, cudaStream_t s);
 cudaError_t launch_hist_prime(double* hist_e, double* hist_b, double* hist_k, DevState* st,
                               cudaStream_t s);
+
+// Laser pulse of the initial conditions (§3.2), added to E|B (6 components)
+// with its guard images; x of node column 0 is (moves + 0) dx with moves read
+// from st->win_moves.
+struct LaserDev {
+    int type;           // 0 plane, 1 Gaussian
+    double start, fwhm, a0, omega0, polarization, W0, focus, axis;
+};
+cudaError_t launch_add_laser(const Geom& g, float* F, const LaserDev& l, const DevState* st,
+                             cudaStream_t s);
+// zero the x guard columns (-1, nx, nx+1) of ncomp components (open box)
+cudaError_t launch_zero_x_guards(const Geom& g, float* F, int ncomp, cudaStream_t s);
 
 }  // namespace pic

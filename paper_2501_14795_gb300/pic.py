@@ -49,12 +49,27 @@ class pic_diag(C.Structure):
                 ("w_b", C.c_double), ("w_k", C.c_double), ("gauss_max", C.c_double),
                 ("continuity_max", C.c_double), ("charge_total", C.c_double),
                 ("n_particles", C.c_int64 * PIC_MAX_SPECIES), ("leavers", C.c_int64),
-                ("status_bits", C.c_uint32)]
+                ("status_bits", C.c_uint32), ("window_moves", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "n_particles"}
         d["n_particles"] = list(self.n_particles)
         return d
+
+
+class pic_inject(C.Structure):
+    _fields_ = [("k", C.c_int), ("x_start", C.c_double), ("ux", C.c_float), ("uy", C.c_float),
+                ("uz", C.c_float), ("capacity", C.c_int64)]
+
+
+PIC_LASER_PLANE = 0
+PIC_LASER_GAUSSIAN = 1
+
+
+class pic_laser(C.Structure):
+    _fields_ = [("type", C.c_int), ("start", C.c_double), ("fwhm", C.c_double),
+                ("a0", C.c_double), ("omega0", C.c_double), ("polarization", C.c_double),
+                ("W0", C.c_double), ("focus", C.c_double), ("axis", C.c_double)]
 
 
 _lib = None
@@ -116,6 +131,8 @@ def load_library() -> C.CDLL:
                                               C.POINTER(C.c_double), C.c_int]
         L.pic_set_denoiser.argtypes = [_P, _P]
         L.pic_set_binomial_filter.argtypes = [_P, C.c_int]
+        L.pic_set_moving_window.argtypes = [_P, _P]
+        L.pic_add_laser.argtypes = [_P, C.POINTER(pic_laser)]
         L.pic_denoiser_last_error.argtypes = [_P]
         L.pic_denoiser_last_error.restype = C.c_char_p
         L.pic_denoiser_destroy.argtypes = [_P]
@@ -424,6 +441,32 @@ def pic_set_binomial_filter(h, passes):
     _check(h, load_library().pic_set_binomial_filter(h, int(passes)))
 
 
+def pic_set_moving_window(h, injects=None):
+    """injects: None or one dict per species with keys k, x_start, ux, uy, uz,
+    capacity (None entries: no injection)."""
+    L = load_library()
+    if injects is None:
+        _check(h, L.pic_set_moving_window(h, None))
+        return
+    arr = (pic_inject * len(injects))()
+    for a, q in zip(arr, injects):
+        q = q or {}
+        a.k = int(q.get("k", 0))
+        a.x_start = float(q.get("x_start", 0.0))
+        a.ux, a.uy, a.uz = (float(q.get(c, 0.0)) for c in ("ux", "uy", "uz"))
+        a.capacity = int(q.get("capacity", 0))
+    _check(h, L.pic_set_moving_window(h, arr))
+
+
+def pic_add_laser(h, kind="plane", start=0.0, fwhm=1.0, a0=1.0, omega0=10.0, polarization=0.0,
+                  W0=1.0, focus=0.0, axis=0.0):
+    l = pic_laser(PIC_LASER_GAUSSIAN if kind == "gaussian" else PIC_LASER_PLANE, start, fwhm, a0,
+                  omega0, polarization, W0, focus, axis)
+    if kind not in ("plane", "gaussian"):
+        raise ValueError(kind)
+    _check(h, load_library().pic_add_laser(h, C.byref(l)))
+
+
 def pic_denoiser_destroy(d):
     load_library().pic_denoiser_destroy(d)
 
@@ -518,12 +561,15 @@ class Simulation:
 
     def __init__(self, cfg: pic_config, stream=None):
         self.cfg = cfg
+        self.window = False
         self.h = pic_init(cfg, stream)
 
     @classmethod
     def from_workload(cls, w, tile=None, threads=256, flags=0, stream=None, device=False,
                       chunk=0):
         sim = cls(config_for(w, tile, threads, flags, chunk), stream)
+        if getattr(w, "window", None) is not None:
+            sim.set_moving_window(w.window)
         for k, s in enumerate(w.species):
             arrs = s.arrays()
             if device:
@@ -534,7 +580,16 @@ class Simulation:
             E = None if w.E0 is None else np.ascontiguousarray(w.E0, np.float32).reshape(-1)
             B = None if w.B0 is None else np.ascontiguousarray(w.B0, np.float32).reshape(-1)
             pic_set_fields(sim.h, E, B)
+        for l in getattr(w, "lasers", None) or []:
+            sim.add_laser(**l)
         return sim
+
+    def set_moving_window(self, injects=None):
+        pic_set_moving_window(self.h, injects)
+        self.window = True
+
+    def add_laser(self, **laser):
+        pic_add_laser(self.h, **laser)
 
     @classmethod
     def init_batch(cls, cfgs, stream=None):
@@ -570,6 +625,8 @@ class Simulation:
         return out.reshape((n, self.cfg.ny, self.cfg.nx) if n == 3 else (self.cfg.ny, self.cfg.nx))
 
     def particles(self, species=0, ids=False):
+        if self.window:
+            pic_sync(self.h)     # synchronises and refreshes the changing counts
         n = pic_num_particles(self.h, species)
         out = dict(ix=np.empty(n, np.int32), iy=np.empty(n, np.int32), x=np.empty(n, np.float32),
                    y=np.empty(n, np.float32), ux=np.empty(n, np.float32),

@@ -55,6 +55,8 @@ class Workload:
     E0: np.ndarray | None = None     # (3, ny, nx) float32 at the Yee locations, or None = 0
     B0: np.ndarray | None = None
     meta: dict = field(default_factory=dict)
+    window: list | None = None       # moving window: one injection dict (or None) per species
+    lasers: list = field(default_factory=list)   # laser pulses (keyword dicts) added at start
 
     @property
     def n_particles(self) -> int:
@@ -227,3 +229,32 @@ def random_fields(nx, ny, amp=0.1, seed=1):
     E = (amp * rng.standard_normal((3, ny, nx))).astype(np.float32)
     B = (amp * rng.standard_normal((3, ny, nx))).astype(np.float32)
     return E, B
+
+
+def laser_wakefield(nx=128, ny=64, k=2, dx=0.1, dy=0.1, dt=0.05, tile=16, steps=200,
+                    x_start=None, a0=1.0, omega0=10.0, fwhm=1.0, kind="gaussian", W0=1.5,
+                    capacity_margin=1.25, seed=SEED_BASE + 7) -> Workload:
+    """A laser pulse entering a cold plasma in a moving window (the steps around
+    the loop of Listing 3.1; §3.2 lasers and moving window): cold electrons on
+    a k x k quiet-start lattice per cell at physical x >= x_start (half the
+    box), the ions immobile (they carry no current; they would enter only
+    rho, which a moving-window run does not report, so no background is set);
+    a Gaussian (or plane) pulse focused on the plasma edge, its front 5 % of
+    the box behind it; the window injects the same lattice at its right edge.
+    Deterministic (no random draws)."""
+    del seed
+    Lx = nx * dx
+    if x_start is None:
+        x_start = 0.5 * Lx
+    ix, iy, x, y, a, _ = lattice(nx, ny, k)
+    keep = (ix.astype(np.float64) + (a.astype(np.float64) + 0.5) / k) * dx >= x_start
+    n = int(keep.sum())
+    z = np.zeros(n, np.float32)
+    sp = Species(-1.0, -1.0 / (k * k), ix[keep], iy[keep], x[keep], y[keep], z, z.copy(), z.copy())
+    cap = int(capacity_margin * nx * ny * k * k) + 1024
+    laser = dict(kind=kind, start=x_start - 0.05 * Lx, fwhm=fwhm, a0=a0, omega0=omega0,
+                 W0=W0, focus=x_start, axis=0.5 * ny * dy)
+    return Workload("laser_wakefield", nx, ny, dx, dy, dt, tile, steps, [sp], background=0.0,
+                    window=[dict(k=k, x_start=x_start, capacity=cap)], lasers=[laser],
+                    meta=dict(ppc=k * k, x_start=x_start, a0=a0, omega0=omega0, kind=kind))
+

@@ -1,0 +1,237 @@
+"""Moving window, injection and lasers on the GPU (through the C ABI) against
+the CPU oracle.
+
+* laser fields: the library's FP64 evaluation rounded to FP32 equals the
+  oracle's within 1e-6 of the peak field (plane and Gaussian, any polarisation);
+* a cold plasma at rest under the window: fields exactly zero and the
+  particles exactly the lattice particles inside the moved window (shift,
+  removal at the left edge, part-filled injection at the right edge);
+* a laser entering a plasma: the strict build takes a window-shifting step
+  from an identical state bit for bit like the FP32 oracle (cells, offsets,
+  momenta, removed and injected particles, tile bookmarks), and the fast
+  build follows the FP64 oracle over many steps within FP32 tolerance;
+* the combinations the window refuses (filters, batches, late call).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import window as OW
+from paper_2501_14795_gb300 import pic
+from paper_2501_14795_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_14795_gb300 import build
+    build.build_library()
+    oracle.build_oracle()
+
+
+def _laser(d):
+    return OW.Laser(kind=d["kind"], start=d["start"], fwhm=d["fwhm"], a0=d["a0"],
+                    omega0=d["omega0"], polarization=d.get("polarization", 0.0),
+                    W0=d.get("W0", 1.0), focus=d.get("focus", 0.0), axis=d.get("axis", 0.0))
+
+
+def _inject(d):
+    return None if d is None or not d.get("k") else OW.Inject(
+        k=d["k"], x_start=d.get("x_start", 0.0), ux=d.get("ux", 0.0), uy=d.get("uy", 0.0),
+        uz=d.get("uz", 0.0))
+
+
+@pytest.mark.parametrize("window", [False, True])
+@pytest.mark.parametrize("laser", [
+    dict(kind="plane", start=4.0, fwhm=1.2, a0=0.7, omega0=9.0, polarization=0.3),
+    dict(kind="gaussian", start=5.0, fwhm=1.0, a0=1.5, omega0=12.0, polarization=-1.1,
+         W0=1.2, focus=6.5, axis=2.9),
+])
+def test_laser_fields_match_the_oracle(laser, window):
+    w = wl.Workload("vacuum", 96, 64, 0.1, 0.1, 0.05, 16, 1,
+                    [wl.Species(-1.0, -1.0, *(np.zeros(0, np.int32),) * 2,
+                                *(np.zeros(0, np.float32),) * 5)],
+                    background=0.0, window=[None] if window else None, lasers=[laser])
+    with pic.Simulation.from_workload(w) as sim:
+        E, B = sim.fields(pic.FIELD_E), sim.fields(pic.FIELD_B)
+    Eo, Bo = OW.laser_fields(w.nx, w.ny, w.dx, w.dy, _laser(laser))
+    peak = laser["a0"] * laser["omega0"]
+    assert np.max(np.abs(E - Eo)) <= 1e-6 * peak
+    assert np.max(np.abs(B - Bo)) <= 1e-6 * peak
+    assert np.max(np.abs(Eo)) > 0.3 * peak
+
+
+def _lattice(nx, ny, k, x_start, dx, moves=0):
+    ix, iy, x, y, a, _ = wl.lattice(nx + moves, ny, k)
+    keep = ((ix.astype(np.float64) + (a + 0.5) / k) * dx >= x_start) & (ix >= moves)
+    return ix[keep] - moves, iy[keep], x[keep], y[keep]
+
+
+def _key_set(ix, iy, x, y):
+    return sorted(zip(ix.tolist(), iy.tolist(), x.tolist(), y.tolist()))
+
+
+@pytest.mark.parametrize("flags", [0, pic.PIC_STRICT_FP])
+def test_cold_plasma_at_rest_is_exactly_relabelled_by_the_window(flags):
+    nx, ny, k, dx, dt, T = 64, 32, 3, 0.1, 0.05, 16
+    x_start = (nx // 2 + 0.4) * dx
+    ix, iy, x, y = _lattice(nx, ny, k, x_start, dx)
+    z = np.zeros(ix.size, np.float32)
+    w = wl.Workload("cold_window", nx, ny, dx, dx, dt, T, 60,
+                    [wl.Species(-1.0, -1.0 / k ** 2, ix, iy, x, y, z, z.copy(), z.copy())],
+                    background=0.0,
+                    window=[dict(k=k, x_start=x_start, capacity=nx * ny * k * k)])
+    with pic.Simulation.from_workload(w, flags=flags) as sim:
+        for n in (7, 30, 60):
+            sim.step(n - (0 if n == 7 else (7 if n == 30 else 30)))
+            d = sim.diagnostics()
+            moves = OW.window_moves(n, dt, dx)
+            assert d["window_moves"] == moves and d["status_bits"] == 0
+            got = sim.particles(0)
+            want = _lattice(nx, ny, k, x_start, dx, moves)
+            assert d["n_particles"][0] == want[0].size == got["ix"].size
+            assert _key_set(got["ix"], got["iy"], got["x"], got["y"]) == _key_set(*want)
+            assert not np.any(got["ux"]) and not np.any(got["uy"]) and not np.any(got["uz"])
+            for f in (pic.FIELD_E, pic.FIELD_B, pic.FIELD_J):
+                assert not np.any(sim.fields(f))
+            # every particle sits in the range of its tile
+            off = got["tile_offset"]
+            tid = (got["iy"] // T) * (nx // T) + got["ix"] // T
+            for t in range(len(off) - 1):
+                assert np.all(tid[off[t]:off[t + 1]] == t)
+
+
+def _oracle_from(w, state, E, B, dtype, step_count, moves):
+    sps = []
+    for s, st in zip(w.species, state):
+        sp = oracle.SpeciesState(s.q_over_m, s.qtilde, st["ix"], st["iy"], st["x"], st["y"],
+                                 st["ux"], st["uy"], st["uz"])
+        sp.pid = st["id"].astype(np.int64)
+        sps.append(sp)
+    o = oracle.OracleSim(w.nx, w.ny, w.dx, w.dy, w.dt, w.tile, sps, dtype=dtype, E=E, B=B,
+                         window=[_inject(q) for q in w.window])
+    for sp, st in zip(o.species, state):
+        sp.pid = st["id"].astype(np.int64)
+    o.step_count, o.moves = step_count, moves
+    return o
+
+
+def _split(d):
+    """Particles by id (ids >= 0) and the injected ones (id -1) as a sorted list."""
+    old = d["id"] >= 0
+    o = np.argsort(d["id"][old], kind="stable")
+    by_id = {k: d[k][old][o] for k in ("id", "ix", "iy", "x", "y", "ux", "uy", "uz")}
+    new = sorted(zip(*(d[k][~old].tolist() for k in ("ix", "iy", "x", "y", "ux", "uy", "uz"))))
+    return by_id, new
+
+
+def _oracle_split(sp):
+    d = dict(id=np.asarray(sp.pid), ix=sp.ix, iy=sp.iy, x=sp.x, y=sp.y, ux=sp.ux, uy=sp.uy,
+             uz=sp.uz)
+    return _split(d)
+
+
+def test_strict_window_shifting_step_is_bit_exact_with_fp32_oracle():
+    """From the state after one step (read back from the GPU), the second step
+    shifts the window (dt/dx = 1/2): particles leaving the box are removed,
+    the rest move one cell left, a plasma column is injected.  The strict build
+    and the FP32 oracle agree bit for bit on every particle and on the tile
+    bookmarks; the fields agree within FP32 accumulation of J."""
+    w = wl.laser_wakefield(nx=64, ny=32, k=2, tile=16, a0=2.0, x_start=2.0)
+    flags = pic.PIC_STRICT_FP | pic.PIC_TRACK_IDS
+    with pic.Simulation.from_workload(w, flags=flags) as sim:
+        for rep in range(6):           # several shifting steps, each from the GPU's own state
+            sim.step(1)
+            s1 = sim.particles(0, ids=True)
+            E1, B1 = sim.fields(pic.FIELD_E), sim.fields(pic.FIELD_B)
+            n1 = sim.diagnostics()["step"]
+            m1 = sim.diagnostics()["window_moves"]
+            sim.step(1)
+            got = sim.particles(0, ids=True)
+            E2, B2 = sim.fields(pic.FIELD_E), sim.fields(pic.FIELD_B)
+            d2 = sim.diagnostics()
+            assert d2["window_moves"] == m1 + 1 == OW.window_moves(n1 + 1, w.dt, w.dx)
+            o = _oracle_from(w, [s1], E1, B1, np.float32, n1, m1)
+            o.step(1)
+            assert o.moves == m1 + 1
+            g_old, g_new = _split(got)
+            r_old, r_new = _oracle_split(o.species[0])
+            for k in ("id", "ix", "iy", "x", "y", "ux", "uy", "uz"):
+                np.testing.assert_array_equal(g_old[k], r_old[k], err_msg=k)
+            assert g_new == r_new and len(g_new) > 0
+            np.testing.assert_array_equal(got["tile_offset"], o.tile_offsets())
+            peakE = max(np.max(np.abs(o.E)), 1e-30)
+            assert np.max(np.abs(E2 - o.E)) <= 1e-5 * peakE
+            assert np.max(np.abs(B2 - o.B)) <= 1e-5 * max(np.max(np.abs(o.B)), 1e-30)
+            assert d2["status_bits"] == 0
+    assert sum(np.asarray(s1["ix"]) < 0) == 0
+
+
+def test_fast_laser_wakefield_follows_the_fp64_oracle():
+    """60 steps (30 window moves) of a relativistic pulse (a0 = 2) entering the
+    plasma: E and B within 2e-4 of their peak, the particle count equal, the
+    positions of the original particles within 1e-3 cell."""
+    w = wl.laser_wakefield(nx=64, ny=32, k=2, tile=16, a0=2.0, x_start=2.0)
+    steps = 60
+    with pic.Simulation.from_workload(w, flags=pic.PIC_TRACK_IDS) as sim:
+        sim.step(steps)
+        got = sim.particles(0, ids=True)
+        E, B = sim.fields(pic.FIELD_E), sim.fields(pic.FIELD_B)
+        d = sim.diagnostics()
+    sp = oracle.SpeciesState(w.species[0].q_over_m, w.species[0].qtilde, *w.species[0].arrays())
+    sp.pid = np.arange(sp.n, dtype=np.int64)
+    E0, B0 = OW.laser_fields(w.nx, w.ny, w.dx, w.dy, _laser(w.lasers[0]))
+    o = oracle.OracleSim(w.nx, w.ny, w.dx, w.dy, w.dt, w.tile, [sp], dtype=np.float64,
+                         E=E0.astype(np.float32), B=B0.astype(np.float32),
+                         window=[_inject(q) for q in w.window])
+    o.species[0].pid = np.arange(sp.n, dtype=np.int64)
+    o.step(steps)
+    assert d["window_moves"] == o.moves == steps // 2
+    assert d["status_bits"] == 0 and o.status == 0
+    assert d["n_particles"][0] == o.species[0].n
+    assert np.max(np.abs(E - o.E)) <= 2e-4 * np.max(np.abs(o.E))
+    assert np.max(np.abs(B - o.B)) <= 2e-4 * np.max(np.abs(o.B))
+    g_old, _ = _split(got)
+    r_old, _ = _oracle_split(o.species[0])
+    common = np.intersect1d(g_old["id"], r_old["id"])
+    assert common.size > 0.9 * r_old["id"].size
+    gi = np.searchsorted(g_old["id"], common)
+    ri = np.searchsorted(r_old["id"], common)
+    px = (g_old["ix"][gi] + g_old["x"][gi].astype(np.float64)) - (r_old["ix"][ri] + r_old["x"][ri])
+    assert np.max(np.abs(px)) < 1e-3
+    # the laser pushed the plasma: momenta far above round-off
+    assert np.max(np.abs(r_old["uy"])) > 0.1
+
+
+def test_window_refuses_periodic_filters_batches_and_late_calls():
+    w = wl.laser_wakefield(nx=64, ny=32, k=2, tile=16)
+    with pic.Simulation.from_workload(w) as sim:
+        with pytest.raises(pic.PicError):
+            pic.pic_set_binomial_filter(sim.h, 1)
+        with pytest.raises(pic.PicError):
+            pic.pic_set_moving_window(sim.h, None)      # particles already loaded
+        with pytest.raises(pic.PicError):
+            pic.Batch([sim])
+        sim.step(4)
+        assert sim.diagnostics()["status_bits"] == 0
+    cfg = pic.config_for(w)
+    with pic.Simulation(cfg) as sim:
+        pic.pic_set_binomial_filter(sim.h, 1)
+        with pytest.raises(pic.PicError):
+            pic.pic_set_moving_window(sim.h, None)      # a filter is installed
+        pic.pic_set_binomial_filter(sim.h, 0)
+        with pytest.raises(pic.PicError):               # lattice side out of range
+            pic.pic_set_moving_window(sim.h, [dict(k=65)])
+        # plasma in the right half only: the first shift injects a column and
+        # removes nothing, beyond the capacity (= the loaded count)
+        pic.pic_set_moving_window(sim.h, [dict(k=2, x_start=3.2, capacity=10)])
+        ix, iy, x, y = _lattice(64, 32, 2, 3.2, 0.1)
+        z = np.zeros(ix.size, np.float32)
+        pic.pic_load_particles(sim.h, 0, ix, iy, x, y, z, z, z)
+        sim.step(4)
+        with pytest.raises(pic.PicError):
+            pic.pic_sync(sim.h)
