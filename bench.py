@@ -50,6 +50,12 @@ WORKLOADS = {
     # ppc from {4,16,64}, drift U[0.1,0.5], u_th 0.05, per-simulation seeds)
     # stepped as one batch; tiles and threads autotuned per (grid, ppc)
     "batched_64": dict(kind="batch", kw=dict(members=64), tile=0),
+    # laser pulse (a0 = 2, Gaussian, W0 = 3) entering a cold 4x4-ppc plasma that
+    # fills the right half of a 2048x1024 moving window (16.8M particles at
+    # the start, more as the window injects plasma)
+    "laser_wakefield_2048": dict(kind="laser_wakefield",
+                                 kw=dict(nx=2048, ny=1024, k=4, a0=2.0, W0=3.0, steps=500),
+                                 tile=16),
     # learned current denoiser: 256x256 two-stream draws, 2,000 training pairs
     # (64 ppc vs its 1/16 subsample), the denoised 4-ppc run against 64 ppc
     "denoiser": dict(kind="denoiser", kw=dict(nx=256, ny=256, pairs_per_draw=200, draws=10,
@@ -483,6 +489,7 @@ def run_gpu(args, rank, world, local_rank):
     pic.pic_sync(sim.h)
     pic.pic_timing(sim.h, reset=True)
     l0 = pic.pic_kernel_launches(sim.h)
+    n_start = sum(sim.diagnostics()["n_particles"])   # changes with a moving window
     dist = world > 1
     if dist:
         torch.distributed.barrier()
@@ -504,6 +511,10 @@ def run_gpu(args, rank, world, local_rank):
     sim.close()
     del sim
 
+    n_end = sum(d["n_particles"])
+    if w.window is not None:
+        n = 0.5 * (n_start + n_end)   # the count grows about linearly with the injection
+
     # ---- end to end through the C ABI from pinned host buffers ----
     host = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in sp.arrays()]
             for sp in w.species]
@@ -515,8 +526,12 @@ def run_gpu(args, rank, world, local_rank):
         torch.distributed.barrier()
     t0 = time.perf_counter()
     sim = pic.Simulation(pic.config_for(w, w.tile, args.threads, 0), stream.cuda_stream)
+    if w.window is not None:
+        sim.set_moving_window(w.window)
     for k, h in enumerate(host):
         pic.pic_load_particles(sim.h, k, *h)
+    for laser in w.lasers:
+        sim.add_laser(**laser)
     sim.step(args.steps)
     pic.pic_get_fields(sim.h, pic.FIELD_E, fields_out)
     pic.pic_get_fields(sim.h, pic.FIELD_B, fields_out)
@@ -545,12 +560,17 @@ def run_gpu(args, rank, world, local_rank):
     leavers = d["leavers"]
     f_leave = leavers / n if n else 0.0
     step_bytes = 48.0 + 48.0 * f_leave + 96.0 * cells / n
+    config = dict(workload_config(args.workload, w, args.threads),
+                  parallelism=f"replicas x{world}" if world > 1 else "single GPU")
+    if w.window is not None:
+        config.update(moving_window=True, particles_start=n_start, particles_end=n_end,
+                      window_moves=d.get("window_moves"),
+                      particles="mean of start and end (the window injects plasma)")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(workload_config(args.workload, w, args.threads),
-                       parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+        "config": config,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": recorded_traffic(args.workload),
                      "kernel": "k_push (gather+Boris+move+deposit+leaver emission)",

@@ -269,7 +269,9 @@ __device__ __forceinline__ void deposit_warp(bool has, int o, const float v[8], 
 // bar[1..NSTAGE]); fphase is the parity of the next halo phase and gb counts
 // the particle batches taken so far, both carried from item to item.
 // Returns false (after flagging the timeout) if a bounded wait ran out.
-template <int T, bool PW>
+// OPEN: the simulation has a moving window (box open along x); a separate
+// instantiation so that the periodic path carries none of its registers.
+template <int T, bool PW, bool OPEN = false>
 __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorMap* fmap, int t,
                                           int chunk, unsigned& fphase, unsigned& gb) {
     using L = Tile<T, PW>;
@@ -295,7 +297,7 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
     const long long step = *((volatile long long*)&prm.st->step);
     // moving window (open box along x): cells are written in the frame of the
     // window after this step's shift; particles leaving the box are removed
-    const int wshift = g.open_x ? window_shift(step, g) : 0;
+    const int wshift = OPEN ? window_shift(step, g) : 0;
 
     for (int i = tid; i < L::NCNT; i += nth) sDir[i] = 0;
     __syncthreads();
@@ -489,7 +491,7 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
                         // ---- new cell and tile ----
                         int nix = ix + di - wshift, niy = iy + dj;
                         bool gone = false;
-                        if (g.open_x)  // left the box (before or by the shift)
+                        if (OPEN)  // left the box (before or by the shift)
                             gone = nix < 0 || nix >= nx - wshift;
                         else
                             nix = nix < 0 ? nix + nx : (nix >= nx ? nix - nx : nix);
@@ -561,7 +563,7 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
                 if (lane == leader) wbase = atomicAdd(&S.leave[t], __popc(lm));
                 wbase = __shfl_sync(FULL, wbase, leader);
                 slot = wbase + __popc(lm & ((1u << lane) - 1u));
-                if (g.open_x) {
+                if (OPEN) {
                     const unsigned rm = __ballot_sync(FULL, dir == 8);
                     if (rm && lane == leader)
                         atomicAdd(reinterpret_cast<unsigned long long*>(&prm.st->removed[s]),
@@ -642,7 +644,7 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
         const bool deep = whole && lx >= 2 && lx < T - 1 && ly >= 2 && ly < T - 1;
         if (!deep && v == 0.f) continue;
         int i = ix0 + lx, j = iy0 + ly;
-        if (g.open_x && (i < 0 || i >= nx)) continue;  // outside the open box: dropped
+        if (OPEN && (i < 0 || i >= nx)) continue;  // outside the open box: dropped
         i = i < 0 ? i + nx : (i >= nx ? i - nx : i);
         j = j < 0 ? j + ny : (j >= ny ? j - ny : j);
         float* dst = prm.J + comp * g.cstride + (long long)(j + GY) * g.P + (i + GX);
@@ -662,12 +664,12 @@ __device__ __forceinline__ void init_barriers(uint64_t* bar) {
 }
 
 // One simulation: CTA (tile, chunk) = (blockIdx.x, blockIdx.y).
-template <int T, bool PW>
+template <int T, bool PW, bool OPEN>
 __global__ void __launch_bounds__(MAX_PUSH_THREADS, 1) k_push(const __grid_constant__ CUtensorMap fmap,
                                                const PushParams prm) {
     extern __shared__ __align__(128) unsigned char smem[];
     init_barriers(reinterpret_cast<uint64_t*>(smem + Tile<T, PW>::off_misc(blockDim.x)));
-    if (prm.g.open_x && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    if (OPEN && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
         // the window decision of this step, for the re-sort and field kernels
         // that follow (no CTA of this launch reads them)
         const int w = window_shift(*((volatile long long*)&prm.st->step), prm.g);
@@ -675,7 +677,7 @@ __global__ void __launch_bounds__(MAX_PUSH_THREADS, 1) k_push(const __grid_const
         prm.st->win_moves += w;
     }
     unsigned fphase = 0, gb = 0;
-    push_item<T, PW>(prm, &fmap, blockIdx.x, blockIdx.y, fphase, gb);
+    push_item<T, PW, OPEN>(prm, &fmap, blockIdx.x, blockIdx.y, fphase, gb);
 }
 
 // Many simulations in one persistent launch: each CTA takes work items
@@ -720,7 +722,9 @@ static cudaError_t set_smem_limit() {
     size_t b = Tile<T, PW>::bytes_batch(1024);
     if (b > SMEM_MAX) b = SMEM_MAX;
     cudaError_t e =
-        cudaFuncSetAttribute(k_push<T, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+        cudaFuncSetAttribute(k_push<T, PW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_push<T, PW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_push_batch<T, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)b);
@@ -739,10 +743,15 @@ static cudaError_t launch_T(const CUtensorMap* fmap, const PushParams& p, int th
     }
     if (p.g.ntiles == 0) return cudaSuccess;
     const dim3 grid(p.g.ntiles, p.chunks);
-    if (kPW && Tile<T, kPW>::bytes(threads) <= SMEM_MAX)
-        k_push<T, kPW><<<grid, threads, Tile<T, kPW>::bytes(threads), s>>>(*fmap, p);
-    else
-        k_push<T, false><<<grid, threads, Tile<T, false>::bytes(threads), s>>>(*fmap, p);
+    const bool pw = kPW && Tile<T, kPW>::bytes(threads) <= SMEM_MAX;
+    const size_t bytes = pw ? Tile<T, kPW>::bytes(threads) : Tile<T, false>::bytes(threads);
+    if (p.g.open_x) {
+        if (pw) k_push<T, kPW, true><<<grid, threads, bytes, s>>>(*fmap, p);
+        else k_push<T, false, true><<<grid, threads, bytes, s>>>(*fmap, p);
+    } else {
+        if (pw) k_push<T, kPW, false><<<grid, threads, bytes, s>>>(*fmap, p);
+        else k_push<T, false, false><<<grid, threads, bytes, s>>>(*fmap, p);
+    }
     return cudaGetLastError();
 }
 
