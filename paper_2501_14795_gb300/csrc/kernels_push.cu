@@ -685,8 +685,11 @@ __global__ void __launch_bounds__(MAX_PUSH_THREADS, 1) k_push(const __grid_const
 // list is ordered costliest first, so this is greedy longest-first
 // balancing); the item's parameters are copied into shared memory and its
 // TMA descriptor is read from global memory.
+// Two CTAs of 512 threads per SM: the persistent batched kernel keeps the
+// 64-register budget of the single-simulation one (without the bound the
+// item bookkeeping pushes it past 100 registers and to one CTA per SM).
 template <int T, bool PW>
-__global__ void __launch_bounds__(MAX_PUSH_THREADS, 1) k_push_batch(const PushBatch pb) {
+__global__ void __launch_bounds__(MAX_PUSH_THREADS, 2) k_push_batch(const PushBatch pb) {
     using L = Tile<T, PW>;
     extern __shared__ __align__(128) unsigned char smem[];
     init_barriers(reinterpret_cast<uint64_t*>(smem + L::off_misc(blockDim.x)));
