@@ -80,6 +80,26 @@ def workload_config(name, w, threads):
 
 # ------------------------------------------------------------ measurements
 
+def max_over_ranks(*vals):
+    """Each value's maximum over the ranks of the default process group (the
+    slowest replica sets the time of the whole job); the values themselves
+    without a group.  NCCL reduces on the GPU, gloo on the host."""
+    import torch
+    import torch.distributed as td
+    if not (td.is_available() and td.is_initialized()) or td.get_world_size() == 1:
+        return [float(v) for v in vals]
+    dev = "cuda" if td.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=dev)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job_rate(units_per_rank, world, steps, ms_max):
+    """Units every replica processed in `steps` steps over the slowest
+    replica's time in ms (weak scaling: each rank holds the same workload)."""
+    return units_per_rank * world * steps / (ms_max * 1e-3)
+
+
 def read_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -310,9 +330,11 @@ def run_batched(args, rank, world, local_rank):
     eb.close()
     for s in e2e_sims:
         s.close()
+    ms, e2e_ms, seq_ms = max_over_ranks(ms, e2e_s * 1e3, seq_ms)
+    e2e_s = e2e_ms * 1e-3
     if rank != 0:
         return
-    value = n * world * args.steps / (ms * 1e-3)
+    value = whole_job_rate(n, world, args.steps, ms)
     peak, peak_kind = read_peaks()
     f_leave = leavers / n
     step_bytes = 48.0 + 48.0 * f_leave + 96.0 * cells / n
@@ -326,14 +348,14 @@ def run_batched(args, rank, world, local_rank):
                    "autotune_s": tune_s,
                    "l2": f"inputs larger than L2 (particle state {n * 24 / 1e6:.0f} MB > 129 MB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "sequential": {"value": n * args.steps / (seq_ms * 1e-3), "ms_per_step": seq_ms / args.steps,
+        "sequential": {"value": whole_job_rate(n, world, args.steps, seq_ms), "ms_per_step": seq_ms / args.steps,
                        "what": "the same simulations stepped one after another, each its own "
                                "step graph"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "whole batched step (algorithmic bytes of all stages)",
                      "peak_source": f"{peak_kind} hbm_gbs"},
-        "e2e": {"value": n * args.steps / e2e_s, "unit": UNIT,
+        "e2e": {"value": whole_job_rate(n, world, args.steps, e2e_s * 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps},
         "gpu_launches": int(launches),
         "launches_per_step": per_step,
@@ -540,14 +562,11 @@ def run_gpu(args, rank, world, local_rank):
     sim.close()
 
     # ---- max over ranks ----
-    t = torch.tensor([ms, e2e_s * 1e3], dtype=torch.float64, device="cuda")
-    if dist:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms, e2e_ms = float(t[0]), float(t[1])
+    ms, e2e_ms = max_over_ranks(ms, e2e_s * 1e3)
     if rank != 0:
         return
     total = n * world
-    value = total * args.steps / (ms * 1e-3)
+    value = whole_job_rate(n, world, args.steps, ms)
     peak, peak_kind = read_peaks()
     T = w.tile
     cells = w.nx * w.ny
