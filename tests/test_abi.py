@@ -93,3 +93,44 @@ def test_batch_and_tuner_entry_points_check_arguments_without_gpu(lib):
     assert L.pic_init_batch(cfgs, 1, None, hs) == 2 and hs[0] is None
     assert L.pic_init_batch(None, 1, None, hs) == 1
     del good
+
+
+def test_window_and_laser_entry_points_check_arguments_without_gpu(lib):
+    """Null handles answer PIC_EINVAL before any CUDA call; the ABI structs of
+    the binding have the sizes of the C declarations (field by field)."""
+    from paper_2501_14795_gb300 import pic
+    L = pic.load_library()
+    assert L.pic_set_moving_window(None, None) == 1
+    l = pic.pic_laser(pic.PIC_LASER_PLANE, 1.0, 1.0, 1.0, 10.0, 0.0, 1.0, 0.0, 0.0)
+    assert L.pic_add_laser(None, ctypes.byref(l)) == 1
+    assert L.pic_add_laser(None, None) == 1
+
+
+def test_binding_structs_match_the_c_header(tmp_path):
+    """sizeof and offsetof of every ABI struct as gcc lays them out from
+    include/pic.h equal the ctypes mirrors of the binding."""
+    import shutil
+    import subprocess
+    from paper_2501_14795_gb300 import pic
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    structs = {"pic_config": pic.pic_config, "pic_diag": pic.pic_diag,
+               "pic_inject": pic.pic_inject, "pic_laser": pic.pic_laser,
+               "pic_species_cfg": pic.pic_species_cfg}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pic.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "abi"
+    inc = os.path.join(ROOT, "include")
+    subprocess.run(["gcc", "-std=c11", f"-I{inc}", str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
