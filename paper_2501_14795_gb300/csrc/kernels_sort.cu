@@ -97,6 +97,36 @@ __device__ __forceinline__ void copy_particle(const SortSpecies& S, int from_out
     if (track) S.id[to_main] = S.oid[from_out];
 }
 
+// two particles from the out arrays: all loads, then all stores
+__device__ __forceinline__ void copy_two(const SortSpecies& S, int f0, int t0, int f1, int t1,
+                                         int track) {
+    const int c0 = S.ocell[f0], c1 = S.ocell[f1];
+    const float x0 = S.ox[f0], x1 = S.ox[f1], y0 = S.oy[f0], y1 = S.oy[f1];
+    const float a0 = S.oux[f0], a1 = S.oux[f1], b0 = S.ouy[f0], b1 = S.ouy[f1];
+    const float z0 = S.ouz[f0], z1 = S.ouz[f1];
+    int i0 = 0, i1 = 0;
+    if (track) {
+        i0 = S.oid[f0];
+        i1 = S.oid[f1];
+    }
+    S.cell[t0] = c0;
+    S.cell[t1] = c1;
+    S.x[t0] = x0;
+    S.x[t1] = x1;
+    S.y[t0] = y0;
+    S.y[t1] = y1;
+    S.ux[t0] = a0;
+    S.ux[t1] = a1;
+    S.uy[t0] = b0;
+    S.uy[t1] = b1;
+    S.uz[t0] = z0;
+    S.uz[t1] = z1;
+    if (track) {
+        S.id[t0] = i0;
+        S.id[t1] = i1;
+    }
+}
+
 constexpr int SCAN_THREADS = 1024;
 
 // Step 1 of §4.3 for tile t of species s: the tile's new count = its stayers
@@ -360,27 +390,41 @@ __device__ __forceinline__ void fill_tile(const SortParams& prm, int s, int t, i
         ex[k] = __shfl_sync(0xffffffffu, pre - nl, k);
         qq[k] = __shfl_sync(0xffffffffu, q0, k);
     }
-    for (int base = 0; base < total; base += 32) {
-        const int e = base + lane;
-        bool take = false;
-        int src = 0;
-        if (e < total) {
-            // the list holding e: the last one starting at or before it (lists
-            // of length 0 share their start with the next one)
-            int k = 0;
+    // the list holding entry e: the last one starting at or before it (lists
+    // of length 0 share their start with the next one)
+    auto source_of = [&](int e) {
+        int q = qq[0], x = ex[0];  // selects, not an indexed array: stays in registers
 #pragma unroll
-            for (int j = 1; j < 8; ++j)
-                if (ex[j] <= e) k = j;
-            src = qq[k] + (e - ex[k]);
-            take = tile_of(S.ocell[src], T, g.ntx) == t;
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, take);
-        if (take) {
-            const int slot = nsrc + __popc(m & lt);
-            if (slot < cap) S.isrc[r0 + slot] = src;
+        for (int j = 1; j < 8; ++j)
+            if (ex[j] <= e) {
+                q = qq[j];
+                x = ex[j];
+            }
+        return q + (e - x);
+    };
+    // two chunks of 32 entries per round: both chunks' cell loads are in
+    // flight together (the fill is bound by memory latency, not bandwidth)
+    for (int base = 0; base < total; base += 64) {
+        const int e0 = base + lane, e1 = e0 + 32;
+        const int src0 = e0 < total ? source_of(e0) : 0;
+        const int src1 = e1 < total ? source_of(e1) : 0;
+        const int c0 = e0 < total ? S.ocell[src0] : HOLE;
+        const int c1 = e1 < total ? S.ocell[src1] : HOLE;
+        const bool take0 = e0 < total && tile_of(c0, T, g.ntx) == t;
+        const bool take1 = e1 < total && tile_of(c1, T, g.ntx) == t;
+        const unsigned m0 = __ballot_sync(0xffffffffu, take0);
+        const unsigned m1 = __ballot_sync(0xffffffffu, take1);
+        if (take0) {
+            const int slot = nsrc + __popc(m0 & lt);
+            if (slot < cap) S.isrc[r0 + slot] = src0;
             else overflow = true;
         }
-        nsrc += __popc(m);
+        if (take1) {
+            const int slot = nsrc + __popc(m0) + __popc(m1 & lt);
+            if (slot < cap) S.isrc[r0 + slot] = src1;
+            else overflow = true;
+        }
+        nsrc += __popc(m0) + __popc(m1);
     }
     // ... plus this tile's displaced stayers
     for (int base = 0; base < ev; base += 32) {
@@ -437,11 +481,23 @@ __device__ __forceinline__ void fill_tile(const SortParams& prm, int s, int t, i
         if (lane == 0) dev::set_status(prm.st, ST_SORT);
         return;
     }
-    // move source -> target
-    for (int k = lane; k < nsrc; k += 32) {
-        const int src = S.isrc[r0 + k];
-        if (src >= 0) copy_particle(S, src, S.fslot[r0 + k], prm.track_ids);
-        else inject_particle(prm, S, t, inj, -1 - src, S.fslot[r0 + k]);
+    // move source -> target, two particles per lane and round with all their
+    // loads issued before the stores
+    for (int k = lane; k < nsrc; k += 64) {
+        const bool two = k + 32 < nsrc;
+        const int src0 = S.isrc[r0 + k], to0 = S.fslot[r0 + k];
+        const int src1 = two ? S.isrc[r0 + k + 32] : -1;
+        const int to1 = two ? S.fslot[r0 + k + 32] : 0;
+        if (src0 >= 0 && src1 >= 0) {
+            copy_two(S, src0, to0, src1, to1, prm.track_ids);
+        } else {
+            if (src0 >= 0) copy_particle(S, src0, to0, prm.track_ids);
+            else inject_particle(prm, S, t, inj, -1 - src0, to0);
+            if (two) {
+                if (src1 >= 0) copy_particle(S, src1, to1, prm.track_ids);
+                else inject_particle(prm, S, t, inj, -1 - src1, to1);
+            }
+        }
     }
 }
 
