@@ -178,7 +178,9 @@ __device__ __forceinline__ void yee_tile(const YeeParams& prm, int bx, int by) {
     if (tid == 0) atomicAdd(&prm.hist_b[n & (HIST - 1)], 0.5 * sb * dxdy);
 }
 
-__global__ void __launch_bounds__(YTHREADS) k_yee(const YeeParams prm) {
+// 6 CTAs of 256 threads per SM (42 registers): the kernel waits on memory,
+// more warps in flight hide more of it.
+__global__ void __launch_bounds__(YTHREADS, 6) k_yee(const YeeParams prm) {
     yee_tile(prm, blockIdx.x, blockIdx.y);
 }
 
@@ -567,6 +569,17 @@ cudaError_t launch_yee_batch(const YeeBatch& b, cudaStream_t s) {
     if (b.nmembers == 0 || b.total_ytiles == 0) return cudaSuccess;
     k_yee_batch<<<b.total_ytiles, YTHREADS, 0, s>>>(b);
     return cudaGetLastError();
+}
+
+// Once per process, before any capture: the Yee kernels prefer the largest
+// shared-memory carveout (22 KB of static shared memory per CTA).
+cudaError_t init_grid_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(k_yee, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_yee_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    return e;
 }
 
 cudaError_t launch_yee(const YeeParams& p, cudaStream_t s) {

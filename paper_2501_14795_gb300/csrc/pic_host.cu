@@ -553,7 +553,8 @@ pic_status pic_init(const pic_config* cfg, void* cuda_stream, pic_sim** out) {
         memset(&p0, 0, sizeof p0);
         p0.g = g;
         if (launch_push_fast(nullptr, p0, c.threads, sim->stream) != cudaSuccess ||
-            launch_push_strict(nullptr, p0, c.threads, sim->stream) != cudaSuccess)
+            launch_push_strict(nullptr, p0, c.threads, sim->stream) != cudaSuccess ||
+            init_grid_kernels() != cudaSuccess)
             return cleanup_fail(PIC_ECUDA, "smem attribute", e);
     }
     if (cudaStreamCreateWithFlags(&sim->cap_stream, cudaStreamNonBlocking) != cudaSuccess)

@@ -224,6 +224,7 @@ cudaError_t launch_scan(const SortParams& p, cudaStream_t s);
 cudaError_t launch_evict(const SortParams& p, int threads, cudaStream_t s);
 cudaError_t launch_fill(const SortParams& p, int threads, cudaStream_t s);
 cudaError_t launch_yee(const YeeParams& p, cudaStream_t s);
+cudaError_t init_grid_kernels();  // kernel attributes, once before any capture
 
 // grid utilities
 cudaError_t launch_set_grid(const Geom& g, float* F, int ncomp, const float* src, cudaStream_t s);

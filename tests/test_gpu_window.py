@@ -253,3 +253,30 @@ def test_window_refuses_periodic_filters_batches_and_late_calls():
         sim.step(4)
         with pytest.raises(pic.PicError):
             pic.pic_sync(sim.h)
+
+
+def test_retiling_and_autotuning_keep_the_window_state():
+    """Re-tiling and the autotuner (which saves, times and restores the state)
+    on a moving-window run: afterwards it steps like an untouched twin (same
+    counts and window position, fields within FP32 summation-order noise)."""
+    w = wl.laser_wakefield(nx=64, ny=32, k=2, tile=16, a0=2.0, x_start=2.0)
+    with pic.Simulation.from_workload(w) as a, pic.Simulation.from_workload(w) as b:
+        a.step(5)
+        b.step(5)
+        b.set_tiling(8)
+        b.step(4)
+        b.set_tiling(16, 128)
+        a.step(4)
+        T, nthr, _ = b.autotune(steps=2, force=True)
+        a.step(10)
+        b.step(10)
+        da, db = a.diagnostics(), b.diagnostics()
+        assert da["status_bits"] == db["status_bits"] == 0
+        assert da["window_moves"] == db["window_moves"] == OW.window_moves(19, w.dt, w.dx)
+        assert da["n_particles"] == db["n_particles"]
+        Ea, Eb = a.fields(pic.FIELD_E), b.fields(pic.FIELD_E)
+        assert np.max(np.abs(Ea - Eb)) <= 1e-4 * np.max(np.abs(Ea))
+        pa, pb = a.particles(0), b.particles(0)
+        ka = sorted(zip(pa["ix"].tolist(), pa["iy"].tolist()))
+        kb = sorted(zip(pb["ix"].tolist(), pb["iy"].tolist()))
+        assert sum(x != y for x, y in zip(ka, kb)) < 0.01 * len(ka)
