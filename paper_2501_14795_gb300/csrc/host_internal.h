@@ -19,6 +19,7 @@ struct pic_sim {
     float* F[2] = {nullptr, nullptr};  // E|B, ping-pong
     float* J[2] = {nullptr, nullptr};  // current, ping-pong
     CUtensorMap fmap[2];
+    CUtensorMap ymapF[2], ymapJ[2];    // the field kernel's boxes of F[b] and J[b]
     float* gtmp = nullptr;             // 3*nx*ny staging for set/get
     double* rho = nullptr;             // nx*ny FP64 charge density (no background)
     double* rho_prev = nullptr;

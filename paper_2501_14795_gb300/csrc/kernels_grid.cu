@@ -31,58 +31,43 @@ constexpr int EW = YX + 3, EH = YY + 3;
 constexpr int BW = YX + 2, BH = YY + 2;
 constexpr int JWY = YX + 1, JHY = YY + 1;
 
-__device__ __forceinline__ void yee_tile(const YeeParams& prm, int bx, int by) {
-    __shared__ float sE[3][EH][EW];
-    __shared__ float sB[3][BH][BW];
-    __shared__ float sJ[3][JHY][JWY];
-    __shared__ double sRed[32];
+// Shared-memory layouts of the Yee halos: local (q, r) is cell (i0-1+q,
+// j0-1+r) for E and B and (i0+q, j0+r) for J.
+struct YeePlain {  // the plain-load kernel's arrays [3][EH][EW], [3][BH][BW], [3][JHY][JWY]
+    static __device__ __forceinline__ int e(int c, int r, int q) { return (c * EH + r) * EW + q; }
+    static __device__ __forceinline__ int b(int c, int r, int q) { return (c * BH + r) * BW + q; }
+    static __device__ __forceinline__ int j(int c, int r, int q) { return (c * JHY + r) * JWY + q; }
+};
+// TMA boxes: E and B as [3][19][40] from cell (i0-4, j0-1) (the box's x origin
+// on a 16-byte boundary), J as [3][17][36] from cell (i0, j0)
+constexpr int TEW = 40, TEH = 19, TJW = 36, TJH = 17;
+struct YeeTma {
+    static __device__ __forceinline__ int e(int c, int r, int q) { return (c * TEH + r) * TEW + q + 3; }
+    static __device__ __forceinline__ int b(int c, int r, int q) { return (c * TEH + r) * TEW + q + 3; }
+    static __device__ __forceinline__ int j(int c, int r, int q) { return (c * TJH + r) * TJW + q; }
+};
+
+// The three sub-steps and the write-out of tile (i0, j0) from its halos in
+// shared memory (updated in place); the tile's field energies are added to
+// we, wb.  Every thread of the CTA calls it.
+template <class LAY>
+__device__ __forceinline__ void yee_body(const YeeParams& prm, int i0, int j0, float* sE,
+                                         float* sB, const float* sJ, float& we, float& wb) {
     const Geom& g = prm.g;
-    const int i0 = bx * YX, j0 = by * YY;
     const int tid = threadIdx.x;
     const long long cs = g.cstride;
-    const float* Ein = prm.Fin;
-    const float* Bin = prm.Fin + 3 * cs;
-
-    for (int k = tid; k < EW * EH; k += YTHREADS) {
-        const int r = k / EW, q = k - r * EW;
-        const int i = i0 - 1 + q, j = j0 - 1 + r;
-        const bool in = i <= g.nx + 1 && j <= g.ny + 1;
-        const long long o = gidx(g, i, j);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) sE[c][r][q] = in ? Ein[c * cs + o] : 0.f;
-    }
-    for (int k = tid; k < BW * BH; k += YTHREADS) {
-        const int r = k / BW, q = k - r * BW;
-        const int i = i0 - 1 + q, j = j0 - 1 + r;
-        const bool in = i <= g.nx + 1 && j <= g.ny + 1;
-        const long long o = gidx(g, i, j);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) sB[c][r][q] = in ? Bin[c * cs + o] : 0.f;
-    }
-    for (int k = tid; k < JWY * JHY; k += YTHREADS) {
-        const int r = k / JWY, q = k - r * JWY;
-        int i = i0 + q, j = j0 + r;
-        i = i >= g.nx ? i - g.nx : i;
-        j = j >= g.ny ? j - g.ny : j;
-        const bool in = i < g.nx && j < g.ny;
-        const long long o = gidx(g, i, j);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) sJ[c][r][q] = in ? prm.J[c * cs + o] : 0.f;
-    }
-    __syncthreads();
-
     const float hx = g.hdt_dx, hy = g.hdt_dy;
     const bool open = g.open_x != 0;
     // B half step on [-1, YX+1) x [-1, YY+1): local (q, r) <-> cell (i0-1+q, j0-1+r)
     for (int k = tid; k < BW * BH; k += YTHREADS) {
         const int r = k / BW, q = k - r * BW;
         if (open && (i0 - 1 + q < 0 || i0 - 1 + q >= g.nx)) {  // outside the open box
-            sB[0][r][q] = sB[1][r][q] = sB[2][r][q] = 0.f;
+            sB[LAY::b(0, r, q)] = sB[LAY::b(1, r, q)] = sB[LAY::b(2, r, q)] = 0.f;
             continue;
         }
-        sB[0][r][q] -= hy * (sE[2][r + 1][q] - sE[2][r][q]);
-        sB[1][r][q] += hx * (sE[2][r][q + 1] - sE[2][r][q]);
-        sB[2][r][q] -= hx * (sE[1][r][q + 1] - sE[1][r][q]) - hy * (sE[0][r + 1][q] - sE[0][r][q]);
+        sB[LAY::b(0, r, q)] -= hy * (sE[LAY::e(2, r + 1, q)] - sE[LAY::e(2, r, q)]);
+        sB[LAY::b(1, r, q)] += hx * (sE[LAY::e(2, r, q + 1)] - sE[LAY::e(2, r, q)]);
+        sB[LAY::b(2, r, q)] -= hx * (sE[LAY::e(1, r, q + 1)] - sE[LAY::e(1, r, q)]) - hy * (sE[LAY::e(0, r + 1, q)] - sE[LAY::e(0, r, q)]);
     }
     __syncthreads();
     // E full step on cells [0, YX+1) x [0, YY+1): E at (q+1, r+1), B at (q+1, r+1)
@@ -91,17 +76,16 @@ __device__ __forceinline__ void yee_tile(const YeeParams& prm, int bx, int by) {
         const int r = k / JWY, q = k - r * JWY;
         const int e = q + 1, f = r + 1;
         if (open && i0 + q >= g.nx) {
-            sE[0][f][e] = sE[1][f][e] = sE[2][f][e] = 0.f;
+            sE[LAY::e(0, f, e)] = sE[LAY::e(1, f, e)] = sE[LAY::e(2, f, e)] = 0.f;
             continue;
         }
-        sE[0][f][e] += dty * (sB[2][f][e] - sB[2][f - 1][e]) - dt * sJ[0][r][q];
-        sE[1][f][e] += -dtx * (sB[2][f][e] - sB[2][f][e - 1]) - dt * sJ[1][r][q];
-        sE[2][f][e] += dtx * (sB[1][f][e] - sB[1][f][e - 1]) -
-                       dty * (sB[0][f][e] - sB[0][f - 1][e]) - dt * sJ[2][r][q];
+        sE[LAY::e(0, f, e)] += dty * (sB[LAY::b(2, f, e)] - sB[LAY::b(2, f - 1, e)]) - dt * sJ[LAY::j(0, r, q)];
+        sE[LAY::e(1, f, e)] += -dtx * (sB[LAY::b(2, f, e)] - sB[LAY::b(2, f, e - 1)]) - dt * sJ[LAY::j(1, r, q)];
+        sE[LAY::e(2, f, e)] += dtx * (sB[LAY::b(1, f, e)] - sB[LAY::b(1, f, e - 1)]) -
+                       dty * (sB[LAY::b(0, f, e)] - sB[LAY::b(0, f - 1, e)]) - dt * sJ[LAY::j(2, r, q)];
     }
     __syncthreads();
     // B second half step on the tile, write out with images, energies, J ring
-    float we = 0.f, wb = 0.f;
     float* Eout = prm.Fout;
     float* Bout = prm.Fout + 3 * cs;
     const int T = g.T;
@@ -111,11 +95,11 @@ __device__ __forceinline__ void yee_tile(const YeeParams& prm, int bx, int by) {
         const int i = i0 + q, j = j0 + r;
         if (i >= g.nx || j >= g.ny) continue;
         const int e = q + 1, f = r + 1;
-        float bx = sB[0][f][e] - hy * (sE[2][f + 1][e] - sE[2][f][e]);
-        float by = sB[1][f][e] + hx * (sE[2][f][e + 1] - sE[2][f][e]);
-        float bz = sB[2][f][e] - (hx * (sE[1][f][e + 1] - sE[1][f][e]) -
-                                  hy * (sE[0][f + 1][e] - sE[0][f][e]));
-        const float ex = sE[0][f][e], ey = sE[1][f][e], ez = sE[2][f][e];
+        float bx = sB[LAY::b(0, f, e)] - hy * (sE[LAY::e(2, f + 1, e)] - sE[LAY::e(2, f, e)]);
+        float by = sB[LAY::b(1, f, e)] + hx * (sE[LAY::e(2, f, e + 1)] - sE[LAY::e(2, f, e)]);
+        float bz = sB[LAY::b(2, f, e)] - (hx * (sE[LAY::e(1, f, e + 1)] - sE[LAY::e(1, f, e)]) -
+                                  hy * (sE[LAY::e(0, f + 1, e)] - sE[LAY::e(0, f, e)]));
+        const float ex = sE[LAY::e(0, f, e)], ey = sE[LAY::e(1, f, e)], ez = sE[LAY::e(2, f, e)];
         we += ex * ex + ey * ey + ez * ez;
         wb += bx * bx + by * by + bz * bz;
         // images: i' in {i, i+nx if i<2, i-nx if i==nx-1}, same for j
@@ -169,6 +153,142 @@ __device__ __forceinline__ void yee_tile(const YeeParams& prm, int bx, int by) {
             prm.Jnext[cs + o] = 0.f;
             prm.Jnext[2 * cs + o] = 0.f;
         }
+    }
+}
+
+__device__ __forceinline__ void yee_tile(const YeeParams& prm, int bx, int by) {
+    __shared__ float sE[3 * EH * EW];
+    __shared__ float sB[3 * BH * BW];
+    __shared__ float sJ[3 * JHY * JWY];
+    __shared__ double sRed[32];
+    const Geom& g = prm.g;
+    const int i0 = bx * YX, j0 = by * YY;
+    const int tid = threadIdx.x;
+    const long long cs = g.cstride;
+    const float* Ein = prm.Fin;
+    const float* Bin = prm.Fin + 3 * cs;
+
+    for (int k = tid; k < EW * EH; k += YTHREADS) {
+        const int r = k / EW, q = k - r * EW;
+        const int i = i0 - 1 + q, j = j0 - 1 + r;
+        const bool in = i <= g.nx + 1 && j <= g.ny + 1;
+        const long long o = gidx(g, i, j);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sE[YeePlain::e(c, r, q)] = in ? Ein[c * cs + o] : 0.f;
+    }
+    for (int k = tid; k < BW * BH; k += YTHREADS) {
+        const int r = k / BW, q = k - r * BW;
+        const int i = i0 - 1 + q, j = j0 - 1 + r;
+        const bool in = i <= g.nx + 1 && j <= g.ny + 1;
+        const long long o = gidx(g, i, j);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sB[YeePlain::b(c, r, q)] = in ? Bin[c * cs + o] : 0.f;
+    }
+    for (int k = tid; k < JWY * JHY; k += YTHREADS) {
+        const int r = k / JWY, q = k - r * JWY;
+        int i = i0 + q, j = j0 + r;
+        i = i >= g.nx ? i - g.nx : i;
+        j = j >= g.ny ? j - g.ny : j;
+        const bool in = i < g.nx && j < g.ny;
+        const long long o = gidx(g, i, j);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sJ[YeePlain::j(c, r, q)] = in ? prm.J[c * cs + o] : 0.f;
+    }
+    __syncthreads();
+    float we = 0.f, wb = 0.f;
+    yee_body<YeePlain>(prm, i0, j0, sE, sB, sJ, we, wb);
+    const double dxdy = g.dx * g.dy;
+    const long long n = *((volatile long long*)&prm.st->step);
+    const double se = dev::block_sum((double)we, sRed);
+    if (tid == 0) atomicAdd(&prm.hist_e[n & (HIST - 1)], 0.5 * se * dxdy);
+    const double sb = dev::block_sum((double)wb, sRed);
+    if (tid == 0) atomicAdd(&prm.hist_b[n & (HIST - 1)], 0.5 * sb * dxdy);
+}
+
+// One simulation, persistent: CTA k takes Yee tiles k, k + gridDim.x, ...;
+// each tile's E|B and J halos come in by three TMA boxes into one of two
+// stages while the other stage is being computed.  J's guard cells hold no
+// images, so the J values of cells nx and ny (which the E step needs at the
+// tile edges) are patched in from cells 0 after the copy.
+// bytes each stage receives, and its layout with every box on a 128-byte boundary
+constexpr unsigned TBOX_E = 3 * TEH * TEW * 4, TBOX_J = 3 * TJH * TJW * 4;  // 9120, 7344
+constexpr unsigned TTX_BYTES = 2 * TBOX_E + TBOX_J;
+constexpr int TOFF_B = ((TBOX_E + 127) / 128) * 128 / 4;        // floats
+constexpr int TOFF_J = 2 * TOFF_B;
+constexpr int TSTAGE_FLOATS = TOFF_J + ((TBOX_J + 127) / 128) * 128 / 4;
+constexpr unsigned TSTAGE_BYTES = TSTAGE_FLOATS * 4;
+constexpr size_t YEE_TMA_SMEM = 2 * (size_t)TSTAGE_BYTES + 64 + 32 * sizeof(double);
+static_assert(TSTAGE_BYTES % 128 == 0, "stages on 128-byte boundaries");
+
+__global__ void __launch_bounds__(YTHREADS) k_yee_tma(const __grid_constant__ CUtensorMap mapF,
+                                                     const __grid_constant__ CUtensorMap mapJ,
+                                                     const YeeParams prm) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    float* stage0 = reinterpret_cast<float*>(smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * (size_t)TSTAGE_BYTES);
+    double* sRed = reinterpret_cast<double*>(smem + 2 * (size_t)TSTAGE_BYTES + 64);
+    const Geom& g = prm.g;
+    const int tid = threadIdx.x;
+    const long long cs = g.cstride;
+    const int nbx = (g.nx + YX - 1) / YX, nt = nbx * ((g.ny + YY - 1) / YY);
+    if (tid == 0) {
+        dev::mbar_init(bar, 1);
+        dev::mbar_init(bar + 1, 1);
+        dev::fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t, int st) {
+        float* dst = stage0 + st * TSTAGE_FLOATS;
+        const int i0 = (t % nbx) * YX, j0 = (t / nbx) * YY;
+        dev::mbar_arrive_expect_tx(bar + st, TTX_BYTES);
+        // column i0 of the array is cell i0 - GX = i0 - 4; row j0 is cell j0 - 1
+        dev::tma_load_3d(dst, &mapF, i0, j0, 0, bar + st);                    // E
+        dev::tma_load_3d(dst + TOFF_B, &mapF, i0, j0, 3, bar + st);           // B
+        dev::tma_load_3d(dst + TOFF_J, &mapJ, i0 + GX, j0 + GY, 0, bar + st); // J
+    };
+    if (tid == 0) {
+        if ((int)blockIdx.x < nt) issue(blockIdx.x, 0);
+        if ((int)(blockIdx.x + gridDim.x) < nt) issue(blockIdx.x + gridDim.x, 1);
+    }
+    float we = 0.f, wb = 0.f;
+    bool ok = true;
+    int it = 0;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x, ++it) {
+        const int st = it & 1;
+        float* sE = stage0 + st * TSTAGE_FLOATS;
+        float* sB = sE + TOFF_B;
+        float* sJ = sE + TOFF_J;
+        const int i0 = (t % nbx) * YX, j0 = (t / nbx) * YY;
+        if (!dev::mbar_wait_bounded(bar + st, (it >> 1) & 1u)) ok = false;
+        if (__syncthreads_or(!ok)) break;
+        // J at cells nx (periodic box) and ny: the images of cells 0
+        if (!g.open_x && i0 <= g.nx && g.nx <= i0 + YX)
+            for (int k = tid; k < 3 * JHY; k += YTHREADS) {
+                const int c = k / JHY, r = k - c * JHY;
+                int j = j0 + r;
+                j = j >= g.ny ? j - g.ny : j;
+                sJ[YeeTma::j(c, r, g.nx - i0)] = prm.J[c * cs + gidx(g, 0, j)];
+            }
+        if (j0 <= g.ny && g.ny <= j0 + YY)
+            for (int k = tid; k < 3 * JWY; k += YTHREADS) {
+                const int c = k / JWY, q = k - c * JWY;
+                int i = i0 + q;
+                if (i >= g.nx && (g.open_x || i > g.nx)) continue;  // only cells < nx, and nx when periodic
+                i = i >= g.nx ? i - g.nx : i;
+                sJ[YeeTma::j(c, g.ny - j0, q)] = prm.J[c * cs + gidx(g, i, 0)];
+            }
+        __syncthreads();
+        yee_body<YeeTma>(prm, i0, j0, sE, sB, sJ, we, wb);
+        __syncthreads();  // every thread is done with this stage
+        const int nxt = t + 2 * gridDim.x;
+        if (tid == 0 && nxt < nt) {
+            dev::fence_proxy_async_smem();  // the generic writes above before the async overwrite
+            issue(nxt, st);
+        }
+    }
+    if (!ok) {
+        if (tid == 0) dev::set_status(prm.st, ST_TIMEOUT);
+        return;
     }
     const double dxdy = g.dx * g.dy;
     const long long n = *((volatile long long*)&prm.st->step);
@@ -571,6 +691,8 @@ cudaError_t launch_yee_batch(const YeeBatch& b, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+static int g_yee_grid = 0;  // persistent CTAs of k_yee_tma (set once)
+
 // Once per process, before any capture: the Yee kernels prefer the largest
 // shared-memory carveout (22 KB of static shared memory per CTA).
 cudaError_t init_grid_kernels() {
@@ -579,10 +701,29 @@ cudaError_t init_grid_kernels() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_yee_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_yee_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)YEE_TMA_SMEM);
+    if (e == cudaSuccess && g_yee_grid == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_yee_tma, YTHREADS,
+                                                              YEE_TMA_SMEM);
+        if (e == cudaSuccess) g_yee_grid = sms * (per_sm > 0 ? per_sm : 1);
+    }
     return e;
 }
 
-cudaError_t launch_yee(const YeeParams& p, cudaStream_t s) {
+cudaError_t launch_yee(const YeeParams& p, const CUtensorMap* mapF, const CUtensorMap* mapJ,
+                       cudaStream_t s) {
+    const int nt = yee_tiles(p.g);
+    if (mapF && mapJ && g_yee_grid > 0) {
+        const int grid = nt < g_yee_grid ? nt : g_yee_grid;
+        k_yee_tma<<<grid, YTHREADS, YEE_TMA_SMEM, s>>>(*mapF, *mapJ, p);
+        return cudaGetLastError();
+    }
     dim3 grid((p.g.nx + YX - 1) / YX, (p.g.ny + YY - 1) / YY);
     k_yee<<<grid, YTHREADS, 0, s>>>(p);
     return cudaGetLastError();

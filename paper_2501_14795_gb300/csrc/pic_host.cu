@@ -73,6 +73,27 @@ bool make_field_map(CUtensorMap* map, const Geom& g, float* base) {
     return r == CUDA_SUCCESS;
 }
 
+// The field kernel's TMA boxes: E or B of F (3 of its 6 components) as
+// 40 x 19 x 3 and J as 36 x 17 x 3 (the x extents multiples of 16 bytes).
+bool make_yee_maps(CUtensorMap* mapF, CUtensorMap* mapJ, const Geom& g, float* F, float* J) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t strides[2] = {(cuuint64_t)g.P * 4, (cuuint64_t)g.cstride * 4};
+    cuuint32_t estr[3] = {1, 1, 1};
+    cuuint64_t dF[3] = {(cuuint64_t)g.P, (cuuint64_t)g.R, 6};
+    cuuint32_t bF[3] = {40, 19, 3};
+    CUresult r = enc(mapF, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, F, dF, strides, bF, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    cuuint64_t dJ[3] = {(cuuint64_t)g.P, (cuuint64_t)g.R, 3};
+    cuuint32_t bJ[3] = {36, 17, 3};
+    r = enc(mapJ, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, J, dJ, strides, bJ, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // Geometry of a configuration (tile size included).
 void set_geometry(Geom& g, const pic_config& c) {
     g.nx = c.nx;
@@ -276,7 +297,7 @@ int enqueue_step(pic_sim* sim, cudaStream_t s, int b, cudaEvent_t ev_a, cudaEven
         if (k < 0) return -1;
         n += k;
     }
-    if ((e = launch_yee(yp, s)) != cudaSuccess) goto bad;
+    if ((e = launch_yee(yp, &sim->ymapF[b], &sim->ymapJ[b], s)) != cudaSuccess) goto bad;
     n += 1;
     return n;
 bad:
@@ -546,7 +567,9 @@ pic_status pic_init(const pic_config* cfg, void* cuda_stream, pic_sim** out) {
     if (e != cudaSuccess) return cleanup_fail(e == cudaErrorMemoryAllocation ? PIC_ENOMEM : PIC_ECUDA,
                                               "alloc", e);
     for (int b = 0; b < 2; ++b)
-        if (!make_field_map(&sim->fmap[b], g, sim->F[b])) return cleanup_fail(PIC_ECUDA, "tmap", e);
+        if (!make_field_map(&sim->fmap[b], g, sim->F[b]) ||
+            !make_yee_maps(&sim->ymapF[b], &sim->ymapJ[b], g, sim->F[b], sim->J[b]))
+            return cleanup_fail(PIC_ECUDA, "tmap", e);
     {
         // raise the particle kernels' shared-memory limit before any capture
         PushParams p0;

@@ -223,7 +223,10 @@ cudaError_t launch_binomial(const Geom& g, float* J, float* tmp, cudaStream_t s)
 cudaError_t launch_scan(const SortParams& p, cudaStream_t s);
 cudaError_t launch_evict(const SortParams& p, int threads, cudaStream_t s);
 cudaError_t launch_fill(const SortParams& p, int threads, cudaStream_t s);
-cudaError_t launch_yee(const YeeParams& p, cudaStream_t s);
+// field advance; with both tensor maps (E|B of the input parity: 3D box 40 x
+// 19 x 3; J: box 36 x 17 x 3) the persistent TMA kernel, else one CTA per tile
+cudaError_t launch_yee(const YeeParams& p, const CUtensorMap* mapF, const CUtensorMap* mapJ,
+                       cudaStream_t s);
 cudaError_t init_grid_kernels();  // kernel attributes, once before any capture
 
 // grid utilities
