@@ -442,7 +442,7 @@ def run_denoiser(args, rank, world, local_rank):
     # step times of 64 ppc, 4 ppc and denoised 4 ppc
     by_grid = {}
     d0 = dn.draws(1, offset=500)[0]
-    for side in (512, 1024):
+    for side in (512, 1024, 2048):
         big = pic.Denoiser(side, side, 1, scale)
         big.set_params(net.params())
         row = {}
