@@ -343,11 +343,12 @@ pic_status pic_set_tiling(pic_sim* sim, int tile, int threads);
  * samples in the field layout of the header comment (3 x ny x nx FP32 each).
  * A handle is not thread-safe; its work is ordered on `cuda_stream`, and while
  * it is installed in a simulation it also runs on that simulation's stream.
- * Convolutions whose rows are multiples of 128 pixels run on the tcgen05
- * tensor-core kernel when the launch is large (>= 600 work units of 2 x 128
- * pixels), else on an mma.sync kernel; the environment variable
- * PIC_DENOISER_TC=always, read at creation, selects the tcgen05 kernel
- * whenever the shape allows (used by the tests). */
+ * Convolutions whose rows are multiples of 128 pixels and with at least 17
+ * output channels run on the tcgen05 tensor-core kernel when the launch is
+ * large (>= 600 work units of 2 x 128 pixels), else on an mma.sync kernel;
+ * the environment variable PIC_DENOISER_TC, read at creation, selects the
+ * tcgen05 kernel whenever the shape allows (=always, used by the tests) or
+ * never (=never). */
 typedef struct pic_denoiser pic_denoiser;
 
 int64_t pic_denoiser_num_params(void);

@@ -71,7 +71,7 @@ struct pic_denoiser {
     double* dloss = nullptr;
     unsigned* status = nullptr;      // device word: bit 2 = a bounded wait in a kernel ran out
     unsigned* cur_status = nullptr;  // where the next launches report (own word or a simulation's)
-    int force_tc = 0;                // PIC_DENOISER_TC=always: tensor-core path whenever possible
+    int force_tc = 0;                // PIC_DENOISER_TC: always (1) / never (-1) the tcgen05 path
     // host-buffer staging
     float *stage_in = nullptr, *stage_t = nullptr;
     std::vector<void*> allocs;
@@ -425,7 +425,8 @@ pic_status pic_denoiser_create(int nx, int ny, int batch_max, double scale, void
     d->Bmax = batch_max;
     d->scale = scale;
     d->stream = (cudaStream_t)cuda_stream;
-    if (const char* v = getenv("PIC_DENOISER_TC")) d->force_tc = strcmp(v, "always") == 0;
+    if (const char* v = getenv("PIC_DENOISER_TC"))
+        d->force_tc = strcmp(v, "always") == 0 ? 1 : (strcmp(v, "never") == 0 ? -1 : 0);
     build_table(d);
     const long long P1 = P0 / 4, P2 = P0 / 16;
     cudaError_t e = cudaSuccess;
