@@ -191,7 +191,7 @@ def test_strict_window_shifting_step_is_bit_exact_with_fp32_oracle(tile, chunk, 
 
 def test_fast_laser_wakefield_follows_the_fp64_oracle():
     """60 steps (30 window moves) of a relativistic pulse (a0 = 2) entering the
-    plasma: E and B within 2e-4 of their peak, the particle count equal, the
+    plasma: E and B within 5e-6 of their peak, the particle count equal, the
     positions of the original particles within 1e-3 cell."""
     w = wl.laser_wakefield(nx=64, ny=32, k=2, tile=16, a0=2.0, x_start=2.0)
     steps = 60
@@ -211,8 +211,10 @@ def test_fast_laser_wakefield_follows_the_fp64_oracle():
     assert d["window_moves"] == o.moves == steps // 2
     assert d["status_bits"] == 0 and o.status == 0
     assert d["n_particles"][0] == o.species[0].n
-    assert np.max(np.abs(E - o.E)) <= 2e-4 * np.max(np.abs(o.E))
-    assert np.max(np.abs(B - o.B)) <= 2e-4 * np.max(np.abs(o.B))
+    eE = np.max(np.abs(E - o.E)) / np.max(np.abs(o.E))
+    eB = np.max(np.abs(B - o.B)) / np.max(np.abs(o.B))
+    print(f"\nfast window run vs FP64 after {steps} steps: E {eE:.2e}, B {eB:.2e} of the peak")
+    assert eE <= 5e-6 and eB <= 5e-6    # measured 2.8e-7 / 2.4e-7
     g_old, _ = _split(got)
     r_old, _ = _oracle_split(o.species[0])
     common = np.intersect1d(g_old["id"], r_old["id"])
@@ -275,8 +277,10 @@ def test_retiling_and_autotuning_keep_the_window_state():
         assert da["window_moves"] == db["window_moves"] == OW.window_moves(19, w.dt, w.dx)
         assert da["n_particles"] == db["n_particles"]
         Ea, Eb = a.fields(pic.FIELD_E), b.fields(pic.FIELD_E)
-        assert np.max(np.abs(Ea - Eb)) <= 1e-4 * np.max(np.abs(Ea))
+        eE = np.max(np.abs(Ea - Eb)) / np.max(np.abs(Ea))
         pa, pb = a.particles(0), b.particles(0)
         ka = sorted(zip(pa["ix"].tolist(), pa["iy"].tolist()))
         kb = sorted(zip(pb["ix"].tolist(), pb["iy"].tolist()))
-        assert sum(x != y for x, y in zip(ka, kb)) < 0.01 * len(ka)
+        moved = sum(x != y for x, y in zip(ka, kb)) / len(ka)
+        print(f"\nre-tiled / tuned twin: E {eE:.2e} of the peak, {moved:.2e} of the cells differ")
+        assert eE <= 2e-6 and moved < 1e-3    # measured 1.1e-7, 0
