@@ -81,10 +81,15 @@ __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >=
 // no earlier kernel of the forward pass writes, before waiting for the
 // previous kernel, and lets the next kernel start staging once its own
 // products are issued.
-template <int CIN, int CT>
+// UP: the input is the half-resolution tensor read through nearest 2x
+// upsampling; the patch then holds the 6 x 10 source pixels of the tile's
+// 10 x 18 halo (tiles start on even pixels) and each lane addresses its own
+// source pixel, a quarter of the shared memory and of the loads.
+constexpr int CPH = PH / 2 + 1, CPW = PW / 2 + 1;  // 6 x 10
+template <int CIN, int CT, bool UP = false>
 struct ConvSmem {
     static constexpr int CS = CIN + 8;  // row stride in elements (16 B of padding: no bank conflicts)
-    static constexpr int PATCH = PH * PW * CS;
+    static constexpr int PATCH = (UP ? CPH * CPW : PH * PW) * CS;
     static constexpr int WTS = 9 * CT * CS;
     // the CTA's weights, then two patches
     static constexpr size_t bytes = (size_t)(WTS + 2 * PATCH) * 2;
@@ -94,9 +99,9 @@ struct ConvSmem {
 // channels [z CT, z CT + CT) in shared memory and runs through the tiles
 // blockIdx.x, blockIdx.x + gridDim.x, ... of all images; the next tile's
 // patch is copied in while the current one is computed.
-template <int CIN, int CT>
+template <int CIN, int CT, bool UP = false>
 __global__ void __launch_bounds__(CONV_THREADS) k_conv(const ConvParams p) {
-    using L = ConvSmem<CIN, CT>;
+    using L = ConvSmem<CIN, CT, UP>;
     extern __shared__ __align__(16) unsigned char smem[];
     bf16* sW = reinterpret_cast<bf16*>(smem);
     bf16* sP0 = sW + L::WTS;
@@ -113,6 +118,17 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv(const ConvParams p) {
     auto load_patch = [&](int tile, bf16* sP) {
         const int b = tile / tiles_img, tl = tile - b * tiles_img;
         const int ty0 = (tl / tilesx) * TH, tx0 = (tl % tilesx) * TW;
+        if constexpr (UP) {
+            // source pixels (ty0/2 - 1 + cy, tx0/2 - 1 + cx), periodic
+            for (int i = tid; i < CPH * CPW * CH; i += CONV_THREADS) {
+                const int pix = i / CH, c = i - pix * CH;
+                const int cy = pix / CPW, cx = pix - cy * CPW;
+                const int y = wrap((ty0 >> 1) - 1 + cy, Hi), x = wrap((tx0 >> 1) - 1 + cx, Wi);
+                cp_async16(sP + pix * L::CS + c * 8,
+                           p.x + (((size_t)b * Hi + y) * Wi + x) * CIN + c * 8);
+            }
+            return;
+        }
         for (int i = tid; i < PH * PW * CH; i += CONV_THREADS) {
             const int pix = i / CH, c = i - pix * CH;
             const int r = pix / PW, q = pix - r * PW;
@@ -149,7 +165,11 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv(const ConvParams p) {
 #pragma unroll 1
         for (int tap = 0; tap < 9; ++tap) {
             const int ky = tap / 3, kx = tap - 3 * (tap / 3);
-            const bf16* pa = sP + ((r + ky) * PW + kx + (lane & 15)) * L::CS + (lane >> 4) * 8;
+            // halo pixel (r + ky, px + kx); with UP its source pixel ((f + 1) >> 1)
+            const int px = lane & 15;
+            const int pix = UP ? ((r + ky + 1) >> 1) * CPW + ((px + kx + 1) >> 1)
+                               : (r + ky) * PW + kx + px;
+            const bf16* pa = sP + pix * L::CS + (lane >> 4) * 8;
             const bf16* pw = sW + tap * CT * L::CS;
 #pragma unroll
             for (int kc = 0; kc < CIN / 16; ++kc) {
@@ -607,12 +627,13 @@ __global__ void k_pack_weights(const PackTable t, const float* master, bf16* wf,
     }
 }
 
-template <int CIN, int CT>
+template <int CIN, int CT, bool UP = false>
 cudaError_t conv_attr() {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_conv<CIN, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ConvSmem<CIN, CT>::bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_conv<CIN, CT, UP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ConvSmem<CIN, CT, UP>::bytes);
     done = e == cudaSuccess;
     return e;
 }
@@ -627,9 +648,9 @@ cudaError_t wgrad_attr() {
     return e;
 }
 
-template <int CIN, int CT>
+template <int CIN, int CT, bool UP = false>
 cudaError_t conv_T(const ConvParams& p, cudaStream_t s) {
-    cudaError_t e = conv_attr<CIN, CT>();
+    cudaError_t e = conv_attr<CIN, CT, UP>();
     if (e != cudaSuccess) return e;
     static int per_sm = 0, sms = 0;
     if (!per_sm) {
@@ -640,7 +661,7 @@ cudaError_t conv_T(const ConvParams& p, cudaStream_t s) {
         if ((e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) !=
             cudaSuccess)
             return e;
-        per_sm = smem / (int)(ConvSmem<CIN, CT>::bytes + 1024);
+        per_sm = smem / (int)(ConvSmem<CIN, CT, UP>::bytes + 1024);
         if (per_sm < 1) per_sm = 1;
         if (per_sm * CONV_THREADS > 2048) per_sm = 2048 / CONV_THREADS;
     }
@@ -650,7 +671,8 @@ cudaError_t conv_T(const ConvParams& p, cudaStream_t s) {
     if (gx > ntiles) gx = ntiles;
     if (gx < 1) gx = 1;
     const dim3 grid(gx, 1, zt);
-    return launch_pdl(k_conv<CIN, CT>, grid, dim3(CONV_THREADS), ConvSmem<CIN, CT>::bytes, s, p);
+    return launch_pdl(k_conv<CIN, CT, UP>, grid, dim3(CONV_THREADS), ConvSmem<CIN, CT, UP>::bytes,
+                      s, p);
 }
 
 template <int CI, int CO>
@@ -672,6 +694,8 @@ int blocks(long long n, int t) { return (int)((n + t - 1) / t); }
 
 cudaError_t init_kernels() {
     cudaError_t e = init_tc_kernels();
+    if (e == cudaSuccess) e = conv_attr<128, 32, true>();
+    if (e == cudaSuccess) e = conv_attr<64, 32, true>();
 #define PIC_C_ATTR(A, B) if (e == cudaSuccess) e = conv_attr<A, B>();
 #define PIC_W_ATTR(A, B) if (e == cudaSuccess) e = wgrad_attr<A, B>();
     PIC_CONV_SHAPES(PIC_C_ATTR)
@@ -688,6 +712,10 @@ cudaError_t launch_conv(const ConvParams& p, int cin, int ct, cudaStream_t s) {
     if (p.H % TH || p.W % TW || p.cout_pad % ct) return cudaErrorInvalidValue;
     if (conv_tc_supported(p, cin)) return launch_conv_tc(p, cin, s);
     if (cin == 128 && ct == 64) ct = 32;
+    // the decoder's upsampling layers (c7: 128 -> 64, c9: 64 -> 32) read
+    // their source pixels directly
+    if (p.up && cin == 128 && ct == 32) return conv_T<128, 32, true>(p, s);
+    if (p.up && cin == 64 && ct == 32) return conv_T<64, 32, true>(p, s);
 #define PIC_CONV_CASE(CI, C) \
     if (cin == CI && ct == C) return conv_T<CI, C>(p, s);
     PIC_CONV_SHAPES(PIC_CONV_CASE)
