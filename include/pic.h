@@ -86,7 +86,7 @@ typedef struct {
     int threads;      /* threads per tile in the particle kernels: 64..512, multiple
                          of 32; 0 = 256 */
     int chunk;        /* particles per CTA in the particle kernels: a tile holding more
-                         is split over several CTAs (16..1<<20); 0 = 4096 */
+                         is split over several CTAs (16..1<<20); 0 = 8192 */
     int n_species;    /* 1..PIC_MAX_SPECIES */
     pic_species_cfg species[PIC_MAX_SPECIES];
     double background;/* fixed neutralising ion charge density (enters rho only) */
