@@ -164,9 +164,12 @@ def yee(E, B, J, dx, dy, dt, open_x=False):
 
 
 def rho_nodes(nx, ny, species, dtype=np.float64, background=0.0):
-    """Charge density on nodes (area weighting) plus a uniform background."""
+    """Charge density on nodes (area weighting) plus a uniform background,
+    accumulated in `dtype` (the offsets are taken in that precision)."""
     rho = np.zeros((ny, nx), dtype)
     for sp in species:
+        if sp.x.dtype != np.dtype(dtype):
+            sp = sp.astype(dtype)
         getattr(lib(), "orc_rho" + _sfx(dtype))(nx, ny, sp.qtilde, sp.n, _ptr(sp.ix), _ptr(sp.iy),
                                                 _ptr(sp.x), _ptr(sp.y), _ptr(rho))
     return rho.astype(np.float64) + background

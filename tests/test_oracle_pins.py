@@ -370,3 +370,21 @@ def test_binomial_filter_is_the_3x3_stencil():
                 want[c, j, i] = sum(w[a] * w[b] * J[c, (j + b - 1) % 7, (i + a - 1) % 9]
                                     for a in range(3) for b in range(3))
     np.testing.assert_allclose(binomial_filter(J, 1), want, atol=1e-13)
+
+
+def test_rho_of_an_fp32_state_equals_its_fp64_evaluation():
+    """The charge density of FP32 particles (Fig. 3.3 area weights) does not
+    depend on the precision the state is stored in: the FP32 offsets are exact
+    doubles."""
+    import numpy as np
+    import oracle as orc
+    rng = np.random.default_rng(5)
+    n, nx, ny = 2000, 16, 8
+    sp = orc.SpeciesState(-1.0, -0.25, rng.integers(0, nx, n).astype(np.int32),
+                          rng.integers(0, ny, n).astype(np.int32),
+                          rng.random(n).astype(np.float32), rng.random(n).astype(np.float32),
+                          np.zeros(n, np.float32), np.zeros(n, np.float32), np.zeros(n, np.float32))
+    r32 = orc.rho_nodes(nx, ny, [sp], np.float64, 0.0)
+    r64 = orc.rho_nodes(nx, ny, [sp.astype(np.float64)], np.float64, 0.0)
+    np.testing.assert_array_equal(r32, r64)
+    assert abs(r64.sum() + 0.25 * n) < 1e-9
