@@ -53,3 +53,25 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
         workload, steps, warmup, threads = "weibel_512", 1, 3, 256
     assert bench.run_reference(A(), rank=1, world=2) is None
     assert capsys.readouterr().out == ""
+
+
+def test_recorded_traffic_is_used_only_at_the_captured_source(tmp_path, monkeypatch):
+    """The DRAM traffic of the committed capture is reported only while the
+    particle-advance sources hash as they did at capture time."""
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    h = bench.push_source_hash()
+    (prof / "traffic.txt").write_text(f"# comment\nweibel_512 123456 {h}\nthermal_2048 9 0000\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "push_source_hash", lambda: h)
+    assert bench.recorded_traffic("weibel_512") == 123456.0
+    assert bench.recorded_traffic("thermal_2048") is None      # captured at another source
+    assert bench.recorded_traffic("weibel_256") is None        # never captured
+
+
+def test_peaks_fall_back_without_the_measured_file(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    peak, kind = bench.read_peaks()
+    assert kind == "fallback" and peak == bench.PEAK_FALLBACK_GBS
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6779.0}')
+    assert bench.read_peaks() == (6779.0, "measured")
