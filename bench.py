@@ -364,6 +364,11 @@ def run_batched(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# passes of the denoiser's low-wavenumber restoration evaluated beside the
+# plain network
+LOW_K_PASSES = (2, 4, 8)
+
+
 def run_denoiser(args, rank, world, local_rank):
     """Learned denoiser: pairs from 64-ppc runs, training on the GPU, then true
     4-ppc runs with the network in the current-filter slot against plain 64-ppc
@@ -409,15 +414,27 @@ def run_denoiser(args, rank, world, local_rank):
     torch.cuda.synchronize()
     fwd_ms = ev0.elapsed_time(ev1) / nf
 
+    # where the network shrinks the coherent current: shell-by-shell gains on
+    # the validation pairs, without and with the low-wavenumber restoration
+    spectral = {}
+    for n in (0,) + LOW_K_PASSES:
+        net.set_low_k_restore(n)
+        spectral[f"low_k_{n}"] = dn.spectral_gain(net, Vn, Vc, B)
+    net.set_low_k_restore(0)
+    del Vn, Vc
+
     steps = args.steps
+    variants = [("ppc64", 8, False, 0, 0), ("ppc4", 2, False, 0, 0),
+                ("ppc4_denoised", 2, True, 0, 0), ("ppc4_binomial", 2, False, 1, 0)]
+    variants += [(f"ppc4_denoised_low_k_{n}", 2, True, 0, n) for n in LOW_K_PASSES]
     results = []
     for d in dn.draws(3, offset=500):
         theory = dn.kinetic_growth_rate(d.drift, d.u_th, nx * 0.1)
         row = {"seed": d.seed, "drift": d.drift, "u_th": d.u_th, "theory_gamma": theory,
                "eligible": theory > 0.05}
         runs = {}
-        for name, k, use, binom in (("ppc64", 8, False, 0), ("ppc4", 2, False, 0),
-                                    ("ppc4_denoised", 2, True, 0), ("ppc4_binomial", 2, False, 1)):
+        for name, k, use, binom, lowk in variants:
+            net.set_low_k_restore(lowk)
             w = dn.workload(d, nx, ny, k, steps)
             we, _, diag, spec = dn.field_energy_run(w, steps, net if use else None, modes=True,
                                                      binomial=binom)
@@ -435,9 +452,10 @@ def run_denoiser(args, rank, world, local_rank):
                          "continuity_max": diag["continuity_max"]}
         row["mode"] = m
         g64 = row["ppc64"]["gamma_mode"]
-        for name in ("ppc4", "ppc4_denoised", "ppc4_binomial"):
+        for name, *_ in variants[1:]:
             row[name]["gamma_mode_rel_err"] = abs(row[name]["gamma_mode"] - g64) / g64
         results.append(row)
+    net.set_low_k_restore(0)
     # the same trained network on larger grids (it is translation invariant):
     # step times of 64 ppc, 4 ppc and denoised 4 ppc
     by_grid = {}
@@ -446,7 +464,11 @@ def run_denoiser(args, rank, world, local_rank):
         big = pic.Denoiser(side, side, 1, scale)
         big.set_params(net.params())
         row = {}
-        for name, k, use in (("ppc64", 8, False), ("ppc4", 2, False), ("ppc4_denoised", 2, True)):
+        for name, k, use, lowk in (("ppc64", 8, False, 0), ("ppc4", 2, False, 0),
+                                   ("ppc4_denoised", 2, True, 0),
+                                   (f"ppc4_denoised_low_k_{LOW_K_PASSES[-1]}", 2, True,
+                                    LOW_K_PASSES[-1])):
+            big.set_low_k_restore(lowk)
             w = dn.workload(d0, side, side, k, 60)
             _, ms, _, _ = dn.field_energy_run(w, 60, big if use else None)
             row[name] = ms
@@ -490,6 +512,9 @@ def run_denoiser(args, rank, world, local_rank):
         "growth_within_5pct": [r["ppc4_denoised"]["gamma_mode_rel_err"] < 0.05 for r in elig],
         "growth_within_5pct_binomial": [r["ppc4_binomial"]["gamma_mode_rel_err"] < 0.05
                                         for r in elig],
+        "growth_within_5pct_low_k": {n: [r[f"ppc4_denoised_low_k_{n}"]["gamma_mode_rel_err"] < 0.05
+                                         for r in elig] for n in LOW_K_PASSES},
+        "spectral_gain_validation": spectral,
     }
     print(json.dumps(line), flush=True)
 

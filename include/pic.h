@@ -348,8 +348,19 @@ pic_status pic_set_tiling(pic_sim* sim, int tile, int threads);
  * large (>= 600 work units of 2 x 128 pixels), else on an mma.sync kernel;
  * the environment variable PIC_DENOISER_TC, read at creation, selects the
  * tcgen05 kernel whenever the shape allows (=always, used by the tests) or
- * never (=never). */
+ * never (=never).
+ * Low-wavenumber restoration (off unless pic_denoiser_set_low_k_restore sets
+ * n > 0 passes): after the network, out <- out + L^n (J_in - out), where L is
+ * one pass of the periodic binomial smoothing (1/4, 1/2, 1/4) along x and
+ * along y, which multiplies the Fourier mode (mx, my) of the nx x ny lattice
+ * by cos^2(pi mx / nx) cos^2(pi my / ny).  It hands back the long-wavelength
+ * part of the correction the network made: a network trained on the mean
+ * squared error shrinks a weak coherent mode together with the noise, and the
+ * growth of that mode is what the simulation has to get right.  Applied by
+ * pic_denoiser_forward and in the current-filter slot, not in training. */
 typedef struct pic_denoiser pic_denoiser;
+
+#define PIC_LOW_K_MAX_PASSES 64
 
 int64_t pic_denoiser_num_params(void);
 
@@ -366,6 +377,12 @@ pic_status pic_denoiser_get_params(pic_denoiser* d, float* params, int on_device
 /* J_out = the denoised J_in (batch samples).  J_out may equal J_in.  Synchronises. */
 pic_status pic_denoiser_forward(pic_denoiser* d, const float* J_in, float* J_out, int batch,
                                 int on_device);
+
+/* Passes n of the low-wavenumber restoration (0: off, the default; at most
+ * PIC_LOW_K_MAX_PASSES, else PIC_EINVAL).  A simulation captures the setting
+ * when pic_set_denoiser installs d: call pic_set_denoiser again after a
+ * change.  The restoration uses the gradient buffers as scratch. */
+pic_status pic_denoiser_set_low_k_restore(pic_denoiser* d, int passes);
 
 /* Loss (mean squared error of the normalised output against J_target / scale)
  * and, if grads is non-NULL, its gradient with respect to the parameter
@@ -395,7 +412,11 @@ void pic_denoiser_destroy(pic_denoiser* d);
  *   pic_nn_conv3x3_dgrad: dx (FP32 NHWC, cin channels) = input gradient of
  *     the convolution for the output gradient dz; cin in {32, 64, 128}.
  *   pic_nn_conv3x3_wgrad: dw (FP32 [3][3][cin][cout], overwritten) = weight
- *     gradient; B*H*W a multiple of 64. */
+ *     gradient; B*H*W a multiple of 64.
+ *   pic_nn_low_k_restore: the denoiser's low-wavenumber restoration on FP32
+ *     currents [B][3][H][W]: out <- out + L^passes (raw - out) (B <= 4096,
+ *     H <= 65535, B H W <= 2^28; passes 0..PIC_LOW_K_MAX_PASSES); raw and out must not overlap; allocates
+ *     and frees its own scratch (3 B H W floats). */
 pic_status pic_nn_conv3x3(const void* x, int B, int H, int W, int cin, int cout, const float* w,
                           const float* bias, int relu, const void* skip, void* a_out, void* y_out,
                           void* cuda_stream);
@@ -403,6 +424,8 @@ pic_status pic_nn_conv3x3_dgrad(const void* dz, int B, int H, int W, int cin, in
                                 const float* w, float* dx, void* cuda_stream);
 pic_status pic_nn_conv3x3_wgrad(const void* x, const void* dz, int B, int H, int W, int cin,
                                 int cout, float* dw, void* cuda_stream);
+pic_status pic_nn_low_k_restore(const float* raw, float* out, int B, int H, int W, int passes,
+                                void* cuda_stream);
 
 /* ---- Allocation-free tile sort ---------------------------------------------
  * The paper has no counterpart: this entry point is for callers that cannot

@@ -23,11 +23,16 @@ cores as bfloat16 and accumulates in FP32.  ``forward``/``backward`` take a
 rounding function ``rnd`` applied at exactly those storage points (``bf16`` to
 mirror the GPU, ``ident`` for plain FP64 maths); everything else is FP64.
 
+The optional low-wavenumber restoration after the network,
+den + L^n (raw - den) with L the binomial current filter, is ``low_k_restore``.
+
 Pins (``tests/test_denoiser_oracle.py``): brute-force loops on tiny inputs,
 an FFT circular correlation, adjoint identities <A x, y> = <x, A^T y>, central
 finite differences of the whole network's loss in FP64, the first Adam step
 (-lr sign(g)) and Adam's convergence on a quadratic, the bfloat16 rounding
-against hand-computed bit patterns.
+against hand-computed bit patterns; the restoration against the closed-form
+response of a Fourier mode, a uniform difference (given back whole) and the
+Nyquist checkerboard (removed by one pass).
 """
 from __future__ import annotations
 
@@ -247,6 +252,24 @@ def loss_and_grads(p, x, target, rnd=ident):
     out, cache = forward(p, x, rnd)
     L, dout = mse(out, target)
     return L, backward(p, cache, dout, rnd), out
+
+
+# ------------------------------------------------------------ restoration
+
+def low_k_restore(raw, den, passes):
+    """Low-wavenumber restoration after the network: den + L^passes (raw - den),
+    L one pass of the periodic binomial smoothing of the time loop's current
+    filter (``binomial_filter``: (1/4, 1/2, 1/4) along x, then along y).
+    Arrays [..., 3, H, W] (field layout); FP64.  passes = 0 means no
+    restoration (the network's output), not L^0 = identity."""
+    from .oracle import binomial_filter
+    raw = np.asarray(raw, np.float64)
+    den = np.asarray(den, np.float64)
+    if passes == 0:
+        return den.copy()
+    diff = (raw - den).reshape((-1,) + raw.shape[-3:])
+    back = np.stack([binomial_filter(v, passes) for v in diff]).reshape(raw.shape)
+    return den + back
 
 
 # ------------------------------------------------------------ Adam

@@ -9,6 +9,10 @@
 //   c1 3->32, c2 32->32 [s1] | pool | c3 32->64, c4 64->64 [s2] | pool |
 //   c5 64->128, c6 128->128 | up | c7 128->64 (+s2), c8 64->64 | up |
 //   c9 64->32 (+s1), c10 32->32, c11 32->3;  out = x + c11.
+// Optional low-wavenumber restoration after the network (n > 0 passes):
+//   out <- out + L^n (x - out), L one pass of the periodic binomial smoothing,
+// which gives back the long-wavelength part of what the network removed (a
+// mean-squared-error denoiser shrinks a weak coherent mode with the noise).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -72,6 +76,7 @@ struct pic_denoiser {
     unsigned* status = nullptr;      // device word: bit 2 = a bounded wait in a kernel ran out
     unsigned* cur_status = nullptr;  // where the next launches report (own word or a simulation's)
     int force_tc = 0;                // PIC_DENOISER_TC: always (1) / never (-1) the tcgen05 path
+    int restore = 0;                 // passes of the low-wavenumber restoration (0: off)
     // host-buffer staging
     float *stage_in = nullptr, *stage_t = nullptr;
     std::vector<void*> allocs;
@@ -320,6 +325,20 @@ int backward(pic_denoiser* d, int B, const float* target, cudaStream_t s) {
     return n;
 }
 
+// Low-wavenumber restoration out <- out + L^n (raw - out) over B samples
+// (t: dense scratch of 3 B H W floats).  Returns kernels launched, or -1 with
+// the reason in *err.
+int low_k_chain(int n, int B, int H, int W, const FieldView& raw, const FieldView& out, float* t,
+                cudaStream_t s, std::string* err) {
+    if (n <= 0) return 0;
+    const cudaError_t e = launch_lowk(raw, out, t, out, n, B, H, W, s);
+    if (e != cudaSuccess) {
+        *err = std::string("low-wavenumber restoration launch failed: ") + cudaGetErrorString(e);
+        return -1;
+    }
+    return 2;
+}
+
 pic_status pack(pic_denoiser* d) {
     DCK(launch_pack_weights(d->tab, d->master, d->wf, d->wd, d->stream));
     return PIC_OK;
@@ -374,12 +393,30 @@ pic_status run_grad(pic_denoiser* d, const float* J_in, const float* J_t, int ba
 int filter_hook(void* ctx, pic_sim* sim, cudaStream_t s, int b) {
     pic_denoiser* d = static_cast<pic_denoiser*>(ctx);
     const Geom& g = sim->g;
+    const FieldView J{sim->J[b], 3 * g.cstride, g.cstride, g.P, GY * g.P + GX};
+    // scratch of the restoration (the gradient buffers, idle outside training):
+    // the raw current and the row-filtered difference, 3 H W floats each
+    const long long n3 = 3LL * d->H * d->W;
+    const FieldView raw{d->G0, n3, (long long)d->H * d->W, d->W, 0};
+    int k0 = 0;
+    if (d->restore > 0) {
+        const cudaError_t e = launch_field_copy(J, raw, 1, d->H, d->W, s);
+        if (e != cudaSuccess) {
+            sim->err = std::string("denoiser copy launch failed: ") + cudaGetErrorString(e);
+            return -1;
+        }
+        k0 = 1;
+    }
     d->cur_status = &sim->st->status;  // timeouts show in the simulation's status (ST_TIMEOUT)
     const int k = forward(d, 1, sim->J[b], 3 * g.cstride, g.cstride, g.P, GY * g.P + GX, sim->J[b],
                           1.f, (float)d->scale, s);
     d->cur_status = d->status;
-    if (k < 0) sim->err = d->err;
-    return k;
+    if (k < 0) {
+        sim->err = d->err;
+        return k;
+    }
+    const int kr = low_k_chain(d->restore, 1, d->H, d->W, raw, J, d->G0 + n3, s, &sim->err);
+    return kr < 0 ? -1 : k0 + k + kr;
 }
 
 // Pack random-access probe weights ([9][cin][cout] FP32, device) for one layer shape.
@@ -508,7 +545,17 @@ pic_status pic_denoiser_forward(pic_denoiser* d, const float* J_in, float* J_out
     if (st != PIC_OK) return st;
     float* o = on_device ? J_out : d->stage_t;
     const long long HW = (long long)d->H * d->W;
+    FieldView vin{const_cast<float*>(in), 3 * HW, HW, d->W, 0};
+    const FieldView vout{o, 3 * HW, HW, d->W, 0};
+    if (d->restore > 0 && in == o) {
+        // in place: keep the raw current for the restoration
+        const FieldView keep{d->G0 + cnt, 3 * HW, HW, d->W, 0};
+        DCK(launch_field_copy(vin, keep, batch, d->H, d->W, d->stream));
+        vin = keep;
+    }
     if (forward(d, batch, in, 3 * HW, HW, d->W, 0, o, 1.f, (float)d->scale, d->stream) < 0)
+        return PIC_ECUDA;
+    if (low_k_chain(d->restore, batch, d->H, d->W, vin, vout, d->G0, d->stream, &d->err) < 0)
         return PIC_ECUDA;
     if (!on_device)
         DCK(cudaMemcpyAsync(J_out, o, cnt * 4, cudaMemcpyDeviceToHost, d->stream));
@@ -563,6 +610,15 @@ pic_status pic_set_denoiser(pic_sim* sim, pic_denoiser* d) {
     sim->jfilter_ctx = d;
     sim->binomial_passes = 0;
     invalidate_graphs(sim);
+    return PIC_OK;
+}
+
+pic_status pic_denoiser_set_low_k_restore(pic_denoiser* d, int passes) {
+    if (!d) return PIC_EINVAL;
+    d->err.clear();
+    if (passes < 0 || passes > PIC_LOW_K_MAX_PASSES)
+        return dfail(d, PIC_EINVAL, "passes %d not in 0..%d", passes, PIC_LOW_K_MAX_PASSES);
+    d->restore = passes;
     return PIC_OK;
 }
 
@@ -658,6 +714,24 @@ pic_status pic_nn_conv3x3_dgrad(const void* dz, int B, int H, int W, int cin, in
     p.g_out = dx;
     if (launch_conv(p, L.dg_cin_pad, ctile(cin), s) != cudaSuccess) return PIC_ECUDA;
     return pr.finish(s);
+}
+
+pic_status pic_nn_low_k_restore(const float* raw, float* out, int B, int H, int W, int passes,
+                                void* cuda_stream) {
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!raw || !out || B < 1 || B > 4096 || H < 1 || H > 65535 || W < 1 || passes < 0 ||
+        passes > PIC_LOW_K_MAX_PASSES || (long long)B * H * W > (1LL << 28))
+        return PIC_EINVAL;
+    const long long n = 3LL * B * H * W, HW = (long long)H * W;
+    float* scratch = nullptr;
+    if (passes > 0 && cudaMalloc((void**)&scratch, n * sizeof(float)) != cudaSuccess)
+        return PIC_ENOMEM;
+    const FieldView vr{const_cast<float*>(raw), 3 * HW, HW, W, 0}, vo{out, 3 * HW, HW, W, 0};
+    std::string err;
+    const int k = low_k_chain(passes, B, H, W, vr, vo, scratch, s, &err);
+    const bool ok = k >= 0 && cudaStreamSynchronize(s) == cudaSuccess;
+    cudaFree(scratch);
+    return ok ? PIC_OK : PIC_ECUDA;
 }
 
 pic_status pic_nn_conv3x3_wgrad(const void* x, const void* dz, int B, int H, int W, int cin,

@@ -48,6 +48,21 @@ struct ConvParams {
     int force_tc;            // take the tensor-core path whenever the shape allows (tests)
 };
 
+// A three-component current in field layout: element (b, c, y, x) at
+// p[b*bstride + c*cstride + offset + y*pitch + x].
+struct FieldView {
+    float* p;
+    long long bstride, cstride;
+    int pitch, offset;
+};
+
+// taps of the (2n+1)-point kernel C(2n, k) / 4^n (n passes of the binomial stencil)
+constexpr int LOWK_MAX = 64;
+struct LowkTaps {
+    int n;
+    float w[2 * LOWK_MAX + 1];
+};
+
 struct WgradParams {
     const __nv_bfloat16* x;   // layer input NHWC (CI channels)
     const __nv_bfloat16* dz;  // output gradient NHWC (CO channels)
@@ -132,6 +147,13 @@ cudaError_t launch_mse(const float* out, const float* target, long long bstride,
                        __nv_bfloat16* dz, float* db, double* loss, cudaStream_t s);
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr,
                         float b1, float b2, float eps, float c1, float c2, cudaStream_t s);
+// o += L^n (a - b) (b.p null: L^n a), L one pass of the periodic binomial
+// smoothing; t is dense scratch of 3 B H W floats; 0 <= n <= LOWK_MAX
+cudaError_t launch_lowk(const FieldView& a, const FieldView& b, float* t, const FieldView& o,
+                        int n, int B, int H, int W, cudaStream_t s);
+// o = a (three-component currents of B samples, any layouts)
+cudaError_t launch_field_copy(const FieldView& a, const FieldView& o, int B, int H, int W,
+                              cudaStream_t s);
 cudaError_t launch_pack_weights(const PackTable& t, const float* master, __nv_bfloat16* wf,
                                 __nv_bfloat16* wd, cudaStream_t s);
 

@@ -23,6 +23,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+#include <cstring>
+
 #include "nn_internal.h"
 
 namespace pic {
@@ -586,6 +589,78 @@ __global__ void __launch_bounds__(256) k_mse(const float* out, const float* targ
 
 // Adam (Kingma & Ba, Algorithm 1) on the FP32 master parameters; c1, c2 are
 // the bias corrections 1/(1 - beta^t).
+// Low-wavenumber restoration, out <- out + L^n (a - b), as two separable
+// passes: n passes of the periodic binomial stencil (1/4, 1/2, 1/4) compose to
+// the (2n+1)-tap kernel C(2n, k) / 4^n along each axis, which multiplies the
+// Fourier mode (mx, my) of an H x W periodic lattice by
+// (cos^2(pi mx / W) cos^2(pi my / H))^n.  Rows first (k_lowk_x: the row
+// segment and its halo staged in shared memory, coalesced), then columns
+// (k_lowk_y: a 64-row x 32-column tile and its halo rows).
+// i mod n in [0, n) for any i (the halo may wrap several times on small lattices)
+__device__ __forceinline__ int wrap_any(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+constexpr int LK_ROW = 256;                    // outputs per CTA of the row pass
+constexpr int LK_TY = 64, LK_TX = 32, LK_YT = 8;  // column pass: tile rows, columns, thread rows
+
+// t = rows of (a - b) (b.p null: a) filtered along x; t dense [B][3][H][W]
+__global__ void k_lowk_x(FieldView a, FieldView b, float* t, LowkTaps w, int B, int H, int W) {
+    extern __shared__ float sRow[];  // LK_ROW + 2n values
+    const int n = w.n;
+    const int x0 = blockIdx.x * LK_ROW, y = blockIdx.y;
+    const int c = blockIdx.z % 3, smp = blockIdx.z / 3;
+    const float* pa = a.p + smp * a.bstride + c * a.cstride + a.offset + (long long)y * a.pitch;
+    const float* pb =
+        b.p ? b.p + smp * b.bstride + c * b.cstride + b.offset + (long long)y * b.pitch : nullptr;
+    for (int i = threadIdx.x; i < LK_ROW + 2 * n; i += blockDim.x) {
+        const int x = wrap_any(x0 + i - n, W);
+        sRow[i] = pb ? pa[x] - pb[x] : pa[x];
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x;
+    if (x >= W) return;
+    float v = 0.f;
+    for (int k = 0; k <= 2 * n; ++k) v = fmaf(w.w[k], sRow[threadIdx.x + k], v);
+    t[((long long)blockIdx.z * H + y) * W + x] = v;
+}
+
+// out += columns of t filtered along y
+__global__ void k_lowk_y(const float* t, FieldView o, LowkTaps w, int B, int H, int W) {
+    extern __shared__ float sCol[];  // (LK_TY + 2n) rows x (LK_TX + 1)
+    const int n = w.n;
+    const int x0 = blockIdx.x * LK_TX, y0 = blockIdx.y * LK_TY;
+    const int c = blockIdx.z % 3, smp = blockIdx.z / 3;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x = x0 + tx;
+    const float* pt = t + (long long)blockIdx.z * H * W;
+    for (int r = ty; r < LK_TY + 2 * n; r += LK_YT)
+        sCol[r * (LK_TX + 1) + tx] = x < W ? pt[(long long)wrap_any(y0 + r - n, H) * W + x] : 0.f;
+    __syncthreads();
+    if (x >= W) return;
+    float* po = o.p + smp * o.bstride + c * o.cstride + o.offset + x;
+    for (int r = ty; r < LK_TY && y0 + r < H; r += LK_YT) {
+        float v = 0.f;
+        for (int k = 0; k <= 2 * n; ++k) v = fmaf(w.w[k], sCol[(r + k) * (LK_TX + 1) + tx], v);
+        po[(long long)(y0 + r) * o.pitch] += v;
+    }
+}
+
+// o = a, element by element (layouts may differ)
+__global__ void k_field_copy(FieldView a, FieldView o, int B, int H, int W) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)B * 3 * H * W) return;
+    const int x = (int)(i % W);
+    long long r = i / W;
+    const int y = (int)(r % H);
+    r /= H;
+    const int c = (int)(r % 3);
+    const long long smp = r / 3;
+    o.p[smp * o.bstride + c * o.cstride + o.offset + (long long)y * o.pitch + x] =
+        a.p[smp * a.bstride + c * a.cstride + a.offset + (long long)y * a.pitch + x];
+}
+
 __global__ void k_adam(float* p, const float* g, float* m, float* v, long long n, float lr,
                        float b1, float b2, float eps, float c1, float c2) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -800,6 +875,43 @@ cudaError_t launch_mse(const float* out, const float* target, long long bstride,
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr,
                         float b1, float b2, float eps, float c1, float c2, cudaStream_t s) {
     k_adam<<<blocks(n, 256), 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+LowkTaps lowk_taps(int n) {
+    LowkTaps w;
+    memset(&w, 0, sizeof w);
+    w.n = n;
+    // C(2n, k) / 4^n by Pascal's rule in FP64 (exact up to n = 26), then FP32
+    double row[2 * LOWK_MAX + 1] = {1.0};
+    for (int m = 1; m <= 2 * n; ++m) {
+        for (int k = m; k >= 1; --k) row[k] = 0.5 * (row[k] + row[k - 1]);
+        row[0] *= 0.5;
+    }
+    for (int k = 0; k <= 2 * n; ++k) w.w[k] = (float)row[k];
+    return w;
+}
+
+cudaError_t launch_lowk(const FieldView& a, const FieldView& b, float* t, const FieldView& o,
+                        int n, int B, int H, int W, cudaStream_t s) {
+    if (n <= 0 || (long long)B * H * W == 0) return cudaSuccess;
+    if (n > LOWK_MAX) return cudaErrorInvalidValue;
+    const LowkTaps w = lowk_taps(n);
+    const dim3 gx((W + LK_ROW - 1) / LK_ROW, H, 3 * B);
+    k_lowk_x<<<gx, LK_ROW, (LK_ROW + 2 * n) * sizeof(float), s>>>(a, b, t, w, B, H, W);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const dim3 gy((W + LK_TX - 1) / LK_TX, (H + LK_TY - 1) / LK_TY, 3 * B);
+    k_lowk_y<<<gy, dim3(LK_TX, LK_YT), (LK_TY + 2 * n) * (LK_TX + 1) * sizeof(float), s>>>(
+        t, o, w, B, H, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_copy(const FieldView& a, const FieldView& o, int B, int H, int W,
+                              cudaStream_t s) {
+    const long long n = (long long)B * 3 * H * W;
+    if (n == 0) return cudaSuccess;
+    k_field_copy<<<blocks(n, 256), 256, 0, s>>>(a, o, B, H, W);
     return cudaGetLastError();
 }
 

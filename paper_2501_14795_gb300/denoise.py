@@ -165,6 +165,47 @@ def mse_gain(net: pic.Denoiser, Jn, Jc, batch):
     return raw / Jn.numel(), den / Jn.numel()
 
 
+def spectral_gain(net: pic.Denoiser, Jn, Jc, batch, edges=(1, 2, 4, 8, 16, 32, 64, 182)):
+    """Shell-by-shell comparison of the raw subsample current and of the
+    network's output (with the net's current restoration setting) against the
+    high-ppc current, over all pairs: per shell of |m| (Fourier index radius,
+    lo <= |m| < hi) the gain sum Re(F(out) conj F(Jc)) / sum |F(Jc)|^2 (1: the
+    coherent part passes unchanged; below 1: it is shrunk) and the error
+    power sum |F(out) - F(Jc)|^2 / sum |F(Jc)|^2."""
+    import torch
+    N, _, H, W = Jn.shape
+    dev = Jn.device
+    ky = torch.fft.fftfreq(H, 1.0 / H, device=dev, dtype=torch.float64)
+    kx = torch.fft.rfftfreq(W, 1.0 / W, device=dev, dtype=torch.float64)
+    m = torch.sqrt(ky[:, None] ** 2 + kx[None, :] ** 2)
+    masks = [(m >= lo) & (m < hi) for lo, hi in zip(edges[:-1], edges[1:])]
+    z = lambda: torch.zeros(len(masks), dtype=torch.float64, device=dev)
+    auto, cr_n, cr_d, er_n, er_d = z(), z(), z(), z(), z()
+    out = torch.empty_like(Jn[:batch])
+    for s in range(0, N, batch):
+        b = min(batch, N - s)
+        xb = Jn[s:s + b].contiguous()
+        o = out[:b]
+        pic.pic_denoiser_forward(net.d, xb, o, b)
+        Fc = torch.fft.rfft2(Jc[s:s + b].double())
+        Fn = torch.fft.rfft2(xb.double())
+        Fd = torch.fft.rfft2(o.double())
+        for i, mk in enumerate(masks):
+            c = Fc[..., mk]
+            auto[i] += (c.abs() ** 2).sum()
+            cr_n[i] += (Fn[..., mk] * c.conj()).real.sum()
+            cr_d[i] += (Fd[..., mk] * c.conj()).real.sum()
+            er_n[i] += ((Fn[..., mk] - c).abs() ** 2).sum()
+            er_d[i] += ((Fd[..., mk] - c).abs() ** 2).sum()
+    a = auto.cpu().numpy()
+    rows = []
+    for i, (lo, hi) in enumerate(zip(edges[:-1], edges[1:])):
+        rows.append({"shell": [lo, hi], "gain_raw": float(cr_n[i] / auto[i]),
+                     "gain_out": float(cr_d[i] / auto[i]), "err_raw": float(er_n[i] / auto[i]),
+                     "err_out": float(er_d[i] / auto[i]), "power": float(a[i])})
+    return rows
+
+
 def field_energy_run(w, steps, net=None, stream=None, modes=False, binomial=0):
     """W_E(t) history (t = 0..steps) of a run (with the denoiser `net` or
     `binomial` passes of the binomial filter in the current-filter slot), its

@@ -143,6 +143,8 @@ def load_library() -> C.CDLL:
                                            _P, _P]
         L.pic_nn_conv3x3_wgrad.argtypes = [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                            _P, _P]
+        L.pic_denoiser_set_low_k_restore.argtypes = [_P, C.c_int]
+        L.pic_nn_low_k_restore.argtypes = [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P]
         for name in ("pic_init", "pic_load_particles", "pic_set_fields", "pic_step",
                      "pic_get_fields", "pic_get_particles", "pic_diagnostics",
                      "pic_get_history", "pic_sync", "pic_clear_status", "pic_timing",
@@ -151,7 +153,8 @@ def load_library() -> C.CDLL:
                      "pic_denoiser_set_params", "pic_denoiser_get_params", "pic_denoiser_forward",
                      "pic_denoiser_grad", "pic_denoiser_train_step", "pic_set_denoiser",
                      "pic_nn_conv3x3", "pic_nn_conv3x3_dgrad", "pic_nn_conv3x3_wgrad",
-                     "pic_set_binomial_filter"):
+                     "pic_set_binomial_filter", "pic_denoiser_set_low_k_restore",
+                     "pic_nn_low_k_restore"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -433,6 +436,10 @@ def pic_denoiser_train_step(d, J_in, J_target, batch, lr):
     return loss.value
 
 
+def pic_denoiser_set_low_k_restore(d, passes):
+    _dcheck(d, load_library().pic_denoiser_set_low_k_restore(d, int(passes)))
+
+
 def pic_set_denoiser(h, d):
     _check(h, load_library().pic_set_denoiser(h, d))
 
@@ -512,6 +519,18 @@ def pic_nn_conv3x3_wgrad(x, dz, dw, stream=None):
                                              stream)
     if st != 0:
         raise PicError(st, "pic_nn_conv3x3_wgrad")
+
+
+def pic_nn_low_k_restore(raw, out, passes, stream=None):
+    """out <- out + L^passes (raw - out) on device FP32 currents [B, 3, H, W]."""
+    B, three, H, W = out.shape
+    if three != 3 or tuple(raw.shape) != tuple(out.shape):
+        raise ValueError("raw and out must both be [B, 3, H, W]")
+    if stream is None:
+        stream = _default_stream()
+    st = load_library().pic_nn_low_k_restore(_dptr(raw), _dptr(out), B, H, W, int(passes), stream)
+    if st != 0:
+        raise PicError(st, "pic_nn_low_k_restore")
 
 
 def pic_tile_sort_noalloc(nx, ny, tile, ix, iy, x, y, ux, uy, uz, ix_out, iy_out, x_out,
@@ -720,6 +739,11 @@ class Denoiser:
             J_out = np.empty_like(J_in)
         pic_denoiser_forward(self.d, J_in, J_out, batch)
         return J_out
+
+    def set_low_k_restore(self, passes):
+        """Passes of the low-wavenumber restoration after the network (0: off);
+        a simulation picks a change up when the denoiser is installed again."""
+        pic_denoiser_set_low_k_restore(self.d, passes)
 
     def grad(self, J_in, J_target, grads=None):
         batch = J_in.shape[0] if J_in.ndim == 4 else 1

@@ -106,6 +106,19 @@ def test_window_and_laser_entry_points_check_arguments_without_gpu(lib):
     assert L.pic_add_laser(None, None) == 1
 
 
+def test_denoiser_restoration_entry_points_check_arguments_without_gpu(lib):
+    """Null handles and buffers, and pass counts out of range, answer PIC_EINVAL
+    before any CUDA call."""
+    from paper_2501_14795_gb300 import pic
+    L = pic.load_library()
+    assert L.pic_denoiser_set_low_k_restore(None, 2) == 1
+    assert L.pic_nn_low_k_restore(None, None, 1, 8, 8, 1, None) == 1
+    fake = ctypes.c_void_p(16)      # never dereferenced: the arguments fail first
+    assert L.pic_nn_low_k_restore(fake, fake, 1, 8, 8, -1, None) == 1
+    assert L.pic_nn_low_k_restore(fake, fake, 1, 8, 8, 65, None) == 1
+    assert L.pic_nn_low_k_restore(fake, fake, 0, 8, 8, 1, None) == 1
+
+
 def test_binding_structs_match_the_c_header(tmp_path):
     """sizeof and offsetof of every ABI struct as gcc lays them out from
     include/pic.h equal the ctypes mirrors of the binding."""

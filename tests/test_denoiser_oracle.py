@@ -220,3 +220,40 @@ def test_library_parameter_layout_and_init_match_the_oracle():
     np.testing.assert_array_equal(dn.init_params(5), D.flatten(D.init_params(5)).astype(np.float32))
     assert dn.forward_flops(256, 256) == sum(2.0 * 65536 / 4 ** lv * 9 * ci * co
                                               for _, ci, co, lv, _, _ in D.LAYERS)
+
+
+def _mode(H, W, mx, my):
+    y, x = np.mgrid[0:H, 0:W]
+    return np.cos(2 * np.pi * (mx * x / W + my * y / H) + 0.3)
+
+
+@pytest.mark.parametrize("passes", [1, 3, 8])
+def test_low_k_restore_gives_back_each_mode_by_the_closed_form_factor(passes):
+    """raw - den a Fourier mode (mx, my) per component: the restoration adds it
+    back times cos^2(pi mx / W)^n cos^2(pi my / H)^n (the response of n passes
+    of the binomial stencil), on top of an arbitrary den."""
+    H, W = 12, 20
+    rng = np.random.default_rng(3)
+    den = rng.normal(size=(2, 3, H, W))
+    modes = [(1, 0), (3, 2), (7, 5)]
+    diff = np.stack([_mode(H, W, mx, my) for mx, my in modes])
+    raw = den + np.stack([diff, 2.0 * diff])
+    out = D.low_k_restore(raw, den, passes)
+    for c, (mx, my) in enumerate(modes):
+        f = (np.cos(np.pi * mx / W) ** 2 * np.cos(np.pi * my / H) ** 2) ** passes
+        for b, amp in enumerate((1.0, 2.0)):
+            np.testing.assert_allclose(out[b, c] - den[b, c], amp * f * diff[c], rtol=0, atol=1e-12)
+
+
+def test_low_k_restore_special_cases():
+    H, W = 8, 16
+    rng = np.random.default_rng(4)
+    den = rng.normal(size=(3, H, W))
+    raw = rng.normal(size=(3, H, W))
+    # no passes: the network's output unchanged
+    np.testing.assert_array_equal(D.low_k_restore(raw, den, 0), den)
+    # a uniform difference is the k = 0 mode: given back whole
+    np.testing.assert_allclose(D.low_k_restore(den + 0.7, den, 5), den + 0.7, rtol=0, atol=1e-12)
+    # the Nyquist checkerboard along x is removed by one pass
+    chk = np.broadcast_to((-1.0) ** np.arange(W), (3, H, W))
+    np.testing.assert_allclose(D.low_k_restore(den + chk, den, 1), den, rtol=0, atol=1e-12)

@@ -227,3 +227,77 @@ def test_identity_network_in_the_filter_slot_changes_nothing():
         pic.pic_set_denoiser(b.h, None)
         b.step(1)
         assert b.diagnostics()["status_bits"] == 0
+
+
+# ---- low-wavenumber restoration after the network ---------------------------
+
+@pytest.mark.parametrize("passes,H,W", [(0, 24, 40), (1, 24, 40), (2, 24, 40), (5, 70, 300),
+                                         (64, 8, 12)])
+def test_low_k_restore_kernels_match_oracle(passes, H, W):
+    """out + L^n (raw - out) on ragged lattices (not multiples of the kernels'
+    tiles; 8 x 12 with 64 passes wraps the halo several times), FP32 on the GPU
+    (the (2n+1)-tap binomial kernel) against the FP64 oracle (n passes of the
+    3-point stencil)."""
+    B = 2
+    rng = _rng(60 + passes)
+    raw = rng.normal(size=(B, 3, H, W))
+    out = rng.normal(size=(B, 3, H, W))
+    r, o = _f32(raw), _f32(out)
+    pic.pic_nn_low_k_restore(r, o, passes)
+    want = D.low_k_restore(raw.astype(np.float32), out.astype(np.float32), passes)
+    np.testing.assert_allclose(_np(o), want, rtol=0, atol=2e-6 * np.max(np.abs(want)))
+
+
+def _bias_only(b):
+    """parameters whose network output is x + b (per component): all zero but c11's bias"""
+    p = D.unflatten(np.zeros(D.n_params()))
+    p["c11.b"] = np.asarray(b, np.float64)
+    return _flat32(p)
+
+
+def test_restoration_gives_back_a_uniform_correction():
+    """A network that only adds a constant per component moves the k = 0 mode
+    alone, which the restoration gives back whole: out = x for n >= 1, and
+    out = x + scale * b without it (host buffers, and device in place)."""
+    import torch
+    B, ny, nx, scale = 2, 32, 64, 0.5
+    Jn, _ = _currents(8, B, ny, nx)
+    Jn = Jn.astype(np.float32)
+    b = np.array([0.3, -0.2, 0.1])
+    with pic.Denoiser(nx, ny, B, scale) as net:
+        net.set_params(_bias_only(b))
+        plain = net.forward(Jn)
+        np.testing.assert_allclose(plain, Jn + scale * b[None, :, None, None], rtol=0, atol=1e-6)
+        net.set_low_k_restore(3)
+        back = net.forward(Jn)
+        np.testing.assert_allclose(back, Jn, rtol=0, atol=2e-6)
+        t = _f32(Jn)
+        net.forward(t, t)                  # in place on the device
+        np.testing.assert_allclose(_np(t), Jn, rtol=0, atol=2e-6)
+        with pytest.raises(pic.PicError):
+            net.set_low_k_restore(-1)
+        with pytest.raises(pic.PicError):
+            net.set_low_k_restore(65)
+        torch.cuda.synchronize()
+
+
+def test_restoration_in_the_filter_slot():
+    """In the current-filter slot, the constant-adding network with the
+    restoration steps like the unfiltered simulation; without it, it does not."""
+    w = wl.two_stream(nx=64, ny=32, k=2, u_th=0.1, drift=0.2, tile=16, seed=9)
+    with pic.Simulation.from_workload(w, device=True) as a, \
+            pic.Simulation.from_workload(w, device=True) as b, \
+            pic.Simulation.from_workload(w, device=True) as c, \
+            pic.Denoiser(64, 32, 1, 0.1) as net, pic.Denoiser(64, 32, 1, 0.1) as net0:
+        net.set_params(_bias_only([0.5, -0.5, 0.25]))
+        net.set_low_k_restore(2)
+        net0.set_params(_bias_only([0.5, -0.5, 0.25]))
+        pic.pic_set_denoiser(b.h, net.d)
+        pic.pic_set_denoiser(c.h, net0.d)
+        for s in (a, b, c):
+            s.step(20)
+        da, db, dc = a.diagnostics(), b.diagnostics(), c.diagnostics()
+        assert db["status_bits"] == 0 and dc["status_bits"] == 0
+        np.testing.assert_allclose(db["w_e"], da["w_e"], rtol=1e-4, atol=1e-12)
+        np.testing.assert_allclose(db["w_k"], da["w_k"], rtol=1e-6)
+        assert abs(dc["w_e"] - da["w_e"]) > 1e-2 * da["w_e"]
