@@ -645,6 +645,62 @@ __global__ void __launch_bounds__(1024) k_scan_counts(const int32_t* cnt, int nt
     if (tid == 1023) off[nt] = run;
 }
 
+// Exclusive scan of the per-cell counts of a load, in three coalesced passes
+// over segments of SCAN_SEG cells: segment sums, their scan (k_scan_counts,
+// one CTA), then each segment's own scan plus its offset.
+constexpr int SCAN_SEG = 4096;  // cells per CTA of 1024 threads (4 consecutive each)
+
+__device__ __forceinline__ int block_excl_scan_1024(int v, int* sWarp, int* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) sWarp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int w = sWarp[lane];
+        int wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += u;
+        }
+        sWarp[lane] = wi - w;
+        if (lane == 31) sWarp[32] = wi;
+    }
+    __syncthreads();
+    *total = sWarp[32];
+    return sWarp[wid] + incl - v;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_seg_sums(const int32_t* cnt, long long n,
+                                                        int32_t* part) {
+    __shared__ int sWarp[33];
+    const long long k0 = (long long)blockIdx.x * SCAN_SEG + 4 * threadIdx.x;
+    int v = 0;
+    for (int j = 0; j < 4; ++j)
+        if (k0 + j < n) v += cnt[k0 + j];
+    int total;
+    block_excl_scan_1024(v, sWarp, &total);
+    if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_seg_apply(const int32_t* cnt, long long n,
+                                                         const int32_t* partoff, int32_t* off) {
+    __shared__ int sWarp[33];
+    const long long k0 = (long long)blockIdx.x * SCAN_SEG + 4 * threadIdx.x;
+    int c[4];
+    for (int j = 0; j < 4; ++j) c[j] = k0 + j < n ? cnt[k0 + j] : 0;
+    int total;
+    int run = partoff[blockIdx.x] + block_excl_scan_1024(c[0] + c[1] + c[2] + c[3], sWarp, &total);
+    for (int j = 0; j < 4; ++j) {
+        if (k0 + j < n) off[k0 + j] = run;
+        run += c[j];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) off[n] = partoff[gridDim.x];
+}
+
 __global__ void k_unpack(const int32_t* cell, int n, int32_t* ix, int32_t* iy) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int c = cell[k];
@@ -795,8 +851,14 @@ cudaError_t launch_load(const Geom& g, SpeciesDev& sp, int track_ids, int64_t n,
         if (nn > 0) k_load_count<<<grid_for(nn, 256), 256, 0, s>>>(g, sp, nn, st);
         return cudaGetLastError();
     }
-    // phase 1: cell offsets from the counts, tile bookmarks, then scatter
-    k_scan_counts<<<1, 1024, 0, s>>>(sp.cursor, (int)ncell, celloff);
+    // phase 1: cell offsets from the counts (segment sums and their offsets
+    // behind the ncell + 1 cell offsets), tile bookmarks, then scatter
+    const int nseg = (int)((ncell + SCAN_SEG - 1) / SCAN_SEG);
+    int32_t* part = celloff + ncell + 1;
+    int32_t* partoff = part + nseg;
+    k_scan_seg_sums<<<nseg, 1024, 0, s>>>(sp.cursor, ncell, part);
+    k_scan_counts<<<1, 1024, 0, s>>>(part, nseg, partoff);
+    k_scan_seg_apply<<<nseg, 1024, 0, s>>>(sp.cursor, ncell, partoff, celloff);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_tile_from_cells<<<grid_for(g.ntiles + 1, 256), 256, 0, s>>>(celloff, g.ntiles, g.T * g.T,

@@ -655,7 +655,8 @@ pic_status pic_load_particles(pic_sim* sim, int species, int64_t n, const int32_
         return fail(sim, PIC_EINVAL, "%d particles with a cell outside the grid, an offset outside [0,1) or a non-finite momentum",
                     h.load_bad);
     }
-    // the FP64 charge-density buffer (2 nx*ny ints) serves as the cell-offset scratch
+    // the FP64 charge-density buffer (2 nx*ny ints, nx*ny >= 64) serves as the
+    // cell-offset scratch (nx*ny + 2 + 2 ceil(nx*ny / 4096) ints)
     e = launch_load(sim->g, W, track, n, W.off[sim->cur], sim->st, s, 1,
                     (track && id) ? W.isrc : nullptr, reinterpret_cast<int32_t*>(sim->rho));
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

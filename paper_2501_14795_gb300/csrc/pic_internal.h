@@ -244,8 +244,9 @@ cudaError_t launch_grid_residuals(const Geom& g, const float* F, const float* J,
 // each tile.  The input is staged in the out arrays: ix in ocell, iy in hole,
 // x..uz in ox..ouz; ids (optional) in `staged_ids`.  phase 0 validates and
 // counts per key (sp.cursor holds nx*ny counters), phase 1 scans the counts into
-// `celloff` (nx*ny + 1 ints of scratch), writes the tile bookmarks `off` and
-// scatters into the particle arrays.
+// `celloff` (scratch of nx*ny + 2 + 2 ceil(nx*ny / 4096) ints: the cell offsets,
+// then the scan's segment sums and their offsets), writes the tile bookmarks
+// `off` and scatters into the particle arrays.
 cudaError_t launch_load(const Geom& g, SpeciesDev& sp, int track_ids, int64_t n, int32_t* off,
                         DevState* st, cudaStream_t s, int phase, const int32_t* staged_ids,
                         int32_t* celloff);
