@@ -215,8 +215,10 @@ pic_status pic_get_fields(pic_sim* sim, int which, float* out, int on_device);
 /* Copy one species' particles out, in the library's current (tile-sorted)
  * order.  Each non-NULL array receives n_particles values; id is filled only
  * with PIC_TRACK_IDS.  tile_offset, if non-NULL, receives the ntiles+1
- * bookmark array of §4.1 (int64; tile t = ty*(nx/T) + tx owns particles
- * [tile_offset[t], tile_offset[t+1])).  Synchronises. */
+ * bookmark array of §4.1 (int64; tile t owns particles
+ * [tile_offset[t], tile_offset[t+1]), with t = ty*(nx/T) + tx in a periodic
+ * box and t = (nx/T - 1 - tx)*(ny/T) + ty with a moving window: tile columns
+ * from the right edge, where the plasma enters).  Synchronises. */
 pic_status pic_get_particles(pic_sim* sim, int species, int32_t* ix, int32_t* iy, float* x,
                              float* y, float* ux, float* uy, float* uz, int32_t* id,
                              int64_t* tile_offset, int on_device);

@@ -22,6 +22,9 @@ Parity status per function (what pins each one; the pins live in
 * ``orc_rho``      pinned: the weights of each particle sum to its charge; a
   uniform lattice gives a uniform density.
 * ``orc_tile_sort`` pinned: equal to numpy's stable argsort by tile id.
+* ``tile_order`` / ``tile_offsets_in_order`` (the order of the tiles in the
+  arrays: rows, or with the moving window columns from the right edge) pinned
+  by brute-force counts of the particles in each tile of that order.
 * ``binomial_filter`` pinned: the closed-form response cos^2(k dx/2) cos^2(k dy/2)
   per pass on single Fourier modes, exact conservation of the sum (k = 0), the
   Nyquist mode removed, brute-force 3x3 stencil (1 2 1)(1 2 1)/16.
@@ -55,6 +58,8 @@ from .oracle import (  # noqa: F401
     binomial_filter,
     rho_nodes,
     tile_sort,
+    tile_order,
+    tile_offsets_in_order,
     field_energy,
     div_e,
     div_j,

@@ -188,6 +188,26 @@ def tile_sort(nx, ny, T, ix, iy):
     return perm, counts, offsets
 
 
+def tile_order(nx, ny, T, window=False):
+    """Tile ids (ty * ntx + tx, the order of ``tile_sort``) in the order in
+    which the tile-sorted arrays hold the tiles: row by row in a periodic box;
+    in the moving window's open box column by column from the right edge
+    (tx = ntx - 1 first), each column from ty = 0 up.  §4.1 fixes only that a
+    tile's particles are contiguous; the order of the tiles is free."""
+    ntx, nty = nx // T, ny // T
+    if not window:
+        return np.arange(ntx * nty)
+    return np.array([ty * ntx + tx for tx in range(ntx - 1, -1, -1) for ty in range(nty)],
+                    np.int64)
+
+
+def tile_offsets_in_order(nx, ny, T, ix, iy, window=False):
+    """Bookmarks (ntiles + 1) of particles (ix, iy) with the tiles in
+    ``tile_order``."""
+    counts = tile_sort(nx, ny, T, ix, iy)[1]
+    return np.concatenate([[0], np.cumsum(counts[tile_order(nx, ny, T, window)])]).astype(np.int64)
+
+
 # ---------------------------------------------------------- grid diagnostics
 
 def field_energy(F, dx, dy):
@@ -331,7 +351,8 @@ class OracleSim:
 
     def tile_offsets(self, s: int = 0):
         sp = self.species[s]
-        return tile_sort(self.nx, self.ny, self.tile, sp.ix, sp.iy)[2]
+        return tile_offsets_in_order(self.nx, self.ny, self.tile, sp.ix, sp.iy,
+                                     window=self.window is not None)
 
     def rho(self):
         return rho_nodes(self.nx, self.ny, self.species, np.float64, self.background)

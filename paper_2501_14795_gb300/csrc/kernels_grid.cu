@@ -493,7 +493,7 @@ __global__ void k_rho(const RhoParams prm) {
     const Geom& g = prm.g;
     const int T = g.T, W = T + 1;
     const int t = blockIdx.x;
-    const int tx = t % g.ntx, ty = t / g.ntx;
+    const int tx = tile_x(g, t), ty = tile_y(g, t);
     const int ix0 = tx * T, iy0 = ty * T;
     for (int k = threadIdx.x; k < W * W; k += blockDim.x) sR[k] = 0.0;
     __syncthreads();
@@ -570,7 +570,7 @@ __global__ void k_residuals(const Geom g, const float* F, const float* J, const 
 // phase 1: scan the counts into cell offsets, take the tile bookmarks from
 //          them and scatter into the particle arrays.
 __device__ __forceinline__ int load_key(const Geom& g, int ix, int iy, int k) {
-    const int t = (iy / g.T) * g.ntx + ix / g.T;
+    const int t = tile_index(g, ix / g.T, iy / g.T);
     const unsigned h = ((unsigned)k * 2654435761u) >> 8;  // Knuth's multiplicative hash
     return t * g.T * g.T + (int)(h % (unsigned)(g.T * g.T));
 }

@@ -292,7 +292,7 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
     const unsigned stage_bytes = (unsigned)L::stage_words(nth) * 4u;
 
     const Geom& g = prm.g;
-    const int tx = t % g.ntx, ty = t / g.ntx;
+    const int tx = tile_x(g, t), ty = tile_y(g, t);
     const int ix0 = tx * T, iy0 = ty * T;
     const long long step = *((volatile long long*)&prm.st->step);
     // moving window (open box along x): cells are written in the frame of the

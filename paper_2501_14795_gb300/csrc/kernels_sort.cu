@@ -25,9 +25,9 @@ namespace pic {
 
 namespace {
 
-__device__ __forceinline__ int tile_of(int c, int T, int ntx) {
+__device__ __forceinline__ int tile_of(int c, const Geom& g) {
     const int ix = c & 0xffff, iy = (int)((unsigned)c >> 16);
-    return (iy / T) * ntx + ix / T;
+    return tile_index(g, ix / g.T, iy / g.T);
 }
 
 // neighbour of tile (tx, ty) displaced by direction d (0..7 over the 3x3
@@ -59,7 +59,7 @@ struct Injection {
 __device__ __forceinline__ Injection injection(const SortParams& prm, const SortSpecies& S, int t) {
     Injection r{0, 0, 0};
     const Geom& g = prm.g;
-    if (!g.open_x || S.inj_k == 0 || t % g.ntx != g.ntx - 1) return r;
+    if (!g.open_x || S.inj_k == 0 || tile_x(g, t) != g.ntx - 1) return r;
     if (!*((volatile int*)&prm.st->win_shift)) return r;
     const long long gcol = *((volatile long long*)&prm.st->win_moves) + g.nx - 1;
     r.a0 = inject_first(gcol, S.inj_k, S.inj_x0, g.dx);
@@ -76,7 +76,7 @@ __device__ __forceinline__ void inject_particle(const SortParams& prm, const Sor
     const int k = S.inj_k, na = k - inj.a0;
     const int r = m / inj.per_row, rem = m - r * inj.per_row;
     const int b = rem / na, a = inj.a0 + rem % na;
-    const int iy = (t / g.ntx) * g.T + r;
+    const int iy = tile_y(g, t) * g.T + r;
     S.cell[to] = (g.nx - 1) | (iy << 16);
     S.x[to] = (float)(((double)a + 0.5) / (double)k);
     S.y[to] = (float)(((double)b + 0.5) / (double)k);
@@ -136,7 +136,7 @@ constexpr int SCAN_THREADS = 1024;
 __device__ __forceinline__ int count_tile(const SortParams& prm, int s, int t) {
     const SortSpecies& S = prm.sp[s];
     const Geom& g = prm.g;
-    const int tx = t % g.ntx, ty = t / g.ntx;
+    const int tx = tile_x(g, t), ty = tile_y(g, t);
     const int lv = S.leave[t];
     int c = S.off_old[t + 1] - S.off_old[t] - lv;
 #pragma unroll
@@ -145,7 +145,7 @@ __device__ __forceinline__ int count_tile(const SortParams& prm, int s, int t) {
         dir_delta(d, ddx, ddy);
         if ((g.ntx == 1 && ddx) || (g.nty == 1 && ddy)) continue;
         const int sx = dev::wrapi(tx - ddx, g.ntx), sy = dev::wrapi(ty - ddy, g.nty);
-        c += S.dirc[(sy * g.ntx + sx) * 8 + d];
+        c += S.dirc[tile_index(g, sx, sy) * 8 + d];
     }
     c += injection(prm, S, t).total;
     S.off_new[t] = c;
@@ -239,7 +239,7 @@ __device__ __forceinline__ void scan_species(const SortParams& prm, int s, bool 
         bool bad;
         if (prm.g.open_x) {
             // the count changes by the removed and injected particles
-            const Injection inj = injection(prm, S, prm.g.ntx - 1);
+            const Injection inj = injection(prm, S, tile_index(prm.g, prm.g.ntx - 1, 0));
             const long long want =
                 prm.st->np[s] - prm.st->removed[s] + (long long)inj.total * prm.g.nty;
             bad = carry != want || carry > S.cap;
@@ -339,7 +339,7 @@ __device__ __forceinline__ void fill_tile(const SortParams& prm, int s, int t, i
     const SortSpecies& S = prm.sp[s];
     const Geom& g = prm.g;
     const int T = g.T;
-    const int tx = t % g.ntx, ty = t / g.ntx;
+    const int tx = tile_x(g, t), ty = tile_y(g, t);
     const int p0 = S.off_old[t], p1 = S.off_old[t + 1];
     const int r0 = S.off_new[t], r1 = S.off_new[t + 1];
     const int cap = r1 - r0;
@@ -365,7 +365,7 @@ __device__ __forceinline__ void fill_tile(const SortParams& prm, int s, int t, i
     if (lane < 8) {
         int ddx, ddy;
         dir_delta(lane, ddx, ddy);
-        nb = dev::wrapi(ty + ddy, g.nty) * g.ntx + dev::wrapi(tx + ddx, g.ntx);
+        nb = tile_index(g, dev::wrapi(tx + ddx, g.ntx), dev::wrapi(ty + ddy, g.nty));
     }
     bool keep = lane < 8 && nb != t;
 #pragma unroll
@@ -410,8 +410,8 @@ __device__ __forceinline__ void fill_tile(const SortParams& prm, int s, int t, i
         const int src1 = e1 < total ? source_of(e1) : 0;
         const int c0 = e0 < total ? S.ocell[src0] : HOLE;
         const int c1 = e1 < total ? S.ocell[src1] : HOLE;
-        const bool take0 = e0 < total && tile_of(c0, T, g.ntx) == t;
-        const bool take1 = e1 < total && tile_of(c1, T, g.ntx) == t;
+        const bool take0 = e0 < total && tile_of(c0, g) == t;
+        const bool take1 = e1 < total && tile_of(c1, g) == t;
         const unsigned m0 = __ballot_sync(0xffffffffu, take0);
         const unsigned m1 = __ballot_sync(0xffffffffu, take1);
         if (take0) {

@@ -90,6 +90,28 @@ struct Geom {
     int pad_g;
 };
 
+// Order of the tiles in the tile-sorted arrays (the bookmarks are indexed by
+// it).  A periodic box takes them row by row, t = ty * ntx + tx.  The moving
+// window's open box takes them column by column from its right edge,
+// t = (ntx - 1 - tx) * nty + ty: the plasma (a step profile, filled beyond
+// its edge) enters at the right edge, and its edge walks left through the
+// tiles, one cell per shift.  The tiles around the edge change their counts
+// on every shift, which moves the ranges of all tiles after them in the
+// arrays; in this order those are the tiles to the left of the edge, still
+// empty, instead of the whole plasma.  The tile column that receives the
+// injected plasma comes first and hands its left cell column to the next
+// tile column on each shift, which keeps the counts of the filled tiles
+// balanced.
+__host__ __device__ inline int tile_index(const Geom& g, int tx, int ty) {
+    return g.open_x ? (g.ntx - 1 - tx) * g.nty + ty : ty * g.ntx + tx;
+}
+__host__ __device__ inline int tile_x(const Geom& g, int t) {
+    return g.open_x ? g.ntx - 1 - t / g.nty : t % g.ntx;
+}
+__host__ __device__ inline int tile_y(const Geom& g, int t) {
+    return g.open_x ? t % g.nty : t / g.ntx;
+}
+
 // Moving window (the last steps of Listing 3.1; the window moves at c = 1).
 // Cells moved after k steps, M(k) = floor(k dt / dx + 1e-9), in IEEE double
 // with the operation order of the host and the tests.

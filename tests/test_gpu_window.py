@@ -98,9 +98,10 @@ def test_cold_plasma_at_rest_is_exactly_relabelled_by_the_window(flags):
             assert not np.any(got["ux"]) and not np.any(got["uy"]) and not np.any(got["uz"])
             for f in (pic.FIELD_E, pic.FIELD_B, pic.FIELD_J):
                 assert not np.any(sim.fields(f))
-            # every particle sits in the range of its tile
+            # every particle sits in the range of its tile (the window's
+            # tile order: columns from the right edge)
             off = got["tile_offset"]
-            tid = (got["iy"] // T) * (nx // T) + got["ix"] // T
+            tid = (nx // T - 1 - got["ix"] // T) * (ny // T) + got["iy"] // T
             for t in range(len(off) - 1):
                 assert np.all(tid[off[t]:off[t + 1]] == t)
 

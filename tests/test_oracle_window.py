@@ -166,3 +166,21 @@ def test_gaussian_beam_diffracts_down_to_its_waist_at_the_focus():
     for _ in range(int(round(zR / dt))):
         orc.yee(E, B, J, dx, dy, dt)
     assert width() == pytest.approx(W0 / 2, rel=2e-2)
+
+
+@pytest.mark.parametrize("window", [False, True])
+def test_tile_order_bookmarks_count_each_tile_by_brute_force(window):
+    """Tile t of the order owns off[t+1] - off[t] particles: those whose tile
+    coordinates are (t % ntx, t // ntx) in rows, or (ntx - 1 - t // nty,
+    t % nty) in the window's columns from the right edge."""
+    nx, ny, T = 48, 32, 8
+    ntx, nty = nx // T, ny // T
+    rng = np.random.default_rng(21)
+    ix = rng.integers(0, nx, 500).astype(np.int32)
+    iy = rng.integers(0, ny, 500).astype(np.int32)
+    off = orc.tile_offsets_in_order(nx, ny, T, ix, iy, window=window)
+    assert off[0] == 0 and off[-1] == ix.size and off.size == ntx * nty + 1
+    for t in range(ntx * nty):
+        tx, ty = (ntx - 1 - t // nty, t % nty) if window else (t % ntx, t // ntx)
+        n = sum(1 for a, b in zip(ix, iy) if a // T == tx and b // T == ty)
+        assert off[t + 1] - off[t] == n
