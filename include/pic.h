@@ -230,6 +230,16 @@ int64_t pic_num_particles(const pic_sim* sim, int species);
 /* Number of tiles (nx/T)*(ny/T). */
 int64_t pic_num_tiles(const pic_sim* sim);
 
+/* The failure path of the library's bounded device waits, on its own (every
+ * wait of its kernels on an mbarrier gives up after about 2e9 clock cycles,
+ * about a second, drains the copies it had issued and reports PIC_ETIMEOUT
+ * instead of hanging).  One CTA waits on an mbarrier with the same helper:
+ * with arrive != 0 the phase completes first (PIC_OK); with arrive == 0
+ * nothing completes it and the wait gives up after limit_cycles
+ * (1..4e9; PIC_ETIMEOUT).  No copy is in flight either way, and the context
+ * stays usable.  Synchronises `cuda_stream`. */
+pic_status pic_probe_bounded_wait(int arrive, int64_t limit_cycles, void* cuda_stream);
+
 /* Diagnostics at the current time level (see pic_diag).  Synchronises; FP64
  * reductions on the device. */
 pic_status pic_diagnostics(pic_sim* sim, pic_diag* out);

@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(YTHREADS) k_yee_tma(const __grid_constant__ CU
     }
     float we = 0.f, wb = 0.f;
     bool ok = true;
-    int it = 0;
+    int it = 0, t_stop = -1;
     for (int t = blockIdx.x; t < nt; t += gridDim.x, ++it) {
         const int st = it & 1;
         float* sE = stage0 + st * TSTAGE_FLOATS;
@@ -260,7 +260,10 @@ __global__ void __launch_bounds__(YTHREADS) k_yee_tma(const __grid_constant__ CU
         float* sJ = sE + TOFF_J;
         const int i0 = (t % nbx) * YX, j0 = (t / nbx) * YY;
         if (!dev::mbar_wait_bounded(bar + st, (it >> 1) & 1u)) ok = false;
-        if (__syncthreads_or(!ok)) break;
+        if (__syncthreads_or(!ok)) {
+            t_stop = t;
+            break;
+        }
         // J at cells nx (periodic box) and ny: the images of cells 0
         if (!g.open_x && i0 <= g.nx && g.nx <= i0 + YX)
             for (int k = tid; k < 3 * JHY; k += YTHREADS) {
@@ -286,8 +289,15 @@ __global__ void __launch_bounds__(YTHREADS) k_yee_tma(const __grid_constant__ CU
             issue(nxt, st);
         }
     }
-    if (!ok) {
-        if (tid == 0) dev::set_status(prm.st, ST_TIMEOUT);
+    if (t_stop >= 0) {
+        if (tid == 0) {
+            // the copies still in flight, once more, before leaving: this
+            // tile's stage and, if it was issued, the next tile's
+            dev::mbar_wait_bounded(bar + (it & 1), (it >> 1) & 1u);
+            if (t_stop + (int)gridDim.x < nt)
+                dev::mbar_wait_bounded(bar + ((it + 1) & 1), ((it + 1) >> 1) & 1u);
+            dev::set_status(prm.st, ST_TIMEOUT);
+        }
         return;
     }
     const double dxdy = g.dx * g.dy;
@@ -714,6 +724,24 @@ __global__ void k_off64(const int32_t* off, int n, int64_t* out) {
         out[k] = off[k];
 }
 
+// The failure path of the bounded waits, on its own: one CTA waits on an
+// mbarrier with the helper every kernel uses.  With `arrive` thread 0 arrives
+// first and the phase completes; without it nothing ever completes the phase
+// (no copy is issued, so none is in flight) and the wait gives up after
+// `limit` cycles.  result: 0, or ST_TIMEOUT.
+__global__ void k_probe_wait(int arrive, long long limit, unsigned* result) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        dev::mbar_init(&bar, 1);
+        dev::fence_mbar_init();
+    }
+    __syncthreads();
+    if (arrive && threadIdx.x == 0) dev::mbar_arrive_expect_tx(&bar, 0);
+    const bool ok = dev::mbar_wait_bounded(&bar, 0u, limit);
+    const bool out = __syncthreads_or(!ok);
+    if (threadIdx.x == 0) *result = out ? ST_TIMEOUT : 0u;
+}
+
 __global__ void k_hist_prime(double* he, double* hb, double* hk, DevState* st) {
     const long long n = st->step;
     he[n & (HIST - 1)] = 0.0;
@@ -879,6 +907,11 @@ cudaError_t launch_unpack_cells(const int32_t* cell, int64_t n, int32_t* ix, int
 
 cudaError_t launch_offsets_to_i64(const int32_t* off, int64_t n, int64_t* out, cudaStream_t s) {
     k_off64<<<grid_for(n, 256), 256, 0, s>>>(off, (int)n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probe_wait(int arrive, long long limit, unsigned* result, cudaStream_t s) {
+    k_probe_wait<<<1, 64, 0, s>>>(arrive, limit, result);
     return cudaGetLastError();
 }
 

@@ -68,11 +68,17 @@ constexpr unsigned FULL = 0xffffffffu;
 #define PIC_J_FIXED 1
 #endif
 // At most 512 threads per CTA, one CTA per SM guaranteed: with these bounds
-// the compiler gives the particle path 64 registers (56 under a 1024-thread
-// bound, 51 under a bare 512-thread one), enough to avoid recomputing values
-// (measured on GB300: -7 % particle-advance time with the flush-to-zero
-// build), and 4 CTAs of 256 threads still fit on an SM.
+// the compiler gives the periodic particle path 63-64 registers (56 under a
+// 1024-thread bound, 51 under a bare 512-thread one), enough to avoid
+// recomputing values (measured on GB300: -7 % particle-advance time with the
+// flush-to-zero build), and 4 CTAs of 256 threads still fit on an SM.  The
+// choice is fragile: small changes outside the particle loop (an early exit
+// from the species loop) moved it to 80, and on the periodic kernel explicit
+// caps at 64 (__maxnreg__, a (512, 2) bound) measured 8-10 % slower than
+// this bound.  Under the same bound the moving-window kernel took 68-69 (3
+// CTAs per SM, 8 % slower); it is capped explicitly instead.
 constexpr int MAX_PUSH_THREADS = 512;
+constexpr int PUSH_WINDOW_REGS = 64;
 constexpr int NSTAGE = PIC_NSTAGE;  // particle batches (blockDim particles each) in flight per CTA
 constexpr int PAD = 4;     // a batch is copied from a 16-byte aligned start: <= 3 extra
 // warps sharing one fixed-point J tile (per-warp tiles: 1)
@@ -310,7 +316,10 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
     const bool ok = dev::mbar_wait_bounded(bar, fphase);
     fphase ^= 1u;
     if (__syncthreads_or(!ok)) {
-        if (tid == 0) dev::set_status(prm.st, ST_TIMEOUT);
+        if (tid == 0) {
+            dev::mbar_wait_bounded(bar, fphase ^ 1u);  // the halo copy, once more, before leaving
+            dev::set_status(prm.st, ST_TIMEOUT);
+        }
         return false;
     }
 
@@ -609,7 +618,22 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
         gb += nb;
         ke_tot += (double)ke * S.ke_w;
     }
-    __syncthreads();
+    if (__syncthreads_or(bad_bits & ST_TIMEOUT)) {
+        // a wait ran out: wait (bounded) once more for the last copy issued
+        // into each stage, so that none is in flight when the CTA leaves.
+        // Every batch of every species was issued (releases and refills go on
+        // after a wait runs out), so the copies issued are those of the
+        // global batch indices below gb, in order.
+        if (tid == 0) {
+            for (unsigned st = 0; st < (unsigned)NSTAGE; ++st)
+                if (gb > st) {
+                    const unsigned g = st + ((gb - 1 - st) / NSTAGE) * NSTAGE;
+                    dev::mbar_wait_bounded(sbar + st, (g / NSTAGE) & 1u);
+                }
+            dev::set_status(prm.st, ST_TIMEOUT);
+        }
+        return false;
+    }
 
     // ---- leavers by destination, for the re-sort's counts ----
     for (int s = 0; s < prm.nsp; ++s)
@@ -663,13 +687,24 @@ __device__ __forceinline__ void init_barriers(uint64_t* bar) {
     }
 }
 
-// One simulation: CTA (tile, chunk) = (blockIdx.x, blockIdx.y).
-template <int T, bool PW, bool OPEN>
+// One simulation: CTA (tile, chunk) = (blockIdx.x, blockIdx.y).  The
+// periodic box and the moving window's open box are separate kernels, each
+// with the register budget measured best for it (see MAX_PUSH_THREADS).
+template <int T, bool PW>
 __global__ void __launch_bounds__(MAX_PUSH_THREADS, 1) k_push(const __grid_constant__ CUtensorMap fmap,
-                                               const PushParams prm) {
+                                                             const PushParams prm) {
     extern __shared__ __align__(128) unsigned char smem[];
     init_barriers(reinterpret_cast<uint64_t*>(smem + Tile<T, PW>::off_misc(blockDim.x)));
-    if (OPEN && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    unsigned fphase = 0, gb = 0;
+    push_item<T, PW, false>(prm, &fmap, blockIdx.x, blockIdx.y, fphase, gb);
+}
+
+template <int T, bool PW>
+__global__ void __maxnreg__(PUSH_WINDOW_REGS) k_push_window(const __grid_constant__ CUtensorMap fmap,
+                                                            const PushParams prm) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    init_barriers(reinterpret_cast<uint64_t*>(smem + Tile<T, PW>::off_misc(blockDim.x)));
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
         // the window decision of this step, for the re-sort and field kernels
         // that follow (no CTA of this launch reads them)
         const int w = window_shift(*((volatile long long*)&prm.st->step), prm.g);
@@ -677,7 +712,7 @@ __global__ void __launch_bounds__(MAX_PUSH_THREADS, 1) k_push(const __grid_const
         prm.st->win_moves += w;
     }
     unsigned fphase = 0, gb = 0;
-    push_item<T, PW, OPEN>(prm, &fmap, blockIdx.x, blockIdx.y, fphase, gb);
+    push_item<T, PW, true>(prm, &fmap, blockIdx.x, blockIdx.y, fphase, gb);
 }
 
 // Many simulations in one persistent launch: each CTA takes work items
@@ -725,9 +760,9 @@ static cudaError_t set_smem_limit() {
     size_t b = Tile<T, PW>::bytes_batch(1024);
     if (b > SMEM_MAX) b = SMEM_MAX;
     cudaError_t e =
-        cudaFuncSetAttribute(k_push<T, PW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+        cudaFuncSetAttribute(k_push<T, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_push<T, PW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+    e = cudaFuncSetAttribute(k_push_window<T, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_push_batch<T, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)b);
@@ -749,11 +784,11 @@ static cudaError_t launch_T(const CUtensorMap* fmap, const PushParams& p, int th
     const bool pw = kPW && Tile<T, kPW>::bytes(threads) <= SMEM_MAX;
     const size_t bytes = pw ? Tile<T, kPW>::bytes(threads) : Tile<T, false>::bytes(threads);
     if (p.g.open_x) {
-        if (pw) k_push<T, kPW, true><<<grid, threads, bytes, s>>>(*fmap, p);
-        else k_push<T, false, true><<<grid, threads, bytes, s>>>(*fmap, p);
+        if (pw) k_push_window<T, kPW><<<grid, threads, bytes, s>>>(*fmap, p);
+        else k_push_window<T, false><<<grid, threads, bytes, s>>>(*fmap, p);
     } else {
-        if (pw) k_push<T, kPW, false><<<grid, threads, bytes, s>>>(*fmap, p);
-        else k_push<T, false, false><<<grid, threads, bytes, s>>>(*fmap, p);
+        if (pw) k_push<T, kPW><<<grid, threads, bytes, s>>>(*fmap, p);
+        else k_push<T, false><<<grid, threads, bytes, s>>>(*fmap, p);
     }
     return cudaGetLastError();
 }

@@ -296,7 +296,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
             for (int rr = 0; rr < TC_R; ++rr)
                 epilogue<NT>(p, sBias, tmem + (pb * TC_R + rr) * L::NTC, prev, rr, warp, lane);
     }
-    if (!ok && tid == 0 && p.status) atomicOr(p.status, 2u);  // a bounded wait ran out
+    if (!ok && tid == 0) {
+        if (p.status) atomicOr(p.status, 2u);  // a bounded wait ran out
+        // the products still in flight, once more, before the accumulators
+        // are freed: the last commit on each of the two barriers (unit j
+        // commits on barrier j & 1, phase (j >> 1) & 1)
+        for (int j = i - 1; j >= 0 && j >= i - 2; --j) wait_bar(bar0 + 8 * (j & 1), (j >> 1) & 1);
+    }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();

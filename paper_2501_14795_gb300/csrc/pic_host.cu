@@ -835,6 +835,20 @@ int64_t pic_num_particles(const pic_sim* sim, int species) {
 
 int64_t pic_num_tiles(const pic_sim* sim) { return sim ? sim->g.ntiles : -1; }
 
+pic_status pic_probe_bounded_wait(int arrive, int64_t limit_cycles, void* cuda_stream) {
+    if (limit_cycles < 1 || limit_cycles > 4000000000LL) return PIC_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    unsigned* d = nullptr;
+    if (cudaMalloc((void**)&d, sizeof(unsigned)) != cudaSuccess) return PIC_ENOMEM;
+    unsigned h = 0;
+    const bool ok = launch_probe_wait(arrive != 0, limit_cycles, d, s) == cudaSuccess &&
+                    cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+                    cudaStreamSynchronize(s) == cudaSuccess;
+    cudaFree(d);
+    if (!ok) return PIC_ECUDA;
+    return (h & ST_TIMEOUT) ? PIC_ETIMEOUT : PIC_OK;
+}
+
 pic_status pic_diagnostics(pic_sim* sim, pic_diag* out) {
     if (!sim || !out) return PIC_EINVAL;
     sim->err.clear();

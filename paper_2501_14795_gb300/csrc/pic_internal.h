@@ -277,6 +277,9 @@ cudaError_t launch_unpack_cells(const int32_t* cell, int64_t n, int32_t* ix, int
 cudaError_t launch_offsets_to_i64(const int32_t* off, int64_t n, int64_t* out, cudaStream_t s);
 cudaError_t launch_hist_prime(double* hist_e, double* hist_b, double* hist_k, DevState* st,
                               cudaStream_t s);
+// one CTA waiting on an mbarrier that completes (arrive) or never does;
+// *result = 0 or ST_TIMEOUT (device word)
+cudaError_t launch_probe_wait(int arrive, long long limit, unsigned* result, cudaStream_t s);
 
 // Laser pulse of the initial conditions (§3.2), added to E|B (6 components)
 // with its guard images; x of node column 0 is (moves + 0) dx with moves read

@@ -143,6 +143,7 @@ def load_library() -> C.CDLL:
                                            _P, _P]
         L.pic_nn_conv3x3_wgrad.argtypes = [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                            _P, _P]
+        L.pic_probe_bounded_wait.argtypes = [C.c_int, C.c_int64, _P]
         L.pic_denoiser_set_low_k_restore.argtypes = [_P, C.c_int]
         L.pic_nn_low_k_restore.argtypes = [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P]
         for name in ("pic_init", "pic_load_particles", "pic_set_fields", "pic_step",
@@ -154,7 +155,7 @@ def load_library() -> C.CDLL:
                      "pic_denoiser_grad", "pic_denoiser_train_step", "pic_set_denoiser",
                      "pic_nn_conv3x3", "pic_nn_conv3x3_dgrad", "pic_nn_conv3x3_wgrad",
                      "pic_set_binomial_filter", "pic_denoiser_set_low_k_restore",
-                     "pic_nn_low_k_restore"):
+                     "pic_nn_low_k_restore", "pic_probe_bounded_wait"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -519,6 +520,13 @@ def pic_nn_conv3x3_wgrad(x, dz, dw, stream=None):
                                              stream)
     if st != 0:
         raise PicError(st, "pic_nn_conv3x3_wgrad")
+
+
+def pic_probe_bounded_wait(arrive, limit_cycles, stream=None):
+    """Status code of the bounded-wait probe (0 = PIC_OK, PIC_ETIMEOUT)."""
+    if stream is None:
+        stream = _default_stream()
+    return load_library().pic_probe_bounded_wait(int(arrive), int(limit_cycles), stream)
 
 
 def pic_nn_low_k_restore(raw, out, passes, stream=None):

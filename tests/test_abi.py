@@ -119,6 +119,13 @@ def test_denoiser_restoration_entry_points_check_arguments_without_gpu(lib):
     assert L.pic_nn_low_k_restore(fake, fake, 0, 8, 8, 1, None) == 1
 
 
+def test_bounded_wait_probe_checks_its_limit_without_gpu(lib):
+    from paper_2501_14795_gb300 import pic
+    L = pic.load_library()
+    assert L.pic_probe_bounded_wait(0, 0, None) == 1
+    assert L.pic_probe_bounded_wait(0, 4_000_000_001, None) == 1
+
+
 def test_binding_structs_match_the_c_header(tmp_path):
     """sizeof and offsetof of every ABI struct as gcc lays them out from
     include/pic.h equal the ctypes mirrors of the binding."""
