@@ -377,7 +377,7 @@ typedef struct pic_denoiser pic_denoiser;
 int64_t pic_denoiser_num_params(void);
 
 /* nx a multiple of 64, ny of 32 (two 2x poolings onto 16x8 convolution
- * tiles); batch_max >= 1 samples per call; scale > 0 the current
+ * tiles), ny <= 65535; batch_max >= 1 samples per call; scale > 0 the current
  * normalisation.  Parameters start at zero (the network is the identity). */
 pic_status pic_denoiser_create(int nx, int ny, int batch_max, double scale, void* cuda_stream,
                                pic_denoiser** out);

@@ -451,7 +451,7 @@ pic_status pic_denoiser_create(int nx, int ny, int batch_max, double scale, void
                                pic_denoiser** out) {
     if (!out) return PIC_EINVAL;
     *out = nullptr;
-    if (nx < 64 || ny < 32 || nx % 64 || ny % 32 || batch_max < 1 || batch_max > 4096 ||
+    if (nx < 64 || ny < 32 || nx % 64 || ny % 32 || ny > 65535 || batch_max < 1 || batch_max > 4096 ||
         !(scale > 0) || !std::isfinite(scale))
         return PIC_EINVAL;
     const long long P0 = (long long)batch_max * nx * ny;

@@ -598,32 +598,44 @@ __global__ void __launch_bounds__(256) k_mse(const float* out, const float* targ
 // (k_lowk_y: a 64-row x 32-column tile and its halo rows).
 // i mod n in [0, n) for any i (the halo may wrap several times on small lattices)
 __device__ __forceinline__ int wrap_any(int i, int n) {
+    if (i >= 0 && i < n) return i;  // nearly every index: no division
     i %= n;
     return i < 0 ? i + n : i;
 }
 
-constexpr int LK_ROW = 256;                    // outputs per CTA of the row pass
+constexpr int LK_ROW = 256;                    // outputs per row of the row pass
+// rows per CTA of the row pass and of the copy: 8 on large lattices (fewer,
+// longer CTAs), 1 on small ones (more CTAs in flight)
+__host__ __device__ inline int lk_rows(int B, int H, int W) {
+    return 3LL * B * H * W >= (1LL << 23) ? 8 : 1;
+}
 constexpr int LK_TY = 64, LK_TX = 32, LK_YT = 8;  // column pass: tile rows, columns, thread rows
 
-// t = rows of (a - b) (b.p null: a) filtered along x; t dense [B][3][H][W]
+// t = rows of (a - b) (b.p null: a) filtered along x; t dense [B][3][H][W].
+// CTA = LK_ROW columns of lk_rows rows.
 __global__ void k_lowk_x(FieldView a, FieldView b, float* t, LowkTaps w, int B, int H, int W) {
     extern __shared__ float sRow[];  // LK_ROW + 2n values
     const int n = w.n;
-    const int x0 = blockIdx.x * LK_ROW, y = blockIdx.y;
+    const int x0 = blockIdx.x * LK_ROW;
     const int c = blockIdx.z % 3, smp = blockIdx.z / 3;
-    const float* pa = a.p + smp * a.bstride + c * a.cstride + a.offset + (long long)y * a.pitch;
-    const float* pb =
-        b.p ? b.p + smp * b.bstride + c * b.cstride + b.offset + (long long)y * b.pitch : nullptr;
-    for (int i = threadIdx.x; i < LK_ROW + 2 * n; i += blockDim.x) {
-        const int x = wrap_any(x0 + i - n, W);
-        sRow[i] = pb ? pa[x] - pb[x] : pa[x];
-    }
-    __syncthreads();
     const int x = x0 + threadIdx.x;
-    if (x >= W) return;
-    float v = 0.f;
-    for (int k = 0; k <= 2 * n; ++k) v = fmaf(w.w[k], sRow[threadIdx.x + k], v);
-    t[((long long)blockIdx.z * H + y) * W + x] = v;
+    const int rows = lk_rows(B, H, W);
+    for (int y = blockIdx.y * rows; y < min(H, (int)(blockIdx.y + 1) * rows); ++y) {
+        const float* pa = a.p + smp * a.bstride + c * a.cstride + a.offset + (long long)y * a.pitch;
+        const float* pb =
+            b.p ? b.p + smp * b.bstride + c * b.cstride + b.offset + (long long)y * b.pitch : nullptr;
+        __syncthreads();  // the previous row's reads of sRow are done
+        for (int i = threadIdx.x; i < LK_ROW + 2 * n; i += blockDim.x) {
+            const int xs = wrap_any(x0 + i - n, W);
+            sRow[i] = pb ? pa[xs] - pb[xs] : pa[xs];
+        }
+        __syncthreads();
+        if (x < W) {
+            float v = 0.f;
+            for (int k = 0; k <= 2 * n; ++k) v = fmaf(w.w[k], sRow[threadIdx.x + k], v);
+            t[((long long)blockIdx.z * H + y) * W + x] = v;
+        }
+    }
 }
 
 // out += columns of t filtered along y
@@ -647,18 +659,17 @@ __global__ void k_lowk_y(const float* t, FieldView o, LowkTaps w, int B, int H, 
     }
 }
 
-// o = a, element by element (layouts may differ)
+// o = a, element by element (layouts may differ); CTA = 256 columns of
+// lk_rows rows of one component of one sample (blockIdx.z)
 __global__ void k_field_copy(FieldView a, FieldView o, int B, int H, int W) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)B * 3 * H * W) return;
-    const int x = (int)(i % W);
-    long long r = i / W;
-    const int y = (int)(r % H);
-    r /= H;
-    const int c = (int)(r % 3);
-    const long long smp = r / 3;
-    o.p[smp * o.bstride + c * o.cstride + o.offset + (long long)y * o.pitch + x] =
-        a.p[smp * a.bstride + c * a.cstride + a.offset + (long long)y * a.pitch + x];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= W) return;
+    const int c = blockIdx.z % 3, smp = blockIdx.z / 3;
+    const float* pa = a.p + smp * a.bstride + c * a.cstride + a.offset + x;
+    float* po = o.p + smp * o.bstride + c * o.cstride + o.offset + x;
+    const int rows = lk_rows(B, H, W);
+    for (int y = blockIdx.y * rows; y < min(H, (int)(blockIdx.y + 1) * rows); ++y)
+        po[(long long)y * o.pitch] = pa[(long long)y * a.pitch];
 }
 
 __global__ void k_adam(float* p, const float* g, float* m, float* v, long long n, float lr,
@@ -897,7 +908,8 @@ cudaError_t launch_lowk(const FieldView& a, const FieldView& b, float* t, const 
     if (n <= 0 || (long long)B * H * W == 0) return cudaSuccess;
     if (n > LOWK_MAX) return cudaErrorInvalidValue;
     const LowkTaps w = lowk_taps(n);
-    const dim3 gx((W + LK_ROW - 1) / LK_ROW, H, 3 * B);
+    const int rows = lk_rows(B, H, W);
+    const dim3 gx((W + LK_ROW - 1) / LK_ROW, (H + rows - 1) / rows, 3 * B);
     k_lowk_x<<<gx, LK_ROW, (LK_ROW + 2 * n) * sizeof(float), s>>>(a, b, t, w, B, H, W);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -911,7 +923,8 @@ cudaError_t launch_field_copy(const FieldView& a, const FieldView& o, int B, int
                               cudaStream_t s) {
     const long long n = (long long)B * 3 * H * W;
     if (n == 0) return cudaSuccess;
-    k_field_copy<<<blocks(n, 256), 256, 0, s>>>(a, o, B, H, W);
+    const int rows = lk_rows(B, H, W);
+    k_field_copy<<<dim3((W + 255) / 256, (H + rows - 1) / rows, 3 * B), 256, 0, s>>>(a, o, B, H, W);
     return cudaGetLastError();
 }
 
