@@ -60,6 +60,9 @@ WORKLOADS = {
     # (64 ppc vs its 1/16 subsample), the denoised 4-ppc run against 64 ppc
     "denoiser": dict(kind="denoiser", kw=dict(nx=256, ny=256, pairs_per_draw=200, draws=10,
                                               iters=4000, batch=16), tile=16),
+    # the denoiser's forward pass alone on one 2048x2048 sample (the largest
+    # grid the in-loop speedup is quoted on), parameters of the network's shapes
+    "denoiser_fwd_2048": dict(kind="denoiser_fwd", kw=dict(nx=2048, ny=2048), tile=16),
 }
 
 
@@ -228,6 +231,10 @@ def run_reference(args, rank, world):
         return
     import oracle
     from paper_2501_14795_gb300 import workloads as wl
+    kind = WORKLOADS[args.workload]["kind"]
+    if kind == "denoiser_fwd":
+        run_reference_denoiser_fwd(args, world)
+        return
     w = wl.weibel(nx=64, ny=64, k=8, tile=16)
     s = w.species[0]
     o = oracle.OracleSim(w.nx, w.ny, w.dx, w.dy, w.dt, w.tile,
@@ -238,18 +245,50 @@ def run_reference(args, rank, world):
     o.step(args.steps)
     dt = time.perf_counter() - t0
     value = w.n_particles * args.steps / dt
-    full = make_workload(args.workload)
+    if kind in ("batch", "denoiser"):
+        config = {"workload": args.workload}
+    else:
+        config = workload_config(args.workload, make_workload(args.workload), args.threads)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": workload_config(args.workload, full, args.threads),
+            "config": config,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"each step: the Weibel physics on a 64x64 periodic grid, "
                                        f"2x8x8 ppc ({w.n_particles} particles), FP64 single-thread "
                                        f"C oracle"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_reference_denoiser_fwd(args, world):
+    """Reference arm of the forward-only denoiser workload: the FP64 numpy
+    oracle's forward pass on a bounded 64x64 sample, in the same unit."""
+    from oracle import denoiser as D
+    from paper_2501_14795_gb300 import denoise as dn
+    n = 64
+    rng = np.random.Generator(np.random.PCG64(dn.SEED_DENOISER + 11))
+    x = 0.03 * rng.standard_normal((1, n, n, 3))
+    p = D.init_params(dn.SEED_DENOISER + 7)
+    for _ in range(args.warmup):
+        D.forward(p, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        D.forward(p, x)
+    dt = time.perf_counter() - t0
+    value = dn.forward_flops(n, n) * args.steps / dt / 1e12
+    print(json.dumps({
+        "impl": "reference", "metric": "denoiser forward throughput", "value": value,
+        "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: the FP64 numpy oracle's forward pass of one "
+                                   f"{n}x{n} sample"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
 
 
 def run_batched(args, rank, world, local_rank):
@@ -519,6 +558,73 @@ def run_denoiser(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_denoiser_fwd(args, rank, world, local_rank):
+    """Tensor-core throughput of the denoiser's forward pass on one large
+    sample: K forwards timed with CUDA events on the launching stream, the
+    input resident in HBM; end to end, the same forwards from a host buffer
+    (the library stages it and copies the result back)."""
+    import torch
+    from paper_2501_14795_gb300 import denoise as dn
+    from paper_2501_14795_gb300 import pic
+
+    torch.cuda.set_device(local_rank)
+    kw = WORKLOADS[args.workload]["kw"]
+    nx, ny = kw["nx"], kw["ny"]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(dn.SEED_DENOISER + 11)
+    x = 0.03 * torch.randn((1, 3, ny, nx), device="cuda", generator=gen)
+    o = torch.empty_like(x)
+    net = pic.Denoiser(nx, ny, 1, 0.03)
+    params = dn.init_params(dn.SEED_DENOISER + 7)
+    rng = np.random.Generator(np.random.PCG64(dn.SEED_DENOISER + 8))
+    params[-(9 * 32 * 3 + 3):] = rng.uniform(-0.05, 0.05, 9 * 32 * 3 + 3)  # a live last layer
+    net.set_params(params.astype(np.float32))
+    for _ in range(args.warmup):
+        pic.pic_denoiser_forward(net.d, x, o, 1)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            pic.pic_denoiser_forward(net.d, x, o, 1)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    xh = x.cpu().numpy()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oh = net.forward(xh)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    net.close()
+    ms, e2e_ms = max_over_ranks(ms, e2e_ms)
+    if rank != 0:
+        return
+    flops = dn.forward_flops(nx, ny)
+    achieved = flops / (ms * 1e-3) / 1e12
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak = float(json.load(open(p))["bf16_tflops"]) if os.path.exists(p) else 1900.0
+    line = {
+        "metric": "denoiser forward throughput", "value": achieved * world, "unit": "TFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 (accumulate f32)", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": [nx, ny], "batch": 1,
+                   "flops_per_forward": flops,
+                   "l2": "inputs larger than L2 (one full-resolution activation 268 MB > 129 MB)"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "whole forward pass (14 launches)",
+                     "peak_source": "measured bf16_tflops" if os.path.exists(p) else "fallback"},
+        "e2e": {"value": flops / (e2e_ms * 1e-3) / 1e12 * world, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": xh.nbytes, "d2h_bytes_per_step": oh.nbytes},
+        "gpu_launches": 14 * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_2501_14795_gb300 import pic
@@ -662,6 +768,8 @@ def main():
             run_batched(args, rank, world, local_rank)
         elif args.workload == "denoiser":
             run_denoiser(args, rank, world, local_rank)
+        elif args.workload == "denoiser_fwd_2048":
+            run_denoiser_fwd(args, rank, world, local_rank)
         else:
             run_gpu(args, rank, world, local_rank)
     finally:
