@@ -391,9 +391,10 @@ pic_status pic_denoiser_forward(pic_denoiser* d, const float* J_in, float* J_out
                                 int on_device);
 
 /* Passes n of the low-wavenumber restoration (0: off, the default; at most
- * PIC_LOW_K_MAX_PASSES, else PIC_EINVAL).  A simulation captures the setting
- * when pic_set_denoiser installs d: call pic_set_denoiser again after a
- * change.  The restoration uses the gradient buffers as scratch. */
+ * PIC_LOW_K_MAX_PASSES, else PIC_EINVAL).  A simulation that has already
+ * stepped with d keeps the setting it had in its captured step graphs: call
+ * pic_set_denoiser again after a change (that rebuilds them).  The
+ * restoration uses the gradient buffers as scratch. */
 pic_status pic_denoiser_set_low_k_restore(pic_denoiser* d, int passes);
 
 /* Loss (mean squared error of the normalised output against J_target / scale)

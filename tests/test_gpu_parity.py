@@ -509,3 +509,24 @@ def test_electron_positron_weibel_follows_the_oracle():
     assert d["w_k"] == pytest.approx(o.ke_history[-1], rel=1e-5)
     assert abs(d["charge_total"]) < 1e-9
     assert d2["continuity_max"] < 1e-4
+
+
+@pytest.mark.parametrize("nx,ny,T,n", [(1040, 528, 16, 2_000_003), (160, 48, 16, 30_011)])
+def test_load_sorts_ragged_lattices_like_the_oracle(nx, ny, T, n):
+    """The load path's per-cell count scan runs over segments of 4096 cells:
+    on 1040 x 528 (549,120 cells, 134 segments and a ragged last one) and
+    160 x 48 (7,680 cells, two segments) the tile bookmarks equal the oracle's
+    bit for bit and every input particle is in its tile's range, unchanged."""
+    w, _, _ = _random_case(nx, ny, T, n, seed=nx + ny)
+    with _gpu(w, pic.PIC_TRACK_IDS, tile=T) as sim:
+        got = sim.particles(0, ids=True)
+    s = w.species[0]
+    np.testing.assert_array_equal(got["tile_offset"],
+                                  oracle.tile_offsets_in_order(nx, ny, T, s.ix, s.iy))
+    tid = _tile_ids(got["ix"], got["iy"], nx, T)
+    off = got["tile_offset"]
+    assert np.all(np.repeat(np.arange(off.size - 1), np.diff(off)) == tid)
+    d = _by_id(got)
+    assert np.array_equal(d["id"], np.arange(n))
+    for k, v in zip(("ix", "iy", "x", "y", "ux", "uy", "uz"), s.arrays()):
+        np.testing.assert_array_equal(d[k], v)
