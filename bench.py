@@ -63,6 +63,8 @@ WORKLOADS = {
     # the denoiser's forward pass alone on one 2048x2048 sample (the largest
     # grid the in-loop speedup is quoted on), parameters of the network's shapes
     "denoiser_fwd_2048": dict(kind="denoiser_fwd", kw=dict(nx=2048, ny=2048), tile=16),
+    # the same at 1024x1024 (a smaller case of the same kernels, for profiling)
+    "denoiser_fwd_1024": dict(kind="denoiser_fwd", kw=dict(nx=1024, ny=1024), tile=16),
 }
 
 
@@ -768,7 +770,7 @@ def main():
             run_batched(args, rank, world, local_rank)
         elif args.workload == "denoiser":
             run_denoiser(args, rank, world, local_rank)
-        elif args.workload == "denoiser_fwd_2048":
+        elif WORKLOADS[args.workload]["kind"] == "denoiser_fwd":
             run_denoiser_fwd(args, rank, world, local_rank)
         else:
             run_gpu(args, rank, world, local_rank)
