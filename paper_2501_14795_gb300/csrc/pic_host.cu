@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -34,10 +35,21 @@ pic_status fail(pic_sim* s, pic_status code, const char* fmt, ...) {
 
 #define CK(call) PIC_CK(sim, call)
 
+// Host-side fault injection for the allocation-failure paths: with
+// PIC_FAULT=alloc in the environment (read at every call, so it can be set
+// around a single call) each device allocation of a simulation reports
+// cudaErrorMemoryAllocation without calling cudaMalloc.  Nothing reaches the
+// GPU; the clean-up and the PIC_ENOMEM report run as they would.
+bool fault_alloc() {
+    const char* v = getenv("PIC_FAULT");
+    return v && strcmp(v, "alloc") == 0;
+}
+
 template <class P>
 cudaError_t dalloc(P** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
+    if (fault_alloc()) return cudaErrorMemoryAllocation;
     return cudaMalloc((void**)p, sizeof(P) * count);
 }
 

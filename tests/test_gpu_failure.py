@@ -42,3 +42,30 @@ def test_bounded_wait_runs_out_and_the_context_stays_usable():
         sim.step(5)
         d = sim.diagnostics()
     assert d["status_bits"] == 0 and d["n_particles"][0] == w.n_particles
+
+
+def test_allocation_failures_report_enomem_and_keep_the_state(monkeypatch):
+    """PIC_FAULT=alloc (host-side injection) makes every device allocation of a
+    simulation fail: creating one reports PIC_ENOMEM; a load that needs more
+    capacity reports PIC_ENOMEM and keeps the loaded particles; with the
+    variable cleared both work again."""
+    import numpy as np
+    w = wl.two_stream(nx=64, ny=32, k=2, u_th=0.1, drift=0.2, tile=16, seed=9)
+    monkeypatch.setenv("PIC_FAULT", "alloc")
+    with pytest.raises(pic.PicError) as ei:
+        pic.Simulation.from_workload(w, device=True)
+    assert ei.value.status == 3
+    monkeypatch.delenv("PIC_FAULT")
+    with pic.Simulation.from_workload(w, device=True) as sim:
+        s = w.species[0]
+        twice = [np.concatenate([a, a]) for a in s.arrays()]
+        monkeypatch.setenv("PIC_FAULT", "alloc")
+        with pytest.raises(pic.PicError) as ei:
+            pic.pic_load_particles(sim.h, 0, *twice)
+        assert ei.value.status == 3
+        monkeypatch.delenv("PIC_FAULT")
+        assert pic.pic_num_particles(sim.h, 0) == s.n
+        sim.step(3)
+        assert sim.diagnostics()["status_bits"] == 0
+        pic.pic_load_particles(sim.h, 0, *twice)
+        assert pic.pic_num_particles(sim.h, 0) == 2 * s.n
