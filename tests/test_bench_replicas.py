@@ -75,3 +75,26 @@ def test_peaks_fall_back_without_the_measured_file(tmp_path, monkeypatch):
     assert kind == "fallback" and peak == bench.PEAK_FALLBACK_GBS
     (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6779.0}')
     assert bench.read_peaks() == (6779.0, "measured")
+
+
+@pytest.mark.parametrize("workload,metric", [
+    ("weibel_512", "particle updates/s (push+deposit+sort)"),
+    ("denoiser_fwd_2048", "denoiser forward throughput"),
+])
+def test_reference_arm_prints_one_contract_line(workload, metric):
+    """`bench.py --impl reference` (the CPU oracle on a bounded sample) prints
+    one JSON line with the keys of the contract, on the GPU arm's metric."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, bench.__file__, "--impl", "reference", "--workload", workload,
+                        "--steps", "1", "--warmup", "3"], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == metric and d["value"] > 0
+    assert d["higher_is_better"] is True and d["warmup"] == 3 and d["steps"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["config"]["workload"] == workload
