@@ -1,14 +1,15 @@
 """Throughput benchmark of the PIC step (push + deposit + re-sort + Yee).
 
-Default workload (N=1): the Weibel instability at full size, 512x512 cells,
-two electron populations of 8x8 particles per cell (33,554,432 particles),
-16x16-cell tiles, uz = +-0.6, u_th = 0.05, dt = 0.05, dx = dy = 0.1, random
-synthetic inputs.  A step is one pass of the whole hot path over all
-particles.  ``value`` is particle updates per second with the state resident
-in HBM; ``e2e`` is the same metric through the C ABI from pinned host
-buffers (load, K steps, field read-back and diagnostics inside the timed
-region).  The particle state (805 MB) is larger than the 129 MB L2, so no L2
-flush is needed between steps.
+Default workload (N=1): the large single-run thermal plasma at full size,
+2048x2048 cells, 4x4 thermal electrons per cell (67,108,864 particles,
+u_th = 0.2) with a seeded sinusoidal Ex mode (k = 2 pi / L_x, amplitude 1e-3),
+16x16-cell tiles, dt = 0.05, dx = dy = 0.1, random synthetic inputs.  A step
+is one pass of the whole hot path over all particles.  ``value`` is particle
+updates per second with the state resident in HBM; ``e2e`` is the same
+metric through the C ABI from pinned host buffers (load, K steps, field
+read-back and diagnostics inside the timed region).  The particle state
+(1.6 GB) is larger than the 129 MB L2, so no L2 flush is needed between
+steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -79,6 +80,7 @@ def workload_config(name, w, threads):
     return {"workload": name, "grid": [w.nx, w.ny], "particles": w.n_particles,
             "ppc": w.meta.get("ppc"), "tile": w.tile, "threads_per_tile": threads,
             "dt": w.dt, "dx": w.dx, "steps_of_workload": w.steps,
+            "timed_steps": "the K steps after W warm-up steps from the workload's initial state",
             "l2": "inputs larger than L2 (particle state {:.0f} MB > 129 MB)".format(
                 w.n_particles * 24 / 1e6)}
 
@@ -191,27 +193,63 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(budget_s=12.0):
-    """The FP64 oracle as it stands, single thread, on a bounded sample of the
-    Weibel workload: a 64x64 periodic instance (524,288 particles)."""
-    import oracle
+# reduced instance of each workload's physics for the CPU oracle's timed
+# samples (the full sizes take minutes per step on the host)
+CPU_SAMPLES = {
+    "thermal_seeded": ("thermal_seeded", dict(nx=256, ny=256, k=4)),
+    "weibel": ("weibel", dict(nx=64, ny=64, k=8)),
+    "weibel_pair": ("weibel_pair", dict(nx=64, ny=64, k=10)),
+    "two_stream": ("two_stream", dict(nx=64, ny=64, k=4)),
+}
+
+
+def cpu_sample(name):
+    """(workload, description) of the bounded CPU sample of workload `name`:
+    the same physics on a smaller periodic grid (the Weibel sample for the
+    kinds without a periodic single-grid form)."""
     from paper_2501_14795_gb300 import workloads as wl
-    w = wl.weibel(nx=64, ny=64, k=8, tile=16)
-    s = w.species[0]
-    o = oracle.OracleSim(w.nx, w.ny, w.dx, w.dy, w.dt, w.tile,
-                         [oracle.SpeciesState(s.q_over_m, s.qtilde, *s.arrays())],
-                         background=w.background)
+    kind = WORKLOADS[name]["kind"] if name in WORKLOADS else name
+    fac, kw = CPU_SAMPLES.get(kind, CPU_SAMPLES["weibel"])
+    w = getattr(wl, fac)(tile=16, **kw)
+    return w, (f"{fac} physics on a {w.nx}x{w.ny} periodic grid, {w.meta.get('ppc')} ppc "
+               f"({w.n_particles} particles)")
+
+
+def oracle_sim(w, threads):
+    import oracle
+    sps = [oracle.SpeciesState(s.q_over_m, s.qtilde, *s.arrays()) for s in w.species]
+    return oracle.OracleSim(w.nx, w.ny, w.dx, w.dy, w.dt, w.tile, sps,
+                            background=w.background, E=w.E0, B=w.B0, threads=threads)
+
+
+def time_oracle(w, threads, budget_s):
+    """Oracle steps of `w` for about budget_s seconds after one warm-up step;
+    returns (particle updates/s, steps)."""
+    o = oracle_sim(w, threads)
     o.step(1)
     t0 = time.perf_counter()
     steps = 0
     while time.perf_counter() - t0 < budget_s:
         o.step(1)
         steps += 1
-    dt = time.perf_counter() - t0
-    return {"value": w.n_particles * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"Weibel physics on a 64x64 periodic grid, 2x8x8 ppc ({w.n_particles} "
-                      f"particles), {steps} steps after 1 warm-up, FP64 single-thread C oracle",
-            "cpu_model": _cpu_model(), "host_cores": os.cpu_count()}
+    return w.n_particles * steps / (time.perf_counter() - t0), steps
+
+
+def cpu_baseline(name, budget_s=12.0):
+    """The FP64 oracle as it stands on a bounded sample of the workload's
+    physics: its threaded particle loop (the thesis's CPU scheme: blocks of
+    tile-sorted particles over threads, private current arrays) on all host
+    cores, and the plain single-threaded loop beside it."""
+    w, what = cpu_sample(name)
+    cores = os.cpu_count() or 1
+    v, steps = time_oracle(w, cores, budget_s)
+    v1, steps1 = time_oracle(w, 1, budget_s / 2)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{what}, {steps} steps after 1 warm-up, FP64 C oracle, particle loop "
+                      f"over {cores} threads (private current arrays), serial re-sort and field "
+                      f"advance",
+            "single_thread": {"value": v1, "steps": steps1},
+            "cpu_model": _cpu_model(), "host_cores": cores}
 
 
 def _cpu_model():
@@ -231,17 +269,13 @@ def run_reference(args, rank, world):
     """Reference arm: the CPU oracle on bounded samples of the same workload."""
     if rank != 0:
         return
-    import oracle
-    from paper_2501_14795_gb300 import workloads as wl
     kind = WORKLOADS[args.workload]["kind"]
     if kind == "denoiser_fwd":
         run_reference_denoiser_fwd(args, world)
         return
-    w = wl.weibel(nx=64, ny=64, k=8, tile=16)
-    s = w.species[0]
-    o = oracle.OracleSim(w.nx, w.ny, w.dx, w.dy, w.dt, w.tile,
-                         [oracle.SpeciesState(s.q_over_m, s.qtilde, *s.arrays())],
-                         background=w.background)
+    w, what = cpu_sample(args.workload)
+    cores = os.cpu_count() or 1
+    o = oracle_sim(w, cores)
     o.step(args.warmup)
     t0 = time.perf_counter()
     o.step(args.steps)
@@ -256,10 +290,9 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": config,
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: the Weibel physics on a 64x64 periodic grid, "
-                                       f"2x8x8 ppc ({w.n_particles} particles), FP64 single-thread "
-                                       f"C oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: {what}, FP64 C oracle, particle loop over "
+                                       f"{cores} threads (private current arrays)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -660,7 +693,7 @@ def run_gpu(args, rank, world, local_rank):
         torch.distributed.barrier()
     ms = ev0.elapsed_time(ev1)
     pic.pic_sync(sim.h)
-    adv_ms, adv_n = pic.pic_timing(sim.h, reset=True)
+    (adv_ms, sort_ms, field_ms), adv_n = pic.pic_timing_stages(sim.h, reset=True)
     launches = pic.pic_kernel_launches(sim.h) - l0
     d = sim.diagnostics()
     sim.close()
@@ -731,6 +764,16 @@ def run_gpu(args, rank, world, local_rank):
         "step_hbm": {"bytes_per_particle": step_bytes, "leaver_fraction_last_step": f_leave,
                      "achieved_gbs": step_bytes * value / world / 1e9,
                      "frac": step_bytes * value / world / 1e9 / peak},
+        # CUDA events on the simulation's stream around each stage of every
+        # timed step (per step, in ms); re-sort algorithmic bytes: each
+        # leaver's 24 B state read and written once more (2 S_p f_leave of the
+        # step's bytes per particle)
+        "stages_ms_per_step": {"advance": adv_ms / max(adv_n, 1), "resort": sort_ms / max(adv_n, 1),
+                               "field": field_ms / max(adv_n, 1)},
+        "resort_hbm": {"moved_particles_last_step": leavers,
+                       "bytes_per_step": 48.0 * leavers,
+                       "achieved_gbs": 48.0 * leavers / (sort_ms / max(adv_n, 1) * 1e-3) / 1e9
+                       if sort_ms > 0 else None},
         "e2e": {"value": total * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps},
         "gpu_launches": int(launches),
@@ -738,7 +781,7 @@ def run_gpu(args, rank, world, local_rank):
         "status_bits": d["status_bits"],
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(line), flush=True)
 
 
@@ -748,7 +791,7 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="weibel_512", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="thermal_2048", choices=sorted(WORKLOADS))
     ap.add_argument("--threads", type=int, default=256)
     ap.add_argument("--tile", type=int, default=0, help="override the workload's tile size")
     ap.add_argument("--no-cpu-baseline", action="store_true")

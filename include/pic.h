@@ -262,6 +262,14 @@ pic_status pic_clear_status(pic_sim* sim);
  * event durations in ms and their count since the last reset.  Synchronises. */
 pic_status pic_timing(pic_sim* sim, double* advance_ms, int64_t* advance_launches, int reset);
 
+/* The same events split by stage of the step loop (Listing 3.1; PIC_TIMING):
+ * stage_ms[0] the particle advance (gather, push, move, deposit, leaver
+ * emission), stage_ms[1] the tile re-sort (§4.3: count, scan, evict, fill),
+ * stage_ms[2] the current filter if any plus the field advance (Eqs. 19-20),
+ * each summed over the steps since the last reset (CUDA events on the
+ * simulation's stream), and their count in *steps.  Synchronises. */
+pic_status pic_timing_stages(pic_sim* sim, double stage_ms[3], int64_t* steps, int reset);
+
 /* Number of kernels this simulation has launched (graph nodes included). */
 int64_t pic_kernel_launches(const pic_sim* sim);
 
@@ -451,10 +459,11 @@ pic_status pic_nn_low_k_restore(const float* raw, float* out, int B, int H, int 
  * counting sort pic_load_particles performs; order inside a tile is
  * unspecified.  It allocates nothing: its scratch is a fixed device array of
  * PIC_NOALLOC_MAX_TILES + 64 int32 (256 KB + 256 B) that every GPU loading the
- * library holds until exit.  The first call on a device looks up that
- * array's address (make it before any stream capture).  Calls share the
- * array: two calls whose work overlaps on the GPU race and give wrong
- * results.  Synchronises `cuda_stream` (a cudaStream_t, NULL = default).
+ * library holds until exit.  Every call looks up that array's address on the
+ * current device.  Calls share the array: two calls whose work overlaps on
+ * the GPU race and give wrong results.  Synchronises `cuda_stream` (a
+ * cudaStream_t, NULL = default) twice, so it cannot be called during a stream
+ * capture.  n = 0 is valid (all bookmarks zero).
  * Returns PIC_EINVAL for a bad size or tile, more than PIC_NOALLOC_MAX_TILES
  * tiles, or an invalid particle (outputs then unspecified); PIC_ECUDA on a
  * CUDA error. */

@@ -20,13 +20,27 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 ORC_EPARTICLE = 1
 
 
+def _openmp_flag() -> list:
+    """["-fopenmp"] when gcc can build and link OpenMP code here, else [] (the
+    threaded particle loop then runs its blocks one after another)."""
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "t.c")
+        with open(src, "w") as f:
+            f.write("#include <omp.h>\nint main(void){return omp_get_max_threads() < 1;}\n")
+        r = subprocess.run(["gcc", "-fopenmp", src, "-o", os.path.join(d, "t")],
+                           capture_output=True)
+    return ["-fopenmp"] if r.returncode == 0 else []
+
+
 def build_oracle(force: bool = False) -> str:
     """Compile the oracle (both precisions) into oracle/liboracle.so."""
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     objs = []
-    flags = ["-O2", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-std=c11"]
+    omp = _openmp_flag()
+    flags = ["-O2", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-std=c11", *omp]
     for real, sfx, extra in (("double", "_f64", ["-DREAL_IS_DOUBLE"]),
                              ("float", "_f32", [])):
         obj = os.path.join(_HERE, f"_pic_oracle{sfx}.o")
@@ -35,7 +49,7 @@ def build_oracle(force: bool = False) -> str:
         subprocess.run(cmd, check=True)
         objs.append(obj)
     tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", "-shared", "-o", tmp, *objs, "-lm"], check=True)
+    subprocess.run(["gcc", "-shared", *omp, "-o", tmp, *objs, "-lm"], check=True)
     os.replace(tmp, _LIB)
     for o in objs:
         os.remove(o)
@@ -70,6 +84,8 @@ def _declare(L):
         getattr(L, "orc_deposit_move" + sfx).restype = None
         getattr(L, "orc_advance" + sfx).argtypes = [_I, _I, _I, _D, _D, _D, _D, _D, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
         getattr(L, "orc_advance" + sfx).restype = _I
+        getattr(L, "orc_advance_par" + sfx).argtypes = [_I, _I, _I, _D, _D, _D, _D, _D, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I]
+        getattr(L, "orc_advance_par" + sfx).restype = _I
         getattr(L, "orc_yee" + sfx).argtypes = [_I, _I, _I, _D, _D, _D, _P, _P, _P]
         getattr(L, "orc_yee" + sfx).restype = None
         getattr(L, "orc_rho" + sfx).argtypes = [_I, _I, _D, _I64, _P, _P, _P, _P, _P]
@@ -127,18 +143,26 @@ def deposit_move(J, ix, iy, x0, y0, x1, y1, qjx, qjy, qvz, open_x=False):
         r(qjx), r(qjy), r(qvz))
 
 
-def advance(sp: "SpeciesState", E, B, J, dx, dy, dt, open_x=False):
+def advance(sp: "SpeciesState", E, B, J, dx, dy, dt, open_x=False, threads=1):
     """Particle loop of Listing 3.1 for one species; returns (status,
     sum(gamma-1)).  With open_x, particles that left the box along x are
-    removed from ``sp`` afterwards."""
+    removed from ``sp`` afterwards.  threads > 1: the thesis's CPU scheme
+    (blocks of tile-sorted particles over threads, private current arrays
+    added afterwards), identical particles, J equal up to the order of the
+    additions."""
     _, ny, nx = E.shape
     ke = C.c_double(0.0)
     gone = np.zeros(sp.n, np.uint8) if open_x else None
-    st = getattr(lib(), "orc_advance" + _sfx(E.dtype))(
-        nx, ny, int(bool(open_x)), dx, dy, dt, sp.q_over_m, sp.qtilde, sp.n,
-        _ptr(sp.ix), _ptr(sp.iy), _ptr(sp.x), _ptr(sp.y),
-        _ptr(sp.ux), _ptr(sp.uy), _ptr(sp.uz), _ptr(E), _ptr(B), _ptr(J),
-        None if gone is None else _ptr(gone), C.byref(ke))
+    args = (nx, ny, int(bool(open_x)), dx, dy, dt, sp.q_over_m, sp.qtilde, sp.n,
+            _ptr(sp.ix), _ptr(sp.iy), _ptr(sp.x), _ptr(sp.y),
+            _ptr(sp.ux), _ptr(sp.uy), _ptr(sp.uz), _ptr(E), _ptr(B), _ptr(J),
+            None if gone is None else _ptr(gone), C.byref(ke))
+    if threads > 1:
+        st = getattr(lib(), "orc_advance_par" + _sfx(E.dtype))(*args, int(threads))
+        if st < 0:
+            raise MemoryError("oracle: private current arrays")
+    else:
+        st = getattr(lib(), "orc_advance" + _sfx(E.dtype))(*args)
     if open_x and gone.any():
         sp.keep(gone == 0)
     return st, ke.value
@@ -305,6 +329,7 @@ class OracleSim:
     filter_passes: int = 0          # binomial current filter (0: off)
     window: list | None = None      # moving window: injection per species
     moves: int = 0                  # cells the window has moved
+    threads: int = 1                # > 1: the threaded particle loop (same particles)
     step_count: int = 0
     status: int = 0
     ke_history: list = field(default_factory=list)
@@ -329,7 +354,8 @@ class OracleSim:
             self.J[...] = 0
             ke = 0.0
             for sp in self.species:
-                st, g = advance(sp, self.E, self.B, self.J, self.dx, self.dy, self.dt, open_x)
+                st, g = advance(sp, self.E, self.B, self.J, self.dx, self.dy, self.dt, open_x,
+                                self.threads)
                 self.status |= st
                 ke += self.kinetic_energy_of(sp, g)
             self.ke_history.append(ke)

@@ -218,18 +218,21 @@ void FN(orc_deposit_move)(int nx, int ny, int open_x, REAL *J, int ix, int iy,
  * set to 1 for a particle whose new cell lies outside 0 <= ix < nx (it has
  * left the box; the caller removes it), else 0; its cell index is then left
  * unwrapped. */
-int FN(orc_advance)(int nx, int ny, int open_x, double dx, double dy, double dt,
-                    double q_over_m, double qtilde, int64_t n, int32_t *ix,
-                    int32_t *iy, REAL *x, REAL *y, REAL *ux, REAL *uy,
-                    REAL *uz, const REAL *E, const REAL *B, REAL *J,
-                    uint8_t *gone, double *ke_sum) {
+/* The particles [p0, p1) of orc_advance below, their current added into J;
+ * returns the status bits and adds sum(gamma(u-) - 1) to *ke. */
+static int FN(advance_range)(int nx, int ny, int open_x, double dx, double dy,
+                             double dt, double q_over_m, double qtilde,
+                             int64_t p0, int64_t p1, int32_t *ix, int32_t *iy,
+                             REAL *x, REAL *y, REAL *ux, REAL *uy, REAL *uz,
+                             const REAL *E, const REAL *B, REAL *J,
+                             uint8_t *gone, double *ke_sum) {
     REAL tem = (REAL)(0.5 * q_over_m * dt);
     REAL cx = (REAL)(dt / dx), cy = (REAL)(dt / dy);
     REAL qjx = (REAL)(qtilde * dx / dt), qjy = (REAL)(qtilde * dy / dt);
     REAL qjz = (REAL)qtilde;
     int status = 0;
     double ke = 0.0;
-    for (int64_t p = 0; p < n; ++p) {
+    for (int64_t p = p0; p < p1; ++p) {
         REAL Ep[3], Bp[3], u[3] = {ux[p], uy[p], uz[p]};
         FN(orc_gather)(nx, ny, open_x, E, B, ix[p], iy[p], x[p], y[p], Ep, Bp);
         if (gone) gone[p] = 0;
@@ -277,7 +280,69 @@ int FN(orc_advance)(int nx, int ny, int open_x, double dx, double dy, double dt,
         }
         iy[p] = wrap(iy[p] + dj, ny);
     }
+    *ke_sum += ke;
+    return status;
+}
+
+int FN(orc_advance)(int nx, int ny, int open_x, double dx, double dy, double dt,
+                    double q_over_m, double qtilde, int64_t n, int32_t *ix,
+                    int32_t *iy, REAL *x, REAL *y, REAL *ux, REAL *uy,
+                    REAL *uz, const REAL *E, const REAL *B, REAL *J,
+                    uint8_t *gone, double *ke_sum) {
+    *ke_sum = 0.0;
+    return FN(advance_range)(nx, ny, open_x, dx, dy, dt, q_over_m, qtilde, 0, n,
+                             ix, iy, x, y, ux, uy, uz, E, B, J, gone, ke_sum);
+}
+
+/* The same particle loop spread over `nthreads` threads, the thesis's CPU
+ * scheme (§4.2, OpenMP): each thread takes a contiguous block of the
+ * tile-sorted particles (whole groups of tiles), deposits into a private
+ * current array, and the private arrays are added into J afterwards in
+ * thread order.  Every particle's update is the same arithmetic as in
+ * orc_advance, so positions and momenta are identical bit for bit; J and the
+ * kinetic-energy sum differ only by the order of the additions.  Built
+ * without OpenMP it runs the blocks one after another.  Returns -1 if the
+ * private arrays cannot be allocated. */
+int FN(orc_advance_par)(int nx, int ny, int open_x, double dx, double dy,
+                        double dt, double q_over_m, double qtilde, int64_t n,
+                        int32_t *ix, int32_t *iy, REAL *x, REAL *y, REAL *ux,
+                        REAL *uy, REAL *uz, const REAL *E, const REAL *B,
+                        REAL *J, uint8_t *gone, double *ke_sum, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    size_t ncell = (size_t)3 * nx * ny;
+    REAL *Jt = (REAL *)calloc((size_t)nthreads * ncell, sizeof(REAL));
+    double *ket = (double *)calloc((size_t)nthreads, sizeof(double));
+    int *stt = (int *)calloc((size_t)nthreads, sizeof(int));
+    if (!Jt || !ket || !stt) {
+        free(Jt);
+        free(ket);
+        free(stt);
+        return -1;
+    }
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads) schedule(static, 1)
+#endif
+    for (int t = 0; t < nthreads; ++t) {
+        int64_t p0 = n * t / nthreads, p1 = n * (t + 1) / nthreads;
+        stt[t] = FN(advance_range)(nx, ny, open_x, dx, dy, dt, q_over_m, qtilde,
+                                   p0, p1, ix, iy, x, y, ux, uy, uz, E, B,
+                                   Jt + (size_t)t * ncell, gone, &ket[t]);
+    }
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+#endif
+    for (int64_t c = 0; c < (int64_t)ncell; ++c)
+        for (int t = 0; t < nthreads; ++t) J[c] += Jt[(size_t)t * ncell + c];
+    int status = 0;
+    double ke = 0.0;
+    for (int t = 0; t < nthreads; ++t) {
+        status |= stt[t];
+        ke += ket[t];
+    }
     *ke_sum = ke;
+    free(Jt);
+    free(ket);
+    free(stt);
     return status;
 }
 

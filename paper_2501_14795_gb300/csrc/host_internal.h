@@ -34,10 +34,13 @@ struct pic_sim {
     // graphs
     cudaGraph_t graph[2] = {nullptr, nullptr};  // kept alive: its nodes address the exec's
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    cudaGraphNode_t ev_node[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-    cudaEvent_t ev_placeholder[2] = {nullptr, nullptr};
-    std::vector<cudaEvent_t> ev_pool;  // timing pairs
-    size_t ev_used = 0;                // pairs recorded since reset
+    // timing (PIC_TIMING): four events per step, recorded before the particle
+    // advance, after it, after the re-sort and after the field advance
+    static constexpr int kStepEvents = 4;
+    cudaGraphNode_t ev_node[2][kStepEvents] = {};
+    cudaEvent_t ev_placeholder[kStepEvents] = {};
+    std::vector<cudaEvent_t> ev_pool;  // kStepEvents per timed step
+    size_t ev_used = 0;                // steps recorded since reset
     long long launches = 0;
     int launches_per_step = 0;
     std::string err;

@@ -13,15 +13,16 @@
 // The array is file-scope `static __device__`: every GPU that loads this
 // library holds its 256 KB + 256 B until the process exits, and every call
 // on a device shares it.  Host code may not use the array's name as a device
-// address (in host code it names a host-side stand-in), so the first call on
-// each device looks up the device address with cudaGetSymbolAddress, with
-// that device current, and caches it; make that first call before any stream
-// capture.  Each call clears the counters it uses before using them.  Two
-// calls whose work overlaps on the GPU (different streams, or different host
-// threads) race on the shared array and give wrong results: serialise them.
+// address (in host code it names a host-side stand-in), so every call looks
+// up the device address with cudaGetSymbolAddress, with the caller's device
+// current, and checks the result; the address is not cached, so a device
+// reset between calls (which reloads the module and may move the array) is
+// harmless.  Each call clears the counters it uses before using them.  Each
+// call synchronises its stream (it reads the validation counter back before
+// scanning), so it cannot be made during a stream capture.  Two calls whose
+// work overlaps on the GPU (different streams, or different host threads)
+// race on the shared array and give wrong results: serialise them.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "pic.h"
 #include "device_util.cuh"
@@ -31,27 +32,20 @@ namespace {
 constexpr int kMaxTiles = PIC_NOALLOC_MAX_TILES;
 constexpr int kBadSlot = kMaxTiles;  // validation-failure counter after the tile counters
 constexpr int kScratchInts = kMaxTiles + 64;
-constexpr int kMaxDevices = 64;
-
 static __device__ __align__(256) int32_t g_scratch[kScratchInts];
 
-std::mutex g_setup_mutex;
-int32_t* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_scratch on the current device (set-up on first use).
-cudaError_t scratch_address(int32_t** out) {
+// Device address of g_scratch and the SM count of the current device.
+cudaError_t scratch_address(int32_t** out, int* sms) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = static_cast<int32_t*>(p);
-    }
-    *out = g_scratch_addr[dev];
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return e;
+    if (!p) return cudaErrorInvalidSymbol;
+    e = cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<int32_t*>(p);
     return cudaSuccess;
 }
 
@@ -150,13 +144,15 @@ extern "C" pic_status pic_tile_sort_noalloc(int nx, int ny, int tile, int64_t n,
         return PIC_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     int32_t* scratch = nullptr;
-    if (scratch_address(&scratch) != cudaSuccess) return PIC_ECUDA;
+    int sms = 0;
+    if (scratch_address(&scratch, &sms) != cudaSuccess) return PIC_ECUDA;
     const int nn = static_cast<int>(n), ntx = nx / tile;
     const In a{ix, iy, x, y, ux, uy, uz};
     const Out b{ix_out, iy_out, x_out, y_out, ux_out, uy_out, uz_out, tile_offset};
     int blocks = (nn + 255) / 256;
     if (blocks < 1) blocks = 1;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (sms < 1) sms = 1;
+    if (blocks > sms * 16) blocks = sms * 16;  // grid-stride loops beyond this
     // clear the counters and the validation counter left by the previous call
     if (cudaMemsetAsync(scratch, 0, sizeof(int32_t) * ntiles, s) != cudaSuccess ||
         cudaMemsetAsync(scratch + kBadSlot, 0, sizeof(int32_t), s) != cudaSuccess)

@@ -192,7 +192,7 @@ void invalidate_graphs(pic_sim* sim) {
         if (sim->graph[b]) cudaGraphDestroy(sim->graph[b]);
         sim->gexec[b] = nullptr;
         sim->graph[b] = nullptr;
-        sim->ev_node[b][0] = sim->ev_node[b][1] = nullptr;
+        for (auto& nd : sim->ev_node[b]) nd = nullptr;
     }
     sim->gen += 1;
 }
@@ -280,10 +280,11 @@ YeeParams yee_params(const pic_sim* sim, int b, int chunks) {
 }
 
 // Enqueue one step at parity b.  Returns the number of kernels launched or
-// -1 on a launch error (message in sim->err).  ev_a/ev_b bracket the particle
-// advance when non-null (external event records inside a capture).
-int enqueue_step(pic_sim* sim, cudaStream_t s, int b, cudaEvent_t ev_a, cudaEvent_t ev_b,
-                 bool capturing) {
+// -1 on a launch error (message in sim->err).  ev, when non-null, holds the
+// kStepEvents events recorded before the particle advance, after it, after
+// the re-sort and after the field advance (external event records inside a
+// capture).
+int enqueue_step(pic_sim* sim, cudaStream_t s, int b, const cudaEvent_t* ev, bool capturing) {
     const int threads = sim->cfg.threads;
     const PushParams pp = push_params(sim, b);
     const SortParams sp = sort_params(sim, b);
@@ -291,17 +292,18 @@ int enqueue_step(pic_sim* sim, cudaStream_t s, int b, cudaEvent_t ev_a, cudaEven
     int n = 0;
     cudaError_t e;
     const unsigned rec = capturing ? cudaEventRecordExternal : 0u;
-    if (ev_a && (e = cudaEventRecordWithFlags(ev_a, s, rec)) != cudaSuccess) goto bad;
+    if (ev && (e = cudaEventRecordWithFlags(ev[0], s, rec)) != cudaSuccess) goto bad;
     e = (sim->cfg.flags & PIC_STRICT_FP) ? launch_push_strict(&sim->fmap[b], pp, threads, s)
                                          : launch_push_fast(&sim->fmap[b], pp, threads, s);
     if (e != cudaSuccess) goto bad;
     n += sim->g.ntiles > 0;
-    if (ev_b && (e = cudaEventRecordWithFlags(ev_b, s, rec)) != cudaSuccess) goto bad;
+    if (ev && (e = cudaEventRecordWithFlags(ev[1], s, rec)) != cudaSuccess) goto bad;
     if ((e = launch_scan(sp, s)) != cudaSuccess) goto bad;
     n += (sp.nsp > 0 && sim->g.ntiles > 0) ? 2 : 1;  // count + scan
     if ((e = launch_evict(sp, threads, s)) != cudaSuccess) goto bad;
     if ((e = launch_fill(sp, threads, s)) != cudaSuccess) goto bad;
     n += (sp.nsp > 0 && sim->g.ntiles > 0) ? 2 : 0;
+    if (ev && (e = cudaEventRecordWithFlags(ev[2], s, rec)) != cudaSuccess) goto bad;
     if (sim->jfilter) {
         // the current-filter slot of Listing 3.1: after the deposit and its
         // guard-cell reduction, before the field advance
@@ -311,6 +313,7 @@ int enqueue_step(pic_sim* sim, cudaStream_t s, int b, cudaEvent_t ev_a, cudaEven
     }
     if ((e = launch_yee(yp, &sim->ymapF[b], &sim->ymapJ[b], s)) != cudaSuccess) goto bad;
     n += 1;
+    if (ev && (e = cudaEventRecordWithFlags(ev[3], s, rec)) != cudaSuccess) goto bad;
     return n;
 bad:
     sim->err = std::string("kernel launch failed: ") + cudaGetErrorString(e);
@@ -323,8 +326,8 @@ pic_status build_graph(pic_sim* sim, int b) {
     // capture on the private stream (the caller's may be the legacy default
     // stream, which cannot be captured); the graph is launched on the caller's
     CK(cudaStreamBeginCapture(sim->cap_stream, cudaStreamCaptureModeThreadLocal));
-    const int n = enqueue_step(sim, sim->cap_stream, b, timing ? sim->ev_placeholder[0] : nullptr,
-                               timing ? sim->ev_placeholder[1] : nullptr, true);
+    const int n =
+        enqueue_step(sim, sim->cap_stream, b, timing ? sim->ev_placeholder : nullptr, true);
     cudaError_t e = cudaStreamEndCapture(sim->cap_stream, &graph);
     if (n < 0) {
         if (graph) cudaGraphDestroy(graph);
@@ -343,8 +346,8 @@ pic_status build_graph(pic_sim* sim, int b) {
             if (ty != cudaGraphNodeTypeEventRecord) continue;
             cudaEvent_t ev;
             CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
-            if (ev == sim->ev_placeholder[0]) sim->ev_node[b][0] = nd;
-            if (ev == sim->ev_placeholder[1]) sim->ev_node[b][1] = nd;
+            for (int k = 0; k < pic_sim::kStepEvents; ++k)
+                if (ev == sim->ev_placeholder[k]) sim->ev_node[b][k] = nd;
         }
     }
     e = cudaGraphInstantiate(&sim->gexec[b], graph, 0);
@@ -353,15 +356,16 @@ pic_status build_graph(pic_sim* sim, int b) {
     return PIC_OK;
 }
 
-pic_status timing_pair(pic_sim* sim, cudaEvent_t* a, cudaEvent_t* b) {
-    const size_t need = 2 * (sim->ev_used + 1);
+// The next step's kStepEvents timing events from the pool (grown on demand).
+pic_status timing_events(pic_sim* sim, cudaEvent_t** out) {
+    constexpr size_t K = pic_sim::kStepEvents;
+    const size_t need = K * (sim->ev_used + 1);
     while (sim->ev_pool.size() < need) {
         cudaEvent_t ev;
         CK(cudaEventCreate(&ev));
         sim->ev_pool.push_back(ev);
     }
-    *a = sim->ev_pool[2 * sim->ev_used];
-    *b = sim->ev_pool[2 * sim->ev_used + 1];
+    *out = sim->ev_pool.data() + K * sim->ev_used;
     sim->ev_used += 1;
     return PIC_OK;
 }
@@ -595,7 +599,7 @@ pic_status pic_init(const pic_config* cfg, void* cuda_stream, pic_sim** out) {
     if (cudaStreamCreateWithFlags(&sim->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         return cleanup_fail(PIC_ECUDA, "stream", e);
     if (c.flags & PIC_TIMING)
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < pic_sim::kStepEvents; ++k)
             if (cudaEventCreate(&sim->ev_placeholder[k]) != cudaSuccess)
                 return cleanup_fail(PIC_ECUDA, "event", e);
     if (refresh_level_energy(sim) != PIC_OK) return cleanup_fail(PIC_ECUDA, "energy", e);
@@ -730,9 +734,9 @@ pic_status pic_step(pic_sim* sim, int nsteps) {
     const bool graph = (sim->cfg.flags & PIC_NO_GRAPH) == 0;
     for (int k = 0; k < nsteps; ++k) {
         const int b = sim->cur;
-        cudaEvent_t ea = nullptr, eb = nullptr;
+        cudaEvent_t* ev = nullptr;
         if (timing) {
-            pic_status r = timing_pair(sim, &ea, &eb);
+            pic_status r = timing_events(sim, &ev);
             if (r != PIC_OK) return r;
         }
         if (graph) {
@@ -740,14 +744,14 @@ pic_status pic_step(pic_sim* sim, int nsteps) {
                 pic_status r = build_graph(sim, b);
                 if (r != PIC_OK) return r;
             }
-            if (timing) {
-                CK(cudaGraphExecEventRecordNodeSetEvent(sim->gexec[b], sim->ev_node[b][0], ea));
-                CK(cudaGraphExecEventRecordNodeSetEvent(sim->gexec[b], sim->ev_node[b][1], eb));
-            }
+            if (timing)
+                for (int k = 0; k < pic_sim::kStepEvents; ++k)
+                    CK(cudaGraphExecEventRecordNodeSetEvent(sim->gexec[b], sim->ev_node[b][k],
+                                                            ev[k]));
             CK(cudaGraphLaunch(sim->gexec[b], sim->stream));
             sim->launches += sim->launches_per_step;
         } else {
-            const int n = enqueue_step(sim, sim->stream, b, ea, eb, false);
+            const int n = enqueue_step(sim, sim->stream, b, ev, false);
             if (n < 0) return PIC_ECUDA;
             sim->launches += n;
         }
@@ -1015,19 +1019,29 @@ pic_status pic_clear_status(pic_sim* sim) {
     return PIC_OK;
 }
 
-pic_status pic_timing(pic_sim* sim, double* advance_ms, int64_t* advance_launches, int reset) {
+pic_status pic_timing_stages(pic_sim* sim, double stage_ms[3], int64_t* steps, int reset) {
     if (!sim) return PIC_EINVAL;
     CK(cudaStreamSynchronize(sim->stream));
-    double tot = 0.0;
-    for (size_t k = 0; k < sim->ev_used; ++k) {
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, sim->ev_pool[2 * k], sim->ev_pool[2 * k + 1]));
-        tot += ms;
-    }
-    if (advance_ms) *advance_ms = tot;
-    if (advance_launches) *advance_launches = (int64_t)sim->ev_used;
+    constexpr size_t K = pic_sim::kStepEvents;
+    double tot[3] = {0.0, 0.0, 0.0};
+    for (size_t k = 0; k < sim->ev_used; ++k)
+        for (int st = 0; st < 3; ++st) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, sim->ev_pool[K * k + st], sim->ev_pool[K * k + st + 1]));
+            tot[st] += ms;
+        }
+    if (stage_ms)
+        for (int st = 0; st < 3; ++st) stage_ms[st] = tot[st];
+    if (steps) *steps = (int64_t)sim->ev_used;
     if (reset) sim->ev_used = 0;
     return PIC_OK;
+}
+
+pic_status pic_timing(pic_sim* sim, double* advance_ms, int64_t* advance_launches, int reset) {
+    double ms[3];
+    const pic_status r = pic_timing_stages(sim, ms, advance_launches, reset);
+    if (r == PIC_OK && advance_ms) *advance_ms = ms[0];
+    return r;
 }
 
 int64_t pic_kernel_launches(const pic_sim* sim) { return sim ? sim->launches : -1; }
@@ -1043,8 +1057,9 @@ void pic_destroy(pic_sim* sim) {
     for (int b = 0; b < 2; ++b) {
         dfree(sim->F[b]);
         dfree(sim->J[b]);
-        if (sim->ev_placeholder[b]) cudaEventDestroy(sim->ev_placeholder[b]);
     }
+    for (auto ev : sim->ev_placeholder)
+        if (ev) cudaEventDestroy(ev);
     for (auto ev : sim->ev_pool) cudaEventDestroy(ev);
     dfree(sim->gtmp);
     dfree(sim->rho);

@@ -99,6 +99,7 @@ def load_library() -> C.CDLL:
         L.pic_sync.argtypes = [_P]
         L.pic_clear_status.argtypes = [_P]
         L.pic_timing.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]
+        L.pic_timing_stages.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]
         L.pic_kernel_launches.argtypes = [_P]
         L.pic_kernel_launches.restype = C.c_int64
         L.pic_last_error.argtypes = [_P]
@@ -149,6 +150,7 @@ def load_library() -> C.CDLL:
         for name in ("pic_init", "pic_load_particles", "pic_set_fields", "pic_step",
                      "pic_get_fields", "pic_get_particles", "pic_diagnostics",
                      "pic_get_history", "pic_sync", "pic_clear_status", "pic_timing",
+                     "pic_timing_stages",
                      "pic_init_batch", "pic_batch_create", "pic_batch_step", "pic_batch_sync",
                      "pic_autotune", "pic_set_tiling", "pic_denoiser_create",
                      "pic_denoiser_set_params", "pic_denoiser_get_params", "pic_denoiser_forward",
@@ -288,6 +290,15 @@ def pic_timing(h, reset=False):
     cnt = C.c_int64()
     _check(h, load_library().pic_timing(h, C.byref(ms), C.byref(cnt), int(reset)))
     return ms.value, cnt.value
+
+
+def pic_timing_stages(h, reset=False):
+    """(advance, re-sort, field) milliseconds summed over the timed steps, and
+    the number of steps."""
+    ms = (C.c_double * 3)()
+    cnt = C.c_int64()
+    _check(h, load_library().pic_timing_stages(h, ms, C.byref(cnt), int(reset)))
+    return (ms[0], ms[1], ms[2]), cnt.value
 
 
 def pic_kernel_launches(h):

@@ -1,0 +1,214 @@
+"""Macroscopic parity over many steps (multi-step parity of the method,
+§3.1 physics): the GPU and the FP64 oracle start from the same seeded state
+and their growth rates, oscillation frequency and energy drift are fitted the
+same way and compared.
+
+* two-stream (the 64x64 workload: 4x4 ppc, u_th 0.1, drift +-0.2), 600 steps,
+  the k_y = 0 modes m = 2 and 3 of E_x: GPU rate within 2 % of the oracle's;
+* cold two-stream with the modes m = 2 and 3 seeded: a clean exponential, GPU
+  within 2 % of the oracle and both within 5 % of the cold-beam rate;
+* Weibel (the 512^2 workload's physics on its 128^2 periodic instance: 2x8x8
+  ppc, uz +-0.6, u_th 0.05), 300 steps: the peak growth rate of W_B, GPU
+  within 3 % of the oracle's;
+* the large thermal workload's seeded mode on a 2048 x 8 strip: E_x oscillates
+  at the oracle's frequency within 0.2 % and at the relativistic Langmuir
+  frequency within 0.5 %;
+* the large thermal workload's physics on a 128^2 grid, 200 steps: the GPU's
+  total-energy drift within 20 % of the oracle's, and under 1 %.
+
+The oracle runs its threaded particle loop (identical particles to the
+single-threaded one, current equal up to the order of the additions) on all
+host cores.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_14795_gb300 import pic
+from paper_2501_14795_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+THREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_14795_gb300 import build
+    build.build_library()
+    oracle.build_oracle()
+
+
+def _oracle(w):
+    sps = [oracle.SpeciesState(s.q_over_m, s.qtilde, *s.arrays()) for s in w.species]
+    return oracle.OracleSim(w.nx, w.ny, w.dx, w.dy, w.dt, w.tile, sps, background=w.background,
+                            E=w.E0, B=w.B0, threads=THREADS)
+
+
+def _gpu(w, tile=None):
+    return pic.Simulation.from_workload(w, tile=tile, threads=256, flags=0, device=True)
+
+
+def _mode_amplitudes(Ex, modes):
+    f = np.abs(np.fft.rfft(np.asarray(Ex, np.float64).mean(axis=0)))
+    return [f[m] for m in modes]
+
+
+def _run_modes(w, steps, modes):
+    """|FFT(mean_y E_x)| of the given modes at every level 0..steps-1, GPU and
+    oracle."""
+    g, o = [], []
+    with _gpu(w) as sim:
+        for _ in range(steps):
+            g.append(_mode_amplitudes(sim.fields(pic.FIELD_E)[0], modes))
+            sim.step(1)
+        assert sim.diagnostics()["status_bits"] == 0
+    s = _oracle(w)
+    for _ in range(steps):
+        o.append(_mode_amplitudes(s.E[0], modes))
+        s.step(1)
+    return np.array(g), np.array(o)
+
+
+def _rate(amp, dt, a, b):
+    t = np.arange(amp.size) * dt
+    return float(np.polyfit(t[a:b], np.log(amp[a:b]), 1)[0])
+
+
+def test_two_stream_growth_rates_follow_the_oracle():
+    w = wl.two_stream()
+    g, o = _run_modes(w, 600, (2, 3))
+    for k, m in enumerate((2, 3)):
+        ro = _rate(o[:, k], w.dt, 200, 500)
+        rg = _rate(g[:, k], w.dt, 200, 500)
+        print(f"two-stream m={m}: oracle {ro:.4f} GPU {rg:.4f} ({(rg - ro) / ro:+.2%})")
+        assert ro > 0.05
+        assert abs(rg - ro) <= 0.02 * ro
+
+
+def _cold_two_stream_rate(k, u=0.2):
+    """Two cold beams of density 1/2 with momenta +-u (relativistic
+    longitudinal mass): 1 = wb^2/(w - k v)^2 + wb^2/(w + k v)^2."""
+    g = math.sqrt(1 + u * u)
+    a, wb2 = k * u / g, 0.5 / g ** 3
+    z = np.roots([1.0, -(2 * a * a + 2 * wb2), a ** 4 - 2 * wb2 * a * a])
+    return float(np.max(np.sqrt(z.astype(complex)).imag))
+
+
+def test_cold_seeded_two_stream_rates_follow_the_oracle_and_theory():
+    """Cold beams (u_th = 0) on a 64 x 8 grid, 4x4 ppc, both beams displaced
+    by 1e-5 (sin k2 x + sin k3 x) (Gauss-consistent for the fixed ions): each
+    seeded mode grows at the cold rate (0.2978 for m = 2, 0.3430 for m = 3)."""
+    nx, ny, k, T = 64, 8, 4, 8
+    ix, iy, x, y, a, b = wl.lattice(nx, ny, k)
+    sgn = np.where((a + b) % 2 == 0, 1.0, -1.0)
+    x0 = (ix + x.astype(np.float64)) * 0.1
+    xi = 1e-5 * sum(np.sin(2 * np.pi * m * x0 / (nx * 0.1)) for m in (2, 3))
+    ix2, x2 = wl.displace_x(ix, x, xi / 0.1, nx)
+    n = ix.size
+    sp = wl.Species(-1.0, -1.0 / (k * k), ix2, iy, x2, y, (0.2 * sgn).astype(np.float32),
+                    np.zeros(n, np.float32), np.zeros(n, np.float32))
+    E0 = np.zeros((3, ny, nx), np.float32)
+    xh = (np.arange(nx) + 0.5) * 0.1
+    E0[0] = (1e-5 * sum(np.sin(2 * np.pi * m * xh / (nx * 0.1)) for m in (2, 3)))[None, :]
+    w = wl.Workload("cold_two_stream", nx, ny, 0.1, 0.1, 0.05, T, 400, [sp], E0=E0)
+    g, o = _run_modes(w, 400, (2, 3))
+    for j, m in enumerate((2, 3)):
+        want = _cold_two_stream_rate(2 * np.pi * m / (nx * 0.1))
+        ro = _rate(o[:, j], w.dt, 100, 300)
+        rg = _rate(g[:, j], w.dt, 100, 300)
+        print(f"cold two-stream m={m}: theory {want:.4f} oracle {ro:.4f} GPU {rg:.4f}")
+        assert ro == pytest.approx(want, rel=0.05)
+        assert abs(rg - ro) <= 0.02 * ro
+
+
+def _peak_rate(WB, dt, width=80, start=20, stride=10):
+    """Largest growth rate of the field amplitude (half the slope of ln W_B)
+    over sliding windows of `width` levels."""
+    lw = np.log(np.asarray(WB[1:]))
+    t = np.arange(1, len(WB)) * dt
+    rates = [0.5 * np.polyfit(t[a:a + width], lw[a:a + width], 1)[0]
+             for a in range(start, len(lw) - width + 1, stride)]
+    return max(rates)
+
+
+def test_weibel_128_peak_growth_rate_follows_the_oracle():
+    w = wl.weibel(nx=128, ny=128, k=8, tile=16)
+    steps = 300
+    with _gpu(w) as sim:
+        sim.step(steps)
+        _, hb, _ = sim.history(0, steps)
+        d = sim.diagnostics()
+    assert d["status_bits"] == 0
+    s = _oracle(w)
+    WB = []
+    for _ in range(steps):
+        WB.append(s.energies()[1])
+        s.step(1)
+    ro = _peak_rate(WB, w.dt)
+    rg = _peak_rate(hb, w.dt)
+    # bounded by the cold-fluid asymptote b / sqrt(g) (u = 0.6)
+    g0 = math.sqrt(1.36)
+    print(f"Weibel 128^2: oracle {ro:.4f} GPU {rg:.4f} ({(rg - ro) / ro:+.2%}), cold bound "
+          f"{0.6 / g0 / math.sqrt(g0):.4f}")
+    assert 0.2 < ro <= 0.6 / g0 / math.sqrt(g0)
+    assert abs(rg - ro) <= 0.03 * ro
+
+
+def _zero_crossing_frequency(a, dt):
+    t = np.arange(a.size) * dt
+    z = np.where(np.diff(np.sign(a)) != 0)[0]
+    tz = t[z] - a[z] * (t[z + 1] - t[z]) / (a[z + 1] - a[z])
+    return np.pi * (len(tz) - 1) / (tz[-1] - tz[0]), len(tz)
+
+
+def test_seeded_thermal_mode_frequency_follows_the_oracle():
+    from test_oracle_physics import relativistic_langmuir_frequency
+    w = wl.thermal_seeded(nx=2048, ny=8, k=4, u_th=0.2, amp=1e-3, tile=8)
+    kx = w.meta["kx"]
+    proj = np.sin(kx * (np.arange(w.nx) + 0.5) * w.dx)[None, :]
+    steps = 720
+    ag, ao = [], []
+    with _gpu(w, tile=8) as sim:
+        for _ in range(steps):
+            ag.append(2 * np.mean(sim.fields(pic.FIELD_E)[0] * proj))
+            sim.step(1)
+    s = _oracle(w)
+    for _ in range(steps):
+        ao.append(2 * np.mean(s.E[0] * proj))
+        s.step(1)
+    wg, ng = _zero_crossing_frequency(np.array(ag), w.dt)
+    wo, no = _zero_crossing_frequency(np.array(ao), w.dt)
+    want, _ = relativistic_langmuir_frequency(0.2, kx, w.dt)
+    print(f"seeded thermal mode: theory {want:.5f} oracle {wo:.5f} GPU {wg:.5f}")
+    assert ng >= 10 and no >= 10
+    assert wg == pytest.approx(wo, rel=2e-3)
+    assert wg == pytest.approx(want, rel=5e-3)
+
+
+def test_thermal_energy_drift_follows_the_oracle():
+    w = wl.thermal_seeded(nx=128, ny=128, k=4, u_th=0.2, amp=1e-3, tile=16)
+    steps = 200
+    with _gpu(w) as sim:
+        sim.step(steps + 1)
+        he, hb, hk = sim.history(0, steps + 1)
+    tot_g = np.asarray(he[1:steps + 1]) + np.asarray(hb[1:steps + 1]) + np.asarray(hk[1:steps + 1])
+    # levels 1..steps: W_E + W_B at level n (after the n-th step) plus W_K at
+    # level n (from gamma(u-) of the push that starts there, i.e. of step n+1)
+    s = _oracle(w)
+    fields = []
+    for _ in range(steps + 1):
+        s.step(1)
+        fields.append(sum(s.energies()))
+    tot_o = np.array([fields[n - 1] + s.ke_history[n] for n in range(1, steps + 1)])
+    do = (tot_o[-1] - tot_o[0]) / tot_o[0]
+    dg = (tot_g[-1] - tot_g[0]) / tot_g[0]
+    print(f"thermal 128^2 energy drift over {steps} steps: oracle {do:.3e} GPU {dg:.3e}")
+    assert abs(do) < 1e-2 and abs(dg) < 1e-2
+    assert abs(dg - do) <= 0.2 * abs(do)

@@ -93,6 +93,57 @@ def test_langmuir_frequency(orc):
     assert a[0] == pytest.approx(1e-3, rel=1e-6)
 
 
+def relativistic_langmuir_frequency(u_th, k, dt):
+    """Frequency of a long-wavelength Langmuir mode of a plasma whose momenta
+    u = gamma v are Gaussian with spread u_th per axis (omega_p = 1).  A
+    particle's velocity answers a field E_x by dv_x/dt = (q/m) E_x (1 - v_x^2)
+    / gamma (the relativistic mass of Eqs. 6-10 along and across the motion),
+    so omega^2 = <(1 - v_x^2)/gamma> + 3 k^2 <v_x^2> (the Bohm-Gross thermal
+    term); the leapfrog step then gives (2/dt) asin(omega dt / 2).  The
+    average is a 60^3-point Gauss-Hermite quadrature over the Gaussian."""
+    x, w = np.polynomial.hermite_e.hermegauss(60)
+    w = w / w.sum()
+    ux, uy, uz = np.meshgrid(x * u_th, x * u_th, x * u_th, indexing="ij")
+    W = w[:, None, None] * w[None, :, None] * w[None, None, :]
+    g = np.sqrt(1 + ux * ux + uy * uy + uz * uz)
+    vx2 = (ux / g) ** 2
+    om2 = float(np.sum(W * (1 - vx2) / g)) + 3 * k * k * float(np.sum(W * vx2))
+    return 2 / dt * math.asin(math.sqrt(om2) * dt / 2), om2
+
+
+def test_bohm_gross_seeded_thermal_mode(orc):
+    """The seeded mode of the large thermal workload (u_th = 0.2, k = 2 pi /
+    204.8, Ex = 1e-3 sin kx with the Gauss-consistent displacement) on a
+    2048 x 2 strip: Ex oscillates at the relativistic long-wavelength Langmuir
+    frequency 0.95742 (the non-relativistic Bohm-Gross value sqrt(1 + 3 k^2
+    u_th^2) = 1.0000565 would be 4.4 % higher: at u_th = 0.2 the mean
+    relativistic mass lowers omega^2 by 8 %), within 0.5 %."""
+    k = 2 * math.pi / 204.8
+    assert math.sqrt(1 + 3 * k * k * 0.04) == pytest.approx(1.0000565, abs=1e-7)
+    want, om2 = relativistic_langmuir_frequency(0.2, k, DT)
+    assert want == pytest.approx(0.95742, abs=2e-5)
+    # small-spread limit: the plain Bohm-Gross value (to O(u_th^2) relativistic terms)
+    low, _ = relativistic_langmuir_frequency(1e-3, 1.0, DT)
+    assert low == pytest.approx(2 / DT * math.asin(math.sqrt(1 + 3e-6) * DT / 2), rel=1e-5)
+    w = wl.thermal_seeded(nx=2048, ny=2, k=4, u_th=0.2, amp=1e-3, tile=2)
+    s = _sim(orc, w)
+    kx = w.meta["kx"]
+    assert kx == pytest.approx(k, rel=1e-12)
+    xh = (np.arange(w.nx) + 0.5) * w.dx
+    a = []
+    for _ in range(720):
+        a.append(2 * np.mean(s.E[0] * np.sin(kx * xh)[None, :]))
+        s.step(1)
+    a = np.array(a)
+    t = np.arange(a.size) * w.dt
+    z = np.where(np.diff(np.sign(a)) != 0)[0]
+    tz = t[z] - a[z] * (t[z + 1] - t[z]) / (a[z + 1] - a[z])
+    assert len(tz) >= 10
+    omega = np.pi * (len(tz) - 1) / (tz[-1] - tz[0])
+    assert omega == pytest.approx(want, rel=5e-3)
+    assert abs(omega - 1.0000565) > 0.03
+
+
 def _cold_two_stream(orc, m, eps=1e-7, nx=64, ny=2, k=4, vd=0.2):
     ix, iy, x, y, a, b = wl.lattice(nx, ny, k)
     sgn = np.where((a + b) % 2 == 0, 1.0, -1.0)
