@@ -141,30 +141,31 @@ __device__ __forceinline__ float qdiv(float a, float b) {
 }
 
 // Current of one straight piece inside one cell, local start (fx0, fy0), end
-// (fx1, fy1), time fraction frac: v[0..1] Jx on the faces (i+1/2, j) and
-// (i+1/2, j+1) (Eqs. 13-14), v[2..3] Jy on (i, j+1/2) and (i+1, j+1/2)
-// (Eqs. 15-16), v[4..7] Jz on the nodes (i,j), (i+1,j), (i,j+1), (i+1,j+1):
-// q vz frac times the mean over the piece of each node's area weight.
+// (fx1, fy1), fq = q vz times the piece's time fraction: v[0..1] Jx on the
+// faces (i+1/2, j) and (i+1/2, j+1) (Eqs. 13-14), v[2..3] Jy on (i, j+1/2) and
+// (i+1, j+1/2) (Eqs. 15-16), v[4..7] Jz on the nodes (i,j), (i+1,j), (i,j+1),
+// (i+1,j+1): fq times the mean over the piece of each node's area weight.
+// With S0, S1 a node's weights at the start and end, the mean along a straight
+// piece is [S0x (2 S0y + S1y) + S1x (S0y + 2 S1y)] / 6; for the row j+1 the
+// y-factors are a1 = 2 fy0 + fy1 and b1 = fy0 + 2 fy1, for the row j they are
+// 3 - a1 and 3 - b1, and the column i weight is one minus the column i+1
+// weight, so each a = 0 value is the row total minus its a = 1 value.
 __device__ __forceinline__ void piece_current(float v[8], float fx0, float fy0, float fx1,
-                                              float fy1, float frac, float qjx, float qjy,
-                                              float qvz) {
+                                              float fy1, float fq, float qjx, float qjy) {
     const float dxp = fx1 - fx0, dyp = fy1 - fy0;
     const float xm = 0.5f * (fx0 + fx1), ym = 0.5f * (fy0 + fy1);
     const float jxv = qjx * dxp, jyv = qjy * dyp;
-    v[0] = jxv * (1.f - ym);
     v[1] = jxv * ym;
-    v[2] = jyv * (1.f - xm);
+    v[0] = jxv - v[1];
     v[3] = jyv * xm;
-    const float sx0 = 1.f - fx0, sx1 = 1.f - fx1;  // a = 0 weights at start / end
-    const float sy0 = 1.f - fy0, sy1 = 1.f - fy1;
-    const float c = qvz * frac * (1.f / 6.f);
-    // W_ab = [S0x_a (2 S0y_b + S1y_b) + S1x_a (S0y_b + 2 S1y_b)] / 6
-    const float ay0 = 2.f * sy0 + sy1, by0 = sy0 + 2.f * sy1;  // b = 0
-    const float ay1 = 2.f * fy0 + fy1, by1 = fy0 + 2.f * fy1;  // b = 1
-    v[4] = c * (sx0 * ay0 + sx1 * by0);
-    v[5] = c * (fx0 * ay0 + fx1 * by0);
-    v[6] = c * (sx0 * ay1 + sx1 * by1);
-    v[7] = c * (fx0 * ay1 + fx1 * by1);
+    v[2] = jyv - v[3];
+    const float c = fq * (1.f / 6.f);
+    const float a1 = 2.f * fy0 + fy1, b1 = fy0 + 2.f * fy1;  // row j+1
+    const float a0 = 3.f - a1, b0 = 3.f - b1;                // row j
+    v[5] = c * (fx0 * a0 + fx1 * b0);
+    v[4] = c * (a0 + b0) - v[5];
+    v[7] = c * (fx0 * a1 + fx1 * b1);
+    v[6] = c * (a1 + b1) - v[7];
 }
 
 // Offset of value k of piece_current from the piece's cell in the J tile
@@ -528,7 +529,7 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
             if (!__any_sync(FULL, mv && (mdi | mdj))) {
                 float v[8];
                 const int o = (mly + 1) * L::JW + (mlx + 1);
-                piece_current(v, mx0, my0, mx1, my1, 1.f, qjx, qjy, mqvz);
+                piece_current(v, mx0, my0, mx1, my1, mqvz, qjx, qjy);
                 deposit_warp<L::JW, L::JPLANE, L::PER_WARP>(mv, o, v, sJw, lane);
             } else {
                 const float t1 = fminf(fminf(mtx, mty), 1.f);
@@ -550,7 +551,7 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
                             const int cj = (mdj != 0 && mty <= ta) ? mdj : 0;
                             o = (mly + cj + 1) * L::JW + (mlx + ci + 1);
                             piece_current(v, xa - (float)ci, ya - (float)cj, xe - (float)ci,
-                                          ye - (float)cj, tb - ta, qjx, qjy, mqvz);
+                                          ye - (float)cj, mqvz * (tb - ta), qjx, qjy);
                         } else if constexpr (PIC_AGGREGATE) {
 #pragma unroll
                             for (int i = 0; i < 8; ++i) v[i] = 0.f;

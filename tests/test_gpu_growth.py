@@ -103,26 +103,25 @@ def _cold_two_stream_rate(k, u=0.2):
 
 def test_cold_seeded_two_stream_rates_follow_the_oracle_and_theory():
     """Cold beams (u_th = 0) on a 64 x 8 grid, 4x4 ppc, both beams displaced
-    by 1e-5 (sin k2 x + sin k3 x) (Gauss-consistent for the fixed ions): each
-    seeded mode grows at the cold rate (0.2978 for m = 2, 0.3430 for m = 3)."""
+    by 2e-6 (sin k2 x + sin k3 x) with zero initial fields (the seed of the
+    oracle's own cold two-stream pin): each seeded mode grows at the cold rate
+    (0.2978 for m = 2, 0.3430 for m = 3), fitted over t = 10..20, once the
+    seed's oscillating parts are small beside the growing one."""
     nx, ny, k, T = 64, 8, 4, 8
     ix, iy, x, y, a, b = wl.lattice(nx, ny, k)
     sgn = np.where((a + b) % 2 == 0, 1.0, -1.0)
     x0 = (ix + x.astype(np.float64)) * 0.1
-    xi = 1e-5 * sum(np.sin(2 * np.pi * m * x0 / (nx * 0.1)) for m in (2, 3))
+    xi = 2e-6 * sum(np.sin(2 * np.pi * m * x0 / (nx * 0.1)) for m in (2, 3))
     ix2, x2 = wl.displace_x(ix, x, xi / 0.1, nx)
     n = ix.size
     sp = wl.Species(-1.0, -1.0 / (k * k), ix2, iy, x2, y, (0.2 * sgn).astype(np.float32),
                     np.zeros(n, np.float32), np.zeros(n, np.float32))
-    E0 = np.zeros((3, ny, nx), np.float32)
-    xh = (np.arange(nx) + 0.5) * 0.1
-    E0[0] = (1e-5 * sum(np.sin(2 * np.pi * m * xh / (nx * 0.1)) for m in (2, 3)))[None, :]
-    w = wl.Workload("cold_two_stream", nx, ny, 0.1, 0.1, 0.05, T, 400, [sp], E0=E0)
-    g, o = _run_modes(w, 400, (2, 3))
+    w = wl.Workload("cold_two_stream", nx, ny, 0.1, 0.1, 0.05, T, 420, [sp])
+    g, o = _run_modes(w, 420, (2, 3))
     for j, m in enumerate((2, 3)):
         want = _cold_two_stream_rate(2 * np.pi * m / (nx * 0.1))
-        ro = _rate(o[:, j], w.dt, 100, 300)
-        rg = _rate(g[:, j], w.dt, 100, 300)
+        ro = _rate(o[:, j], w.dt, 200, 400)
+        rg = _rate(g[:, j], w.dt, 200, 400)
         print(f"cold two-stream m={m}: theory {want:.4f} oracle {ro:.4f} GPU {rg:.4f}")
         assert ro == pytest.approx(want, rel=0.05)
         assert abs(rg - ro) <= 0.02 * ro
