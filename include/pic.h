@@ -71,6 +71,12 @@ typedef enum {
 #define PIC_TRACK_IDS 2u  /* carry an int32 particle id through the re-sort */
 #define PIC_TIMING 4u     /* record CUDA events around each particle-advance launch */
 #define PIC_NO_GRAPH 8u   /* launch kernels one by one instead of a CUDA graph */
+#define PIC_FP32_J 16u    /* deposit the current into FP32 shared-memory tiles (float
+                             atomics, rounded sums) instead of the default exact 32-bit
+                             fixed-point tiles; slower, and free of the fixed-point
+                             quantum: the default quantum is 64 B |qtilde| / 2^30 per
+                             contribution, B the particle batches of blockDim in a CTA
+                             item (chunk is capped so that B <= 64) */
 
 typedef struct {
     double q_over_m; /* charge-to-mass ratio (electrons: -1) */
@@ -90,7 +96,8 @@ typedef struct {
     int n_species;    /* 1..PIC_MAX_SPECIES */
     pic_species_cfg species[PIC_MAX_SPECIES];
     double background;/* fixed neutralising ion charge density (enters rho only) */
-    unsigned flags;   /* PIC_STRICT_FP | PIC_TRACK_IDS | PIC_TIMING | PIC_NO_GRAPH */
+    unsigned flags;   /* PIC_STRICT_FP | PIC_TRACK_IDS | PIC_TIMING | PIC_NO_GRAPH |
+                         PIC_FP32_J */
 } pic_config;
 
 typedef struct {
@@ -298,7 +305,7 @@ pic_status pic_init_batch(const pic_config* cfgs, int n, void* cuda_stream, pic_
 /* Group n existing simulations into a batch stepped on `cuda_stream`.  Every
  * member must have been created on that same stream (so single-simulation
  * calls on a member stay ordered with the batch's steps), none may belong to
- * another batch, and all must share the PIC_STRICT_FP setting.  The caller
+ * another batch, and all must share the PIC_STRICT_FP and PIC_FP32_J settings.  The caller
  * keeps ownership of the members and must destroy the batch before them.
  * Returns PIC_EINVAL (message through pic_batch_last_error), PIC_ENOMEM,
  * PIC_ECUDA. */

@@ -598,6 +598,7 @@ __device__ __forceinline__ bool push_item(const PushParams& prm, const CUtensorM
                     S.ouz[q] = vzm;
                     if (prm.track_ids) S.oid[q] = S.id[p];
                     S.hole[q] = p;
+                    S.odir[q] = (uint8_t)dir;
                     S.cell[p] = HOLE;
                     if (dir < 8) atomicAdd(&sDir[s * 8 + dir], 1);
                 }
@@ -782,7 +783,7 @@ static cudaError_t launch_T(const CUtensorMap* fmap, const PushParams& p, int th
     }
     if (p.g.ntiles == 0) return cudaSuccess;
     const dim3 grid(p.g.ntiles, p.chunks);
-    const bool pw = kPW && Tile<T, kPW>::bytes(threads) <= SMEM_MAX;
+    const bool pw = kPW && !p.fp32_j && Tile<T, kPW>::bytes(threads) <= SMEM_MAX;
     const size_t bytes = pw ? Tile<T, kPW>::bytes(threads) : Tile<T, false>::bytes(threads);
     if (p.g.open_x) {
         if (pw) k_push_window<T, kPW><<<grid, threads, bytes, s>>>(*fmap, p);
@@ -817,7 +818,7 @@ template <int T>
 static cudaError_t launch_batch_T(const PushBatch& b, int threads, int grid, cudaStream_t s) {
     constexpr bool kPW = PIC_J_PER_WARP && T <= 16;
     if (b.nitems == 0) return cudaSuccess;
-    if (kPW && Tile<T, kPW>::bytes_batch(threads) <= SMEM_MAX)
+    if (kPW && !b.fp32_j && Tile<T, kPW>::bytes_batch(threads) <= SMEM_MAX)
         return launch_batch_TP<T, kPW>(b, threads, grid, s);
     return launch_batch_TP<T, false>(b, threads, grid, s);
 }

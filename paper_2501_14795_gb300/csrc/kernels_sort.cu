@@ -25,11 +25,6 @@ namespace pic {
 
 namespace {
 
-__device__ __forceinline__ int tile_of(int c, const Geom& g) {
-    const int ix = c & 0xffff, iy = (int)((unsigned)c >> 16);
-    return tile_index(g, ix / g.T, iy / g.T);
-}
-
 // neighbour of tile (tx, ty) displaced by direction d (0..7 over the 3x3
 // stencil without its centre)
 __device__ __forceinline__ void dir_delta(int d, int& dx, int& dy) {
@@ -273,13 +268,29 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_batch(const SortBatch b) 
 
 // Warp-per-tile bodies: a warp takes one tile; slots come from the warp's
 // ballots (register counters), so no CTA barrier or shared atomic is needed.
+// The re-sort moves about two per cent of the particles a step and is bound
+// by memory latency, not bandwidth: each body issues its independent loads in
+// one round (the tile's bookmarks with its neighbours' in the fill, four
+// positions per lane in the eviction, sources and holes together) so that a
+// tile costs few dependent round trips.
 constexpr int SORT_WARPS = 4;
+// entries per list (sources, targets) a warp keeps in shared memory; a tile
+// needing more uses the global index arrays
+constexpr int FILL_LIST = 256;
+constexpr int EVICT_UNROLL = 4;  // positions per lane and round in the eviction
 
 __device__ __forceinline__ void evict_tile(const SortParams& prm, int s, int t, int lane) {
     const SortSpecies& S = prm.sp[s];
-    const int p0 = S.off_old[t], p1 = S.off_old[t + 1];
-    const int r0 = S.off_new[t], r1 = S.off_new[t + 1];
-    const int lv = S.leave[t];
+    // the tile's old and new bookmarks and leaver count (lanes 0-4) and its
+    // leavers by direction (lanes 8-15), one round of loads
+    int hv = 0;
+    if (lane < 5)
+        hv = lane < 2 ? S.off_old[t + lane] : (lane < 4 ? S.off_new[t + lane - 2] : S.leave[t]);
+    else if (lane >= 8 && lane < 16)
+        hv = S.dirc[t * 8 + lane - 8];
+    const int p0 = __shfl_sync(0xffffffffu, hv, 0), p1 = __shfl_sync(0xffffffffu, hv, 1);
+    const int r0 = __shfl_sync(0xffffffffu, hv, 2), r1 = __shfl_sync(0xffffffffu, hv, 3);
+    const int lv = __shfl_sync(0xffffffffu, hv, 4);
     const int lim = prm.g.open_x ? S.cap : S.n;
     if (r0 < 0 || r1 < r0 || r1 > lim || p1 - p0 < lv) {
         if (lane == 0) dev::set_status(prm.st, ST_SORT);
@@ -292,32 +303,92 @@ __device__ __forceinline__ void evict_tile(const SortParams& prm, int s, int t, 
     const unsigned lt = (1u << lane) - 1u;
     int count = 0;
     bool overflow = false;
-    for (int base = 0; base < tot; base += 32) {
-        const int k = base + lane;
-        int p = -1;
-        bool take = false;
-        if (k < tot) {
-            p = k < na ? p0 + k : b0 + (k - na);
-            take = S.cell[p] != HOLE;
+    for (int base = 0; base < tot; base += 32 * EVICT_UNROLL) {
+        int p[EVICT_UNROLL], c[EVICT_UNROLL];
+#pragma unroll
+        for (int u = 0; u < EVICT_UNROLL; ++u) {
+            const int k = base + 32 * u + lane;
+            p[u] = k < tot ? (k < na ? p0 + k : b0 + (k - na)) : -1;
+            c[u] = p[u] >= 0 ? S.cell[p[u]] : HOLE;
         }
-        const unsigned m = __ballot_sync(0xffffffffu, take);
-        if (take) {
-            const int q = p0 + lv + count + __popc(m & lt);
-            if (q < p1) {
-                S.ocell[q] = S.cell[p];
-                S.ox[q] = S.x[p];
-                S.oy[q] = S.y[p];
-                S.oux[q] = S.ux[p];
-                S.ouy[q] = S.uy[p];
-                S.ouz[q] = S.uz[p];
-                if (prm.track_ids) S.oid[q] = S.id[p];
-            } else {
+        // slots for the stayers among them, then every copy's loads before its stores
+        int q[EVICT_UNROLL];
+#pragma unroll
+        for (int u = 0; u < EVICT_UNROLL; ++u) {
+            const bool take = c[u] != HOLE;
+            const unsigned m = __ballot_sync(0xffffffffu, take);
+            q[u] = take ? p0 + lv + count + __popc(m & lt) : -1;
+            if (q[u] >= p1) {
                 overflow = true;
+                q[u] = -1;
             }
+            count += __popc(m);
         }
-        count += __popc(m);
+        float x[EVICT_UNROLL], y[EVICT_UNROLL], ux[EVICT_UNROLL], uy[EVICT_UNROLL],
+            uz[EVICT_UNROLL];
+        int id[EVICT_UNROLL];
+#pragma unroll
+        for (int u = 0; u < EVICT_UNROLL; ++u)
+            if (q[u] >= 0) {
+                x[u] = S.x[p[u]];
+                y[u] = S.y[p[u]];
+                ux[u] = S.ux[p[u]];
+                uy[u] = S.uy[p[u]];
+                uz[u] = S.uz[p[u]];
+                if (prm.track_ids) id[u] = S.id[p[u]];
+            }
+#pragma unroll
+        for (int u = 0; u < EVICT_UNROLL; ++u)
+            if (q[u] >= 0) {
+                S.ocell[q[u]] = c[u];
+                S.ox[q[u]] = x[u];
+                S.oy[q[u]] = y[u];
+                S.oux[q[u]] = ux[u];
+                S.ouy[q[u]] = uy[u];
+                S.ouz[q[u]] = uz[u];
+                if (prm.track_ids) S.oid[q[u]] = id[u];
+            }
     }
     if (lane == 0) S.evict[t] = min(count, p1 - p0 - lv);
+
+    // The tile's leavers as one list per direction of motion (the
+    // neighbours' fills read the run heading to them directly): out indices
+    // in lsort[p0 ...], runs starting at ldir[t][d], the total at ldir[t][8].
+    const int d8 = lane - 8;
+    int pre = d8 >= 0 && d8 < 8 ? hv : 0;  // inclusive prefix of the counts over lanes 8-15
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, pre, o);
+        if (d8 >= o) pre += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, pre, 15);
+    if (d8 >= 0 && d8 < 8) S.ldir[t * 9 + d8] = pre - hv;
+    if (lane == 0) S.ldir[t * 9 + 8] = total;
+    int start[8], run[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        start[k] = __shfl_sync(0xffffffffu, pre - hv, 8 + k);
+        run[k] = 0;
+    }
+    if (total > lv) overflow = true;
+    for (int base = 0; base < lv; base += 32) {
+        const int k = base + lane;
+        const int dk = k < lv ? (int)S.odir[p0 + k] : 8;  // 8: removed, or past the end
+#pragma unroll
+        for (int dd = 0; dd < 8; ++dd) {
+            const unsigned m = __ballot_sync(0xffffffffu, dk == dd);
+            if (dk == dd) {
+                const int pos = start[dd] + run[dd] + __popc(m & lt);
+                if (pos < min(total, lv)) S.lsort[p0 + pos] = p0 + k;
+                else overflow = true;
+            }
+            run[dd] += __popc(m);
+        }
+    }
+    int got = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) got += run[k];
+    if (got != total) overflow = true;
     if (overflow) dev::set_status(prm.st, ST_SORT);
 }
 
@@ -335,15 +406,36 @@ __global__ void __launch_bounds__(32 * SORT_WARPS) k_evict_batch(const SortBatch
     if ((int)blockIdx.y < P.nsp) evict_tile(P, blockIdx.y, gt - b.tile_start[m], threadIdx.x & 31);
 }
 
-__device__ __forceinline__ void fill_tile(const SortParams& prm, int s, int t, int lane) {
+// `wl`: this warp's shared lists, 2 * FILL_LIST ints (sources, then targets).
+__device__ __forceinline__ void fill_tile(const SortParams& prm, int s, int t, int lane, int* wl) {
     const SortSpecies& S = prm.sp[s];
     const Geom& g = prm.g;
-    const int T = g.T;
     const int tx = tile_x(g, t), ty = tile_y(g, t);
-    const int p0 = S.off_old[t], p1 = S.off_old[t + 1];
-    const int r0 = S.off_new[t], r1 = S.off_new[t + 1];
+    const unsigned lt = (1u << lane) - 1u;
+    // one round of loads: the tile's bookmarks, leavers and evictions (lanes
+    // 0-5) and, for each of the eight directions of motion d (lanes 8-15),
+    // the run of leavers heading here from the tile the motion comes from:
+    // its out section, the run's start (ldir) and length (dirc).  These are
+    // the sources k_count summed into the new count.
+    int hv = 0;
+    if (lane < 6)
+        hv = lane < 2 ? S.off_old[t + lane]
+                      : (lane < 4 ? S.off_new[t + lane - 2] : (lane == 4 ? S.leave[t] : S.evict[t]));
+    const int d = lane - 8;
+    int q0 = 0, nl = 0;
+    if (d >= 0 && d < 8) {
+        int ddx, ddy;
+        dir_delta(d, ddx, ddy);
+        if (!((g.ntx == 1 && ddx) || (g.nty == 1 && ddy))) {
+            const int src = tile_index(g, dev::wrapi(tx - ddx, g.ntx), dev::wrapi(ty - ddy, g.nty));
+            q0 = S.off_old[src] + S.ldir[src * 9 + d];
+            nl = S.dirc[src * 8 + d];
+        }
+    }
+    const int p0 = __shfl_sync(0xffffffffu, hv, 0), p1 = __shfl_sync(0xffffffffu, hv, 1);
+    const int r0 = __shfl_sync(0xffffffffu, hv, 2), r1 = __shfl_sync(0xffffffffu, hv, 3);
+    const int lvt = __shfl_sync(0xffffffffu, hv, 4), ev = __shfl_sync(0xffffffffu, hv, 5);
     const int cap = r1 - r0;
-    const int lvt = S.leave[t], ev = S.evict[t];
     const int lim = g.open_x ? S.cap : S.n;
     if (r0 < 0 || r1 < r0 || r1 > lim || lvt + ev > p1 - p0) {
         if (lane == 0) dev::set_status(prm.st, ST_SORT);
@@ -352,47 +444,29 @@ __device__ __forceinline__ void fill_tile(const SortParams& prm, int s, int t, i
     // particles to place: incoming = new count - stayers, plus displaced stayers
     const int need = cap - (p1 - p0 - lvt) + ev;
     if (need == 0) return;
-    const unsigned lt = (1u << lane) - 1u;
+    // the lists: in shared memory when they fit, else in the global index arrays
+    int* lsrc = need <= FILL_LIST ? wl : S.isrc + r0;
+    int* ltgt = need <= FILL_LIST ? wl + FILL_LIST : S.fslot + r0;
     int nsrc = 0, ntgt = 0;
     bool overflow = false;
 
-    // source_idx: neighbours' leavers heading here.  Lanes 0-7 take the eight
-    // neighbour tiles (a neighbour that is t itself or repeats a lower lane's,
-    // on grids one or two tiles across, is dropped); their leaver lists are
-    // scanned as one concatenated list, so the loads of a chunk do not wait
-    // for the previous chunk.
-    int nb = -1, q0 = 0, nl = 0;
-    if (lane < 8) {
-        int ddx, ddy;
-        dir_delta(lane, ddx, ddy);
-        nb = tile_index(g, dev::wrapi(tx + ddx, g.ntx), dev::wrapi(ty + ddy, g.nty));
-    }
-    bool keep = lane < 8 && nb != t;
-#pragma unroll
-    for (int k = 0; k < 7; ++k) {
-        const int o = __shfl_sync(0xffffffffu, nb, k);
-        if (k < lane && o == nb) keep = false;
-    }
-    if (keep) {
-        q0 = S.off_old[nb];
-        nl = S.leave[nb];
-    }
-    int pre = nl;  // inclusive prefix over lanes 0-7
+    // source_idx: the eight runs heading here, as one concatenated list
+    int pre = nl;  // inclusive prefix over lanes 8-15
 #pragma unroll
     for (int o = 1; o < 8; o <<= 1) {
         const int v = __shfl_up_sync(0xffffffffu, pre, o);
-        if (lane >= o) pre += v;
+        if (d >= o) pre += v;
     }
-    const int total = __shfl_sync(0xffffffffu, pre, 7);
+    const int total = __shfl_sync(0xffffffffu, pre, 15);
     int ex[8], qq[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        ex[k] = __shfl_sync(0xffffffffu, pre - nl, k);
-        qq[k] = __shfl_sync(0xffffffffu, q0, k);
+        ex[k] = __shfl_sync(0xffffffffu, pre - nl, 8 + k);
+        qq[k] = __shfl_sync(0xffffffffu, q0, 8 + k);
     }
-    // the list holding entry e: the last one starting at or before it (lists
-    // of length 0 share their start with the next one)
-    auto source_of = [&](int e) {
+    // position in lsort of entry e: in the last run starting at or before it
+    // (runs of length 0 share their start with the next one)
+    auto sorted_pos = [&](int e) {
         int q = qq[0], x = ex[0];  // selects, not an indexed array: stays in registers
 #pragma unroll
         for (int j = 1; j < 8; ++j)
@@ -402,36 +476,41 @@ __device__ __forceinline__ void fill_tile(const SortParams& prm, int s, int t, i
             }
         return q + (e - x);
     };
-    // two chunks of 32 entries per round: both chunks' cell loads are in
-    // flight together (the fill is bound by memory latency, not bandwidth)
-    for (int base = 0; base < total; base += 64) {
+    if (total > need) overflow = true;
+    // target_idx: holes of this tile inside its new range.  Sources and holes
+    // are read in the same rounds, two chunks of 32 each, so that all their
+    // loads are in flight together.
+    const int rounds = max(total, lvt);
+    for (int base = 0; base < rounds; base += 64) {
         const int e0 = base + lane, e1 = e0 + 32;
-        const int src0 = e0 < total ? source_of(e0) : 0;
-        const int src1 = e1 < total ? source_of(e1) : 0;
-        const int c0 = e0 < total ? S.ocell[src0] : HOLE;
-        const int c1 = e1 < total ? S.ocell[src1] : HOLE;
-        const bool take0 = e0 < total && tile_of(c0, g) == t;
-        const bool take1 = e1 < total && tile_of(c1, g) == t;
-        const unsigned m0 = __ballot_sync(0xffffffffu, take0);
-        const unsigned m1 = __ballot_sync(0xffffffffu, take1);
-        if (take0) {
-            const int slot = nsrc + __popc(m0 & lt);
-            if (slot < cap) S.isrc[r0 + slot] = src0;
+        const int src0 = e0 < total ? S.lsort[sorted_pos(e0)] : 0;
+        const int src1 = e1 < total ? S.lsort[sorted_pos(e1)] : 0;
+        const int h0 = e0 < lvt ? S.hole[p0 + e0] : -1;
+        const int h1 = e1 < lvt ? S.hole[p0 + e1] : -1;
+        if (e0 < total && e0 < need) lsrc[e0] = src0;
+        if (e1 < total && e1 < need) lsrc[e1] = src1;
+        const bool hk0 = h0 >= r0 && h0 < r1, hk1 = h1 >= r0 && h1 < r1;
+        const unsigned g0 = __ballot_sync(0xffffffffu, hk0);
+        const unsigned g1 = __ballot_sync(0xffffffffu, hk1);
+        if (hk0) {
+            const int slot = ntgt + __popc(g0 & lt);
+            if (slot < need) ltgt[slot] = h0;
             else overflow = true;
         }
-        if (take1) {
-            const int slot = nsrc + __popc(m0) + __popc(m1 & lt);
-            if (slot < cap) S.isrc[r0 + slot] = src1;
+        if (hk1) {
+            const int slot = ntgt + __popc(g0) + __popc(g1 & lt);
+            if (slot < need) ltgt[slot] = h1;
             else overflow = true;
         }
-        nsrc += __popc(m0) + __popc(m1);
+        ntgt += __popc(g0) + __popc(g1);
     }
-    // ... plus this tile's displaced stayers
+    nsrc = total;
+    // sources: this tile's displaced stayers ...
     for (int base = 0; base < ev; base += 32) {
         const int i = base + lane;
         if (i < ev) {
             const int slot = nsrc + i;
-            if (slot < cap) S.isrc[r0 + slot] = p0 + lvt + i;
+            if (slot < need) lsrc[slot] = p0 + lvt + i;
             else overflow = true;
         }
     }
@@ -442,35 +521,22 @@ __device__ __forceinline__ void fill_tile(const SortParams& prm, int s, int t, i
         const int i = base + lane;
         if (i < inj.total) {
             const int slot = nsrc + i;
-            if (slot < cap) S.isrc[r0 + slot] = -1 - i;
+            if (slot < need) lsrc[slot] = -1 - i;
             else overflow = true;
         }
     }
     nsrc += inj.total;
-    // target_idx: holes of this tile inside its new range ...
-    for (int base = 0; base < lvt; base += 32) {
-        const int i = base + lane;
-        const int h = i < lvt ? S.hole[p0 + i] : -1;
-        const bool take = i < lvt && h >= r0 && h < r1;
-        const unsigned m = __ballot_sync(0xffffffffu, take);
-        if (take) {
-            const int slot = ntgt + __popc(m & lt);
-            if (slot < cap) S.fslot[r0 + slot] = h;
-            else overflow = true;
-        }
-        ntgt += __popc(m);
-    }
-    // ... plus the part of the new range outside the old one
+    // targets: the part of the new range outside the old one
     {
         const int a1 = min(p0, r1), b0 = max(p1, r0);
-        const int na = max(a1 - r0, 0), nb = max(r1 - b0, 0);
-        const int tot = na + nb;
+        const int na = max(a1 - r0, 0), nb2 = max(r1 - b0, 0);
+        const int tot = na + nb2;
         for (int base = 0; base < tot; base += 32) {
             const int k = base + lane;
             if (k < tot) {
                 const int slot = ntgt + k;
                 const int pos = k < na ? r0 + k : b0 + (k - na);
-                if (slot < cap) S.fslot[r0 + slot] = pos;
+                if (slot < need) ltgt[slot] = pos;
                 else overflow = true;
             }
         }
@@ -485,9 +551,9 @@ __device__ __forceinline__ void fill_tile(const SortParams& prm, int s, int t, i
     // loads issued before the stores
     for (int k = lane; k < nsrc; k += 64) {
         const bool two = k + 32 < nsrc;
-        const int src0 = S.isrc[r0 + k], to0 = S.fslot[r0 + k];
-        const int src1 = two ? S.isrc[r0 + k + 32] : -1;
-        const int to1 = two ? S.fslot[r0 + k + 32] : 0;
+        const int src0 = lsrc[k], to0 = ltgt[k];
+        const int src1 = two ? lsrc[k + 32] : -1;
+        const int to1 = two ? ltgt[k + 32] : 0;
         if (src0 >= 0 && src1 >= 0) {
             copy_two(S, src0, to0, src1, to1, prm.track_ids);
         } else {
@@ -502,16 +568,21 @@ __device__ __forceinline__ void fill_tile(const SortParams& prm, int s, int t, i
 }
 
 __global__ void __launch_bounds__(32 * SORT_WARPS) k_fill(const SortParams prm) {
-    const int t = blockIdx.x * SORT_WARPS + (threadIdx.x >> 5);
-    if (t < prm.g.ntiles) fill_tile(prm, blockIdx.y, t, threadIdx.x & 31);
+    __shared__ int sList[SORT_WARPS][2 * FILL_LIST];
+    const int w = threadIdx.x >> 5;
+    const int t = blockIdx.x * SORT_WARPS + w;
+    if (t < prm.g.ntiles) fill_tile(prm, blockIdx.y, t, threadIdx.x & 31, sList[w]);
 }
 
 __global__ void __launch_bounds__(32 * SORT_WARPS) k_fill_batch(const SortBatch b) {
-    const int gt = blockIdx.x * SORT_WARPS + (threadIdx.x >> 5);
+    __shared__ int sList[SORT_WARPS][2 * FILL_LIST];
+    const int w = threadIdx.x >> 5;
+    const int gt = blockIdx.x * SORT_WARPS + w;
     if (gt >= b.total_tiles) return;
     const int m = find_member(b.tile_start, b.nmembers, gt);
     const SortParams& P = b.members[m];
-    if ((int)blockIdx.y < P.nsp) fill_tile(P, blockIdx.y, gt - b.tile_start[m], threadIdx.x & 31);
+    if ((int)blockIdx.y < P.nsp)
+        fill_tile(P, blockIdx.y, gt - b.tile_start[m], threadIdx.x & 31, sList[w]);
 }
 
 }  // namespace

@@ -29,6 +29,7 @@ struct pic_batch {
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     bool strict = false;
+    bool fp32_j = false;
     // what the graphs were built for: members' parity at phase 0 and generation
     std::vector<int> cur0;
     std::vector<unsigned long long> gen;
@@ -204,6 +205,7 @@ int enqueue_batch_step(pic_batch* batch, cudaStream_t s, int p) {
         pb.items = batch->d_items + g.first;
         pb.nitems = g.count;
         pb.next = batch->d_next + gi;
+        pb.fp32_j = batch->fp32_j ? 1 : 0;
         e = batch->strict ? launch_push_batch_strict(pb, g.T, g.threads, 0, s)
                           : launch_push_batch_fast(pb, g.T, g.threads, 0, s);
         n += g.count > 0;
@@ -264,7 +266,7 @@ bool stale(const pic_batch* batch) {
 struct TuneKey {
     int nx, ny, nsp;
     long long ppc_milli;  // total particles per cell x 1000
-    int strict, device;
+    int strict, device;  // strict: the PIC_STRICT_FP | PIC_FP32_J bits (other kernels)
     bool operator<(const TuneKey& o) const {
         return std::tie(nx, ny, nsp, ppc_milli, strict, device) <
                std::tie(o.nx, o.ny, o.nsp, o.ppc_milli, o.strict, o.device);
@@ -444,7 +446,7 @@ pic_status pic_autotune(pic_sim* sim, int steps, int force, int* tile, int* thre
     for (int k = 0; k < sim->cfg.n_species; ++k)
         ppc += (double)sim->sp[k].n / ((double)sim->cfg.nx * sim->cfg.ny);
     const TuneKey key{sim->cfg.nx, sim->cfg.ny, sim->cfg.n_species, std::llround(ppc * 1000.0),
-                      (sim->cfg.flags & PIC_STRICT_FP) ? 1 : 0, dev};
+                      (int)(sim->cfg.flags & (PIC_STRICT_FP | PIC_FP32_J)), dev};
     if (!force) {
         std::pair<int, int> hit{0, 0};
         {
@@ -543,6 +545,8 @@ pic_status pic_batch_create(pic_sim* const* members, int n, void* cuda_stream, p
             why = "member listed twice";
         else if (k > 0 && ((sim->cfg.flags ^ members[0]->cfg.flags) & PIC_STRICT_FP))
             why = "members differ in PIC_STRICT_FP";
+        else if (k > 0 && ((sim->cfg.flags ^ members[0]->cfg.flags) & PIC_FP32_J))
+            why = "members differ in PIC_FP32_J";
         else if (sim->jfilter)
             why = "member has a current filter installed";
         else if (sim->window)
@@ -555,6 +559,7 @@ pic_status pic_batch_create(pic_sim* const* members, int n, void* cuda_stream, p
         batch->m.push_back(sim);
     }
     batch->strict = (members[0]->cfg.flags & PIC_STRICT_FP) != 0;
+    batch->fp32_j = (members[0]->cfg.flags & PIC_FP32_J) != 0;
     if (cudaStreamCreateWithFlags(&batch->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete batch;
         return PIC_ECUDA;

@@ -146,6 +146,7 @@ cudaError_t alloc_tile_arrays(SpeciesDev& s, const Geom& g, cudaStream_t st) {
             e = cudaMemsetAsync(s.dirc[b], 0, sizeof(int32_t) * 8 * g.ntiles, st);
     }
     if (e == cudaSuccess) e = dalloc(&s.evict, g.ntiles);
+    if (e == cudaSuccess) e = dalloc(&s.ldir, 9 * (size_t)g.ntiles);
     return e;
 }
 
@@ -157,14 +158,16 @@ void free_tile_arrays(SpeciesDev& s) {
         s.off[b] = s.leave[b] = s.dirc[b] = nullptr;
     }
     dfree(s.evict);
-    s.evict = nullptr;
+    dfree(s.ldir);
+    s.evict = s.ldir = nullptr;
 }
 
 void free_species(SpeciesDev& s) {
-    void* ptrs[] = {s.cell, s.x,  s.y,  s.ux,   s.uy,   s.uz,    s.id,     s.ocell, s.ox,
-                    s.oy,   s.oux, s.ouy, s.ouz, s.oid, s.hole, s.fslot, s.isrc};
+    void* ptrs[] = {s.cell, s.x,   s.y,   s.ux,  s.uy,  s.uz,   s.id,    s.ocell, s.ox, s.oy,
+                    s.oux,  s.ouy, s.ouz, s.oid, s.hole, s.fslot, s.isrc, s.odir,  s.lsort};
     for (void* p : ptrs) dfree(p);
-    s.cell = s.id = s.ocell = s.oid = s.hole = s.fslot = s.isrc = nullptr;
+    s.cell = s.id = s.ocell = s.oid = s.hole = s.fslot = s.isrc = s.lsort = nullptr;
+    s.odir = nullptr;
     s.x = s.y = s.ux = s.uy = s.uz = s.ox = s.oy = s.oux = s.ouy = s.ouz = nullptr;
     s.cap = 0;
 }
@@ -181,7 +184,7 @@ cudaError_t alloc_particles(SpeciesDev& s, int64_t cap) {
     };
     A(&s.cell); A(&s.x); A(&s.y); A(&s.ux); A(&s.uy); A(&s.uz); A(&s.id);
     A(&s.ocell); A(&s.ox); A(&s.oy); A(&s.oux); A(&s.ouy); A(&s.ouz); A(&s.oid);
-    A(&s.hole); A(&s.fslot); A(&s.isrc);
+    A(&s.hole); A(&s.fslot); A(&s.isrc); A(&s.odir); A(&s.lsort);
     if (e == cudaSuccess) s.cap = cap;
     return e;
 }
@@ -202,11 +205,19 @@ void invalidate_graphs(pic_sim* sim) {
 // CTAs per SM and the hardware balances them); one CTA per tile otherwise.
 constexpr int kMaxChunks = 1024;
 
+// With the fixed-point J tiles a CTA item holds at most kMaxItemBatches
+// batches of blockDim particles: the tiles' scale is set by the particles an
+// item can deposit, so this bounds the quantum at 2^-18 |qtilde|.
+constexpr int kMaxItemBatches = 64;
+
 int chunks_per_tile(const pic_sim* sim) {
     int64_t nmax = 0;
     for (int k = 0; k < sim->cfg.n_species; ++k) nmax = std::max(nmax, sim->sp[k].n);
     const int64_t per_tile = sim->g.ntiles ? nmax / sim->g.ntiles : 0;
-    const int64_t c = (per_tile + sim->cfg.chunk - 1) / sim->cfg.chunk;
+    int64_t chunk = sim->cfg.chunk;
+    if (!(sim->cfg.flags & PIC_FP32_J))
+        chunk = std::min<int64_t>(chunk, (int64_t)kMaxItemBatches * sim->cfg.threads);
+    const int64_t c = (per_tile + chunk - 1) / chunk;
     return (int)std::min<int64_t>(std::max<int64_t>(c, 1), kMaxChunks);
 }
 
@@ -217,12 +228,13 @@ PushParams push_params(const pic_sim* sim, int b) {
     p.J = sim->J[b];
     p.nsp = sim->cfg.n_species;
     p.track_ids = (sim->cfg.flags & PIC_TRACK_IDS) ? 1 : 0;
+    p.fp32_j = (sim->cfg.flags & PIC_FP32_J) ? 1 : 0;
     for (int k = 0; k < p.nsp; ++k) {
         const SpeciesDev& s = sim->sp[k];
         PushSpecies& q = p.sp[k];
         q.off = s.off[b];
         q.cell = s.cell; q.id = s.id; q.ocell = s.ocell; q.oid = s.oid; q.hole = s.hole;
-        q.leave = s.leave[b]; q.dirc = s.dirc[b];
+        q.leave = s.leave[b]; q.dirc = s.dirc[b]; q.odir = s.odir;
         q.x = s.x; q.y = s.y; q.ux = s.ux; q.uy = s.uy; q.uz = s.uz;
         q.ox = s.ox; q.oy = s.oy; q.oux = s.oux; q.ouy = s.ouy; q.ouz = s.ouz;
         q.tem = s.tem; q.qjx = s.qjx; q.qjy = s.qjy; q.qjz = s.qjz; q.ke_w = s.ke_w;
@@ -247,6 +259,7 @@ SortParams sort_params(const pic_sim* sim, int b) {
         q.cell = s.cell; q.id = s.id; q.ocell = s.ocell; q.oid = s.oid; q.hole = s.hole;
         q.fslot = s.fslot; q.isrc = s.isrc; q.leave = s.leave[b]; q.dirc = s.dirc[b];
         q.leave_next = s.leave[1 - b]; q.dirc_next = s.dirc[1 - b]; q.evict = s.evict;
+        q.odir = s.odir; q.lsort = s.lsort; q.ldir = s.ldir;
         q.x = s.x; q.y = s.y; q.ux = s.ux; q.uy = s.uy; q.uz = s.uz;
         q.ox = s.ox; q.oy = s.oy; q.oux = s.oux; q.ouy = s.ouy; q.ouz = s.ouz;
         q.n = (int)s.n;
@@ -632,7 +645,8 @@ pic_status pic_load_particles(pic_sim* sim, int species, int64_t n, const int32_
     if (grow) {
         SpeciesDev fresh = S;
         fresh.cell = fresh.id = fresh.ocell = fresh.oid = fresh.hole = fresh.fslot = fresh.isrc =
-            nullptr;
+            fresh.lsort = nullptr;
+        fresh.odir = nullptr;
         fresh.x = fresh.y = fresh.ux = fresh.uy = fresh.uz = nullptr;
         fresh.ox = fresh.oy = fresh.oux = fresh.ouy = fresh.ouz = nullptr;
         fresh.cap = 0;

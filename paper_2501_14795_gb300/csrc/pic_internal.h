@@ -57,12 +57,15 @@ struct SpeciesDev {
     float *ox, *oy, *oux, *ouy, *ouz;
     int32_t* oid;
     int32_t* hole;    // positions vacated by leavers, per source tile
+    uint8_t* odir;    // each leaver's direction (0-7; 8: left the open box), out-array order
+    int32_t* lsort;   // each tile's leavers' out indices sorted by direction
     int32_t* fslot;   // fill lists: target positions ...
     int32_t* isrc;    // ... and source indices into the out arrays
     int32_t* off[2];  // ntiles + 1 bookmarks (tile_offset), ping-pong
     int32_t* leave[2];  // per tile: particles that left (ping-pong; the scan clears the idle one)
     int32_t* dirc[2];   // per tile x 8 directions: leavers by destination (ping-pong)
     int32_t* evict;   // per tile: stayers displaced by the new bookmarks
+    int32_t* ldir;    // per tile x 9: start of each direction's run in lsort (8: total)
     int32_t* cursor;  // per cell scratch for the initial load (nx*ny)
     int64_t n;        // particles
     int64_t cap;      // capacity of the particle arrays
@@ -146,6 +149,7 @@ __host__ __device__ inline int inject_first(long long gcol, int k, double x0, do
 struct PushSpecies {
     const int32_t* off;
     int32_t *cell, *id, *ocell, *oid, *hole, *leave, *dirc;
+    uint8_t* odir;
     float *x, *y, *ux, *uy, *uz, *ox, *oy, *oux, *ouy, *ouz;
     float tem, qjx, qjy, qjz;
     double ke_w;
@@ -157,6 +161,7 @@ struct alignas(16) PushParams {
     int chunks;            // CTAs per tile (gridDim.y): each takes a slice of the tile's particles
     int nsp;
     int track_ids;
+    int fp32_j;            // FP32 J tiles instead of the fixed-point ones (PIC_FP32_J)
     PushSpecies sp[MAX_SPECIES];
     double* hist_k;        // kinetic-energy history ring
     DevState* st;
@@ -167,6 +172,8 @@ struct SortSpecies {
     int32_t* off_new;
     int32_t *cell, *id, *ocell, *oid, *hole, *fslot, *isrc, *leave, *dirc, *evict;
     int32_t *leave_next, *dirc_next;  // cleared here for the next step
+    const uint8_t* odir;
+    int32_t *lsort, *ldir;
     float *x, *y, *ux, *uy, *uz, *ox, *oy, *oux, *ouy, *ouz;
     int n;       // particles (fixed count; with the moving window see DevState::np)
     int cap;     // capacity of the particle arrays
@@ -206,6 +213,7 @@ struct PushBatch {
     const int4* items;          // (member, tile, chunk, 0), costliest first
     int nitems;
     int* next;                  // work-item counter, zero at launch
+    int fp32_j;                 // the members' PIC_FP32_J setting (shared by all)
 };
 
 struct SortBatch {

@@ -24,6 +24,7 @@ PIC_NO_GRAPH = 8
 
 STATUS = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ECFL", 3: "PIC_ENOMEM", 4: "PIC_ECUDA",
           5: "PIC_EOVERFLOW", 6: "PIC_EPARTICLE", 7: "PIC_ETIMEOUT"}
+PIC_FP32_J = 16
 FIELD_E, FIELD_B, FIELD_J, FIELD_RHO = 0, 1, 2, 3
 (PIC_OK, PIC_EINVAL, PIC_ECFL, PIC_ENOMEM, PIC_ECUDA, PIC_EOVERFLOW, PIC_EPARTICLE,
  PIC_ETIMEOUT) = range(8)
