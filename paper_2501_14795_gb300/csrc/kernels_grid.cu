@@ -1,6 +1,8 @@
 // Grid kernels: the fused Yee advance (§3.1 three-step scheme, §4.4 tiled
 // field advance), guard-cell copies, field energies, charge density and the
 // FP64 charge-conservation residuals, and the initial particle load/sort.
+#include <algorithm>
+
 #include "device_util.cuh"
 #include "pic_internal.h"
 
@@ -498,31 +500,111 @@ struct RhoParams {
     double* rho;
 };
 
-__global__ void k_rho(const RhoParams prm) {
-    extern __shared__ double sR[];
+// Charge density on the nodes (area weighting of Fig. 3.3), in FP64.  A CTA
+// takes a slice of a tile's particles (tiles holding many are split over
+// several CTAs, as in the particle advance).  Each particle adds to its own
+// cell the moments 1, x, y and x y as exact integers: fixed-point values
+// x 2^38, y 2^38 and x y 2^48 (the product is split exactly into two FP32
+// terms with a fused multiply-add), added as 19-, 19- and 16-bit chunks to
+// 32-bit shared counters, which cannot overflow for the at most RHO_ROUND
+// particles a round accumulates.  The four corner weights follow from the
+// moments exactly, (1-x)(1-y) = 1 - x - y + x y, x (1-y) = x - x y,
+// (1-x) y = y - x y, in 64-bit integers; each node's sum is scaled to FP64
+// once and added to the global rho with an FP64 atomic.  Shared integer
+// atomics cost a fraction of FP64 ones, and no FP64 arithmetic is done per
+// particle.
+constexpr int RHO_THREADS = 256;
+constexpr int RHO_ROUND = 8192;  // particles per accumulation round of a CTA
+constexpr int RHO_WORDS = 8;     // count, x (2 chunks), y (2 chunks), x y (3 chunks)
+constexpr int RHO_CHUNK = 8192;  // particles per CTA (tiles holding more are split)
+
+__device__ __forceinline__ long long rho_moment(const unsigned* sM, int T2, int c, int k0,
+                                                int shift) {
+    return (long long)sM[k0 * T2 + c] + ((long long)sM[(k0 + 1) * T2 + c] << shift);
+}
+
+__global__ void __launch_bounds__(RHO_THREADS) k_rho(const RhoParams prm) {
+    extern __shared__ __align__(16) unsigned char smem_r[];
     const Geom& g = prm.g;
-    const int T = g.T, W = T + 1;
-    const int t = blockIdx.x;
+    const int T = g.T, W = T + 1, T2 = T * T;
+    unsigned* sM = reinterpret_cast<unsigned*>(smem_r);  // [RHO_WORDS][T*T]
+    double* sR = reinterpret_cast<double*>(smem_r + (((size_t)RHO_WORDS * T2 * 4 + 15) & ~(size_t)15));
+    const int t = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
     const int tx = tile_x(g, t), ty = tile_y(g, t);
     const int ix0 = tx * T, iy0 = ty * T;
-    for (int k = threadIdx.x; k < W * W; k += blockDim.x) sR[k] = 0.0;
-    __syncthreads();
+    for (int k = tid; k < W * W; k += nth) sR[k] = 0.0;
     for (int s = 0; s < prm.nsp; ++s) {
         const RhoSpecies& S = prm.sp[s];
-        for (int p = S.off[t] + threadIdx.x; p < S.off[t + 1]; p += blockDim.x) {
-            const int c = S.cell[p];
-            const int lx = (c & 0xffff) - ix0, ly = (int)((unsigned)c >> 16) - iy0;
-            if (c == HOLE || lx < 0 || lx >= T || ly < 0 || ly >= T) continue;
-            const double x = S.x[p], y = S.y[p];
-            double* r = sR + ly * W + lx;
-            atomicAdd(r, S.q * (1.0 - x) * (1.0 - y));
-            atomicAdd(r + 1, S.q * x * (1.0 - y));
-            atomicAdd(r + W, S.q * (1.0 - x) * y);
-            atomicAdd(r + W + 1, S.q * x * y);
+        const int p0 = S.off[t], nt = S.off[t + 1] - p0;
+        const int len = (nt + (int)gridDim.y - 1) / (int)gridDim.y;
+        const int c0 = p0 + min((int)blockIdx.y * len, nt);
+        const int c1 = p0 + min(((int)blockIdx.y + 1) * len, nt);
+        for (int r0 = c0; r0 < c1; r0 += RHO_ROUND) {
+            const int r1 = min(r0 + RHO_ROUND, c1);
+            for (int k = tid; k < RHO_WORDS * T2; k += nth) sM[k] = 0u;
+            __syncthreads();
+            for (int p = r0 + tid; p < r1; p += nth) {
+                const int c = S.cell[p];
+                const int lx = (c & 0xffff) - ix0, ly = (int)((unsigned)c >> 16) - iy0;
+                if (c == HOLE || lx < 0 || lx >= T || ly < 0 || ly >= T) continue;
+                const float x = S.x[p], y = S.y[p];
+                const unsigned long long vx = __float2ull_rn(x * 0x1p38f);  // < 2^38
+                const unsigned long long vy = __float2ull_rn(y * 0x1p38f);
+                const float pxy = __fmul_rn(x, y);
+                const float exy = __fmaf_rn(x, y, -pxy);  // x y = pxy + exy exactly
+                long long vxy = (long long)__float2ull_rn(pxy * 0x1p48f) +
+                                __float2ll_rn(exy * 0x1p48f);
+                if (vxy < 0) vxy = 0;
+                const int cc = ly * T + lx;
+                atomicAdd(sM + cc, 1u);
+                atomicAdd(sM + T2 + cc, (unsigned)(vx & 0x7ffffu));
+                atomicAdd(sM + 2 * T2 + cc, (unsigned)(vx >> 19));
+                atomicAdd(sM + 3 * T2 + cc, (unsigned)(vy & 0x7ffffu));
+                atomicAdd(sM + 4 * T2 + cc, (unsigned)(vy >> 19));
+                atomicAdd(sM + 5 * T2 + cc, (unsigned)(vxy & 0xffff));
+                atomicAdd(sM + 6 * T2 + cc, (unsigned)((vxy >> 16) & 0xffff));
+                atomicAdd(sM + 7 * T2 + cc, (unsigned)(vxy >> 32));
+            }
+            __syncthreads();
+            // node (i, j) of the tile, 0 <= i, j <= T: the (1-x)(1-y) weight of
+            // cell (i, j), x (1-y) of cell (i-1, j), (1-x) y of cell (i, j-1)
+            // and x y of cell (i-1, j-1), in units of 2^-48
+            for (int k = tid; k < W * W; k += nth) {
+                const int j = k / W, i = k - j * W;
+                long long acc = 0;
+                auto moments = [&](int ci, int cj, long long& n, long long& X, long long& Y,
+                                   long long& XY) {
+                    const int c = cj * T + ci;
+                    n = (long long)sM[c] << 48;
+                    X = rho_moment(sM, T2, c, 1, 19) << 10;
+                    Y = rho_moment(sM, T2, c, 3, 19) << 10;
+                    XY = (long long)sM[5 * T2 + c] + ((long long)sM[6 * T2 + c] << 16) +
+                         ((long long)sM[7 * T2 + c] << 32);
+                };
+                long long n, X, Y, XY;
+                if (i < T && j < T) {
+                    moments(i, j, n, X, Y, XY);
+                    acc += n - X - Y + XY;
+                }
+                if (i > 0 && j < T) {
+                    moments(i - 1, j, n, X, Y, XY);
+                    acc += X - XY;
+                }
+                if (i < T && j > 0) {
+                    moments(i, j - 1, n, X, Y, XY);
+                    acc += Y - XY;
+                }
+                if (i > 0 && j > 0) {
+                    moments(i - 1, j - 1, n, X, Y, XY);
+                    acc += XY;
+                }
+                if (acc) sR[k] += S.q * ((double)acc * 0x1p-48);
+            }
+            __syncthreads();  // the moments are cleared for the next round
         }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < W * W; k += blockDim.x) {
+    for (int k = tid; k < W * W; k += nth) {
         const double v = sR[k];
         if (v == 0.0) continue;
         const int ly = k / W, lx = k - ly * W;
@@ -533,9 +615,6 @@ __global__ void k_rho(const RhoParams prm) {
     }
 }
 
-// FP64 residuals on nodes: max |div E - rho|, max |(rho - rho_prev)/dt +
-// div J| (if rho_prev), sum rho dx dy.  rho excludes the background, which
-// is added here.
 __global__ void k_residuals(const Geom g, const float* F, const float* J, const double* rho,
                             const double* rho_prev, double background, double* out) {
     __shared__ double sRed[32];
@@ -855,8 +934,15 @@ cudaError_t launch_rho(const Geom& g, const SpeciesDev* sp, int nsp, const int32
         p.sp[k].q = sp[k].qtilde;
     }
     p.rho = rho;
-    const size_t bytes = (size_t)(g.T + 1) * (g.T + 1) * sizeof(double);
-    k_rho<<<g.ntiles, 256, bytes, s>>>(p);
+    if (g.ntiles == 0) return cudaSuccess;
+    // slices of at most RHO_CHUNK particles of the fullest species' mean tile
+    int64_t nmax = 0;
+    for (int k = 0; k < nsp; ++k) nmax = std::max<int64_t>(nmax, sp[k].n);
+    const int64_t per_tile = nmax / g.ntiles;
+    const int chunks = (int)std::min<int64_t>(std::max<int64_t>((per_tile + RHO_CHUNK - 1) / RHO_CHUNK, 1), 1024);
+    const size_t bytes = (((size_t)RHO_WORDS * g.T * g.T * 4 + 15) & ~(size_t)15) +
+                         (size_t)(g.T + 1) * (g.T + 1) * sizeof(double);
+    k_rho<<<dim3(g.ntiles, chunks), RHO_THREADS, bytes, s>>>(p);
     return cudaGetLastError();
 }
 
