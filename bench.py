@@ -650,11 +650,11 @@ def run_denoiser_fwd(args, rank, world, local_rank):
                    "l2": "inputs larger than L2 (one full-resolution activation 268 MB > 129 MB)"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "whole forward pass (14 launches)",
+                     "kernel": "whole forward pass (13 launches)",
                      "peak_source": "measured bf16_tflops" if os.path.exists(p) else "fallback"},
         "e2e": {"value": flops / (e2e_ms * 1e-3) / 1e12 * world, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": xh.nbytes, "d2h_bytes_per_step": oh.nbytes},
-        "gpu_launches": 14 * args.steps,
+        "gpu_launches": 13 * args.steps,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

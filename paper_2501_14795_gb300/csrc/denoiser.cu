@@ -224,9 +224,12 @@ int forward(pic_denoiser* d, int B, const float* J, long long bstride, long long
         }                                                                           \
         ++n;                                                                        \
     } while (0)
-    FW(launch_pack_input(J, bstride, cstride, pitch, offset, B, H0, W0, (float)(1.0 / d->scale),
-                         d->xin, s));
-    FW(conv(d, 0, B, d->xin, EPI_ACT, d->a[0], nullptr, nullptr, nullptr, s));
+    {
+        const LayerDesc& L = d->tab.layer[0];
+        FW(launch_conv_first(J, bstride, cstride, pitch, offset, B, H0, W0,
+                             (float)(1.0 / d->scale), d->wf + L.wf_off, L.cout_pad,
+                             d->master + d->boff[0], d->xin, d->a[0], s));
+    }
     FW(conv(d, 1, B, d->a[0], EPI_ACT, d->a[1], nullptr, nullptr, nullptr, s));
     FW(launch_pool_fwd(d->a[1], B, H0, W0, 32, d->p1, s));
     FW(conv(d, 2, B, d->p1, EPI_ACT, d->a[2], nullptr, nullptr, nullptr, s));
@@ -241,8 +244,12 @@ int forward(pic_denoiser* d, int B, const float* J, long long bstride, long long
     FW(conv(d, 8, B, d->a[7], EPI_ACT, d->a[8], d->a[1], d->y9, nullptr, s, nullptr, nullptr, 0,
             0, 0, 0, 0.f, 0.f, 1));
     FW(conv(d, 9, B, d->y9, EPI_ACT, d->a[9], nullptr, nullptr, nullptr, s));
-    FW(conv(d, 10, B, d->a[9], EPI_FINAL, nullptr, nullptr, nullptr, nullptr, s, J, fout, bstride,
-            cstride, pitch, offset, rs, os));
+    {
+        const LayerDesc& L = d->tab.layer[NL - 1];
+        FW(launch_conv_last(d->a[9], B, H0, W0, d->wf + L.wf_off, L.cout_pad,
+                            d->master + d->boff[NL - 1], J, fout, bstride, cstride, pitch, offset,
+                            rs, os, s));
+    }
     return n;
 }
 

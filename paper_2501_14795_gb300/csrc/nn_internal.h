@@ -129,9 +129,17 @@ bool conv_tc_supported(const ConvParams& p, int cin);
 cudaError_t launch_conv_tc(const ConvParams& p, int cin, cudaStream_t s);
 cudaError_t init_tc_kernels();
 cudaError_t launch_wgrad(const WgradParams& p, int ci, int co, cudaStream_t s);
-cudaError_t launch_pack_input(const float* J, long long bstride, long long cstride, int pitch,
-                              int offset, int B, int H, int W, float inv_scale, __nv_bfloat16* out,
-                              cudaStream_t s);
+// the first layer (3 -> 32, ReLU) fused with the input packing, and the
+// output layer (32 -> 3) with the residual epilogue, on the CUDA cores; H and
+// W multiples of 16
+cudaError_t launch_conv_first(const float* J, long long bstride, long long cstride, int pitch,
+                              int offset, int B, int H, int W, float inv_scale,
+                              const __nv_bfloat16* w, int cout_pad, const float* bias,
+                              __nv_bfloat16* xin, __nv_bfloat16* a_out, cudaStream_t s);
+cudaError_t launch_conv_last(const __nv_bfloat16* x, int B, int H, int W, const __nv_bfloat16* w,
+                             int cout_pad, const float* bias, const float* res, float* fout,
+                             long long bstride, long long cstride, int pitch, int offset, float rs,
+                             float os, cudaStream_t s);
 cudaError_t launch_pool_fwd(const __nv_bfloat16* in, int B, int H, int W, int C,
                             __nv_bfloat16* out, cudaStream_t s);
 cudaError_t launch_up_fwd(const __nv_bfloat16* in, int B, int H, int W, int C, __nv_bfloat16* out,

@@ -16,7 +16,9 @@
 //            raw FP32, or the network's residual output in field layout.
 //   k_wgrad  weight gradient: per tap a (cout x cin) GEMM over all pixels,
 //            split over CTAs (FP32 atomics into the gradient).
-//   elementwise: input packing, 2x2 mean pooling / nearest upsampling and
+//   k_conv_first / k_conv_last  the thin end layers (3 -> 32 with the input
+//            packing, 32 -> 3 with the residual output) on the CUDA cores.
+//   elementwise: 2x2 mean pooling / nearest upsampling and
 //            their adjoints, ReLU backward with the bias gradient, MSE loss,
 //            Adam, weight packing.
 #include <cuda_bf16.h>
@@ -374,23 +376,135 @@ __global__ void __launch_bounds__(WG_THREADS) k_wgrad(const WgradParams p) {
 
 // ----------------------------------------------------------- elementwise
 
-// field layout (3 planes) -> bfloat16 NHWC with 16 channels, scaled
-__global__ void k_pack_input(const float* J, long long bstride, long long cstride, int pitch,
-                             int offset, int B, int H, int W, float inv_scale, bf16* out) {
+// The network's thin end layers on the CUDA cores.  c1 (3 -> 32 channels)
+// has 27 inputs per output and c11 (32 -> 3) three outputs per pixel: as
+// implicit GEMMs on the tensor cores most of each tile is padding, and at
+// small grids their time is launch and pipeline latency.  Both keep the
+// arithmetic of the tensor-core path: bfloat16 inputs and weights, FP32
+// products and sums, bias, then the epilogue.
+constexpr int THIN_T = 16;  // 16 x 16 output pixels per CTA, one per thread
+
+__device__ __forceinline__ int wrap_idx(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// c1 fused with the input packing: the current (field layout) is scaled and
+// rounded to bfloat16 (the network input, also stored NHWC with 16 channels
+// for the first layer's weight gradient), then the 3x3 circular convolution
+// with bias and ReLU gives the 32-channel bfloat16 activation.
+__global__ void __launch_bounds__(256) k_conv_first(const float* J, long long bstride,
+                                                    long long cstride, int pitch, int offset,
+                                                    int H, int W, float inv_scale, const bf16* w,
+                                                    int cout_pad, const float* bias, bf16* xin,
+                                                    bf16* a_out) {
+    constexpr int C1 = 32, CI = 3, CINP = 16, E = THIN_T + 2;
+    __shared__ float sX[CI][E][E];
+    __shared__ __align__(16) float sW[9 * CI][C1];  // [tap * 3 + ci][co]
+    const int tid = threadIdx.x, b = blockIdx.z;
+    const int x0 = blockIdx.x * THIN_T, y0 = blockIdx.y * THIN_T;
     pdl_wait();
+    for (int i = tid; i < 9 * CI * C1; i += blockDim.x) {
+        const int co = i % C1, k = i / C1, tap = k / CI, ci = k - tap * CI;
+        sW[k][co] = __bfloat162float(w[((size_t)tap * cout_pad + co) * CINP + ci]);
+    }
+    for (int i = tid; i < CI * E * E; i += blockDim.x) {
+        const int c = i / (E * E), r = (i / E) % E, q = i % E;
+        const int yy = wrap_idx(y0 + r - 1, H), xx = wrap_idx(x0 + q - 1, W);
+        const float v = J[b * bstride + c * cstride + offset + (long long)yy * pitch + xx] * inv_scale;
+        sX[c][r][q] = __bfloat162float(__float2bfloat16_rn(v));
+    }
+    __syncthreads();
     pdl_trigger();
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)B * H * W) return;
-    const int x = (int)(i % W);
-    const long long t = i / W;
-    const int y = (int)(t % H), b = (int)(t / H);
-    const float* s = J + b * bstride + offset + (long long)y * pitch + x;
-    __align__(16) bf16 v[16];
+    const int ty = tid / THIN_T, tx = tid % THIN_T;
+    const size_t pix = ((size_t)b * H + y0 + ty) * W + x0 + tx;
+    {
+        __align__(16) bf16 v[CINP];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(c < 3 ? s[c * cstride] * inv_scale : 0.f);
-    uint4* o = reinterpret_cast<uint4*>(out + i * 16);
-    o[0] = reinterpret_cast<const uint4*>(v)[0];
-    o[1] = reinterpret_cast<const uint4*>(v)[1];
+        for (int c = 0; c < CINP; ++c) v[c] = __float2bfloat16_rn(c < CI ? sX[c][ty + 1][tx + 1] : 0.f);
+        uint4* o = reinterpret_cast<uint4*>(xin + pix * CINP);
+        o[0] = reinterpret_cast<const uint4*>(v)[0];
+        o[1] = reinterpret_cast<const uint4*>(v)[1];
+    }
+    float acc[C1];
+#pragma unroll
+    for (int co = 0; co < C1; ++co) acc[co] = 0.f;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap - 3 * (tap / 3);
+#pragma unroll
+        for (int ci = 0; ci < CI; ++ci) {
+            const float xv = sX[ci][ty + ky][tx + kx];
+            const float4* wr = reinterpret_cast<const float4*>(sW[tap * CI + ci]);
+#pragma unroll
+            for (int q = 0; q < C1 / 4; ++q) {
+                const float4 wv = wr[q];
+                acc[4 * q] += xv * wv.x;
+                acc[4 * q + 1] += xv * wv.y;
+                acc[4 * q + 2] += xv * wv.z;
+                acc[4 * q + 3] += xv * wv.w;
+            }
+        }
+    }
+    __align__(16) bf16 o[C1];
+#pragma unroll
+    for (int co = 0; co < C1; ++co) o[co] = __float2bfloat16_rn(fmaxf(acc[co] + bias[co], 0.f));
+    uint4* dst = reinterpret_cast<uint4*>(a_out + pix * C1);
+#pragma unroll
+    for (int q = 0; q < C1 / 8; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
+}
+
+// c11 with the residual output: z = 3x3 circular convolution of the 32-channel
+// activation (bfloat16 NHWC), then fout = res * rs + (z + bias) * os in field
+// layout for the three components.
+__global__ void __launch_bounds__(256) k_conv_last(const bf16* x, int H, int W, const bf16* w,
+                                                   int cout_pad, const float* bias,
+                                                   const float* res, float* fout,
+                                                   long long bstride, long long cstride,
+                                                   int pitch, int offset, float rs, float os) {
+    constexpr int CI = 32, CO = 3, E = THIN_T + 2, PS = CI + 8;  // padded pixel stride
+    __shared__ __align__(16) bf16 sA[E * E * PS];
+    __shared__ float sW[9 * CI][CO];
+    const int tid = threadIdx.x, b = blockIdx.z;
+    const int x0 = blockIdx.x * THIN_T, y0 = blockIdx.y * THIN_T;
+    pdl_wait();
+    for (int i = tid; i < 9 * CI * CO; i += blockDim.x) {
+        const int co = i % CO, k = i / CO, tap = k / CI, ci = k - tap * CI;
+        sW[k][co] = __bfloat162float(w[((size_t)tap * cout_pad + co) * CI + ci]);
+    }
+    for (int i = tid; i < E * E * (CI / 8); i += blockDim.x) {
+        const int pixl = i / (CI / 8), part = i % (CI / 8);
+        const int r = pixl / E, q = pixl % E;
+        const int yy = wrap_idx(y0 + r - 1, H), xx = wrap_idx(x0 + q - 1, W);
+        const uint4 v = reinterpret_cast<const uint4*>(x + (((size_t)b * H + yy) * W + xx) * CI)[part];
+        *reinterpret_cast<uint4*>(sA + pixl * PS + part * 8) = v;
+    }
+    __syncthreads();
+    pdl_trigger();
+    const int ty = tid / THIN_T, tx = tid % THIN_T;
+    float acc[CO] = {0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap - 3 * (tap / 3);
+        const bf16* a = sA + ((ty + ky) * E + tx + kx) * PS;
+#pragma unroll
+        for (int part = 0; part < CI / 8; ++part) {
+            const uint4 v = *reinterpret_cast<const uint4*>(a + part * 8);
+            const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 f = __bfloat1622float2(h2[e]);
+                const int ci = part * 8 + 2 * e;
+                const float* w0 = sW[tap * CI + ci];
+                const float* w1 = sW[tap * CI + ci + 1];
+#pragma unroll
+                for (int co = 0; co < CO; ++co) acc[co] += f.x * w0[co] + f.y * w1[co];
+            }
+        }
+    }
+    const int y = y0 + ty, xg = x0 + tx;
+#pragma unroll
+    for (int co = 0; co < CO; ++co) {
+        const size_t o = (size_t)b * bstride + (size_t)co * cstride + offset + (size_t)y * pitch + xg;
+        fout[o] = res[o] * rs + (acc[co] + bias[co]) * os;
+    }
 }
 
 // 2x2 mean pooling, bfloat16 -> bfloat16 (FP32 sum of the four)
@@ -826,13 +940,24 @@ cudaError_t launch_wgrad(const WgradParams& p, int ci, int co, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_pack_input(const float* J, long long bstride, long long cstride, int pitch,
-                              int offset, int B, int H, int W, float inv_scale, __nv_bfloat16* out,
-                              cudaStream_t s) {
-    const long long n = (long long)B * H * W;
-    if (n == 0) return cudaSuccess;
-    return launch_pdl(k_pack_input, dim3(blocks(n, 256)), dim3(256), 0, s, J, bstride, cstride,
-                      pitch, offset, B, H, W, inv_scale, out);
+cudaError_t launch_conv_first(const float* J, long long bstride, long long cstride, int pitch,
+                              int offset, int B, int H, int W, float inv_scale,
+                              const __nv_bfloat16* w, int cout_pad, const float* bias,
+                              __nv_bfloat16* xin, __nv_bfloat16* a_out, cudaStream_t s) {
+    if (B <= 0) return cudaSuccess;
+    if (H % THIN_T || W % THIN_T) return cudaErrorInvalidValue;
+    return launch_pdl(k_conv_first, dim3(W / THIN_T, H / THIN_T, B), dim3(256), 0, s, J, bstride,
+                      cstride, pitch, offset, H, W, inv_scale, w, cout_pad, bias, xin, a_out);
+}
+
+cudaError_t launch_conv_last(const __nv_bfloat16* x, int B, int H, int W, const __nv_bfloat16* w,
+                             int cout_pad, const float* bias, const float* res, float* fout,
+                             long long bstride, long long cstride, int pitch, int offset, float rs,
+                             float os, cudaStream_t s) {
+    if (B <= 0) return cudaSuccess;
+    if (H % THIN_T || W % THIN_T) return cudaErrorInvalidValue;
+    return launch_pdl(k_conv_last, dim3(W / THIN_T, H / THIN_T, B), dim3(256), 0, s, x, H, W, w,
+                      cout_pad, bias, res, fout, bstride, cstride, pitch, offset, rs, os);
 }
 
 cudaError_t launch_pool_fwd(const __nv_bfloat16* in, int B, int H, int W, int C,
