@@ -658,9 +658,25 @@ __global__ void k_residuals(const Geom g, const float* F, const float* J, const 
 //          iy on entry) and count per cell key;
 // phase 1: scan the counts into cell offsets, take the tile bookmarks from
 //          them and scatter into the particle arrays.
+// The slot key hashes the input index with full avalanche (xor-shift and
+// multiply rounds): every bit of the index moves every bit of the key.  A
+// multiplicative hash kept only some low bits of the index in the key's low
+// bits, so particles whose indices differ by a power of two (the same cell
+// column of rows a power of two apart, in an input ordered cell by cell)
+// shared a key, landed in the same warp and read the same shared-memory bank
+// group in the gather (5.6 wavefronts per load instead of about 3.5).
+__device__ __forceinline__ unsigned mix32(unsigned h) {
+    h ^= h >> 16;
+    h *= 0x7feb352du;
+    h ^= h >> 15;
+    h *= 0x846ca68bu;
+    h ^= h >> 16;
+    return h;
+}
+
 __device__ __forceinline__ int load_key(const Geom& g, int ix, int iy, int k) {
     const int t = tile_index(g, ix / g.T, iy / g.T);
-    const unsigned h = ((unsigned)k * 2654435761u) >> 8;  // Knuth's multiplicative hash
+    const unsigned h = mix32((unsigned)k);
     return t * g.T * g.T + (int)(h % (unsigned)(g.T * g.T));
 }
 
