@@ -272,9 +272,12 @@ pic_status pic_timing(pic_sim* sim, double* advance_ms, int64_t* advance_launche
 /* The same events split by stage of the step loop (Listing 3.1; PIC_TIMING):
  * stage_ms[0] the particle advance (gather, push, move, deposit, leaver
  * emission), stage_ms[1] the tile re-sort (§4.3: count, scan, evict, fill),
- * stage_ms[2] the current filter if any plus the field advance (Eqs. 19-20),
- * each summed over the steps since the last reset (CUDA events on the
- * simulation's stream), and their count in *steps.  Synchronises. */
+ * stage_ms[2] the rest of the step after the re-sort's fill.  The current
+ * filter (if any) and the field advance (Eqs. 19-20) depend on the deposit
+ * and the scan only, and run on a side stream beside the eviction and the
+ * fill: stage_ms[2] is the part of them not hidden under the re-sort.  Each is
+ * summed over the steps since the last reset (CUDA events on the
+ * simulation's stream), and their count is in *steps.  Synchronises. */
 pic_status pic_timing_stages(pic_sim* sim, double stage_ms[3], int64_t* steps, int reset);
 
 /* Number of kernels this simulation has launched (graph nodes included). */
@@ -425,9 +428,23 @@ pic_status pic_denoiser_train_step(pic_denoiser* d, const float* J_in, const flo
 /* Install d (NULL: remove) in the current-filter slot of sim: every later
  * pic_step applies the network to J in place between the deposit and the
  * field advance (the continuity residual of pic_diagnostics then measures the
- * filtered current).  d must match the grid.  Simulations with a filter
- * cannot be stepped in a batch. */
+ * filtered current).  d must match the grid.  Simulations with a filter of
+ * their own cannot be stepped in a batch (see pic_batch_set_denoiser). */
 pic_status pic_set_denoiser(pic_sim* sim, pic_denoiser* d);
+
+/* Install d (NULL: remove) in the current-filter slot of every member of a
+ * batch: each pic_batch_step gathers the members' currents after the re-sort,
+ * runs the network over them as one batch of samples (groups of at most the
+ * batch_max d was created with), applies d's low-wavenumber restoration and
+ * writes the currents back before the field advance.  Every member must have
+ * the network's grid (PIC_EINVAL otherwise, message through
+ * pic_batch_last_error).  A member gets what pic_set_denoiser would give it
+ * alone, up to the order in which the tensor cores sum a convolution's
+ * products: a larger batch may move a layer from the mma.sync kernel to the
+ * tcgen05 one (PIC_DENOISER_TC=never keeps every batch size on mma.sync, and
+ * the results bit for bit).  d must stay alive while installed; kernel
+ * timeouts show in the first member's status.  Synchronises. */
+pic_status pic_batch_set_denoiser(pic_batch* batch, pic_denoiser* d);
 
 const char* pic_denoiser_last_error(const pic_denoiser* d);
 void pic_denoiser_destroy(pic_denoiser* d);

@@ -15,6 +15,11 @@ struct pic_sim {
     pic::Geom g;
     cudaStream_t stream = nullptr;       // caller's stream: all work is ordered on it
     cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
+    // The field branch of a step (current filter, field advance) runs on a
+    // private side stream beside the re-sort's eviction and fill: forked from
+    // the caller's stream after the scan, joined back before the step ends.
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     pic::DevState* st = nullptr;
     float* F[2] = {nullptr, nullptr};  // E|B, ping-pong
     float* J[2] = {nullptr, nullptr};  // current, ping-pong
@@ -34,8 +39,9 @@ struct pic_sim {
     // graphs
     cudaGraph_t graph[2] = {nullptr, nullptr};  // kept alive: its nodes address the exec's
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    // timing (PIC_TIMING): four events per step, recorded before the particle
-    // advance, after it, after the re-sort and after the field advance
+    // timing (PIC_TIMING): four events per step on the caller's stream,
+    // recorded before the particle advance, after it, after the re-sort's fill
+    // and at the end of the step (after the join with the field branch)
     static constexpr int kStepEvents = 4;
     cudaGraphNode_t ev_node[2][kStepEvents] = {};
     cudaEvent_t ev_placeholder[kStepEvents] = {};
@@ -77,6 +83,15 @@ pic_status retile(pic_sim* sim, int tile);
 // Moving window: copy the device particle counts into the host mirrors
 // (synchronises); no-op for a fixed box.
 pic_status refresh_counts(pic_sim* sim);
+// The denoiser has the grid g.
+bool denoiser_fits(const pic_denoiser* d, const Geom& g);
+// The network in the current-filter slot of B simulations of one grid at
+// once (their currents from the device table jtab): gathered into a dense
+// batch, denoised in groups of at most the network's batch_max, restored and
+// written back.  Kernel timeouts go to `status`.  Returns the kernels
+// launched, or -1 with the message in *err.
+int denoiser_batch_filter(pic_denoiser* d, float* const* jtab, int B, const Geom& g,
+                          unsigned* status, cudaStream_t s, std::string* err);
 
 }  // namespace host
 }  // namespace pic

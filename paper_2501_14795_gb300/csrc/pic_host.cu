@@ -313,6 +313,12 @@ int enqueue_step(pic_sim* sim, cudaStream_t s, int b, const cudaEvent_t* ev, boo
     if (ev && (e = cudaEventRecordWithFlags(ev[1], s, rec)) != cudaSuccess) goto bad;
     if ((e = launch_scan(sp, s)) != cudaSuccess) goto bad;
     n += (sp.nsp > 0 && sim->g.ntiles > 0) ? 2 : 1;  // count + scan
+    // Fork.  The field branch needs the deposit and the scan (it adds its
+    // energies into the history slot of the level the scan moved to) but not
+    // the particles' places, and the eviction and fill touch no field: the
+    // field advance runs beside them, and the next step starts after both.
+    if ((e = cudaEventRecord(sim->ev_fork, s)) != cudaSuccess) goto bad;
+    if ((e = cudaStreamWaitEvent(sim->side_stream, sim->ev_fork, 0)) != cudaSuccess) goto bad;
     if ((e = launch_evict(sp, threads, s)) != cudaSuccess) goto bad;
     if ((e = launch_fill(sp, threads, s)) != cudaSuccess) goto bad;
     n += (sp.nsp > 0 && sim->g.ntiles > 0) ? 2 : 0;
@@ -320,12 +326,16 @@ int enqueue_step(pic_sim* sim, cudaStream_t s, int b, const cudaEvent_t* ev, boo
     if (sim->jfilter) {
         // the current-filter slot of Listing 3.1: after the deposit and its
         // guard-cell reduction, before the field advance
-        const int k = sim->jfilter(sim->jfilter_ctx, sim, s, b);
+        const int k = sim->jfilter(sim->jfilter_ctx, sim, sim->side_stream, b);
         if (k < 0) return -1;
         n += k;
     }
-    if ((e = launch_yee(yp, &sim->ymapF[b], &sim->ymapJ[b], s)) != cudaSuccess) goto bad;
+    if ((e = launch_yee(yp, &sim->ymapF[b], &sim->ymapJ[b], sim->side_stream)) != cudaSuccess)
+        goto bad;
     n += 1;
+    // join
+    if ((e = cudaEventRecord(sim->ev_join, sim->side_stream)) != cudaSuccess) goto bad;
+    if ((e = cudaStreamWaitEvent(s, sim->ev_join, 0)) != cudaSuccess) goto bad;
     if (ev && (e = cudaEventRecordWithFlags(ev[3], s, rec)) != cudaSuccess) goto bad;
     return n;
 bad:
@@ -609,7 +619,10 @@ pic_status pic_init(const pic_config* cfg, void* cuda_stream, pic_sim** out) {
             init_grid_kernels() != cudaSuccess)
             return cleanup_fail(PIC_ECUDA, "smem attribute", e);
     }
-    if (cudaStreamCreateWithFlags(&sim->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    if (cudaStreamCreateWithFlags(&sim->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sim->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sim->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sim->ev_join, cudaEventDisableTiming) != cudaSuccess)
         return cleanup_fail(PIC_ECUDA, "stream", e);
     if (c.flags & PIC_TIMING)
         for (int k = 0; k < pic_sim::kStepEvents; ++k)
@@ -1068,6 +1081,12 @@ void pic_destroy(pic_sim* sim) {
     if (sim->stream) cudaStreamSynchronize(sim->stream);
     invalidate_graphs(sim);
     if (sim->cap_stream) cudaStreamDestroy(sim->cap_stream);
+    if (sim->side_stream) {
+        cudaStreamSynchronize(sim->side_stream);
+        cudaStreamDestroy(sim->side_stream);
+    }
+    if (sim->ev_fork) cudaEventDestroy(sim->ev_fork);
+    if (sim->ev_join) cudaEventDestroy(sim->ev_join);
     for (int b = 0; b < 2; ++b) {
         dfree(sim->F[b]);
         dfree(sim->J[b]);
