@@ -426,6 +426,59 @@ int filter_hook(void* ctx, pic_sim* sim, cudaStream_t s, int b) {
     return kr < 0 ? -1 : k0 + k + kr;
 }
 
+}  // namespace
+
+namespace pic {
+namespace host {
+
+bool denoiser_fits(const pic_denoiser* d, const Geom& g) { return d && d->W == g.nx && d->H == g.ny; }
+
+// The current-filter slot of B simulations of one grid at once: their
+// currents (device table jtab, field layout of g) are gathered into a dense
+// batch of samples, run through the network in groups of at most batch_max,
+// restored, and written back in place.  Kernel timeouts are reported to
+// `status`.  Returns the kernels launched, or -1 with the message in *err.
+int denoiser_batch_filter(pic_denoiser* d, float* const* jtab, int B, const Geom& g,
+                          unsigned* status, cudaStream_t s, std::string* err) {
+    const int H = d->H, W = d->W;
+    const long long HW = (long long)H * W;
+    const FieldView jl{nullptr, 0, g.cstride, g.P, GY * g.P + GX};
+    const FieldView X{d->G1, 3 * HW, HW, W, 0};    // the batch, denoised in place
+    const FieldView raw{d->G0, 3 * HW, HW, W, 0};  // the restoration's copy of the input
+    const FieldView none{nullptr, 0, 0, 0, 0};
+    int n = 0;
+    for (int g0 = 0; g0 < B; g0 += d->Bmax) {
+        const int nb = std::min(d->Bmax, B - g0);
+        cudaError_t e = launch_field_copy_tab(jl, jtab + g0, X, nullptr, d->restore > 0 ? raw : none,
+                                              nb, H, W, s);
+        if (e != cudaSuccess) {
+            *err = std::string("denoiser gather launch failed: ") + cudaGetErrorString(e);
+            return -1;
+        }
+        d->cur_status = status;
+        const int k = forward(d, nb, d->G1, 3 * HW, HW, W, 0, d->G1, 1.f, (float)d->scale, s);
+        d->cur_status = d->status;
+        if (k < 0) {
+            *err = d->err;
+            return -1;
+        }
+        const int kr = low_k_chain(d->restore, nb, H, W, raw, X, d->G0 + 3LL * nb * HW, s, err);
+        if (kr < 0) return -1;
+        e = launch_field_copy_tab(X, nullptr, jl, jtab + g0, none, nb, H, W, s);
+        if (e != cudaSuccess) {
+            *err = std::string("denoiser scatter launch failed: ") + cudaGetErrorString(e);
+            return -1;
+        }
+        n += 2 + k + kr;
+    }
+    return n;
+}
+
+}  // namespace host
+}  // namespace pic
+
+namespace {
+
 // Pack random-access probe weights ([9][cin][cout] FP32, device) for one layer shape.
 struct Probe {
     bf16 *wf = nullptr, *wd = nullptr;

@@ -162,6 +162,11 @@ cudaError_t launch_lowk(const FieldView& a, const FieldView& b, float* t, const 
 // o = a (three-component currents of B samples, any layouts)
 cudaError_t launch_field_copy(const FieldView& a, const FieldView& o, int B, int H, int W,
                               cudaStream_t s);
+// o = a (and o2 = a when o2.p is set) with per-sample base pointers from the
+// device tables atab / otab where they are non-null
+cudaError_t launch_field_copy_tab(const FieldView& a, const float* const* atab, const FieldView& o,
+                                  float* const* otab, const FieldView& o2, int B, int H, int W,
+                                  cudaStream_t s);
 cudaError_t launch_pack_weights(const PackTable& t, const float* master, __nv_bfloat16* wf,
                                 __nv_bfloat16* wd, cudaStream_t s);
 

@@ -786,6 +786,27 @@ __global__ void k_field_copy(FieldView a, FieldView o, int B, int H, int W) {
         po[(long long)y * o.pitch] = pa[(long long)y * a.pitch];
 }
 
+// The same copy with per-sample base pointers: sample b of a starts at
+// atab[b] (when atab is set, else a.p + b a.bstride) and sample b of o at
+// otab[b] (else o.p + b o.bstride); o2 (when o2.p is set) receives a second
+// copy.  Gathers the currents of separate simulations into one dense batch of
+// samples and writes them back.
+__global__ void k_field_copy_tab(FieldView a, const float* const* atab, FieldView o,
+                                 float* const* otab, FieldView o2, int B, int H, int W) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= W) return;
+    const int c = blockIdx.z % 3, smp = blockIdx.z / 3;
+    const float* pa = (atab ? atab[smp] : a.p + smp * a.bstride) + c * a.cstride + a.offset + x;
+    float* po = (otab ? otab[smp] : o.p + smp * o.bstride) + c * o.cstride + o.offset + x;
+    float* po2 = o2.p ? o2.p + smp * o2.bstride + c * o2.cstride + o2.offset + x : nullptr;
+    const int rows = lk_rows(B, H, W);
+    for (int y = blockIdx.y * rows; y < min(H, (int)(blockIdx.y + 1) * rows); ++y) {
+        const float v = pa[(long long)y * a.pitch];
+        po[(long long)y * o.pitch] = v;
+        if (po2) po2[(long long)y * o2.pitch] = v;
+    }
+}
+
 __global__ void k_adam(float* p, const float* g, float* m, float* v, long long n, float lr,
                        float b1, float b2, float eps, float c1, float c2) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1041,6 +1062,17 @@ cudaError_t launch_lowk(const FieldView& a, const FieldView& b, float* t, const 
     const dim3 gy((W + LK_TX - 1) / LK_TX, (H + LK_TY - 1) / LK_TY, 3 * B);
     k_lowk_y<<<gy, dim3(LK_TX, LK_YT), (LK_TY + 2 * n) * (LK_TX + 1) * sizeof(float), s>>>(
         t, o, w, B, H, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_copy_tab(const FieldView& a, const float* const* atab, const FieldView& o,
+                                  float* const* otab, const FieldView& o2, int B, int H, int W,
+                                  cudaStream_t s) {
+    const long long n = (long long)B * 3 * H * W;
+    if (n == 0) return cudaSuccess;
+    const int rows = lk_rows(B, H, W);
+    k_field_copy_tab<<<dim3((W + 255) / 256, (H + rows - 1) / rows, 3 * B), 256, 0, s>>>(
+        a, atab, o, otab, o2, B, H, W);
     return cudaGetLastError();
 }
 

@@ -39,6 +39,8 @@ struct pic_batch {
     CUtensorMap* d_tmaps[2] = {nullptr, nullptr};
     SortParams* d_sort[2] = {nullptr, nullptr};
     YeeParams* d_yee[2] = {nullptr, nullptr};
+    float** d_jtab[2] = {nullptr, nullptr};  // the members' current buffers, per phase
+    pic_denoiser* den = nullptr;  // network in the members' current-filter slot, or none
     int4* d_items = nullptr;
     int* d_tile_start = nullptr;
     int* d_ytile_start = nullptr;
@@ -77,6 +79,8 @@ void free_device(pic_batch* b) {
         cudaFree(b->d_tmaps[p]);
         cudaFree(b->d_sort[p]);
         cudaFree(b->d_yee[p]);
+        cudaFree(b->d_jtab[p]);
+        b->d_jtab[p] = nullptr;
         b->d_push[p] = nullptr;
         b->d_tmaps[p] = nullptr;
         b->d_sort[p] = nullptr;
@@ -113,6 +117,7 @@ pic_status prepare(pic_batch* batch) {
     std::vector<CUtensorMap> ht[2];
     std::vector<SortParams> hs[2];
     std::vector<YeeParams> hy[2];
+    std::vector<float*> hj[2];
     std::vector<int> tile_start(n + 1, 0), ytile_start(n + 1, 0);
     struct Item {
         int4 v;
@@ -134,6 +139,7 @@ pic_status prepare(pic_batch* batch) {
             ht[p].push_back(sim->fmap[b]);
             hs[p].push_back(sort_params(sim, b));
             hy[p].push_back(yee_params(sim, b, chunks));
+            hj[p].push_back(sim->J[b]);
         }
         tile_start[k + 1] = tile_start[k] + sim->g.ntiles;
         ytile_start[k + 1] = ytile_start[k] + yee_tiles(sim->g);
@@ -180,6 +186,7 @@ pic_status prepare(pic_batch* batch) {
         BCK(up(&batch->d_tmaps[p], ht[p]));
         BCK(up(&batch->d_sort[p], hs[p]));
         BCK(up(&batch->d_yee[p], hy[p]));
+        BCK(up(&batch->d_jtab[p], hj[p]));
     }
     BCK(up(&batch->d_items, hv));
     BCK(up(&batch->d_tile_start, tile_start));
@@ -219,6 +226,18 @@ int enqueue_batch_step(pic_batch* batch, cudaStream_t s, int p) {
         sb.max_nsp = batch->max_nsp;
         e = launch_sort_batch(sb, s);
         n += sb.total_tiles > 0 ? 4 : 1;
+    }
+    if (e == cudaSuccess && batch->den) {
+        // the current-filter slot: after the deposit and the re-sort, before
+        // the field advance, all members' currents through the network at once
+        std::string why;
+        const int k = denoiser_batch_filter(batch->den, batch->d_jtab[p], (int)batch->m.size(),
+                                            batch->m[0]->g, &batch->m[0]->st->status, s, &why);
+        if (k < 0) {
+            batch->err = why;
+            return -1;
+        }
+        n += k;
     }
     if (e == cudaSuccess) {
         YeeBatch yb;
@@ -578,6 +597,24 @@ pic_status pic_batch_create(pic_sim* const* members, int n, void* cuda_stream, p
         return r;
     }
     *out = batch;
+    return PIC_OK;
+}
+
+pic_status pic_batch_set_denoiser(pic_batch* batch, pic_denoiser* d) {
+    if (!batch) return PIC_EINVAL;
+    batch->err.clear();
+    if (d)
+        for (size_t k = 0; k < batch->m.size(); ++k) {
+            const Geom& g = batch->m[k]->g;
+            const Geom& g0 = batch->m[0]->g;
+            if (!denoiser_fits(d, g) || g.P != g0.P || g.cstride != g0.cstride)
+                return bfail(batch, PIC_EINVAL,
+                             "pic_batch_set_denoiser: member " + std::to_string(k) +
+                                 " does not have the network's grid");
+        }
+    BCK(cudaStreamSynchronize(batch->stream));
+    batch->den = d;
+    free_graphs(batch);
     return PIC_OK;
 }
 

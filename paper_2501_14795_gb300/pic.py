@@ -121,6 +121,7 @@ def load_library() -> C.CDLL:
         L.pic_batch_last_error.restype = C.c_char_p
         L.pic_batch_destroy.argtypes = [_P]
         L.pic_batch_destroy.restype = None
+        L.pic_batch_set_denoiser.argtypes = [_P, _P]
         L.pic_autotune.argtypes = [_P, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                    C.POINTER(C.c_double)]
         L.pic_set_tiling.argtypes = [_P, C.c_int, C.c_int]
@@ -155,6 +156,7 @@ def load_library() -> C.CDLL:
                      "pic_get_history", "pic_sync", "pic_clear_status", "pic_timing",
                      "pic_timing_stages",
                      "pic_init_batch", "pic_batch_create", "pic_batch_step", "pic_batch_sync",
+                     "pic_batch_set_denoiser",
                      "pic_autotune", "pic_set_tiling", "pic_denoiser_create",
                      "pic_denoiser_set_params", "pic_denoiser_get_params", "pic_denoiser_forward",
                      "pic_denoiser_grad", "pic_denoiser_train_step", "pic_set_denoiser",
@@ -372,6 +374,10 @@ def pic_batch_kernel_launches(b):
 
 def pic_batch_last_error(b):
     return (load_library().pic_batch_last_error(b) or b"").decode()
+
+
+def pic_batch_set_denoiser(b, d):
+    _bcheck(b, load_library().pic_batch_set_denoiser(b, d))
 
 
 def pic_batch_destroy(b):
@@ -717,6 +723,12 @@ class Batch:
 
     def kernel_launches(self):
         return pic_batch_kernel_launches(self.b)
+
+    def set_denoiser(self, net):
+        """Install a Denoiser (None: remove) in every member's current-filter
+        slot, run over all members at once; the network is kept alive here."""
+        pic_batch_set_denoiser(self.b, net.d if net is not None else None)
+        self.net = net
 
     def close(self):
         if self.b:
