@@ -373,9 +373,12 @@ pic_status pic_set_tiling(pic_sim* sim, int tile, int threads);
  * samples in the field layout of the header comment (3 x ny x nx FP32 each).
  * A handle is not thread-safe; its work is ordered on `cuda_stream`, and while
  * it is installed in a simulation it also runs on that simulation's stream.
- * Convolutions whose rows are multiples of 128 pixels and with at least 17
- * output channels run on the tcgen05 tensor-core kernel when the launch is
- * large (>= 600 work units of 2 x 128 pixels), else on an mma.sync kernel;
+ * The thin end layers c1 and c11 run on CUDA-core kernels (fused with the
+ * input scaling and the residual output) when a pass has fewer than 2^18
+ * pixels, else as implicit GEMMs like the others.  Convolutions whose rows
+ * are multiples of 128 pixels and with at least 17 output channels run on
+ * the tcgen05 tensor-core kernel when the launch is large (>= 600 work units
+ * of 2 x 128 pixels), else on an mma.sync kernel;
  * the environment variable PIC_DENOISER_TC, read at creation, selects the
  * tcgen05 kernel whenever the shape allows (=always, used by the tests) or
  * never (=never).
@@ -439,10 +442,10 @@ pic_status pic_set_denoiser(pic_sim* sim, pic_denoiser* d);
  * writes the currents back before the field advance.  Every member must have
  * the network's grid (PIC_EINVAL otherwise, message through
  * pic_batch_last_error).  A member gets what pic_set_denoiser would give it
- * alone, up to the order in which the tensor cores sum a convolution's
- * products: a larger batch may move a layer from the mma.sync kernel to the
- * tcgen05 one (PIC_DENOISER_TC=never keeps every batch size on mma.sync, and
- * the results bit for bit).  d must stay alive while installed; kernel
+ * alone, up to the order of a convolution's FP32 sums: which kernel runs a
+ * layer depends on the pixels of the pass (CUDA cores for the thin end layers
+ * below 2^18 pixels, else implicit GEMMs; mma.sync or tcgen05 by shape and
+ * size), and each sums in its own order.  d must stay alive while installed; kernel
  * timeouts show in the first member's status.  Synchronises. */
 pic_status pic_batch_set_denoiser(pic_batch* batch, pic_denoiser* d);
 

@@ -48,6 +48,8 @@ constexpr LayerSpec kLayers[NL] = {
 };
 
 int pad16(int c) { return (c + 15) / 16 * 16; }
+// below this many pixels per forward pass the thin end layers run on the CUDA cores
+constexpr long long kThinPixels = 1LL << 18;
 // output-channel tile of the convolution kernel for a given channel count
 int ctile(int cout) { return cout <= 8 ? 8 : (cout >= 64 ? 64 : 32); }
 int padct(int cout) { const int t = ctile(cout); return (cout + t - 1) / t * t; }
@@ -224,11 +226,23 @@ int forward(pic_denoiser* d, int B, const float* J, long long bstride, long long
         }                                                                           \
         ++n;                                                                        \
     } while (0)
-    {
+    // The thin end layers c1 (3 -> 32) and c11 (32 -> 3): on small lattices
+    // CUDA-core kernels fused with the input packing and the residual output
+    // (fewer launches, no padded tensor-core tiles); on large ones, where the
+    // CUDA cores' multiply-adds take longer than the tensor cores' padded
+    // products plus one more pass over memory, the packing kernel and the
+    // implicit-GEMM convolutions (measured on GB300 at 2048^2: 296 + 336 us
+    // against 180 + 230 us).
+    const bool thin = (long long)B * H0 * W0 < kThinPixels;
+    if (thin) {
         const LayerDesc& L = d->tab.layer[0];
         FW(launch_conv_first(J, bstride, cstride, pitch, offset, B, H0, W0,
                              (float)(1.0 / d->scale), d->wf + L.wf_off, L.cout_pad,
                              d->master + d->boff[0], d->xin, d->a[0], s));
+    } else {
+        FW(launch_pack_input(J, bstride, cstride, pitch, offset, B, H0, W0, (float)(1.0 / d->scale),
+                             d->xin, s));
+        FW(conv(d, 0, B, d->xin, EPI_ACT, d->a[0], nullptr, nullptr, nullptr, s));
     }
     FW(conv(d, 1, B, d->a[0], EPI_ACT, d->a[1], nullptr, nullptr, nullptr, s));
     FW(launch_pool_fwd(d->a[1], B, H0, W0, 32, d->p1, s));
@@ -244,11 +258,14 @@ int forward(pic_denoiser* d, int B, const float* J, long long bstride, long long
     FW(conv(d, 8, B, d->a[7], EPI_ACT, d->a[8], d->a[1], d->y9, nullptr, s, nullptr, nullptr, 0,
             0, 0, 0, 0.f, 0.f, 1));
     FW(conv(d, 9, B, d->y9, EPI_ACT, d->a[9], nullptr, nullptr, nullptr, s));
-    {
+    if (thin) {
         const LayerDesc& L = d->tab.layer[NL - 1];
         FW(launch_conv_last(d->a[9], B, H0, W0, d->wf + L.wf_off, L.cout_pad,
                             d->master + d->boff[NL - 1], J, fout, bstride, cstride, pitch, offset,
                             rs, os, s));
+    } else {
+        FW(conv(d, 10, B, d->a[9], EPI_FINAL, nullptr, nullptr, nullptr, nullptr, s, J, fout, bstride,
+                cstride, pitch, offset, rs, os));
     }
     return n;
 }

@@ -140,6 +140,9 @@ cudaError_t launch_conv_last(const __nv_bfloat16* x, int B, int H, int W, const 
                              int cout_pad, const float* bias, const float* res, float* fout,
                              long long bstride, long long cstride, int pitch, int offset, float rs,
                              float os, cudaStream_t s);
+cudaError_t launch_pack_input(const float* J, long long bstride, long long cstride, int pitch,
+                              int offset, int B, int H, int W, float inv_scale, __nv_bfloat16* out,
+                              cudaStream_t s);
 cudaError_t launch_pool_fwd(const __nv_bfloat16* in, int B, int H, int W, int C,
                             __nv_bfloat16* out, cudaStream_t s);
 cudaError_t launch_up_fwd(const __nv_bfloat16* in, int B, int H, int W, int C, __nv_bfloat16* out,

@@ -507,6 +507,27 @@ __global__ void __launch_bounds__(256) k_conv_last(const bf16* x, int H, int W, 
     }
 }
 
+// The network input on large lattices, where c1 runs as an implicit GEMM on
+// the tensor cores: the current (field layout) scaled and rounded to
+// bfloat16, NHWC with 16 channels (3 used).
+__global__ void k_pack_input(const float* J, long long bstride, long long cstride, int pitch,
+                             int offset, int B, int H, int W, float inv_scale, bf16* out) {
+    pdl_wait();
+    pdl_trigger();
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)B * H * W) return;
+    const int x = (int)(i % W);
+    const long long t = i / W;
+    const int y = (int)(t % H), b = (int)(t / H);
+    const float* s = J + b * bstride + offset + (long long)y * pitch + x;
+    __align__(16) bf16 v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(c < 3 ? s[c * cstride] * inv_scale : 0.f);
+    uint4* o = reinterpret_cast<uint4*>(out + i * 16);
+    o[0] = reinterpret_cast<const uint4*>(v)[0];
+    o[1] = reinterpret_cast<const uint4*>(v)[1];
+}
+
 // 2x2 mean pooling, bfloat16 -> bfloat16 (FP32 sum of the four)
 __global__ void k_pool_fwd(const bf16* in, int B, int H, int W, int C, bf16* out) {
     pdl_wait();
@@ -979,6 +1000,15 @@ cudaError_t launch_conv_last(const __nv_bfloat16* x, int B, int H, int W, const 
     if (H % THIN_T || W % THIN_T) return cudaErrorInvalidValue;
     return launch_pdl(k_conv_last, dim3(W / THIN_T, H / THIN_T, B), dim3(256), 0, s, x, H, W, w,
                       cout_pad, bias, res, fout, bstride, cstride, pitch, offset, rs, os);
+}
+
+cudaError_t launch_pack_input(const float* J, long long bstride, long long cstride, int pitch,
+                              int offset, int B, int H, int W, float inv_scale, __nv_bfloat16* out,
+                              cudaStream_t s) {
+    const long long n = (long long)B * H * W;
+    if (n == 0) return cudaSuccess;
+    return launch_pdl(k_pack_input, dim3(blocks(n, 256)), dim3(256), 0, s, J, bstride, cstride,
+                      pitch, offset, B, H, W, inv_scale, out);
 }
 
 cudaError_t launch_pool_fwd(const __nv_bfloat16* in, int B, int H, int W, int C,

@@ -16,6 +16,14 @@
 // runs the same epilogues as the mma.sync kernel (bias + ReLU (+ skip) to
 // bfloat16, raw FP32, residual output in field layout).
 //
+// Output channels beyond N = 64 are split over CTAs (blockIdx.y takes channels
+// [64 y, 64 y + 64)).  Inputs of 128 channels (the encoder's last level and
+// the decoder's first layer) do not fit twice in shared memory: their kernel
+// keeps all nine taps of the CTA's weights and one patch of 64 channels, and
+// runs each work unit as two passes over the channel halves into the same
+// accumulator (load a half, multiply it in, load the other half once those
+// products have read the patch).
+//
 // Every wait is bounded; on a timeout the kernel flags it in the status word,
 // frees its TMEM and returns.
 #include <cuda_bf16.h>
@@ -67,6 +75,24 @@ struct TcSmem {
     static constexpr int TMEM_COLS = 2 * TC_R * NTC;          // two work units in flight
 };
 
+// The two-pass kernel: one patch of KC channels, then all CIN channels of
+// the nine taps' weights.
+template <int CIN, int NT, int KC>
+struct TcSmemKC {
+    static constexpr int KG = CIN / 8;                        // k-groups of the weights
+    static constexpr int KGC = KC / 8;                        // k-groups of one patch
+    static constexpr int PPLANE = TC_PR * TC_PW * 16;
+    static constexpr int PATCH = KGC * PPLANE;
+    static constexpr int WPLANE = NT * 16;
+    static constexpr int WTAP = KG * WPLANE;
+    static constexpr size_t off_w = (size_t)PATCH;
+    static constexpr size_t off_bias = off_w + 9 * (size_t)WTAP;
+    static constexpr size_t off_bar = (off_bias + NT * 4 + 15) & ~(size_t)15;
+    static constexpr size_t bytes = off_bar + 32;             // 1 mbarrier + TMEM slot
+    static constexpr int NTC = NT < 32 ? 32 : NT;
+    static constexpr int TMEM_COLS = 2 * TC_R * NTC;
+};
+
 // wait for phase `parity` of an mbarrier, about a second at most
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity) {
     const long long t0 = clock64();
@@ -87,6 +113,27 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity) {
 // patch of work unit `seg` (rows y0-1..y0+R, columns x0-1..x0+M, circular)
 // into k-group planes of 16 B per pixel; a thread takes whole pixels (their
 // CIN channels are contiguous in memory)
+// KGP k-groups per patch plane set, starting at input channel c0 (the
+// two-pass kernel loads one channel half at a time)
+template <int CIN, int KGP, int PPLANE>
+__device__ __forceinline__ void load_patch_ch(const ConvParams& p, unsigned char* sP, int seg,
+                                              int c0, int tid) {
+    const int segs = p.W / TC_M, rows = p.H / TC_R;
+    const int x0 = (seg % segs) * TC_M;
+    const int y0 = ((seg / segs) % rows) * TC_R;
+    const int b = seg / (segs * rows);
+    const int sh = p.up ? 1 : 0;
+    const int Hi = p.H >> sh, Wi = p.W >> sh;
+    for (int pix = tid; pix < TC_PR * TC_PW; pix += TC_THREADS) {
+        const int r = pix / TC_PW, q = pix - r * TC_PW;
+        const int ys = wrap(y0 - 1 + r, p.H) >> sh, xs = wrap(x0 - 1 + q, p.W) >> sh;
+        const bf16* src = p.x + (((size_t)b * Hi + ys) * Wi + xs) * CIN + c0;
+        unsigned char* dst = sP + pix * 16;
+#pragma unroll
+        for (int kg = 0; kg < KGP; ++kg) cp_async16(dst + kg * PPLANE, src + kg * 8);
+    }
+}
+
 template <int CIN, int NT>
 __device__ __forceinline__ void load_patch(const ConvParams& p, unsigned char* sP, int seg, int tid) {
     using L = TcSmem<CIN, NT>;
@@ -110,7 +157,7 @@ __device__ __forceinline__ void load_patch(const ConvParams& p, unsigned char* s
 // x0 + lane of the row, column = output channel
 template <int NT>
 __device__ __forceinline__ void epilogue(const ConvParams& p, const float* sBias, uint32_t acc,
-                                         int seg, int rr, int warp, int lane) {
+                                         int seg, int rr, int warp, int lane, int co0) {
     // warps w and w + 4 read TMEM lanes 32 (w % 4)..+31: the first and the
     // second half of the 16-column chunks
     const int lg = warp & 3, half = warp >> 2;
@@ -131,12 +178,13 @@ __device__ __forceinline__ void epilogue(const ConvParams& p, const float* sBias
               "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (c0 >= p.cout_pad) continue;
+        if (co0 + c0 >= p.cout_pad) continue;
+        const int cg = co0 + c0;  // output channel of column c0
         float v[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
         if (p.epi == EPI_GRAD) {
-            float4* o = reinterpret_cast<float4*>(p.g_out + pix * p.cout_pad + c0);
+            float4* o = reinterpret_cast<float4*>(p.g_out + pix * p.cout_pad + cg);
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
@@ -147,7 +195,7 @@ __device__ __forceinline__ void epilogue(const ConvParams& p, const float* sBias
         if (p.epi == EPI_FINAL) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const int c = c0 + j;
+                const int c = cg + j;
                 if (c >= p.cout) continue;
                 const size_t o = (size_t)b * p.bstride + (size_t)c * p.cstride + p.offset +
                                  (size_t)y * p.pitch + x;
@@ -162,11 +210,11 @@ __device__ __forceinline__ void epilogue(const ConvParams& p, const float* sBias
         __align__(16) __nv_bfloat162 a2[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) a2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-        uint4* ao = reinterpret_cast<uint4*>(p.a_out + pix * p.cout_pad + c0);
+        uint4* ao = reinterpret_cast<uint4*>(p.a_out + pix * p.cout_pad + cg);
         ao[0] = reinterpret_cast<const uint4*>(a2)[0];
         ao[1] = reinterpret_cast<const uint4*>(a2)[1];
         if (p.skip) {
-            const uint4* sk = reinterpret_cast<const uint4*>(p.skip + pix * p.cout_pad + c0);
+            const uint4* sk = reinterpret_cast<const uint4*>(p.skip + pix * p.cout_pad + cg);
             __align__(16) uint4 sv[2] = {sk[0], sk[1]};
             const __nv_bfloat162* s2 = reinterpret_cast<const __nv_bfloat162*>(sv);
             __align__(16) __nv_bfloat162 y2[8];
@@ -175,7 +223,7 @@ __device__ __forceinline__ void epilogue(const ConvParams& p, const float* sBias
                 const float2 af = __bfloat1622float2(a2[j]), sf = __bfloat1622float2(s2[j]);
                 y2[j] = __floats2bfloat162_rn(af.x + sf.x, af.y + sf.y);
             }
-            uint4* yo = reinterpret_cast<uint4*>(p.y_out + pix * p.cout_pad + c0);
+            uint4* yo = reinterpret_cast<uint4*>(p.y_out + pix * p.cout_pad + cg);
             yo[0] = reinterpret_cast<const uint4*>(y2)[0];
             yo[1] = reinterpret_cast<const uint4*>(y2)[1];
         }
@@ -197,6 +245,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nseg = p.B * (p.H / TC_R) * (p.W / TC_M);
     if ((int)blockIdx.x >= nseg) return;
+    const int co0 = blockIdx.y * NT;  // the CTA's output channels
 
     // weights of the nine taps: packed [tap][cout_pad][CIN] -> [tap][kg][n][8]
     for (int i = tid; i < 9 * NT * L::KG; i += TC_THREADS) {
@@ -204,13 +253,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
         const int rn = i / L::KG;
         const int n = rn % NT, tap = rn / NT;
         unsigned char* dst = sW + tap * L::WTAP + kg * L::WPLANE + n * 16;
-        if (n < p.cout_pad)
-            cp_async16(dst, p.w + ((size_t)tap * p.cout_pad + n) * CIN + kg * 8);
+        if (co0 + n < p.cout_pad)
+            cp_async16(dst, p.w + ((size_t)tap * p.cout_pad + co0 + n) * CIN + kg * 8);
         else
             *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
     }
     for (int c = tid; c < NT; c += TC_THREADS)
-        sBias[c] = (p.bias && c < p.cout && p.epi != EPI_GRAD) ? p.bias[c] : 0.f;
+        sBias[c] = (p.bias && co0 + c < p.cout && p.epi != EPI_GRAD) ? p.bias[co0 + c] : 0.f;
     pdl_wait();  // the input is the previous kernel's output
     pdl_trigger();
     load_patch<CIN, NT>(p, smem, blockIdx.x, tid);
@@ -284,7 +333,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
         if (prev >= 0 && ok) {
             const int pb = (i - 1) & 1;
             for (int rr = 0; rr < TC_R; ++rr)
-                epilogue<NT>(p, sBias, tmem + (pb * TC_R + rr) * L::NTC, prev, rr, warp, lane);
+                epilogue<NT>(p, sBias, tmem + (pb * TC_R + rr) * L::NTC, prev, rr, warp, lane, co0);
         }
         prev = seg;
     }
@@ -294,7 +343,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (ok)
             for (int rr = 0; rr < TC_R; ++rr)
-                epilogue<NT>(p, sBias, tmem + (pb * TC_R + rr) * L::NTC, prev, rr, warp, lane);
+                epilogue<NT>(p, sBias, tmem + (pb * TC_R + rr) * L::NTC, prev, rr, warp, lane, co0);
     }
     if (!ok && tid == 0) {
         if (p.status) atomicOr(p.status, 2u);  // a bounded wait ran out
@@ -312,21 +361,167 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
                      "r"(L::TMEM_COLS));
 }
 
+// Two passes over the input channels per work unit (CIN = 2 KC): the CTA
+// keeps its nine taps' weights of all CIN channels and one patch of KC
+// channels.  For unit i (accumulator i & 1) and channel half c: wait until the
+// products issued last have read the patch, load half c of the unit's patch
+// (on the first half, store the previous unit's results meanwhile), then one
+// thread issues the 9 x KC/16 products into the accumulator and commits them.
+// One mbarrier takes every commit in order: commit k completes its phase k.
+template <int CIN, int NT, int KC>
+__global__ void __launch_bounds__(TC_THREADS) k_conv_tc_kc(const ConvParams p) {
+    using L = TcSmemKC<CIN, NT, KC>;
+    constexpr int NCH = CIN / KC;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sW = smem + L::off_w;
+    float* sBias = reinterpret_cast<float*>(smem + L::off_bias);
+    const uint32_t bar = saddr(smem + L::off_bar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::off_bar + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nseg = p.B * (p.H / TC_R) * (p.W / TC_M);
+    if ((int)blockIdx.x >= nseg) return;
+    const int co0 = blockIdx.y * NT;
+
+    for (int i = tid; i < 9 * NT * L::KG; i += TC_THREADS) {
+        const int kg = i % L::KG;
+        const int rn = i / L::KG;
+        const int n = rn % NT, tap = rn / NT;
+        unsigned char* dst = sW + tap * L::WTAP + kg * L::WPLANE + n * 16;
+        if (co0 + n < p.cout_pad)
+            cp_async16(dst, p.w + ((size_t)tap * p.cout_pad + co0 + n) * CIN + kg * 8);
+        else
+            *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int c = tid; c < NT; c += TC_THREADS)
+        sBias[c] = (p.bias && co0 + c < p.cout && p.epi != EPI_GRAD) ? p.bias[co0 + c] : 0.f;
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    pdl_wait();  // the input is the previous kernel's output
+    pdl_trigger();
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         saddr(tslot)),
+                     "r"(L::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
+                               ((uint32_t)(TC_M >> 4) << 24);
+    bool ok = true;
+    uint32_t ncommit = 0;
+    int i = 0, prev = -1;
+    for (int seg = blockIdx.x; seg < nseg; seg += gridDim.x, ++i) {
+        const int buf = i & 1;
+#pragma unroll 1
+        for (int c = 0; c < NCH; ++c) {
+            if (ncommit > 0) {  // the last products issued have read the patch
+                if (ok && !wait_bar(bar, (ncommit - 1) & 1u)) ok = false;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
+            load_patch_ch<CIN, L::KGC, L::PPLANE>(p, smem, seg, c * KC, tid);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            if (c == 0 && prev >= 0 && ok) {
+                // the previous unit's products are complete (its last commit was waited for)
+                const int pb = (i - 1) & 1;
+                for (int rr = 0; rr < TC_R; ++rr)
+                    epilogue<NT>(p, sBias, tmem + (pb * TC_R + rr) * L::NTC, prev, rr, warp, lane,
+                                 co0);
+            }
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (tid == 0) {
+                const uint32_t pa = saddr(smem), pw = saddr(sW);
+#pragma unroll 1
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int ky = tap / 3, kx = tap - 3 * (tap / 3);
+#pragma unroll
+                    for (int kc = 0; kc < KC / 16; ++kc) {
+                        const uint64_t bd = smem_desc(
+                            pw + tap * L::WTAP + (c * L::KGC + 2 * kc) * L::WPLANE, L::WPLANE, 128);
+                        const uint32_t accum = (c | tap | kc) != 0;
+#pragma unroll
+                        for (int rr = 0; rr < TC_R; ++rr) {
+                            const uint32_t acc = tmem + (buf * TC_R + rr) * L::NTC;
+                            const uint64_t ad = smem_desc(
+                                pa + (2 * kc) * L::PPLANE + ((rr + ky) * TC_PW + kx) * 16,
+                                L::PPLANE, 128);
+                            asm volatile(
+                                "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(
+                                    acc),
+                                "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                        }
+                    }
+                }
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        bar));
+            }
+            ++ncommit;
+        }
+        prev = seg;
+    }
+    if (ncommit > 0) {
+        if (ok && !wait_bar(bar, (ncommit - 1) & 1u)) ok = false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (prev >= 0 && ok) {
+        const int pb = (i - 1) & 1;
+        for (int rr = 0; rr < TC_R; ++rr)
+            epilogue<NT>(p, sBias, tmem + (pb * TC_R + rr) * L::NTC, prev, rr, warp, lane, co0);
+    }
+    if (!ok && tid == 0) {
+        if (p.status) atomicOr(p.status, 2u);  // a bounded wait ran out
+        // the last products in flight, once more, before the accumulators are freed
+        if (ncommit > 0) wait_bar(bar, (ncommit - 1) & 1u);
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(L::TMEM_COLS));
+}
+
 // Persistent grid size of a shape: CTAs resident at once (shared memory and
 // 512 TMEM columns per SM); also raises the shared-memory limit.  Called once
 // per shape before any graph capture (init_tc_kernels).
-template <int CIN, int NT>
+template <int CIN, int NT, int KC>
 int& tc_grid_cap() {
     static int cap = 0;
     return cap;
 }
 
-template <int CIN, int NT>
+// KC == CIN: the one-pass kernel (two patches); KC < CIN: the two-pass one
+template <int CIN, int NT, int KC>
+struct TcShape {
+    static constexpr bool kOnePass = KC == CIN;
+    static constexpr size_t bytes = kOnePass ? TcSmem<CIN, NT>::bytes : TcSmemKC<CIN, NT, KC>::bytes;
+    static constexpr int tmem_cols = kOnePass ? TcSmem<CIN, NT>::TMEM_COLS : TcSmemKC<CIN, NT, KC>::TMEM_COLS;
+    static void (*kernel())(const ConvParams) {
+        if constexpr (kOnePass) return k_conv_tc<CIN, NT>;
+        else return k_conv_tc_kc<CIN, NT, KC>;
+    }
+};
+
+template <int CIN, int NT, int KC>
 cudaError_t tc_prepare() {
-    using L = TcSmem<CIN, NT>;
-    if (tc_grid_cap<CIN, NT>()) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<CIN, NT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+    using S = TcShape<CIN, NT, KC>;
+    static_assert(S::bytes <= 227 * 1024, "tcgen05 convolution shape exceeds shared memory");
+    if (tc_grid_cap<CIN, NT, KC>()) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(S::kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)S::bytes);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, smem = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -337,50 +532,61 @@ cudaError_t tc_prepare() {
         return e;
     // resident CTAs: shared memory (plus the 1 KB the system keeps per CTA),
     // TMEM columns, threads
-    int per = smem / (int)(L::bytes + 1024);
+    int per = smem / (int)(S::bytes + 1024);
     per = per < 1 ? 1 : per;
-    if (per * L::TMEM_COLS > 512) per = 512 / L::TMEM_COLS;
+    if (per * S::tmem_cols > 512) per = 512 / S::tmem_cols;
     if (per * TC_THREADS > 2048) per = 2048 / TC_THREADS;
-    tc_grid_cap<CIN, NT>() = sms * per;
+    tc_grid_cap<CIN, NT, KC>() = sms * per;
     return cudaSuccess;
 }
 
-template <int CIN, int NT>
+// grid: (persistent CTAs over the work units, output-channel tiles of NT)
+template <int CIN, int NT, int KC>
 cudaError_t conv_tc_T(const ConvParams& p, cudaStream_t s) {
-    using L = TcSmem<CIN, NT>;
-    cudaError_t e = tc_prepare<CIN, NT>();
+    using S = TcShape<CIN, NT, KC>;
+    cudaError_t e = tc_prepare<CIN, NT, KC>();
     if (e != cudaSuccess) return e;
     const int nseg = p.B * (p.H / TC_R) * (p.W / TC_M);
-    const int cap = tc_grid_cap<CIN, NT>();
-    const int grid = nseg < cap ? nseg : cap;
-    return launch_pdl(k_conv_tc<CIN, NT>, dim3(grid), dim3(TC_THREADS), L::bytes, s, p);
+    const int ntile = (p.cout_pad + NT - 1) / NT;
+    int gx = tc_grid_cap<CIN, NT, KC>() / ntile;
+    gx = gx < 1 ? 1 : (gx > nseg ? nseg : gx);
+    return launch_pdl(S::kernel(), dim3(gx, ntile), dim3(TC_THREADS), S::bytes, s, p);
 }
 
 }  // namespace
 
-// the (CIN, N) shapes built for the tensor-core path (two patches and nine
-// taps of weights within 227 KB of shared memory)
-#define PIC_TC_SHAPES(X) X(16, 32) X(32, 32) X(32, 64) X(64, 32) X(64, 64) X(32, 16)
+// the (CIN, N, channels per pass) shapes built for the tensor-core path (one
+// pass: two patches and nine taps of weights within 227 KB of shared memory;
+// CIN = 128: two passes of 64 channels); output channels beyond N = 64 are
+// split over CTAs
+#define PIC_TC_SHAPES(X) \
+    X(16, 32, 16) X(32, 32, 32) X(32, 64, 32) X(64, 32, 64) X(64, 64, 64) X(32, 16, 32) X(128, 64, 64)
+
+// the N of a launch: the padded output channels rounded up to 16, 32 or 64
+// (more than 64: tiles of 64)
+static int tc_nt(int cout_pad) {
+    return cout_pad <= 16 ? 16 : (cout_pad <= 32 ? 32 : 64);
+}
 
 bool conv_tc_supported(const ConvParams& p, int cin) {
     if (p.force_tc < 0 || p.W % TC_M || p.H % TC_R || p.cout_pad > 128) return false;
     // small problems (a few hundred work units) finish sooner on the mma.sync
     // kernel, whose CTAs do not each stage all nine taps of weights
     if ((long long)p.B * (p.H / TC_R) * (p.W / TC_M) < 600 && p.force_tc <= 0) return false;
-    const int nt = p.cout_pad <= 16 ? 16 : (p.cout_pad <= 32 ? 32 : (p.cout_pad <= 64 ? 64 : 128));
+    const int nt = tc_nt(p.cout_pad);
     // a 16-wide tile (the 3-channel output layer) is faster on the mma.sync
     // kernel (measured on GB300: 66 against 84 us at 1024^2)
     if (nt == 16 && p.force_tc <= 0) return false;
-#define PIC_TC_HAS(A, B) if (cin == A && nt == B) return true;
+#define PIC_TC_HAS(A, B, C) if (cin == A && nt == B) return true;
     PIC_TC_SHAPES(PIC_TC_HAS)
 #undef PIC_TC_HAS
     return false;
 }
 
 cudaError_t launch_conv_tc(const ConvParams& p, int cin, cudaStream_t s) {
-    const int nt = p.cout_pad <= 16 ? 16 : (p.cout_pad <= 32 ? 32 : (p.cout_pad <= 64 ? 64 : 128));
-#define PIC_TC_CASE(A, B) \
-    if (cin == A && nt == B) return conv_tc_T<A, B>(p, s);
+    const int nt = tc_nt(p.cout_pad);
+#define PIC_TC_CASE(A, B, C) \
+    if (cin == A && nt == B) return conv_tc_T<A, B, C>(p, s);
     PIC_TC_SHAPES(PIC_TC_CASE)
 #undef PIC_TC_CASE
     return cudaErrorInvalidValue;
@@ -388,8 +594,8 @@ cudaError_t launch_conv_tc(const ConvParams& p, int cin, cudaStream_t s) {
 
 cudaError_t init_tc_kernels() {
     cudaError_t e = cudaSuccess;
-#define PIC_TC_PREP(A, B) \
-    if (e == cudaSuccess) e = tc_prepare<A, B>();
+#define PIC_TC_PREP(A, B, C) \
+    if (e == cudaSuccess) e = tc_prepare<A, B, C>();
     PIC_TC_SHAPES(PIC_TC_PREP)
 #undef PIC_TC_PREP
     return e;
