@@ -19,10 +19,10 @@
 // Output channels beyond N = 64 are split over CTAs (blockIdx.y takes channels
 // [64 y, 64 y + 64)).  Inputs of 128 channels (the encoder's last level and
 // the decoder's first layer) do not fit twice in shared memory: their kernel
-// keeps all nine taps of the CTA's weights and one patch of 64 channels, and
-// runs each work unit as two passes over the channel halves into the same
-// accumulator (load a half, multiply it in, load the other half once those
-// products have read the patch).
+// keeps all nine taps of the CTA's weights and two patches of 32 channels, and
+// runs each work unit as four passes over the channel quarters into the same
+// accumulator, loading the next quarter while the tensor cores multiply the
+// current one.
 //
 // Every wait is bounded; on a timeout the kernel flags it in the status word,
 // frees its TMEM and returns.
@@ -75,8 +75,8 @@ struct TcSmem {
     static constexpr int TMEM_COLS = 2 * TC_R * NTC;          // two work units in flight
 };
 
-// The two-pass kernel: one patch of KC channels, then all CIN channels of
-// the nine taps' weights.
+// The channel-pass kernel: two patches of KC channels, then all CIN channels
+// of the nine taps' weights.
 template <int CIN, int NT, int KC>
 struct TcSmemKC {
     static constexpr int KG = CIN / 8;                        // k-groups of the weights
@@ -85,10 +85,10 @@ struct TcSmemKC {
     static constexpr int PATCH = KGC * PPLANE;
     static constexpr int WPLANE = NT * 16;
     static constexpr int WTAP = KG * WPLANE;
-    static constexpr size_t off_w = (size_t)PATCH;
+    static constexpr size_t off_w = 2 * (size_t)PATCH;
     static constexpr size_t off_bias = off_w + 9 * (size_t)WTAP;
     static constexpr size_t off_bar = (off_bias + NT * 4 + 15) & ~(size_t)15;
-    static constexpr size_t bytes = off_bar + 32;             // 1 mbarrier + TMEM slot
+    static constexpr size_t bytes = off_bar + 32;             // 2 mbarriers + TMEM slot
     static constexpr int NTC = NT < 32 ? 32 : NT;
     static constexpr int TMEM_COLS = 2 * TC_R * NTC;
 };
@@ -361,13 +361,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
                      "r"(L::TMEM_COLS));
 }
 
-// Two passes over the input channels per work unit (CIN = 2 KC): the CTA
-// keeps its nine taps' weights of all CIN channels and one patch of KC
-// channels.  For unit i (accumulator i & 1) and channel half c: wait until the
-// products issued last have read the patch, load half c of the unit's patch
-// (on the first half, store the previous unit's results meanwhile), then one
-// thread issues the 9 x KC/16 products into the accumulator and commits them.
-// One mbarrier takes every commit in order: commit k completes its phase k.
+// Passes over the input channels (CIN = NCH KC) per work unit: the CTA keeps
+// its nine taps' weights of all CIN channels and two patches of KC channels.
+// Chunk g (unit g / NCH, channels (g % NCH) KC ...) goes to patch g & 1 and
+// its products to the unit's accumulator (unit & 1), committed on mbarrier
+// g & 1 (its (g >> 1)-th commit there).  While the tensor cores multiply
+// chunk g, the CTA waits for chunk g - 1's products (freeing the other patch,
+// and completing the previous unit after its last chunk), loads chunk g + 1
+// there and, at a unit's first chunk, stores the previous unit's results.
 template <int CIN, int NT, int KC>
 __global__ void __launch_bounds__(TC_THREADS) k_conv_tc_kc(const ConvParams p) {
     using L = TcSmemKC<CIN, NT, KC>;
@@ -375,12 +376,16 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc_kc(const ConvParams p) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sW = smem + L::off_w;
     float* sBias = reinterpret_cast<float*>(smem + L::off_bias);
-    const uint32_t bar = saddr(smem + L::off_bar);
+    const uint32_t bar0 = saddr(smem + L::off_bar);  // mbarriers of patches 0, 1
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::off_bar + 16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nseg = p.B * (p.H / TC_R) * (p.W / TC_M);
     if ((int)blockIdx.x >= nseg) return;
     const int co0 = blockIdx.y * NT;
+    // this CTA's units: blockIdx.x, blockIdx.x + gridDim.x, ...
+    const int nunit = (nseg - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int nchunk = nunit * NCH;
+    auto seg_of = [&](int u) { return (int)blockIdx.x + u * (int)gridDim.x; };
 
     for (int i = tid; i < 9 * NT * L::KG; i += TC_THREADS) {
         const int kg = i % L::KG;
@@ -394,11 +399,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc_kc(const ConvParams p) {
     }
     for (int c = tid; c < NT; c += TC_THREADS)
         sBias[c] = (p.bias && co0 + c < p.cout && p.epi != EPI_GRAD) ? p.bias[co0 + c] : 0.f;
-    asm volatile("cp.async.commit_group;" ::: "memory");
     pdl_wait();  // the input is the previous kernel's output
     pdl_trigger();
+    load_patch_ch<CIN, L::KGC, L::PPLANE>(p, smem, seg_of(0), 0, tid);
+    asm volatile("cp.async.commit_group;" ::: "memory");
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -415,75 +422,71 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc_kc(const ConvParams p) {
     constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
                                ((uint32_t)(TC_M >> 4) << 24);
     bool ok = true;
-    uint32_t ncommit = 0;
-    int i = 0, prev = -1;
-    for (int seg = blockIdx.x; seg < nseg; seg += gridDim.x, ++i) {
-        const int buf = i & 1;
 #pragma unroll 1
-        for (int c = 0; c < NCH; ++c) {
-            if (ncommit > 0) {  // the last products issued have read the patch
-                if (ok && !wait_bar(bar, (ncommit - 1) & 1u)) ok = false;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            }
-            load_patch_ch<CIN, L::KGC, L::PPLANE>(p, smem, seg, c * KC, tid);
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            if (c == 0 && prev >= 0 && ok) {
-                // the previous unit's products are complete (its last commit was waited for)
-                const int pb = (i - 1) & 1;
-                for (int rr = 0; rr < TC_R; ++rr)
-                    epilogue<NT>(p, sBias, tmem + (pb * TC_R + rr) * L::NTC, prev, rr, warp, lane,
-                                 co0);
-            }
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (tid == 0) {
-                const uint32_t pa = saddr(smem), pw = saddr(sW);
+    for (int g = 0; g < nchunk; ++g) {
+        const int u = g / NCH, c = g - u * NCH, pbuf = g & 1;
+        // chunk g's patch (and, the first time, the weights) has landed
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint32_t pa = saddr(smem + pbuf * L::PATCH), pw = saddr(sW);
 #pragma unroll 1
-                for (int tap = 0; tap < 9; ++tap) {
-                    const int ky = tap / 3, kx = tap - 3 * (tap / 3);
+            for (int tap = 0; tap < 9; ++tap) {
+                const int ky = tap / 3, kx = tap - 3 * (tap / 3);
 #pragma unroll
-                    for (int kc = 0; kc < KC / 16; ++kc) {
-                        const uint64_t bd = smem_desc(
-                            pw + tap * L::WTAP + (c * L::KGC + 2 * kc) * L::WPLANE, L::WPLANE, 128);
-                        const uint32_t accum = (c | tap | kc) != 0;
+                for (int kc = 0; kc < KC / 16; ++kc) {
+                    const uint64_t bd = smem_desc(
+                        pw + tap * L::WTAP + (c * L::KGC + 2 * kc) * L::WPLANE, L::WPLANE, 128);
+                    const uint32_t accum = (c | tap | kc) != 0;
 #pragma unroll
-                        for (int rr = 0; rr < TC_R; ++rr) {
-                            const uint32_t acc = tmem + (buf * TC_R + rr) * L::NTC;
-                            const uint64_t ad = smem_desc(
-                                pa + (2 * kc) * L::PPLANE + ((rr + ky) * TC_PW + kx) * 16,
-                                L::PPLANE, 128);
-                            asm volatile(
-                                "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
-                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(
-                                    acc),
-                                "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
-                        }
+                    for (int rr = 0; rr < TC_R; ++rr) {
+                        const uint32_t acc = tmem + ((u & 1) * TC_R + rr) * L::NTC;
+                        const uint64_t ad = smem_desc(
+                            pa + (2 * kc) * L::PPLANE + ((rr + ky) * TC_PW + kx) * 16, L::PPLANE,
+                            128);
+                        asm volatile(
+                            "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(acc),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
                     }
                 }
-                asm volatile(
-                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        bar));
             }
-            ++ncommit;
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    bar0 + 8 * pbuf));
         }
-        prev = seg;
+        if (g >= 1) {  // chunk g - 1's products: its patch is free, its unit may be complete
+            const int gp = g - 1;
+            if (ok && !wait_bar(bar0 + 8 * (gp & 1), (gp >> 1) & 1)) ok = false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+        if (g + 1 < nchunk) {
+            const int un = (g + 1) / NCH, cn = (g + 1) - un * NCH;
+            load_patch_ch<CIN, L::KGC, L::PPLANE>(p, smem + (pbuf ^ 1) * L::PATCH, seg_of(un),
+                                                  cn * KC, tid);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        if (c == 0 && u >= 1 && ok)  // unit u - 1 ended with chunk g - 1
+            for (int rr = 0; rr < TC_R; ++rr)
+                epilogue<NT>(p, sBias, tmem + (((u - 1) & 1) * TC_R + rr) * L::NTC, seg_of(u - 1),
+                             rr, warp, lane, co0);
     }
-    if (ncommit > 0) {
-        if (ok && !wait_bar(bar, (ncommit - 1) & 1u)) ok = false;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    }
-    if (prev >= 0 && ok) {
-        const int pb = (i - 1) & 1;
+    // the last chunk's products, then the last unit's results
+    if (ok && !wait_bar(bar0 + 8 * ((nchunk - 1) & 1), ((nchunk - 1) >> 1) & 1)) ok = false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok)
         for (int rr = 0; rr < TC_R; ++rr)
-            epilogue<NT>(p, sBias, tmem + (pb * TC_R + rr) * L::NTC, prev, rr, warp, lane, co0);
-    }
+            epilogue<NT>(p, sBias, tmem + (((nunit - 1) & 1) * TC_R + rr) * L::NTC,
+                         seg_of(nunit - 1), rr, warp, lane, co0);
     if (!ok && tid == 0) {
         if (p.status) atomicOr(p.status, 2u);  // a bounded wait ran out
-        // the last products in flight, once more, before the accumulators are freed
-        if (ncommit > 0) wait_bar(bar, (ncommit - 1) & 1u);
+        // the products still in flight, once more, before the accumulators
+        // are freed: the last commit on each of the two barriers
+        for (int j = nchunk - 1; j >= 0 && j >= nchunk - 2; --j)
+            wait_bar(bar0 + 8 * (j & 1), (j >> 1) & 1);
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -557,10 +560,10 @@ cudaError_t conv_tc_T(const ConvParams& p, cudaStream_t s) {
 
 // the (CIN, N, channels per pass) shapes built for the tensor-core path (one
 // pass: two patches and nine taps of weights within 227 KB of shared memory;
-// CIN = 128: two passes of 64 channels); output channels beyond N = 64 are
-// split over CTAs
+// CIN = 128: four passes of 32 channels through two patches); output
+// channels beyond N = 64 are split over CTAs
 #define PIC_TC_SHAPES(X) \
-    X(16, 32, 16) X(32, 32, 32) X(32, 64, 32) X(64, 32, 64) X(64, 64, 64) X(32, 16, 32) X(128, 64, 64)
+    X(16, 32, 16) X(32, 32, 32) X(32, 64, 32) X(64, 32, 64) X(64, 64, 64) X(32, 16, 32) X(128, 64, 32)
 
 // the N of a launch: the padded output channels rounded up to 16, 32 or 64
 // (more than 64: tiles of 64)
