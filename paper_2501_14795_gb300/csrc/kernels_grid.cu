@@ -995,8 +995,27 @@ cudaError_t launch_load(const Geom& g, SpeciesDev& sp, int track_ids, int64_t n,
                                                                  off);
     e = cudaMemsetAsync(sp.cursor, 0, sizeof(int32_t) * ncell, s);
     if (e != cudaSuccess) return e;
-    if (nn > 0)
-        k_load_scatter<<<grid_for(nn, 256), 256, 0, s>>>(g, sp, nn, staged_ids, celloff, track_ids);
+    if (nn > 0) {
+        // One wave of resident CTAs only: the grid-stride loop then sweeps the
+        // input in order, so the tiles being written at any time are those of
+        // a few hundred thousand consecutive input particles, whose slots the
+        // L2 cache holds until their sectors are complete.  A second wave
+        // would fill the gaps the first left in every tile long after those
+        // sectors went back to memory half-written (each then read back to be
+        // merged: about three times the scatter's bytes in DRAM traffic).
+        static int resident = 0;
+        if (resident == 0) {
+            int dev = 0, sms = 0, per = 0;
+            e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_load_scatter, 256, 0);
+            if (e != cudaSuccess) return e;
+            resident = sms * (per > 0 ? per : 1);
+        }
+        const int grid = grid_for(nn, 256) < resident ? grid_for(nn, 256) : resident;
+        k_load_scatter<<<grid, 256, 0, s>>>(g, sp, nn, staged_ids, celloff, track_ids);
+    }
     return cudaGetLastError();
 }
 
