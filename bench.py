@@ -124,10 +124,11 @@ def push_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload):
-    """DRAM bytes per particle-advance launch from the committed ncu summary,
-    valid only while the kernel sources hash the same as when captured."""
-    p = os.path.join(ROOT, "profiles", "traffic.txt")
+def recorded_value(name, workload):
+    """A per-workload figure of the particle advance from a committed ncu
+    summary under profiles/ (lines: workload value source-hash), valid only
+    while the kernel sources hash the same as when it was captured."""
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     want = push_source_hash()
@@ -136,6 +137,29 @@ def recorded_traffic(workload):
         if len(parts) >= 3 and not line.startswith("#") and parts[0] == workload and parts[2] == want:
             return float(parts[1])
     return None
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per particle-advance launch (profiles/traffic.txt)."""
+    return recorded_value("traffic.txt", workload)
+
+
+def issue_roofline(workload, particles_per_s, sm_mhz):
+    """The particle advance's own ceiling: it is bound by instruction issue
+    (one warp-instruction per scheduler per clock, four schedulers per SM).
+    Warp-instructions per 32 particles from profiles/issue.txt (ncu,
+    smsp__inst_executed.sum at the same kernel source); achieved = that times
+    the particles advanced per second."""
+    per32 = recorded_value("issue.txt", workload)
+    if per32 is None or not sm_mhz:
+        return None
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    achieved = per32 / 32.0 * particles_per_s
+    peak = 4.0 * sms * sm_mhz * 1e6
+    return {"bound": "issue", "warp_instructions_per_32_particles": per32, "achieved": achieved,
+            "peak": peak, "unit": "warp-instructions/s", "frac": achieved / peak,
+            "peak_source": f"4 schedulers x {sms} SMs x the sampled median SM clock"}
 
 
 class ClockSampler:
@@ -751,6 +775,7 @@ def run_gpu(args, rank, world, local_rank):
         config.update(moving_window=True, particles_start=n_start, particles_end=n_end,
                       window_moves=d.get("window_moves"),
                       particles="mean of start and end (the window injects plasma)")
+    clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -761,6 +786,8 @@ def run_gpu(args, rank, world, local_rank):
                      "kernel": "k_push (gather+Boris+move+deposit+leaver emission)",
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "bytes_per_launch": alg_push, "launch_ms": per_launch_s * 1e3},
+        # the same kernel against its own ceiling, instruction issue
+        "issue_roofline": issue_roofline(args.workload, n / per_launch_s, clocks["sm_mhz"]),
         "step_hbm": {"bytes_per_particle": step_bytes, "leaver_fraction_last_step": f_leave,
                      "achieved_gbs": step_bytes * value / world / 1e9,
                      "frac": step_bytes * value / world / 1e9 / peak},
@@ -779,7 +806,7 @@ def run_gpu(args, rank, world, local_rank):
         "e2e": {"value": total * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps},
         "gpu_launches": int(launches),
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "status_bits": d["status_bits"],
     }
     if world == 1 and not args.no_cpu_baseline:
