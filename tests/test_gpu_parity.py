@@ -249,19 +249,20 @@ def test_diagnostics_energies_gauss_and_continuity():
 
 
 def _full_size_checks(w, steps, tile, threads=256, sample=2000):
-    """Run `steps` steps at full size in the bench launch configuration, then one
-    more step on a fetched state; sampled stayers are checked one by one
+    """Run `steps` steps at full size in the bench launch configuration (with
+    particle ids), then one more step on a fetched state; sampled particles
+    that stay in their tile are found again by id and checked one by one
     against the oracle's per-particle push, and whole-grid properties
     (sortedness, counts, continuity, Gauss drift) on everything."""
-    with _gpu(w, 0, tile=tile, threads=threads) as sim:
+    with _gpu(w, pic.PIC_TRACK_IDS, tile=tile, threads=threads) as sim:
         d0 = sim.diagnostics()
         sim.step(steps)
-        before = sim.particles(0)
+        before = sim.particles(0, ids=True)
         E = sim.fields(pic.FIELD_E)
         B = sim.fields(pic.FIELD_B)
         d1 = sim.diagnostics()
         sim.step(1)
-        after = sim.particles(0)
+        after = sim.particles(0, ids=True)
         d2 = sim.diagnostics()
         J = sim.fields(pic.FIELD_J)
     nx, T = w.nx, tile
@@ -272,7 +273,10 @@ def _full_size_checks(w, steps, tile, threads=256, sample=2000):
         counts = np.bincount(tid, minlength=len(st["tile_offset"]) - 1)
         np.testing.assert_array_equal(np.diff(st["tile_offset"]), counts)
         assert np.all(np.diff(tid) >= 0)
-    # sampled particles: stayers that were not displaced keep their index
+    # the ids are a permutation of 0..n-1: where each particle is after the step
+    assert np.array_equal(np.sort(after["id"]), np.arange(n, dtype=np.int32))
+    where = np.empty(n, np.int64)
+    where[after["id"]] = np.arange(n)
     rng = np.random.default_rng(0)
     idx = rng.choice(n, size=min(sample, n), replace=False)
     s = w.species[0]
@@ -285,11 +289,10 @@ def _full_size_checks(w, steps, tile, threads=256, sample=2000):
     assert st == 0
     t_old = _tile_ids(before["ix"][idx], before["iy"][idx], nx, T)
     t_new = _tile_ids(sub.ix, sub.iy, nx, T)
-    ob, oa = before["tile_offset"], after["tile_offset"]
-    keep = (t_old == t_new) & (idx >= np.maximum(ob[t_old], oa[t_old])) & (idx < np.minimum(ob[t_old + 1], oa[t_old + 1]))
+    keep = t_old == t_new
     keep &= (np.minimum(sub.x, 1 - sub.x) > NEAR) & (np.minimum(sub.y, 1 - sub.y) > NEAR)
     assert keep.sum() > 0.5 * len(idx)
-    k = idx[keep]
+    k = where[before["id"][idx][keep]]
     np.testing.assert_array_equal(after["ix"][k], sub.ix[keep])
     np.testing.assert_array_equal(after["iy"][k], sub.iy[keep])
     assert np.max(np.abs(after["x"][k] - sub.x[keep])) <= X_ATOL
