@@ -292,6 +292,8 @@ int backward(pic_denoiser* d, int B, const float* target, cudaStream_t s) {
         p.cin = L.cin;
         p.cout = L.cout;
         p.dw = d->grad + L.woff;
+        p.force_tc = d->force_tc;
+        p.status = d->cur_status;
         return launch_wgrad(p, L.cin_pad, pad16(L.cout), s);
     };
     auto db = [&](int l) { return d->grad + d->boff[l]; };
@@ -827,6 +829,8 @@ pic_status pic_nn_conv3x3_wgrad(const void* x, const void* dz, int B, int H, int
     p.cin = cin;
     p.cout = cout;
     p.dw = dw;
+    p.force_tc = 1;  // a probe exercises the tensor-core kernel whenever the shape allows
+    p.status = nullptr;
     if (cudaMemsetAsync(dw, 0, sizeof(float) * 9 * cin * cout, s) != cudaSuccess) return PIC_ECUDA;
     if (launch_wgrad(p, pad16(cin), pad16(cout), s) != cudaSuccess) return PIC_EINVAL;
     return cudaStreamSynchronize(s) == cudaSuccess ? PIC_OK : PIC_ECUDA;

@@ -70,6 +70,8 @@ struct WgradParams {
     int up;                   // x is H/2 x W/2, read at (y/2, x/2)
     int cin, cout;            // real channel counts
     float* dw;                // += into [9][cin][cout]
+    int force_tc;             // 1: the tcgen05 kernel whenever the shape allows, -1: never
+    unsigned* status;         // tcgen05 kernel: bit 2 set when a bounded wait ran out (may be null)
 };
 
 struct LayerDesc {
@@ -128,6 +130,9 @@ cudaError_t launch_conv(const ConvParams& p, int cin, int ct, cudaStream_t s);
 bool conv_tc_supported(const ConvParams& p, int cin);
 cudaError_t launch_conv_tc(const ConvParams& p, int cin, cudaStream_t s);
 cudaError_t init_tc_kernels();
+// weight gradient on the tensor cores (ci, co: padded channel counts)
+bool wgrad_tc_supported(const WgradParams& p, int ci, int co);
+cudaError_t launch_wgrad_tc(const WgradParams& p, int ci, int co, cudaStream_t s);
 cudaError_t launch_wgrad(const WgradParams& p, int ci, int co, cudaStream_t s);
 // the first layer (3 -> 32, ReLU) fused with the input packing, and the
 // output layer (32 -> 3) with the residual epilogue, on the CUDA cores; H and

@@ -969,6 +969,7 @@ cudaError_t launch_conv(const ConvParams& p, int cin, int ct, cudaStream_t s) {
 cudaError_t launch_wgrad(const WgradParams& p, int ci, int co, cudaStream_t s) {
     const long long npix = (long long)p.B * p.H * p.W;
     if (npix % WG_PIX || p.W < 16 || (p.up && (p.H % 2 || p.W % 2))) return cudaErrorInvalidValue;
+    if (wgrad_tc_supported(p, ci, co)) return launch_wgrad_tc(p, ci, co, s);
     const long long nchunks = npix / WG_PIX;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);

@@ -556,7 +556,314 @@ cudaError_t conv_tc_T(const ConvParams& p, cudaStream_t s) {
     return launch_pdl(S::kernel(), dim3(gx, ntile), dim3(TC_THREADS), S::bytes, s, p);
 }
 
+// ------------------------------------------------------------ weight gradient
+// dW[ky][kx][ci][co] = sum over output pixels p of x[p + (ky - 1, kx - 1)][ci] dz[p][co]
+// (x read through the nearest-neighbour doubling when the layer upsamples).
+// For one kx the three ky taps form one GEMM: M = (ky, ci) in TMEM lanes, N =
+// co in columns, K = pixels.  A CTA takes tiles of R rows x P columns of
+// output pixels (R P = TP): the patch of x around the tile (R + 2 rows, P + 2
+// columns, circular) and the tile of dz go to shared memory, and for each kx,
+// output row and 16 pixels one MMA runs per 128 lanes of (ky, ci).
+//
+// The patch is stored [row][8-channel group][pixel], 16 B per pixel and group:
+// a core matrix (8 pixels x 8 channels) is 128 contiguous bytes, the next 8
+// pixels follow (K stride 128 B) and the next 8 lanes of M, the next channel
+// group or after the last group the first group of the next row, sit one row
+// segment of (P + 2) 16 B further (M stride): the ky taps are consecutive
+// lane groups and the kx shift is a 16-byte offset of the start address.  dz
+// is stored [8-channel group][pixel] (K stride 128 B, N stride TP 16 B).
+// Both operands are MN-major (channels contiguous, as in memory), copied with
+// cp.async in 16-byte pieces, no transpose; NS stages in flight, each tile's
+// products committed to its stage's mbarrier.  Lanes past the third ky row
+// (when 3 CI is not a multiple of 128) read the rows below the patch and are
+// never stored.  At the end each lane adds its (ky, ci) row, CO columns per
+// kx, into dW with atomics (all CTAs of a launch add into the same values).
+constexpr int WT_THREADS = 256;  // 8 warps; in the epilogue warps w and w + 4 share lane quarter w
+
+template <int CI, int CO, int KXS, int TP>
+struct WtSmem {
+    static constexpr int NG = CI / 8;                   // channel groups of x
+    static constexpr int GO = CO / 8;                   // channel groups of dz
+    static constexpr int NCH = (3 * NG + 15) / 16;      // MMAs of 128 lanes per kx and 16 pixels
+    static constexpr int CSMAX = 66 * 16;               // row segment of one group, P = 64
+    static constexpr int PATCH = (TP / 64 + 2) * NG * CSMAX;  // P = 64 is the largest patch
+    static constexpr int DZ = TP * CO * 2;
+    static constexpr int STAGE = PATCH + DZ;
+    static constexpr int SLACK_ROWS = (16 * NCH - 1) / NG > 2 ? (16 * NCH - 1) / NG - 2 : 0;
+    static constexpr int SLACK = SLACK_ROWS * NG * CSMAX;   // rows read below the last patch
+    static constexpr int COLS = KXS * NCH * CO;
+    static constexpr int TMEM_COLS =
+        COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : COLS <= 256 ? 256 : 512;
+    // stages: three, or two, if two CTAs then fit an SM (their issue and
+    // loads overlap); else as many as fit, at most three
+    static constexpr int FIX = SLACK + 64 + 1024;   // + the 1 KB the system keeps per CTA
+    static constexpr bool TWO = 2 * TMEM_COLS <= 512;
+    static constexpr int NSF = (227 * 1024 - SLACK - 64) / STAGE;
+    static constexpr int NS = TWO && 2 * (3 * STAGE + FIX) <= 228 * 1024   ? 3
+                              : TWO && 2 * (2 * STAGE + FIX) <= 228 * 1024 ? 2
+                              : NSF > 3                                    ? 3
+                                                                           : NSF;
+    static constexpr size_t off_bar = (size_t)NS * STAGE + SLACK;
+    static constexpr size_t bytes = off_bar + 8 * NS + 16;  // mbarriers + TMEM slot
+    static_assert(NS >= 2 && COLS <= 512 && (NG & (NG - 1)) == 0 && (GO & (GO - 1)) == 0,
+                  "weight-gradient tile does not fit");
+};
+
+// tile t (batch b, tile row ty, tile column tx) of output pixels: the patch of
+// x and the tile of dz into a stage
+template <int CI, int CO, int KXS, int TP>
+__device__ __forceinline__ void wt_load(const WgradParams& p, unsigned char* st, long long t,
+                                        int pl, int tid) {
+    using L = WtSmem<CI, CO, KXS, TP>;
+    const int P = 1 << pl, R = TP >> pl;
+    const int tilesx = p.W >> pl, tpb = tilesx * (p.H / R);
+    const int b = (int)(t / tpb);
+    const int rem = (int)(t - (long long)b * tpb);
+    const int ty = rem / tilesx, tx = rem - ty * tilesx;
+    const int y0 = ty * R, x0 = tx * P;
+    const int sh = p.up ? 1 : 0;
+    const int Hi = p.H >> sh, Wi = p.W >> sh;
+    const int CS = (P + 2) * 16;
+    const bf16* xb = p.x + (size_t)b * Hi * Wi * CI;
+    // patch rows y0 - 1 .. y0 + R, columns x0 - 1 .. x0 + P; consecutive
+    // threads take consecutive 16-byte pieces of a pixel's channels
+    const int rowpieces = (P + 2) * L::NG;
+    for (int pr = 0; pr < R + 2; ++pr) {
+        const bf16* xr = xb + (size_t)(wrap(y0 - 1 + pr, p.H) >> sh) * Wi * CI;
+        unsigned char* dr = st + pr * L::NG * CS;
+        for (int j = tid; j < rowpieces; j += WT_THREADS) {
+            const int pc = j / L::NG, g = j - pc * L::NG;
+            cp_async16(dr + g * CS + pc * 16, xr + (size_t)(wrap(x0 - 1 + pc, p.W) >> sh) * CI + g * 8);
+        }
+    }
+    // dz: tile pixel k = r P + c of group g at g TP 16 + k 16
+    unsigned char* sd = st + L::PATCH;
+    const bf16* dzb = p.dz + (((size_t)b * p.H + y0) * p.W + x0) * CO;
+    for (int j = tid; j < TP * L::GO; j += WT_THREADS) {
+        const int k = j / L::GO, g = j - k * L::GO;
+        const int r = k >> pl, c = k & (P - 1);
+        cp_async16(sd + g * (TP * 16) + k * 16, dzb + ((size_t)r * p.W + c) * CO + g * 8);
+    }
+}
+
+// grid (3 / KXS: the kx taps of a CTA, splits of the tiles); pl = log2 P
+template <int CI, int CO, int KXS, int TP>
+__global__ void __launch_bounds__(WT_THREADS) k_wgrad_tc(const WgradParams p, const int pl) {
+    using L = WtSmem<CI, CO, KXS, TP>;
+    constexpr int NS = L::NS;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t bar0 = saddr(smem + L::off_bar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::off_bar + 8 * NS);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int P = 1 << pl, R = TP >> pl;
+    const long long ntiles = (long long)p.B * (p.W >> pl) * (p.H / R);
+    const int kx0 = blockIdx.x * KXS;
+    const long long t0 = blockIdx.y, ts = gridDim.y;
+    if (t0 >= ntiles) return;
+    const int nmine = (int)((ntiles - t0 + ts - 1) / ts);  // this CTA's tiles
+    pdl_wait();
+    pdl_trigger();
+    if (tid == 0) {
+        for (int k = 0; k < NS; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * k));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         saddr(tslot)),
+                     "r"(L::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+#pragma unroll
+    for (int k = 0; k < NS - 1; ++k) {
+        if (k < nmine) wt_load<CI, CO, KXS, TP>(p, smem + k * L::STAGE, t0 + k * ts, pl, tid);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    // D f32, A and B bf16, both MN-major (bits 15, 16), N = CO, M = 128
+    constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                               ((uint32_t)(CO >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    const uint32_t CS = (uint32_t)(P + 2) * 16;
+    bool ok = true;
+    for (int i = 0; i < nmine; ++i) {
+        const int stg = i % NS;
+        asm volatile("cp.async.wait_group %0;" ::"n"(NS - 2) : "memory");  // tile i landed
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            // descriptors of the stage's patch and dz tile; an offset of n 16-byte
+            // units is added to the start-address field (addresses stay below 256 KB)
+            const uint32_t pa = saddr(smem + stg * L::STAGE), pb = pa + L::PATCH;
+            const uint64_t a0 = smem_desc(pa, 128, CS) + (uint64_t)kx0;
+            const uint64_t b0 = smem_desc(pb, 128, TP * 16);
+            for (int r = 0; r < R; ++r)
+                for (int c = 0; c < P; c += 16) {
+                    const uint64_t bd = b0 + (uint64_t)(r * P + c);
+                    const uint64_t ar = a0 + (uint64_t)(r * L::NG * (P + 2) + c);
+                    const uint32_t accum = (i | r | c) != 0;
+#pragma unroll
+                    for (int kxl = 0; kxl < KXS; ++kxl)
+#pragma unroll
+                        for (int h = 0; h < L::NCH; ++h) {
+                            const uint64_t ad = ar + (uint64_t)(kxl + h * 16 * (P + 2));
+                            asm volatile(
+                                "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(
+                                    tmem + (uint32_t)((kxl * L::NCH + h) * CO)),
+                                "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                        }
+                }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    bar0 + 8 * stg));
+        }
+        // tile i + NS - 1 into the stage tile i - 1 used, once its products are done
+        const int nx = i + NS - 1;
+        if (nx < nmine) {
+            if (i >= 1) {
+                const int j = i - 1;
+                if (ok && !wait_bar(bar0 + 8 * (j % NS), (j / NS) & 1)) ok = false;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
+            wt_load<CI, CO, KXS, TP>(p, smem + (nx % NS) * L::STAGE, t0 + nx * ts, pl, tid);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    // every tile's products: the last commit on each stage not yet waited for
+    for (int j = nmine - 1; j >= 0 && j >= nmine - NS; --j)
+        if (ok && !wait_bar(bar0 + 8 * (j % NS), (j / NS) & 1)) ok = false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ok = __syncthreads_and(ok);
+    if (ok) {
+        const int lq = warp & 3;        // TMEM lane quarter of this warp
+        const int m = 32 * lq + lane;   // this thread's lane (row of M)
+        const bool vec = (p.cout & 3) == 0 && ((uintptr_t)p.dw & 15) == 0;
+#pragma unroll 1
+        for (int h = 0; h < L::NCH; ++h) {
+            const int G = 16 * h + (m >> 3);             // lane group: (ky, channel group)
+            const int ky = G / L::NG, ci = (G - ky * L::NG) * 8 + (m & 7);
+            const bool valid = ky < 3 && ci < p.cin;
+#pragma unroll 1
+            for (int kxl = 0; kxl < KXS; ++kxl)
+#pragma unroll 1
+                for (int cc = 16 * (warp >> 2); cc < CO; cc += 32) {
+                    uint32_t v[16];
+                    const uint32_t taddr = tmem + ((uint32_t)(32 * lq) << 16) +
+                                           (uint32_t)((kxl * L::NCH + h) * CO + cc);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,"
+                        "%10,%11,%12,%13,%14,%15}, [%16];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                          "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                          "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                        : "r"(taddr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (!valid) continue;
+                    float* dst = p.dw + ((size_t)(3 * ky + kx0 + kxl) * p.cin + ci) * p.cout + cc;
+                    if (vec) {
+#pragma unroll
+                        for (int q = 0; q < 16; q += 4)
+                            if (cc + q < p.cout)
+                                atomicAdd(reinterpret_cast<float4*>(dst + q),
+                                          make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]),
+                                                      __uint_as_float(v[q + 2]),
+                                                      __uint_as_float(v[q + 3])));
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q)
+                            if (cc + q < p.cout) atomicAdd(dst + q, __uint_as_float(v[q]));
+                    }
+                }
+        }
+    } else if (tid == 0) {
+        if (p.status) atomicOr(p.status, 2u);  // a bounded wait ran out
+        // the products still in flight, once more, before the accumulator is freed
+        for (int j = nmine - 1; j >= 0 && j >= nmine - NS; --j)
+            wait_bar(bar0 + 8 * (j % NS), (j / NS) & 1);
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(L::TMEM_COLS));
+}
+
+template <int CI, int CO, int KXS, int TP>
+cudaError_t wgrad_tc_T(const WgradParams& p, int pl, cudaStream_t s) {
+    using L = WtSmem<CI, CO, KXS, TP>;
+    static int per_sm = 0;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (per_sm == 0) {
+        int smem = 0;
+        e = cudaFuncSetAttribute(k_wgrad_tc<CI, CO, KXS, TP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e != cudaSuccess) return e;
+        // resident CTAs: shared memory (plus the 1 KB the system keeps per CTA),
+        // TMEM columns, threads
+        int per = smem / (int)(L::bytes + 1024);
+        if (per * L::TMEM_COLS > 512) per = 512 / L::TMEM_COLS;
+        if (per * WT_THREADS > 2048) per = 2048 / WT_THREADS;
+        per_sm = per < 1 ? 1 : per;
+    }
+    const int gx = 3 / KXS;
+    const long long ntiles = (long long)p.B * (p.W >> pl) * (p.H / (TP >> pl));
+    long long split = (long long)sms * per_sm / gx;  // one wave
+    split = split < 1 ? 1 : (split > ntiles ? ntiles : split);
+    return launch_pdl(k_wgrad_tc<CI, CO, KXS, TP>, dim3(gx, (unsigned)split), dim3(WT_THREADS),
+                      L::bytes, s, p, pl);
+}
+
 }  // namespace
+
+// (CI, CO, kx taps per CTA, pixels per tile): three kx per CTA while their
+// accumulators fit the 512 TMEM columns, smaller tiles where a stage of 256
+// pixels would not leave two stages in shared memory
+#define PIC_WT_SHAPES(X)                                                                \
+    X(16, 32, 3, 256) X(32, 32, 3, 256) X(32, 64, 3, 256) X(32, 16, 3, 256)             \
+    X(64, 64, 3, 256) X(64, 32, 3, 256) X(64, 128, 1, 128) X(128, 128, 1, 128)          \
+    X(128, 64, 1, 128)
+
+namespace {
+// log2 of the tile width: 64, 32 or 16 columns, the widest that divides W
+// (-1: none, or the tile rows do not divide H)
+int wt_log2p(const WgradParams& p, int tp) {
+    const int pl = p.W % 64 == 0 ? 6 : (p.W % 32 == 0 ? 5 : (p.W % 16 == 0 ? 4 : -1));
+    if (pl < 0 || p.H % (tp >> pl)) return -1;
+    return pl;
+}
+}  // namespace
+
+bool wgrad_tc_supported(const WgradParams& p, int ci, int co) {
+    if (p.force_tc < 0) return false;
+#define PIC_WT_HAS(A, B, K, T) \
+    if (ci == A && co == B) return wt_log2p(p, T) >= 0;
+    PIC_WT_SHAPES(PIC_WT_HAS)
+#undef PIC_WT_HAS
+    return false;
+}
+
+cudaError_t launch_wgrad_tc(const WgradParams& p, int ci, int co, cudaStream_t s) {
+#define PIC_WT_CASE(A, B, K, T) \
+    if (ci == A && co == B) {                                                       \
+        const int pl = wt_log2p(p, T);                                              \
+        return pl < 0 ? cudaErrorInvalidValue : wgrad_tc_T<A, B, K, T>(p, pl, s);   \
+    }
+    PIC_WT_SHAPES(PIC_WT_CASE)
+#undef PIC_WT_CASE
+    return cudaErrorInvalidValue;
+}
 
 // the (CIN, N, channels per pass) shapes built for the tensor-core path (one
 // pass: two patches and nine taps of weights within 227 KB of shared memory;

@@ -107,12 +107,14 @@ def test_conv_input_gradient_matches_oracle(cin, cout, B, H, W):
     assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("B,H,W", [(2, 16, 32), (1, 8, 128), (3, 16, 16)])
 @pytest.mark.parametrize("cin,cout", [(3, 32), (32, 32), (32, 64), (64, 64), (64, 128),
                                       (128, 128), (128, 64), (64, 32), (32, 3)])
-def test_conv_weight_gradient_matches_oracle(cin, cout):
+def test_conv_weight_gradient_matches_oracle(cin, cout, B, H, W):
+    """Tiles of 64, 32 and 16 columns (the widest dividing W), several tiles
+    per CTA and the circular edge on both axes."""
     import torch
     rng = _rng(cin * 13 + cout)
-    B, H, W = 2, 16, 32
     x = D.bf16(rng.standard_normal((B, H, W, cin)))
     dz = D.bf16(rng.standard_normal((B, H, W, cout)))
     dw = torch.empty((3, 3, cin, cout), dtype=torch.float32, device="cuda")
