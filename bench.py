@@ -66,6 +66,12 @@ WORKLOADS = {
     "denoiser_fwd_2048": dict(kind="denoiser_fwd", kw=dict(nx=2048, ny=2048), tile=16),
     # the same at 1024x1024 (a smaller case of the same kernels, for profiling)
     "denoiser_fwd_1024": dict(kind="denoiser_fwd", kw=dict(nx=1024, ny=1024), tile=16),
+    # one training step of the denoiser (forward, backward through every layer,
+    # Adam) on a batch of synthetic currents: 16 samples of 256x256, the
+    # training batch of the denoiser workload, and one sample of 2048x2048
+    "denoiser_train_256": dict(kind="denoiser_train", kw=dict(nx=256, ny=256, batch=16), tile=16),
+    "denoiser_train_2048": dict(kind="denoiser_train", kw=dict(nx=2048, ny=2048, batch=1),
+                                tile=16),
 }
 
 
@@ -297,6 +303,9 @@ def run_reference(args, rank, world):
     if kind == "denoiser_fwd":
         run_reference_denoiser_fwd(args, world)
         return
+    if kind == "denoiser_train":
+        run_reference_denoiser_train(args, world)
+        return
     w, what = cpu_sample(args.workload)
     cores = os.cpu_count() or 1
     o = oracle_sim(w, cores)
@@ -348,6 +357,119 @@ def run_reference_denoiser_fwd(args, world):
                                    f"{n}x{n} sample"},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}), flush=True)
+
+
+# kernels of one training step: 11 layers' forward, the loss, the input and
+# weight gradients and ReLU backward of each layer, the pooling and upsampling
+# backward, the weight packing and Adam (counted from an ncu launch list of the
+# 256x256 x 16 step; the same layers run at every grid size)
+TRAIN_LAUNCHES = 53
+
+
+def oracle_train_rate(n, steps, warmup=0):
+    """TFLOP/s of the FP64 numpy oracle's loss and gradients (the arithmetic
+    of a training step) on one n x n sample of synthetic currents."""
+    from oracle import denoiser as D
+    from paper_2501_14795_gb300 import denoise as dn
+    rng = np.random.Generator(np.random.PCG64(dn.SEED_DENOISER + 12))
+    x = 0.05 * rng.standard_normal((1, n, n, 3))
+    p = D.init_params(dn.SEED_DENOISER + 7)
+    for _ in range(warmup):
+        D.loss_and_grads(p, x, 0.5 * x)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        D.loss_and_grads(p, x, 0.5 * x)
+    dt = time.perf_counter() - t0
+    return 3 * dn.forward_flops(n, n) * steps / dt / 1e12, dt
+
+
+def run_reference_denoiser_train(args, world):
+    """Reference arm of the training workloads: the FP64 numpy oracle's loss
+    and gradients on a bounded 32x32 sample, in the same unit."""
+    n = 32
+    value, dt = oracle_train_rate(n, args.steps, args.warmup)
+    print(json.dumps({
+        "impl": "reference", "metric": "denoiser training throughput", "value": value,
+        "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: the FP64 numpy oracle's loss and gradients of "
+                                   f"one {n}x{n} sample"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def run_denoiser_train(args, rank, world, local_rank):
+    """Training throughput of the denoiser: K steps (forward, backward through
+    every layer, Adam) on one batch of synthetic currents resident in HBM;
+    each call synchronises, so the CUDA events bracket whole steps.  End to
+    end, the same steps from host buffers (the library stages the batch and
+    returns the loss)."""
+    import torch
+    from paper_2501_14795_gb300 import denoise as dn
+    from paper_2501_14795_gb300 import pic
+
+    torch.cuda.set_device(local_rank)
+    kw = WORKLOADS[args.workload]["kw"]
+    nx, ny, B = kw["nx"], kw["ny"], kw["batch"]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(dn.SEED_DENOISER + 12)
+    jn = 0.05 * torch.randn((B, 3, ny, nx), device="cuda", generator=gen)
+    jc = 0.5 * jn
+    net = pic.Denoiser(nx, ny, B, 0.05)
+    net.set_params(dn.init_params(dn.SEED_DENOISER + 7).astype(np.float32))
+    for _ in range(args.warmup):
+        net.train_step(jn, jc, 1e-4)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            net.train_step(jn, jc, 1e-4)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    jn_h, jc_h = jn.cpu().numpy(), jc.cpu().numpy()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        net.train_step(jn_h, jc_h, 1e-4)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    net.close()
+    ms, e2e_ms = max_over_ranks(ms, e2e_ms)
+    if rank != 0:
+        return
+    flops = 3 * dn.forward_flops(nx, ny, B)
+    achieved = flops / (ms * 1e-3) / 1e12
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak = float(json.load(open(p))["bf16_tflops"]) if os.path.exists(p) else 1900.0
+    line = {
+        "metric": "denoiser training throughput", "value": achieved * world, "unit": "TFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 (accumulate f32)", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": [nx, ny], "batch": B,
+                   "flops_per_step": flops,
+                   "l2": "inputs larger than L2 (the level-0 activations of a batch exceed 129 MB)"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "whole training step (forward, backward, Adam)",
+                     "peak_source": "measured bf16_tflops" if os.path.exists(p) else "fallback"},
+        "e2e": {"value": flops / (e2e_ms * 1e-3) / 1e12 * world, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": jn_h.nbytes + jc_h.nbytes, "d2h_bytes_per_step": 8},
+        "gpu_launches": TRAIN_LAUNCHES * args.steps,
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        n = 32
+        v, _ = oracle_train_rate(n, 2)
+        line["cpu_baseline"] = {"value": v, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                                "sample": f"2 steps of the FP64 numpy oracle's loss and "
+                                          f"gradients on one {n}x{n} sample"}
+    print(json.dumps(line), flush=True)
 
 
 def run_batched(args, rank, world, local_rank):
@@ -844,6 +966,8 @@ def main():
             run_denoiser(args, rank, world, local_rank)
         elif WORKLOADS[args.workload]["kind"] == "denoiser_fwd":
             run_denoiser_fwd(args, rank, world, local_rank)
+        elif WORKLOADS[args.workload]["kind"] == "denoiser_train":
+            run_denoiser_train(args, rank, world, local_rank)
         else:
             run_gpu(args, rank, world, local_rank)
     finally:

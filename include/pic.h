@@ -460,7 +460,10 @@ void pic_denoiser_destroy(pic_denoiser* d);
  *   pic_nn_conv3x3_dgrad: dx (FP32 NHWC, cin channels) = input gradient of
  *     the convolution for the output gradient dz; cin in {32, 64, 128}.
  *   pic_nn_conv3x3_wgrad: dw (FP32 [3][3][cin][cout], overwritten) = weight
- *     gradient; B*H*W a multiple of 64.
+ *     gradient; B*H*W a multiple of 64.  Runs the tcgen05 kernel when W is a
+ *     multiple of 16 and H of its tile height (256 pixels, 128 when cin or
+ *     cout is 128, over the widest of 64, 32, 16 columns that divides W),
+ *     else the mma.sync kernel.
  *   pic_nn_low_k_restore: the denoiser's low-wavenumber restoration on FP32
  *     currents [B][3][H][W]: out <- out + L^passes (raw - out) (B <= 4096,
  *     H <= 65535, B H W <= 2^28; passes 0..PIC_LOW_K_MAX_PASSES); raw and out must not overlap; allocates

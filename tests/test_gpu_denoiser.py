@@ -154,11 +154,14 @@ def _nhwc(J):
     return np.transpose(J, (0, 2, 3, 1)).astype(np.float64)
 
 
-@pytest.mark.parametrize("ny,nx,tc", [(32, 64, False), (32, 256, False), (32, 256, True)])
+@pytest.mark.parametrize("ny,nx,tc", [(32, 64, None), (32, 256, None), (32, 256, "always"),
+                                      (32, 64, "never")])
 def test_network_loss_and_gradients_match_oracle(ny, nx, tc, monkeypatch):
-    """tc: PIC_DENOISER_TC=always puts every 128-wide row layer on the tcgen05 kernel."""
+    """tc: PIC_DENOISER_TC=always puts every 128-wide row layer on the tcgen05
+    kernels, =never keeps every layer (the weight gradients included) on the
+    mma.sync kernels."""
     if tc:
-        monkeypatch.setenv("PIC_DENOISER_TC", "always")
+        monkeypatch.setenv("PIC_DENOISER_TC", tc)
     B, scale = 2, 0.5
     Jn, Jc = _currents(5, B, ny, nx)
     p = _params(41)
