@@ -825,6 +825,298 @@ cudaError_t wgrad_tc_T(const WgradParams& p, int pl, cudaStream_t s) {
                       L::bytes, s, p, pl);
 }
 
+// ------------------------------------------- weight gradient, kx taps in N
+// The same sums with the three kx taps side by side in N.  With q the patch
+// column (the patch spans columns x0 - 1 .. x0 + P of the tile's rows,
+// padded with zeros to QW = P + 16 columns) and dzk[kx] the dz tile shifted
+// right by kx pixels (dz[r][q - kx], zero outside the tile):
+//   D[(ky, ci)][(kx, co)] += sum over q of patch[r + ky][q][ci] dzk[kx][r][q][co]
+// so one MMA of N = 3 CO covers the three kx taps of 16 patch columns, where
+// the first kernel issues one MMA of N = CO per tap: the 128-lane A operand
+// is read from shared memory a third as often.  The padding makes K = P + 16
+// per row instead of P.  dzk is stored [kx][8-channel group][row][column]
+// (N stride R QW 16 B), the patch as in the first kernel with rows of QW
+// pixels.  Tiles are 64 columns wide; a CTA takes the lane chunks CHS of
+// (ky, ci) whose accumulators (CHS 3 CO columns) fit TMEM: all of them, or
+// for 128 input channels one ky per CTA (then it loads only that tap's R
+// patch rows).
+constexpr int WN_P = 64;
+constexpr int WN_QW = WN_P + 16;
+
+template <int CI, int CO, int TP, int CHS>
+struct WnSmem {
+    static constexpr int NG = CI / 8, GO = CO / 8, R = TP / WN_P;
+    static constexpr int NCH = (3 * NG + 15) / 16;
+    static constexpr int N = 3 * CO;
+    static constexpr int CS = WN_QW * 16;   // one row of one channel group
+    static constexpr int RS = NG * CS;      // one patch row
+    // patch rows a CTA loads: every ky, or (CHS = 1, 16 groups a ky) its own
+    static constexpr int NR = CHS == NCH ? R + 2 : R;
+    static constexpr int PATCH = NR * RS;
+    // lanes past the third ky read this many rows below the patch (into the dzk
+    // tile that follows it in the stage)
+    static constexpr int SLACK_ROWS =
+        CHS == NCH && (16 * NCH - 1) / NG > 2 ? (16 * NCH - 1) / NG - 2 : 0;
+    static constexpr int PL = R * WN_QW * 16;   // one (kx, group) plane of dzk
+    static constexpr int DZK = 3 * GO * PL;
+    static constexpr int STAGE = PATCH + DZK;
+    static constexpr int COLS = CHS * N;
+    static constexpr int TMEM_COLS =
+        COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : COLS <= 256 ? 256 : 512;
+    static constexpr int FIX = 64 + 1024;
+    static constexpr bool TWO = 2 * TMEM_COLS <= 512;
+    static constexpr int NSF = (227 * 1024 - 64) / STAGE;
+    static constexpr int NS = TWO && 2 * (3 * STAGE + FIX) <= 228 * 1024   ? 3
+                              : TWO && 2 * (2 * STAGE + FIX) <= 228 * 1024 ? 2
+                              : NSF > 3                                    ? 3
+                                                                           : NSF;
+    static constexpr size_t off_bar = (size_t)NS * STAGE;
+    static constexpr size_t bytes = off_bar + 8 * NS + 16;  // mbarriers + TMEM slot
+    static_assert(NS >= 2 && COLS <= 512 && N <= 256 && SLACK_ROWS * RS <= DZK &&
+                      (CHS == NCH || (CHS == 1 && NG == 16)),
+                  "weight-gradient tile (kx in N) does not fit");
+};
+
+// the zero columns of every stage: patch columns P + 2 .. QW - 1, and the
+// columns of each dzk copy outside kx .. kx + P - 1 (the loads never write them)
+template <int CI, int CO, int TP, int CHS>
+__device__ __forceinline__ void wn_zero(unsigned char* smem, int tid) {
+    using L = WnSmem<CI, CO, TP, CHS>;
+    constexpr int PZ = WN_QW - (WN_P + 2);                 // 14 patch columns a row
+    constexpr int NPZ = L::NR * L::NG * PZ;
+    constexpr int DZ_Z = 16;                                // 16 dzk columns a row and copy
+    constexpr int NDZ = 3 * L::GO * L::R * DZ_Z;
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    for (int st = 0; st < L::NS; ++st) {
+        unsigned char* base = smem + st * L::STAGE;
+        for (int i = tid; i < NPZ; i += WT_THREADS) {
+            const int row = i / (L::NG * PZ), rem = i - row * (L::NG * PZ);
+            const int g = rem / PZ, q = WN_P + 2 + (rem - g * PZ);
+            *reinterpret_cast<uint4*>(base + row * L::RS + g * L::CS + q * 16) = z;
+        }
+        for (int i = tid; i < NDZ; i += WT_THREADS) {
+            const int plane = i / (L::R * DZ_Z), rem = i - plane * (L::R * DZ_Z);
+            const int r = rem / DZ_Z, j = rem - r * DZ_Z;
+            const int kx = plane / L::GO;
+            // columns 0 .. kx - 1 and kx + P .. QW - 1: 16 of them
+            const int q = j < kx ? j : WN_P + j;
+            *reinterpret_cast<uint4*>(base + L::PATCH + plane * L::PL + (r * WN_QW + q) * 16) = z;
+        }
+    }
+}
+
+template <int CI, int CO, int TP, int CHS>
+__device__ __forceinline__ void wn_load(const WgradParams& p, unsigned char* st, long long t, int lo,
+                                        int tid) {
+    using L = WnSmem<CI, CO, TP, CHS>;
+    constexpr int R = L::R;
+    const int tilesx = p.W / WN_P, tpb = tilesx * (p.H / R);
+    const int b = (int)(t / tpb);
+    const int rem = (int)(t - (long long)b * tpb);
+    const int ty = rem / tilesx, tx = rem - ty * tilesx;
+    const int y0 = ty * R, x0 = tx * WN_P;
+    const int sh = p.up ? 1 : 0;
+    const int Hi = p.H >> sh, Wi = p.W >> sh;
+    const bf16* xb = p.x + (size_t)b * Hi * Wi * CI;
+    // patch rows y0 - 1 + lo + j, columns x0 - 1 .. x0 + P
+    constexpr int ROWP = (WN_P + 2) * L::NG;
+    for (int j = 0; j < L::NR; ++j) {
+        const bf16* xr = xb + (size_t)(wrap(y0 - 1 + lo + j, p.H) >> sh) * Wi * CI;
+        unsigned char* dr = st + j * L::RS;
+        for (int i = tid; i < ROWP; i += WT_THREADS) {
+            const int q = i / L::NG, g = i - q * L::NG;
+            cp_async16(dr + g * L::CS + q * 16, xr + (size_t)(wrap(x0 - 1 + q, p.W) >> sh) * CI + g * 8);
+        }
+    }
+    // dzk: tile pixel (r, c) of group g into column c + kx of each copy; the
+    // second and third copies of a piece come from L1
+    unsigned char* sd = st + L::PATCH;
+    const bf16* dzb = p.dz + (((size_t)b * p.H + y0) * p.W + x0) * CO;
+    for (int i = tid; i < TP * L::GO; i += WT_THREADS) {
+        const int k = i / L::GO, g = i - k * L::GO;
+        const int r = k / WN_P, c = k - r * WN_P;
+        const bf16* src = dzb + ((size_t)r * p.W + c) * CO + g * 8;
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(saddr(
+                             sd + (kx * L::GO + g) * L::PL + (r * WN_QW + c + kx) * 16)),
+                         "l"(src)
+                         : "memory");
+    }
+}
+
+// grid (NCH / CHS lane chunks, splits of the tiles)
+template <int CI, int CO, int TP, int CHS>
+__global__ void __launch_bounds__(WT_THREADS) k_wgrad_tcn(const WgradParams p) {
+    using L = WnSmem<CI, CO, TP, CHS>;
+    constexpr int NS = L::NS, R = L::R;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t bar0 = saddr(smem + L::off_bar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::off_bar + 8 * NS);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long ntiles = (long long)p.B * (p.W / WN_P) * (p.H / R);
+    const int h0 = blockIdx.x * CHS;            // first lane chunk of this CTA
+    const int lo = (16 * h0) / L::NG;           // first patch row (relative to y0 - 1)
+    const long long t0 = blockIdx.y, ts = gridDim.y;
+    if (t0 >= ntiles) return;
+    const int nmine = (int)((ntiles - t0 + ts - 1) / ts);
+    pdl_wait();
+    pdl_trigger();
+    if (tid == 0) {
+        for (int k = 0; k < NS; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * k));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         saddr(tslot)),
+                     "r"(L::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    wn_zero<CI, CO, TP, CHS>(smem, tid);
+#pragma unroll
+    for (int k = 0; k < NS - 1; ++k) {
+        if (k < nmine) wn_load<CI, CO, TP, CHS>(p, smem + k * L::STAGE, t0 + k * ts, lo, tid);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    // D f32, A and B bf16, both MN-major, N = 3 CO, M = 128
+    constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                               ((uint32_t)(L::N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    bool ok = true;
+    for (int i = 0; i < nmine; ++i) {
+        const int stg = i % NS;
+        asm volatile("cp.async.wait_group %0;" ::"n"(NS - 2) : "memory");  // tile i landed
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            // start-address offsets in 16-byte units (addresses stay below 256 KB)
+            const uint32_t pa = saddr(smem + stg * L::STAGE), pb = pa + L::PATCH;
+            const uint64_t a0 = smem_desc(pa, 128, L::CS);
+            const uint64_t b0 = smem_desc(pb, 128, L::PL);
+#pragma unroll 1
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int sk = 0; sk < WN_QW / 16; ++sk) {
+                    const uint64_t bd = b0 + (uint64_t)(r * WN_QW + 16 * sk);
+                    const uint32_t accum = (i | r | sk) != 0;
+#pragma unroll
+                    for (int hl = 0; hl < CHS; ++hl) {
+                        const uint64_t ad =
+                            a0 + (uint64_t)(((r - lo) * L::NG + 16 * (h0 + hl)) * WN_QW + 16 * sk);
+                        asm volatile(
+                            "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(
+                                tmem + (uint32_t)(hl * L::N)),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                    }
+                }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    bar0 + 8 * stg));
+        }
+        const int nx = i + NS - 1;
+        if (nx < nmine) {
+            if (i >= 1) {
+                const int j = i - 1;
+                if (ok && !wait_bar(bar0 + 8 * (j % NS), (j / NS) & 1)) ok = false;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
+            wn_load<CI, CO, TP, CHS>(p, smem + (nx % NS) * L::STAGE, t0 + nx * ts, lo, tid);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    for (int j = nmine - 1; j >= 0 && j >= nmine - NS; --j)
+        if (ok && !wait_bar(bar0 + 8 * (j % NS), (j / NS) & 1)) ok = false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ok = __syncthreads_and(ok);
+    if (ok) {
+        const int lq = warp & 3;
+        const int m = 32 * lq + lane;
+        const bool vec = (p.cout & 3) == 0 && ((uintptr_t)p.dw & 15) == 0;
+#pragma unroll 1
+        for (int hl = 0; hl < CHS; ++hl) {
+            const int G = 16 * (h0 + hl) + (m >> 3);
+            const int ky = G / L::NG, ci = (G - ky * L::NG) * 8 + (m & 7);
+            const bool valid = ky < 3 && ci < p.cin;
+#pragma unroll 1
+            for (int cc = 16 * (warp >> 2); cc < L::N; cc += 32) {
+                uint32_t v[16];
+                const uint32_t taddr =
+                    tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(hl * L::N + cc);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,"
+                    "%10,%11,%12,%13,%14,%15}, [%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                      "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                      "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (!valid) continue;
+                const int kx = cc / CO, co = cc - kx * CO;  // a 16-column chunk lies in one kx
+                float* dst = p.dw + ((size_t)(3 * ky + kx) * p.cin + ci) * p.cout + co;
+                if (vec) {
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4)
+                        if (co + q < p.cout)
+                            atomicAdd(reinterpret_cast<float4*>(dst + q),
+                                      make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]),
+                                                  __uint_as_float(v[q + 2]),
+                                                  __uint_as_float(v[q + 3])));
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        if (co + q < p.cout) atomicAdd(dst + q, __uint_as_float(v[q]));
+                }
+            }
+        }
+    } else if (tid == 0) {
+        if (p.status) atomicOr(p.status, 2u);
+        for (int j = nmine - 1; j >= 0 && j >= nmine - NS; --j)
+            wait_bar(bar0 + 8 * (j % NS), (j / NS) & 1);
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(L::TMEM_COLS));
+}
+
+template <int CI, int CO, int TP, int CHS>
+cudaError_t wgrad_tcn_T(const WgradParams& p, cudaStream_t s) {
+    using L = WnSmem<CI, CO, TP, CHS>;
+    static int per_sm = 0;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (per_sm == 0) {
+        int smem = 0;
+        e = cudaFuncSetAttribute(k_wgrad_tcn<CI, CO, TP, CHS>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e != cudaSuccess) return e;
+        int per = smem / (int)(L::bytes + 1024);
+        if (per * L::TMEM_COLS > 512) per = 512 / L::TMEM_COLS;
+        if (per * WT_THREADS > 2048) per = 2048 / WT_THREADS;
+        per_sm = per < 1 ? 1 : per;
+    }
+    const int gx = L::NCH / CHS;
+    const long long ntiles = (long long)p.B * (p.W / WN_P) * (p.H / L::R);
+    long long split = (long long)sms * per_sm / gx;  // one wave
+    split = split < 1 ? 1 : (split > ntiles ? ntiles : split);
+    return launch_pdl(k_wgrad_tcn<CI, CO, TP, CHS>, dim3(gx, (unsigned)split), dim3(WT_THREADS),
+                      L::bytes, s, p);
+}
+
 }  // namespace
 
 // (CI, CO, kx taps per CTA, pixels per tile): three kx per CTA while their
@@ -845,6 +1137,18 @@ int wt_log2p(const WgradParams& p, int tp) {
 }
 }  // namespace
 
+// (CI, CO, pixels per tile, lane chunks per CTA) of the kx-in-N kernel
+// (measured per layer at 256^2 x 16: faster than the first kernel for these
+// four; for 32 -> 32 (where the first kernel keeps two CTAs per SM), 64 -> 64
+// and 32 -> 64 (where the three dz copies and the halo rows of 128-pixel
+// tiles double the copies per pixel) the first kernel is faster)
+#define PIC_WN_SHAPES(X) X(16, 32, 256, 1) X(32, 16, 256, 1) X(64, 32, 128, 2) X(128, 64, 128, 1)
+
+namespace {
+// the kx-in-N kernel: tiles of 64 columns and TP / 64 rows
+bool wn_fits(const WgradParams& p, int tp) { return p.W % WN_P == 0 && p.H % (tp / WN_P) == 0; }
+}  // namespace
+
 bool wgrad_tc_supported(const WgradParams& p, int ci, int co) {
     if (p.force_tc < 0) return false;
 #define PIC_WT_HAS(A, B, K, T) \
@@ -855,6 +1159,10 @@ bool wgrad_tc_supported(const WgradParams& p, int ci, int co) {
 }
 
 cudaError_t launch_wgrad_tc(const WgradParams& p, int ci, int co, cudaStream_t s) {
+#define PIC_WN_CASE(A, B, T, C) \
+    if (ci == A && co == B && wn_fits(p, T)) return wgrad_tcn_T<A, B, T, C>(p, s);
+    PIC_WN_SHAPES(PIC_WN_CASE)
+#undef PIC_WN_CASE
 #define PIC_WT_CASE(A, B, K, T) \
     if (ci == A && co == B) {                                                       \
         const int pl = wt_log2p(p, T);                                              \
