@@ -48,6 +48,8 @@ constexpr LayerSpec kLayers[NL] = {
 };
 
 int pad16(int c) { return (c + 15) / 16 * 16; }
+// c7 and c9 read the coarser level through the 2x upsampling
+bool up_input(int l) { return l == 6 || l == 8; }
 // below this many pixels per forward pass the thin end layers run on the CUDA cores
 constexpr long long kThinPixels = 1LL << 18;
 // output-channel tile of the convolution kernel for a given channel count
@@ -65,7 +67,7 @@ struct pic_denoiser {
     long long boff[NL];
     float *master = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     long long adam_t = 0;
-    bf16 *wf = nullptr, *wd = nullptr;
+    bf16 *wf = nullptr, *wd = nullptr, *wp = nullptr;
     // activations (Bmax samples)
     bf16* xin = nullptr;
     bf16* a[NL] = {};
@@ -119,7 +121,7 @@ void build_table(pic_denoiser* d) {
     PackTable& t = d->tab;
     memset(&t, 0, sizeof t);
     t.n = NL;
-    long long off = 0, wf = 0, wd = 0;
+    long long off = 0, wf = 0, wd = 0, wp = 0;
     for (int l = 0; l < NL; ++l) {
         LayerDesc& L = t.layer[l];
         L.cin = kLayers[l].cin;
@@ -132,6 +134,11 @@ void build_table(pic_denoiser* d) {
         off += L.cout;
         L.wf_off = wf;
         wf += 9LL * L.cout_pad * L.cin_pad;
+        L.wp_off = -1;
+        if (up_input(l)) {
+            L.wp_off = wp;
+            wp += 16LL * L.cout_pad * L.cin_pad;
+        }
         if (l > 0) {  // no input gradient for the first layer
             L.dg_cin_pad = pad16(L.cout);
             L.dg_cout_pad = padct(L.cin);
@@ -145,6 +152,14 @@ void build_table(pic_denoiser* d) {
 long long packed_fwd(const pic_denoiser* d) {
     const LayerDesc& L = d->tab.layer[NL - 1];
     return L.wf_off + 9LL * L.cout_pad * L.cin_pad;
+}
+long long packed_up(const pic_denoiser* d) {
+    long long n = 0;
+    for (int l = 0; l < NL; ++l) {
+        const LayerDesc& L = d->tab.layer[l];
+        if (L.wp_off >= 0) n = L.wp_off + 16LL * L.cout_pad * L.cin_pad;
+    }
+    return n;
 }
 long long packed_dg(const pic_denoiser* d) {
     const LayerDesc& L = d->tab.layer[NL - 1];
@@ -192,6 +207,7 @@ cudaError_t conv(pic_denoiser* d, int l, int B, const bf16* x, int epi, bf16* a_
         return launch_conv(p, L.dg_cin_pad, ctile_for(L.cin, tiles), s);
     }
     p.w = d->wf + L.wf_off;
+    p.wp = (up && L.wp_off >= 0) ? d->wp + L.wp_off : nullptr;
     p.bias = d->master + d->boff[l];
     p.cout = L.cout;
     p.cout_pad = L.cout_pad;
@@ -214,7 +230,8 @@ cudaError_t conv(pic_denoiser* d, int l, int B, const bf16* x, int epi, bf16* a_
 // parameters); the output goes to `fout` in the same layout as out = J * rs +
 // z11 * os.  Returns kernels launched or -1.
 int forward(pic_denoiser* d, int B, const float* J, long long bstride, long long cstride,
-            int pitch, int offset, float* fout, float rs, float os, cudaStream_t s) {
+            int pitch, int offset, float* fout, float rs, float os, cudaStream_t s,
+            bool keep = false) {
     cudaError_t e;
     int n = 0;
     const int H0 = d->H, W0 = d->W, H1 = H0 / 2, W1 = W0 / 2;
@@ -251,12 +268,13 @@ int forward(pic_denoiser* d, int B, const float* J, long long bstride, long long
     FW(launch_pool_fwd(d->a[3], B, H1, W1, 64, d->p2, s));
     FW(conv(d, 4, B, d->p2, EPI_ACT, d->a[4], nullptr, nullptr, nullptr, s));
     FW(conv(d, 5, B, d->a[4], EPI_ACT, d->a[5], nullptr, nullptr, nullptr, s));
-    // c7 and c9 read the coarser level through the fused 2x upsampling
-    FW(conv(d, 6, B, d->a[5], EPI_ACT, d->a[6], d->a[3], d->y7, nullptr, s, nullptr, nullptr, 0,
-            0, 0, 0, 0.f, 0.f, 1));
+    // c7 and c9 read the coarser level through the fused 2x upsampling; their
+    // activations before the skip sum are kept only for a backward pass (keep)
+    FW(conv(d, 6, B, d->a[5], EPI_ACT, keep ? d->a[6] : nullptr, d->a[3], d->y7, nullptr, s,
+            nullptr, nullptr, 0, 0, 0, 0, 0.f, 0.f, 1));
     FW(conv(d, 7, B, d->y7, EPI_ACT, d->a[7], nullptr, nullptr, nullptr, s));
-    FW(conv(d, 8, B, d->a[7], EPI_ACT, d->a[8], d->a[1], d->y9, nullptr, s, nullptr, nullptr, 0,
-            0, 0, 0, 0.f, 0.f, 1));
+    FW(conv(d, 8, B, d->a[7], EPI_ACT, keep ? d->a[8] : nullptr, d->a[1], d->y9, nullptr, s,
+            nullptr, nullptr, 0, 0, 0, 0, 0.f, 0.f, 1));
     FW(conv(d, 9, B, d->y9, EPI_ACT, d->a[9], nullptr, nullptr, nullptr, s));
     if (thin) {
         const LayerDesc& L = d->tab.layer[NL - 1];
@@ -366,7 +384,7 @@ int low_k_chain(int n, int B, int H, int W, const FieldView& raw, const FieldVie
 }
 
 pic_status pack(pic_denoiser* d) {
-    DCK(launch_pack_weights(d->tab, d->master, d->wf, d->wd, d->stream));
+    DCK(launch_pack_weights(d->tab, d->master, d->wf, d->wd, d->stream, d->wp));
     return PIC_OK;
 }
 
@@ -405,7 +423,7 @@ pic_status run_grad(pic_denoiser* d, const float* J_in, const float* J_t, int ba
     if (st != PIC_OK) return st;
     const long long HW = (long long)d->H * d->W;
     if (forward(d, batch, in, 3 * HW, HW, d->W, 0, d->out, (float)(1.0 / d->scale), 1.f,
-                d->stream) < 0)
+                d->stream, true) < 0)
         return PIC_ECUDA;
     if (backward(d, batch, tg, d->stream) < 0) return PIC_ECUDA;
     if (loss) {
@@ -555,6 +573,7 @@ pic_status pic_denoiser_create(int nx, int ny, int batch_max, double scale, void
     A(&d->v, d->np);
     A(&d->wf, packed_fwd(d));
     A(&d->wd, packed_dg(d));
+    A(&d->wp, packed_up(d));
     A(&d->xin, P0 * 16);
     const long long lvl[3] = {P0, P1, P2};
     for (int l = 0; l < NL - 1; ++l) A(&d->a[l], lvl[kLayers[l].level] * kLayers[l].cout);
@@ -579,7 +598,8 @@ pic_status pic_denoiser_create(int nx, int ny, int batch_max, double scale, void
     if (e == cudaSuccess) e = cudaMemsetAsync(d->master, 0, sizeof(float) * d->np, d->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d->m, 0, sizeof(float) * d->np, d->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d->v, 0, sizeof(float) * d->np, d->stream);
-    if (e == cudaSuccess) e = launch_pack_weights(d->tab, d->master, d->wf, d->wd, d->stream);
+    if (e == cudaSuccess)
+        e = launch_pack_weights(d->tab, d->master, d->wf, d->wd, d->stream, d->wp);
     if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
     if (e != cudaSuccess) {
         pic_denoiser_destroy(d);

@@ -28,10 +28,13 @@ struct ConvParams {
     int B, H, W;             // output (and, without up, input) size
     int up;                  // x is H/2 x W/2, read at (y/2, x/2): fused 2x upsampling
     const __nv_bfloat16* w;  // packed [9][cout_pad][CIN]
+    const __nv_bfloat16* wp; // with up: the sixteen combined taps of the four output
+                             // parities, packed [16][cout_pad][CIN] (null: not packed)
     const float* bias;       // [cout] or null
     int cout, cout_pad;
     int epi, relu;
     // EPI_ACT: a_out = bf16(relu(z + bias)); with skip: y_out = bf16(a + skip)
+    // (a_out may then be null: the activation is kept only for a backward pass)
     __nv_bfloat16* a_out;
     const __nv_bfloat16* skip;
     __nv_bfloat16* y_out;
@@ -80,6 +83,8 @@ struct LayerDesc {
     int dg_cin_pad, dg_cout_pad;  // input-gradient GEMM: k = cout padded to 16, n = cin (0: none)
     long long woff;           // weights in the master vector ([9][cin][cout], then bias)
     long long wf_off, wd_off; // packed bfloat16 arrays
+    long long wp_off;         // combined taps of an upsampling layer ([16][cout_pad][cin_pad];
+                              // -1: none)
 };
 
 constexpr int MAX_LAYERS = 16;
@@ -129,6 +134,9 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 cudaError_t launch_conv(const ConvParams& p, int cin, int ct, cudaStream_t s);
 bool conv_tc_supported(const ConvParams& p, int cin);
 cudaError_t launch_conv_tc(const ConvParams& p, int cin, cudaStream_t s);
+// a 3x3 convolution of a 2x upsampled input as four 2x2 convolutions (tcgen05)
+bool conv_up_tc_supported(const ConvParams& p, int cin);
+cudaError_t launch_conv_up_tc(const ConvParams& p, int cin, cudaStream_t s);
 cudaError_t init_tc_kernels();
 // weight gradient on the tensor cores (ci, co: padded channel counts)
 bool wgrad_tc_supported(const WgradParams& p, int ci, int co);
@@ -175,8 +183,11 @@ cudaError_t launch_field_copy(const FieldView& a, const FieldView& o, int B, int
 cudaError_t launch_field_copy_tab(const FieldView& a, const float* const* atab, const FieldView& o,
                                   float* const* otab, const FieldView& o2, int B, int H, int W,
                                   cudaStream_t s);
+// bfloat16 packings of the master weights: wf (forward), wd (input
+// gradient), and wp (the combined taps of the layers with wp_off >= 0); a
+// null array is skipped
 cudaError_t launch_pack_weights(const PackTable& t, const float* master, __nv_bfloat16* wf,
-                                __nv_bfloat16* wd, cudaStream_t s);
+                                __nv_bfloat16* wd, cudaStream_t s, __nv_bfloat16* wp = nullptr);
 
 }  // namespace nn
 }  // namespace pic

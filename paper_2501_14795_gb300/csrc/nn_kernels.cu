@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv(const ConvParams p) {
                     v1 = fmaxf(v1, 0.f);
                 }
                 const __nv_bfloat162 a2 = __floats2bfloat162_rn(v0, v1);
-                *reinterpret_cast<__nv_bfloat162*>(p.a_out + pix * p.cout_pad + co) = a2;
+                if (p.a_out) *reinterpret_cast<__nv_bfloat162*>(p.a_out + pix * p.cout_pad + co) = a2;
                 if (p.skip) {
                     const __nv_bfloat162 s2 =
                         *reinterpret_cast<const __nv_bfloat162*>(p.skip + pix * p.cout_pad + co);
@@ -842,16 +842,36 @@ __global__ void k_adam(float* p, const float* g, float* m, float* v, long long n
 
 // master FP32 weights [tap][ci][co] -> bfloat16 forward [tap][co_pad][ci_pad]
 // and input-gradient [tap'][ci_padn][co_pad16] layouts (tap' = 8 - tap)
-__global__ void k_pack_weights(const PackTable t, const float* master, bf16* wf, bf16* wd) {
+__global__ void k_pack_weights(const PackTable t, const float* master, bf16* wf, bf16* wd,
+                               bf16* wp) {
     const int l = blockIdx.y;
     if (l >= t.n) return;
     const LayerDesc& d = t.layer[l];
-    const long long nf = 9LL * d.cout_pad * d.cin_pad;
-    const long long nd = 9LL * d.dg_cout_pad * d.dg_cin_pad;
+    const long long nf = wf ? 9LL * d.cout_pad * d.cin_pad : 0;
+    const long long nd = wd ? 9LL * d.dg_cout_pad * d.dg_cin_pad : 0;
+    const long long np = (wp && d.wp_off >= 0) ? 16LL * d.cout_pad * d.cin_pad : 0;
     const float* w = master + d.woff;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nf + nd;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nf + nd + np;
          i += (long long)gridDim.x * blockDim.x) {
-        if (i < nf) {
+        if (i >= nf + nd) {
+            // combined tap t = parity (a, b) x (u, v) of an upsampling layer: the
+            // sum of the 3x3 taps (dy, dx) whose upsampled row and column land
+            // on x pixel (i + u, j + v) for an output pixel of parity (a, b)
+            const long long k = i - nf - nd;
+            const int ci = (int)(k % d.cin_pad);
+            const long long r = k / d.cin_pad;
+            const int co = (int)(r % d.cout_pad), tp = (int)(r / d.cout_pad);
+            const int a = tp >> 3, b = (tp >> 2) & 1, uu = (tp >> 1) & 1, vv = tp & 1;
+            // offsets dy in [ylo, yhi] (a = 0: {-1}, {0, 1}; a = 1: {-1, 0}, {1})
+            const int ylo = uu == 0 ? -1 : (a == 0 ? 0 : 1), yhi = uu == 0 ? (a == 0 ? -1 : 0) : 1;
+            const int xlo = vv == 0 ? -1 : (b == 0 ? 0 : 1), xhi = vv == 0 ? (b == 0 ? -1 : 0) : 1;
+            float v = 0.f;
+            if (ci < d.cin && co < d.cout)
+                for (int dy = ylo; dy <= yhi; ++dy)
+                    for (int dx = xlo; dx <= xhi; ++dx)
+                        v += w[((long long)((dy + 1) * 3 + dx + 1) * d.cin + ci) * d.cout + co];
+            wp[d.wp_off + k] = __float2bfloat16_rn(v);
+        } else if (i < nf) {
             const int ci = (int)(i % d.cin_pad);
             const long long r = i / d.cin_pad;
             const int co = (int)(r % d.cout_pad), tap = (int)(r / d.cout_pad);
@@ -952,6 +972,7 @@ cudaError_t init_kernels() {
 // would not fit in shared memory.
 cudaError_t launch_conv(const ConvParams& p, int cin, int ct, cudaStream_t s) {
     if (p.H % TH || p.W % TW || p.cout_pad % ct) return cudaErrorInvalidValue;
+    if (conv_up_tc_supported(p, cin)) return launch_conv_up_tc(p, cin, s);
     if (conv_tc_supported(p, cin)) return launch_conv_tc(p, cin, s);
     if (cin == 128 && ct == 64) ct = 32;
     // the decoder's upsampling layers (c7: 128 -> 64, c9: 64 -> 32) read
@@ -1117,8 +1138,8 @@ cudaError_t launch_field_copy(const FieldView& a, const FieldView& o, int B, int
 }
 
 cudaError_t launch_pack_weights(const PackTable& t, const float* master, __nv_bfloat16* wf,
-                                __nv_bfloat16* wd, cudaStream_t s) {
-    k_pack_weights<<<dim3(64, t.n), 256, 0, s>>>(t, master, wf, wd);
+                                __nv_bfloat16* wd, cudaStream_t s, __nv_bfloat16* wp) {
+    k_pack_weights<<<dim3(64, t.n), 256, 0, s>>>(t, master, wf, wd, wp);
     return cudaGetLastError();
 }
 

@@ -155,16 +155,13 @@ __device__ __forceinline__ void load_patch(const ConvParams& p, unsigned char* s
 
 // the epilogues on one accumulator (row rr of unit seg): TMEM lane = pixel
 // x0 + lane of the row, column = output channel
+// (b, y, x): the output pixel of this thread's TMEM lane
 template <int NT>
-__device__ __forceinline__ void epilogue(const ConvParams& p, const float* sBias, uint32_t acc,
-                                         int seg, int rr, int warp, int lane, int co0) {
+__device__ __forceinline__ void epilogue_at(const ConvParams& p, const float* sBias, uint32_t acc,
+                                            int b, int y, int x, int warp, int lane, int co0) {
     // warps w and w + 4 read TMEM lanes 32 (w % 4)..+31: the first and the
     // second half of the 16-column chunks
     const int lg = warp & 3, half = warp >> 2;
-    const int segs = p.W / TC_M, rows = p.H / TC_R;
-    const int x = (seg % segs) * TC_M + 32 * lg + lane;
-    const int y = ((seg / segs) % rows) * TC_R + rr;
-    const int b = seg / (segs * rows);
     const size_t pix = ((size_t)b * p.H + y) * p.W + x;
 #pragma unroll 1
     for (int c0 = 16 * half; c0 < NT; c0 += 32) {
@@ -210,9 +207,11 @@ __device__ __forceinline__ void epilogue(const ConvParams& p, const float* sBias
         __align__(16) __nv_bfloat162 a2[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) a2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-        uint4* ao = reinterpret_cast<uint4*>(p.a_out + pix * p.cout_pad + cg);
-        ao[0] = reinterpret_cast<const uint4*>(a2)[0];
-        ao[1] = reinterpret_cast<const uint4*>(a2)[1];
+        if (p.a_out) {
+            uint4* ao = reinterpret_cast<uint4*>(p.a_out + pix * p.cout_pad + cg);
+            ao[0] = reinterpret_cast<const uint4*>(a2)[0];
+            ao[1] = reinterpret_cast<const uint4*>(a2)[1];
+        }
         if (p.skip) {
             const uint4* sk = reinterpret_cast<const uint4*>(p.skip + pix * p.cout_pad + cg);
             __align__(16) uint4 sv[2] = {sk[0], sk[1]};
@@ -228,6 +227,17 @@ __device__ __forceinline__ void epilogue(const ConvParams& p, const float* sBias
             yo[1] = reinterpret_cast<const uint4*>(y2)[1];
         }
     }
+}
+
+// row rr of work unit seg (TC_R rows of TC_M pixels): lane = pixel x0 + lane
+template <int NT>
+__device__ __forceinline__ void epilogue(const ConvParams& p, const float* sBias, uint32_t acc,
+                                         int seg, int rr, int warp, int lane, int co0) {
+    const int segs = p.W / TC_M, rows = p.H / TC_R;
+    const int x = (seg % segs) * TC_M + 32 * (warp & 3) + lane;
+    const int y = ((seg / segs) % rows) * TC_R + rr;
+    const int b = seg / (segs * rows);
+    epilogue_at<NT>(p, sBias, acc, b, y, x, warp, lane, co0);
 }
 
 // Persistent: the CTA keeps the nine taps' weights in shared memory and runs
@@ -554,6 +564,291 @@ cudaError_t conv_tc_T(const ConvParams& p, cudaStream_t s) {
     int gx = tc_grid_cap<CIN, NT, KC>() / ntile;
     gx = gx < 1 ? 1 : (gx > nseg ? nseg : gx);
     return launch_pdl(S::kernel(), dim3(gx, ntile), dim3(TC_THREADS), S::bytes, s, p);
+}
+
+// ------------------------------------------- convolution of a 2x upsampled input
+// A 3x3 convolution of the nearest-neighbour 2x upsampling of x is, for each
+// parity (a, b) of the output pixel (2i + a, 2j + b), a 2x2 convolution of x
+// itself: output row offsets dy -1, 0, 1 land on x rows i + floor((a + dy) / 2),
+// so the taps that land on the same x pixel add their weights
+// (a = 0: dy = -1 -> i - 1, dy = 0, 1 -> i; a = 1: dy = -1, 0 -> i, dy = 1 ->
+// i + 1; the same for columns).  Sixteen combined taps (four parities x 2x2,
+// summed in FP32 from the master weights, then rounded to bfloat16 once)
+// replace nine taps on a grid four times larger: 4/9 of the products.  A work
+// unit is a row segment of 128 x pixels (row i, columns j0 ..); its patch is
+// x rows i - 1 .. i + 1, columns j0 - 1 .. j0 + 128, and it has four
+// accumulators, one per parity, whose lanes m are the output pixels
+// (2i + a, 2 (j0 + m) + b).  Otherwise as k_conv_tc: persistent, weights
+// resident, two patches and two sets of accumulators in flight.
+constexpr int UP_PR = 3;                 // patch rows
+constexpr int UP_PW = TC_M + 2;          // patch columns
+
+template <int CIN, int NT>
+struct UpSmem {
+    static constexpr int KG = CIN / 8;
+    static constexpr int PPLANE = UP_PR * UP_PW * 16;
+    static constexpr int PATCH = KG * PPLANE;
+    static constexpr int WPLANE = NT * 16;
+    static constexpr int WTAP = KG * WPLANE;
+    static constexpr size_t off_w = 2 * (size_t)PATCH;
+    static constexpr size_t off_bias = off_w + 16 * (size_t)WTAP;
+    static constexpr size_t off_bar = (off_bias + NT * 4 + 15) & ~(size_t)15;
+    static constexpr size_t bytes = off_bar + 32;
+    static constexpr int NTC = NT < 32 ? 32 : NT;
+    static constexpr int TMEM_COLS = 2 * 4 * NTC;   // two units of four parities
+    static_assert(bytes <= 227 * 1024 && TMEM_COLS <= 512, "upsampling tile does not fit");
+};
+
+template <int CIN, int NT>
+__device__ __forceinline__ void load_patch_up(const ConvParams& p, unsigned char* sP, int seg,
+                                              int tid) {
+    using L = UpSmem<CIN, NT>;
+    const int Hi = p.H >> 1, Wi = p.W >> 1;
+    const int segs = Wi / TC_M;
+    const int j0 = (seg % segs) * TC_M;
+    const int i = (seg / segs) % Hi;
+    const int b = seg / (segs * Hi);
+    for (int pix = tid; pix < UP_PR * UP_PW; pix += TC_THREADS) {
+        const int r = pix / UP_PW, q = pix - r * UP_PW;
+        const int ys = wrap(i - 1 + r, Hi), xs = wrap(j0 - 1 + q, Wi);
+        const bf16* src = p.x + (((size_t)b * Hi + ys) * Wi + xs) * CIN;
+        unsigned char* dst = sP + pix * 16;
+#pragma unroll
+        for (int kg = 0; kg < L::KG; ++kg) cp_async16(dst + kg * L::PPLANE, src + kg * 8);
+    }
+}
+
+// the four parities' results of unit seg (accumulators acc0 + parity NTC):
+// bf16(relu(z + bias)) and, with a skip, bf16(a + skip).  The skip values
+// and the four accumulators' columns are all requested before the first
+// store, so their latencies overlap instead of adding up per parity.
+template <int CIN, int NT>
+__device__ __forceinline__ void epilogue_up(const ConvParams& p, const float* sBias, uint32_t acc0,
+                                            int seg, int warp, int lane, int co0) {
+    using L = UpSmem<CIN, NT>;
+    const int Hi = p.H >> 1, Wi = p.W >> 1;
+    const int segs = Wi / TC_M;
+    const int lg = warp & 3, half = warp >> 2;
+    const int j = (seg % segs) * TC_M + 32 * lg + lane;
+    const int i = (seg / segs) % Hi;
+    const int b = seg / (segs * Hi);
+#pragma unroll 1
+    for (int c0 = 16 * half; c0 < NT; c0 += 32) {
+        if (co0 + c0 >= p.cout_pad) continue;  // uniform over the warp
+        const int cg = co0 + c0;
+        size_t pix[4];
+#pragma unroll
+        for (int ph = 0; ph < 4; ++ph)
+            pix[ph] = ((size_t)b * p.H + 2 * i + (ph >> 1)) * p.W + 2 * j + (ph & 1);
+        uint4 sk[4][2];
+        if (p.skip) {
+#pragma unroll
+            for (int ph = 0; ph < 4; ++ph) {
+                const uint4* src = reinterpret_cast<const uint4*>(p.skip + pix[ph] * p.cout_pad + cg);
+                sk[ph][0] = src[0];
+                sk[ph][1] = src[1];
+            }
+        }
+        uint32_t r[4][16];
+#pragma unroll
+        for (int ph = 0; ph < 4; ++ph) {
+            const uint32_t taddr = acc0 + ph * L::NTC + ((uint32_t)(32 * lg) << 16) + c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+                "%12,%13,%14,%15}, [%16];"
+                : "=r"(r[ph][0]), "=r"(r[ph][1]), "=r"(r[ph][2]), "=r"(r[ph][3]), "=r"(r[ph][4]),
+                  "=r"(r[ph][5]), "=r"(r[ph][6]), "=r"(r[ph][7]), "=r"(r[ph][8]), "=r"(r[ph][9]),
+                  "=r"(r[ph][10]), "=r"(r[ph][11]), "=r"(r[ph][12]), "=r"(r[ph][13]),
+                  "=r"(r[ph][14]), "=r"(r[ph][15])
+                : "r"(taddr));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int ph = 0; ph < 4; ++ph) {
+            float v[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                v[q] = __uint_as_float(r[ph][q]) + sBias[c0 + q];
+                if (p.relu) v[q] = fmaxf(v[q], 0.f);
+            }
+            __align__(16) __nv_bfloat162 a2[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) a2[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+            if (p.a_out) {
+                uint4* ao = reinterpret_cast<uint4*>(p.a_out + pix[ph] * p.cout_pad + cg);
+                ao[0] = reinterpret_cast<const uint4*>(a2)[0];
+                ao[1] = reinterpret_cast<const uint4*>(a2)[1];
+            }
+            if (p.skip) {
+                const __nv_bfloat162* s2 = reinterpret_cast<const __nv_bfloat162*>(sk[ph]);
+                __align__(16) __nv_bfloat162 y2[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float2 af = __bfloat1622float2(a2[q]), sf = __bfloat1622float2(s2[q]);
+                    y2[q] = __floats2bfloat162_rn(af.x + sf.x, af.y + sf.y);
+                }
+                uint4* yo = reinterpret_cast<uint4*>(p.y_out + pix[ph] * p.cout_pad + cg);
+                yo[0] = reinterpret_cast<const uint4*>(y2)[0];
+                yo[1] = reinterpret_cast<const uint4*>(y2)[1];
+            }
+        }
+    }
+}
+
+// p.w: the sixteen combined taps, packed [parity][u][v][cout_pad][CIN]
+template <int CIN, int NT>
+__global__ void __launch_bounds__(TC_THREADS) k_conv_up_tc(const ConvParams p) {
+    using L = UpSmem<CIN, NT>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sW = smem + L::off_w;
+    float* sBias = reinterpret_cast<float*>(smem + L::off_bias);
+    const uint32_t bar0 = saddr(smem + L::off_bar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::off_bar + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nseg = p.B * (p.H >> 1) * ((p.W >> 1) / TC_M);
+    if ((int)blockIdx.x >= nseg) return;
+    const int co0 = blockIdx.y * NT;
+    for (int idx = tid; idx < 16 * NT * L::KG; idx += TC_THREADS) {
+        const int kg = idx % L::KG;
+        const int rn = idx / L::KG;
+        const int n = rn % NT, tap = rn / NT;
+        unsigned char* dst = sW + tap * L::WTAP + kg * L::WPLANE + n * 16;
+        if (co0 + n < p.cout_pad)
+            cp_async16(dst, p.wp + ((size_t)tap * p.cout_pad + co0 + n) * CIN + kg * 8);
+        else
+            *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int c = tid; c < NT; c += TC_THREADS)
+        sBias[c] = (p.bias && co0 + c < p.cout) ? p.bias[co0 + c] : 0.f;
+    pdl_wait();
+    pdl_trigger();
+    load_patch_up<CIN, NT>(p, smem, blockIdx.x, tid);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         saddr(tslot)),
+                     "r"(L::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
+                               ((uint32_t)(TC_M >> 4) << 24);
+    bool ok = true;
+    int it = 0, prev = -1;
+    for (int seg = blockIdx.x; seg < nseg; seg += gridDim.x, ++it) {
+        const int buf = it & 1;
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint32_t pa = saddr(smem + buf * L::PATCH), pw = saddr(sW);
+#pragma unroll 1
+            for (int ph = 0; ph < 4; ++ph) {
+                const int a = ph >> 1, bp = ph & 1;
+                const uint32_t acc = tmem + (buf * 4 + ph) * L::NTC;
+#pragma unroll
+                for (int t4 = 0; t4 < 4; ++t4) {
+                    // patch row 1 + u, column 1 + v (u, v = offsets of the x pixel)
+                    const int u = a - 1 + (t4 >> 1), v = bp - 1 + (t4 & 1);
+                    const int tap = ph * 4 + t4;
+#pragma unroll
+                    for (int kc = 0; kc < CIN / 16; ++kc) {
+                        const uint64_t bd =
+                            smem_desc(pw + tap * L::WTAP + (2 * kc) * L::WPLANE, L::WPLANE, 128);
+                        const uint64_t ad = smem_desc(
+                            pa + (2 * kc) * L::PPLANE + ((1 + u) * UP_PW + 1 + v) * 16, L::PPLANE, 128);
+                        const uint32_t accum = (t4 | kc) != 0;
+                        asm volatile(
+                            "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(acc),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                    }
+                }
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    bar0 + 8 * buf));
+        }
+        if (prev >= 0) {
+            const int pb = (it - 1) & 1;
+            if (ok && !wait_bar(bar0 + 8 * pb, ((it - 1) >> 1) & 1)) ok = false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+        const int nxt = seg + gridDim.x;
+        if (nxt < nseg) load_patch_up<CIN, NT>(p, smem + (buf ^ 1) * L::PATCH, nxt, tid);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        if (prev >= 0 && ok)
+            epilogue_up<CIN, NT>(p, sBias, tmem + ((it - 1) & 1) * 4 * L::NTC, prev, warp, lane, co0);
+        prev = seg;
+    }
+    if (prev >= 0) {
+        const int pb = (it - 1) & 1;
+        if (ok && !wait_bar(bar0 + 8 * pb, ((it - 1) >> 1) & 1)) ok = false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok) epilogue_up<CIN, NT>(p, sBias, tmem + pb * 4 * L::NTC, prev, warp, lane, co0);
+    }
+    if (!ok && tid == 0) {
+        if (p.status) atomicOr(p.status, 2u);
+        for (int j = it - 1; j >= 0 && j >= it - 2; --j) wait_bar(bar0 + 8 * (j & 1), (j >> 1) & 1);
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(L::TMEM_COLS));
+}
+
+template <int CIN, int NT>
+int& up_grid_cap() {
+    static int cap = 0;
+    return cap;
+}
+
+// the attribute and the grid cap (one CTA per SM: the patches and sixteen taps
+// take most of the shared memory), once per shape before any graph capture
+template <int CIN, int NT>
+cudaError_t up_prepare() {
+    using L = UpSmem<CIN, NT>;
+    if (up_grid_cap<CIN, NT>()) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_conv_up_tc<CIN, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, smem = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    if ((e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) !=
+        cudaSuccess)
+        return e;
+    int per = smem / (int)(L::bytes + 1024);
+    per = per < 1 ? 1 : per;
+    if (per * L::TMEM_COLS > 512) per = 512 / L::TMEM_COLS;
+    up_grid_cap<CIN, NT>() = sms * per;
+    return cudaSuccess;
+}
+
+template <int CIN, int NT>
+cudaError_t conv_up_tc_T(const ConvParams& p, cudaStream_t s) {
+    using L = UpSmem<CIN, NT>;
+    cudaError_t e = up_prepare<CIN, NT>();
+    if (e != cudaSuccess) return e;
+    const int nseg = p.B * (p.H >> 1) * ((p.W >> 1) / TC_M);
+    const int ntile = (p.cout_pad + NT - 1) / NT;
+    int gx = up_grid_cap<CIN, NT>() / ntile;
+    gx = gx < 1 ? 1 : (gx > nseg ? nseg : gx);
+    return launch_pdl(k_conv_up_tc<CIN, NT>, dim3(gx, ntile), dim3(TC_THREADS), L::bytes, s, p);
 }
 
 // ------------------------------------------------------------ weight gradient
@@ -1210,12 +1505,41 @@ cudaError_t launch_conv_tc(const ConvParams& p, int cin, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
+// (CIN, N) shapes of the upsampling convolution: c9 (64 -> 32); c7's 128
+// input channels would need its sixteen taps streamed through shared memory
+#define PIC_UP_SHAPES(X) X(64, 32)
+
+bool conv_up_tc_supported(const ConvParams& p, int cin) {
+    if (!p.up || !p.wp || p.force_tc < 0 || p.epi != EPI_ACT) return false;
+    if (p.H % 2 || (p.W >> 1) % TC_M || p.cout_pad > 128) return false;
+    // the nine-tap kernel's size rule (in its work units of TC_R x TC_M pixels)
+    if ((long long)p.B * (p.H / TC_R) * (p.W / TC_M) < 600 && p.force_tc <= 0) return false;
+    const int nt = tc_nt(p.cout_pad);
+#define PIC_UP_HAS(A, B) if (cin == A && nt == B) return true;
+    PIC_UP_SHAPES(PIC_UP_HAS)
+#undef PIC_UP_HAS
+    return false;
+}
+
+cudaError_t launch_conv_up_tc(const ConvParams& p, int cin, cudaStream_t s) {
+    const int nt = tc_nt(p.cout_pad);
+#define PIC_UP_CASE(A, B) \
+    if (cin == A && nt == B) return conv_up_tc_T<A, B>(p, s);
+    PIC_UP_SHAPES(PIC_UP_CASE)
+#undef PIC_UP_CASE
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t init_tc_kernels() {
     cudaError_t e = cudaSuccess;
 #define PIC_TC_PREP(A, B, C) \
     if (e == cudaSuccess) e = tc_prepare<A, B, C>();
     PIC_TC_SHAPES(PIC_TC_PREP)
 #undef PIC_TC_PREP
+#define PIC_UP_PREP(A, B) \
+    if (e == cudaSuccess) e = up_prepare<A, B>();
+    PIC_UP_SHAPES(PIC_UP_PREP)
+#undef PIC_UP_PREP
     return e;
 }
 
