@@ -583,11 +583,12 @@ cudaError_t conv_tc_T(const ConvParams& p, cudaStream_t s) {
 constexpr int UP_PR = 3;                 // patch rows
 constexpr int UP_PW = TC_M + 2;          // patch columns
 
-template <int CIN, int NT>
+template <int CIN, int NT, int KC>
 struct UpSmem {
-    static constexpr int KG = CIN / 8;
+    static constexpr int KG = CIN / 8;      // k-groups of the weights
+    static constexpr int KGC = KC / 8;      // k-groups of one patch (one pass over KC channels)
     static constexpr int PPLANE = UP_PR * UP_PW * 16;
-    static constexpr int PATCH = KG * PPLANE;
+    static constexpr int PATCH = KGC * PPLANE;
     static constexpr int WPLANE = NT * 16;
     static constexpr int WTAP = KG * WPLANE;
     static constexpr size_t off_w = 2 * (size_t)PATCH;
@@ -599,10 +600,11 @@ struct UpSmem {
     static_assert(bytes <= 227 * 1024 && TMEM_COLS <= 512, "upsampling tile does not fit");
 };
 
-template <int CIN, int NT>
+// channels c0 .. c0 + KC - 1 of unit seg's patch
+template <int CIN, int NT, int KC>
 __device__ __forceinline__ void load_patch_up(const ConvParams& p, unsigned char* sP, int seg,
-                                              int tid) {
-    using L = UpSmem<CIN, NT>;
+                                              int c0, int tid) {
+    using L = UpSmem<CIN, NT, KC>;
     const int Hi = p.H >> 1, Wi = p.W >> 1;
     const int segs = Wi / TC_M;
     const int j0 = (seg % segs) * TC_M;
@@ -611,10 +613,10 @@ __device__ __forceinline__ void load_patch_up(const ConvParams& p, unsigned char
     for (int pix = tid; pix < UP_PR * UP_PW; pix += TC_THREADS) {
         const int r = pix / UP_PW, q = pix - r * UP_PW;
         const int ys = wrap(i - 1 + r, Hi), xs = wrap(j0 - 1 + q, Wi);
-        const bf16* src = p.x + (((size_t)b * Hi + ys) * Wi + xs) * CIN;
+        const bf16* src = p.x + (((size_t)b * Hi + ys) * Wi + xs) * CIN + c0;
         unsigned char* dst = sP + pix * 16;
 #pragma unroll
-        for (int kg = 0; kg < L::KG; ++kg) cp_async16(dst + kg * L::PPLANE, src + kg * 8);
+        for (int kg = 0; kg < L::KGC; ++kg) cp_async16(dst + kg * L::PPLANE, src + kg * 8);
     }
 }
 
@@ -622,10 +624,9 @@ __device__ __forceinline__ void load_patch_up(const ConvParams& p, unsigned char
 // bf16(relu(z + bias)) and, with a skip, bf16(a + skip).  The skip values
 // and the four accumulators' columns are all requested before the first
 // store, so their latencies overlap instead of adding up per parity.
-template <int CIN, int NT>
+template <int NTC, int NT>
 __device__ __forceinline__ void epilogue_up(const ConvParams& p, const float* sBias, uint32_t acc0,
                                             int seg, int warp, int lane, int co0) {
-    using L = UpSmem<CIN, NT>;
     const int Hi = p.H >> 1, Wi = p.W >> 1;
     const int segs = Wi / TC_M;
     const int lg = warp & 3, half = warp >> 2;
@@ -652,7 +653,7 @@ __device__ __forceinline__ void epilogue_up(const ConvParams& p, const float* sB
         uint32_t r[4][16];
 #pragma unroll
         for (int ph = 0; ph < 4; ++ph) {
-            const uint32_t taddr = acc0 + ph * L::NTC + ((uint32_t)(32 * lg) << 16) + c0;
+            const uint32_t taddr = acc0 + ph * NTC + ((uint32_t)(32 * lg) << 16) + c0;
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
                 "%12,%13,%14,%15}, [%16];"
@@ -695,10 +696,17 @@ __device__ __forceinline__ void epilogue_up(const ConvParams& p, const float* sB
     }
 }
 
-// p.w: the sixteen combined taps, packed [parity][u][v][cout_pad][CIN]
-template <int CIN, int NT>
+// p.wp: the sixteen combined taps, packed [parity][u][v][cout_pad][CIN].
+// Passes of KC input channels (CIN / KC per unit) through two patches, as in
+// k_conv_tc_kc: chunk g (unit g / NCH, channels (g % NCH) KC ...) goes to
+// patch g & 1, its products to the unit's four accumulators (unit & 1),
+// committed on mbarrier g & 1; while the tensor cores multiply chunk g the
+// CTA waits for chunk g - 1, loads chunk g + 1 and, at a unit's first chunk,
+// stores the previous unit's results.
+template <int CIN, int NT, int KC>
 __global__ void __launch_bounds__(TC_THREADS) k_conv_up_tc(const ConvParams p) {
-    using L = UpSmem<CIN, NT>;
+    using L = UpSmem<CIN, NT, KC>;
+    constexpr int NCH = CIN / KC;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sW = smem + L::off_w;
     float* sBias = reinterpret_cast<float*>(smem + L::off_bias);
@@ -708,6 +716,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_up_tc(const ConvParams p) {
     const int nseg = p.B * (p.H >> 1) * ((p.W >> 1) / TC_M);
     if ((int)blockIdx.x >= nseg) return;
     const int co0 = blockIdx.y * NT;
+    const int nunit = (nseg - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int nchunk = nunit * NCH;
+    auto seg_of = [&](int u) { return (int)blockIdx.x + u * (int)gridDim.x; };
     for (int idx = tid; idx < 16 * NT * L::KG; idx += TC_THREADS) {
         const int kg = idx % L::KG;
         const int rn = idx / L::KG;
@@ -722,7 +733,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_up_tc(const ConvParams p) {
         sBias[c] = (p.bias && co0 + c < p.cout) ? p.bias[co0 + c] : 0.f;
     pdl_wait();
     pdl_trigger();
-    load_patch_up<CIN, NT>(p, smem, blockIdx.x, tid);
+    load_patch_up<CIN, NT, KC>(p, smem, seg_of(0), 0, tid);
     asm volatile("cp.async.commit_group;" ::: "memory");
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0));
@@ -742,32 +753,33 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_up_tc(const ConvParams p) {
     constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
                                ((uint32_t)(TC_M >> 4) << 24);
     bool ok = true;
-    int it = 0, prev = -1;
-    for (int seg = blockIdx.x; seg < nseg; seg += gridDim.x, ++it) {
-        const int buf = it & 1;
+#pragma unroll 1
+    for (int g = 0; g < nchunk; ++g) {
+        const int u = g / NCH, c = g - u * NCH, pbuf = g & 1;
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0) {
-            const uint32_t pa = saddr(smem + buf * L::PATCH), pw = saddr(sW);
+            const uint32_t pa = saddr(smem + pbuf * L::PATCH), pw = saddr(sW);
 #pragma unroll 1
             for (int ph = 0; ph < 4; ++ph) {
                 const int a = ph >> 1, bp = ph & 1;
-                const uint32_t acc = tmem + (buf * 4 + ph) * L::NTC;
+                const uint32_t acc = tmem + ((u & 1) * 4 + ph) * L::NTC;
 #pragma unroll
                 for (int t4 = 0; t4 < 4; ++t4) {
                     // patch row 1 + u, column 1 + v (u, v = offsets of the x pixel)
-                    const int u = a - 1 + (t4 >> 1), v = bp - 1 + (t4 & 1);
+                    const int du = a - 1 + (t4 >> 1), dv = bp - 1 + (t4 & 1);
                     const int tap = ph * 4 + t4;
 #pragma unroll
-                    for (int kc = 0; kc < CIN / 16; ++kc) {
-                        const uint64_t bd =
-                            smem_desc(pw + tap * L::WTAP + (2 * kc) * L::WPLANE, L::WPLANE, 128);
+                    for (int kc = 0; kc < KC / 16; ++kc) {
+                        const uint64_t bd = smem_desc(
+                            pw + tap * L::WTAP + (c * L::KGC + 2 * kc) * L::WPLANE, L::WPLANE, 128);
                         const uint64_t ad = smem_desc(
-                            pa + (2 * kc) * L::PPLANE + ((1 + u) * UP_PW + 1 + v) * 16, L::PPLANE, 128);
-                        const uint32_t accum = (t4 | kc) != 0;
+                            pa + (2 * kc) * L::PPLANE + ((1 + du) * UP_PW + 1 + dv) * 16, L::PPLANE,
+                            128);
+                        const uint32_t accum = (c | t4 | kc) != 0;
                         asm volatile(
                             "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(acc),
@@ -777,29 +789,31 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_up_tc(const ConvParams p) {
             }
             asm volatile(
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    bar0 + 8 * buf));
+                    bar0 + 8 * pbuf));
         }
-        if (prev >= 0) {
-            const int pb = (it - 1) & 1;
-            if (ok && !wait_bar(bar0 + 8 * pb, ((it - 1) >> 1) & 1)) ok = false;
+        if (g >= 1) {  // chunk g - 1's products: its patch is free, its unit may be complete
+            const int gp = g - 1;
+            if (ok && !wait_bar(bar0 + 8 * (gp & 1), (gp >> 1) & 1)) ok = false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         }
-        const int nxt = seg + gridDim.x;
-        if (nxt < nseg) load_patch_up<CIN, NT>(p, smem + (buf ^ 1) * L::PATCH, nxt, tid);
+        if (g + 1 < nchunk) {
+            const int un = (g + 1) / NCH, cn = (g + 1) - un * NCH;
+            load_patch_up<CIN, NT, KC>(p, smem + (pbuf ^ 1) * L::PATCH, seg_of(un), cn * KC, tid);
+        }
         asm volatile("cp.async.commit_group;" ::: "memory");
-        if (prev >= 0 && ok)
-            epilogue_up<CIN, NT>(p, sBias, tmem + ((it - 1) & 1) * 4 * L::NTC, prev, warp, lane, co0);
-        prev = seg;
+        if (c == 0 && u >= 1 && ok)  // unit u - 1 ended with chunk g - 1
+            epilogue_up<L::NTC, NT>(p, sBias, tmem + ((u - 1) & 1) * 4 * L::NTC, seg_of(u - 1),
+                                    warp, lane, co0);
     }
-    if (prev >= 0) {
-        const int pb = (it - 1) & 1;
-        if (ok && !wait_bar(bar0 + 8 * pb, ((it - 1) >> 1) & 1)) ok = false;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok) epilogue_up<CIN, NT>(p, sBias, tmem + pb * 4 * L::NTC, prev, warp, lane, co0);
-    }
+    if (ok && !wait_bar(bar0 + 8 * ((nchunk - 1) & 1), ((nchunk - 1) >> 1) & 1)) ok = false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok)
+        epilogue_up<L::NTC, NT>(p, sBias, tmem + ((nunit - 1) & 1) * 4 * L::NTC,
+                                seg_of(nunit - 1), warp, lane, co0);
     if (!ok && tid == 0) {
         if (p.status) atomicOr(p.status, 2u);
-        for (int j = it - 1; j >= 0 && j >= it - 2; --j) wait_bar(bar0 + 8 * (j & 1), (j >> 1) & 1);
+        for (int j = nchunk - 1; j >= 0 && j >= nchunk - 2; --j)
+            wait_bar(bar0 + 8 * (j & 1), (j >> 1) & 1);
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -810,7 +824,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_up_tc(const ConvParams p) {
                      "r"(L::TMEM_COLS));
 }
 
-template <int CIN, int NT>
+template <int CIN, int NT, int KC>
 int& up_grid_cap() {
     static int cap = 0;
     return cap;
@@ -818,11 +832,11 @@ int& up_grid_cap() {
 
 // the attribute and the grid cap (one CTA per SM: the patches and sixteen taps
 // take most of the shared memory), once per shape before any graph capture
-template <int CIN, int NT>
+template <int CIN, int NT, int KC>
 cudaError_t up_prepare() {
-    using L = UpSmem<CIN, NT>;
-    if (up_grid_cap<CIN, NT>()) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_conv_up_tc<CIN, NT>,
+    using L = UpSmem<CIN, NT, KC>;
+    if (up_grid_cap<CIN, NT, KC>()) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_conv_up_tc<CIN, NT, KC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, smem = 0;
@@ -835,20 +849,21 @@ cudaError_t up_prepare() {
     int per = smem / (int)(L::bytes + 1024);
     per = per < 1 ? 1 : per;
     if (per * L::TMEM_COLS > 512) per = 512 / L::TMEM_COLS;
-    up_grid_cap<CIN, NT>() = sms * per;
+    up_grid_cap<CIN, NT, KC>() = sms * per;
     return cudaSuccess;
 }
 
-template <int CIN, int NT>
+template <int CIN, int NT, int KC>
 cudaError_t conv_up_tc_T(const ConvParams& p, cudaStream_t s) {
-    using L = UpSmem<CIN, NT>;
-    cudaError_t e = up_prepare<CIN, NT>();
+    using L = UpSmem<CIN, NT, KC>;
+    cudaError_t e = up_prepare<CIN, NT, KC>();
     if (e != cudaSuccess) return e;
     const int nseg = p.B * (p.H >> 1) * ((p.W >> 1) / TC_M);
     const int ntile = (p.cout_pad + NT - 1) / NT;
-    int gx = up_grid_cap<CIN, NT>() / ntile;
+    int gx = up_grid_cap<CIN, NT, KC>() / ntile;
     gx = gx < 1 ? 1 : (gx > nseg ? nseg : gx);
-    return launch_pdl(k_conv_up_tc<CIN, NT>, dim3(gx, ntile), dim3(TC_THREADS), L::bytes, s, p);
+    return launch_pdl(k_conv_up_tc<CIN, NT, KC>, dim3(gx, ntile), dim3(TC_THREADS), L::bytes, s,
+                      p);
 }
 
 // ------------------------------------------------------------ weight gradient
@@ -1505,26 +1520,30 @@ cudaError_t launch_conv_tc(const ConvParams& p, int cin, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
-// (CIN, N) shapes of the upsampling convolution: c9 (64 -> 32); c7's 128
-// input channels would need its sixteen taps streamed through shared memory
-#define PIC_UP_SHAPES(X) X(64, 32)
+// (CIN, N, channels per pass) shapes of the upsampling convolution: c9 (64 ->
+// 32) in one pass; c7 (128 -> 64) as two tiles of 32 output channels (the
+// sixteen taps of 64 output channels and 128 inputs would not fit) and four
+// passes of 32 input channels
+#define PIC_UP_SHAPES(X) X(64, 32, 64) X(128, 32, 32)
+
+static int up_nt(int cin, int cout_pad) { return cin == 128 ? 32 : tc_nt(cout_pad); }
 
 bool conv_up_tc_supported(const ConvParams& p, int cin) {
     if (!p.up || !p.wp || p.force_tc < 0 || p.epi != EPI_ACT) return false;
     if (p.H % 2 || (p.W >> 1) % TC_M || p.cout_pad > 128) return false;
     // the nine-tap kernel's size rule (in its work units of TC_R x TC_M pixels)
     if ((long long)p.B * (p.H / TC_R) * (p.W / TC_M) < 600 && p.force_tc <= 0) return false;
-    const int nt = tc_nt(p.cout_pad);
-#define PIC_UP_HAS(A, B) if (cin == A && nt == B) return true;
+    const int nt = up_nt(cin, p.cout_pad);
+#define PIC_UP_HAS(A, B, C) if (cin == A && nt == B) return true;
     PIC_UP_SHAPES(PIC_UP_HAS)
 #undef PIC_UP_HAS
     return false;
 }
 
 cudaError_t launch_conv_up_tc(const ConvParams& p, int cin, cudaStream_t s) {
-    const int nt = tc_nt(p.cout_pad);
-#define PIC_UP_CASE(A, B) \
-    if (cin == A && nt == B) return conv_up_tc_T<A, B>(p, s);
+    const int nt = up_nt(cin, p.cout_pad);
+#define PIC_UP_CASE(A, B, C) \
+    if (cin == A && nt == B) return conv_up_tc_T<A, B, C>(p, s);
     PIC_UP_SHAPES(PIC_UP_CASE)
 #undef PIC_UP_CASE
     return cudaErrorInvalidValue;
@@ -1536,8 +1555,8 @@ cudaError_t init_tc_kernels() {
     if (e == cudaSuccess) e = tc_prepare<A, B, C>();
     PIC_TC_SHAPES(PIC_TC_PREP)
 #undef PIC_TC_PREP
-#define PIC_UP_PREP(A, B) \
-    if (e == cudaSuccess) e = up_prepare<A, B>();
+#define PIC_UP_PREP(A, B, C) \
+    if (e == cudaSuccess) e = up_prepare<A, B, C>();
     PIC_UP_SHAPES(PIC_UP_PREP)
 #undef PIC_UP_PREP
     return e;

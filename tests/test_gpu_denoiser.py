@@ -155,11 +155,12 @@ def _nhwc(J):
 
 
 @pytest.mark.parametrize("ny,nx,tc", [(32, 64, None), (32, 256, None), (32, 256, "always"),
-                                      (32, 64, "never")])
+                                      (32, 512, "always"), (32, 64, "never")])
 def test_network_loss_and_gradients_match_oracle(ny, nx, tc, monkeypatch):
     """tc: PIC_DENOISER_TC=always puts every 128-wide row layer on the tcgen05
-    kernels, =never keeps every layer (the weight gradients included) on the
-    mma.sync kernels."""
+    kernels (at nx = 256 c9, at nx = 512 c7 and c9 as four 2x2 convolutions of
+    the coarse grid), =never keeps every layer (the weight gradients included)
+    on the mma.sync kernels."""
     if tc:
         monkeypatch.setenv("PIC_DENOISER_TC", tc)
     B, scale = 2, 0.5
