@@ -1531,8 +1531,8 @@ static int up_nt(int cin, int cout_pad) { return cin == 128 ? 32 : tc_nt(cout_pa
 bool conv_up_tc_supported(const ConvParams& p, int cin) {
     if (!p.up || !p.wp || p.force_tc < 0 || p.epi != EPI_ACT) return false;
     if (p.H % 2 || (p.W >> 1) % TC_M || p.cout_pad > 128) return false;
-    // the nine-tap kernel's size rule (in its work units of TC_R x TC_M pixels)
-    if ((long long)p.B * (p.H / TC_R) * (p.W / TC_M) < 600 && p.force_tc <= 0) return false;
+    // no size rule: with 4/9 of the products it beats the mma.sync kernel from
+    // the smallest grids it takes on (measured at 256^2 and 512^2 in the step)
     const int nt = up_nt(cin, p.cout_pad);
 #define PIC_UP_HAS(A, B, C) if (cin == A && nt == B) return true;
     PIC_UP_SHAPES(PIC_UP_HAS)
