@@ -250,7 +250,8 @@ int forward(pic_denoiser* d, int B, const float* J, long long bstride, long long
     // products plus one more pass over memory, the packing kernel and the
     // implicit-GEMM convolutions (measured on GB300 at 2048^2: 296 + 336 us
     // against 180 + 230 us).
-    const bool thin = (long long)B * H0 * W0 < kThinPixels;
+    // (PIC_DENOISER_TC=always takes the tensor-core kernels at every size)
+    const bool thin = (long long)B * H0 * W0 < kThinPixels && d->force_tc <= 0;
     if (thin) {
         const LayerDesc& L = d->tab.layer[0];
         FW(launch_conv_first(J, bstride, cstride, pitch, offset, B, H0, W0,

@@ -134,6 +134,9 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 cudaError_t launch_conv(const ConvParams& p, int cin, int ct, cudaStream_t s);
 bool conv_tc_supported(const ConvParams& p, int cin);
 cudaError_t launch_conv_tc(const ConvParams& p, int cin, cudaStream_t s);
+// the output layer (32 -> 3, EPI_FINAL) with its nine taps in the GEMM's N (tcgen05)
+bool conv_out_tc_supported(const ConvParams& p, int cin);
+cudaError_t launch_conv_out_tc(const ConvParams& p, cudaStream_t s);
 // a 3x3 convolution of a 2x upsampled input as four 2x2 convolutions (tcgen05)
 bool conv_up_tc_supported(const ConvParams& p, int cin);
 cudaError_t launch_conv_up_tc(const ConvParams& p, int cin, cudaStream_t s);

@@ -972,6 +972,7 @@ cudaError_t init_kernels() {
 // would not fit in shared memory.
 cudaError_t launch_conv(const ConvParams& p, int cin, int ct, cudaStream_t s) {
     if (p.H % TH || p.W % TW || p.cout_pad % ct) return cudaErrorInvalidValue;
+    if (conv_out_tc_supported(p, cin)) return launch_conv_out_tc(p, s);
     if (conv_up_tc_supported(p, cin)) return launch_conv_up_tc(p, cin, s);
     if (conv_tc_supported(p, cin)) return launch_conv_tc(p, cin, s);
     if (cin == 128 && ct == 64) ct = 32;

@@ -866,6 +866,264 @@ cudaError_t conv_up_tc_T(const ConvParams& p, cudaStream_t s) {
                       p);
 }
 
+// ------------------------------------------------- the output layer (32 -> 3)
+// out[y][x][co] = sum over taps (ky, kx) and ci of a[y + ky - 1][x + kx - 1][ci]
+// w[ky][kx][ci][co].  With three outputs, the nine-tap GEMM has N = 3 and
+// every MMA reads a 128-pixel operand for almost nothing; here the taps go
+// into N instead: per input row r, one GEMM gives D_r[pixel][(tap, co)] =
+// sum over ci of a[r][pixel][ci] w[tap][ci][co] (27 of 32 columns), and the
+// epilogue adds, for output pixel x of row y, D_{y+ky-1}[x + kx - 1][(ky, kx,
+// co)] over the nine taps.  A work unit is OT_R output rows by 126 output
+// columns: its patch is the OT_R + 2 input rows around them and the 128 input
+// pixels x0 - 1 .. x0 + 126 (TMEM lane m = pixel x0 - 1 + m, circular), one
+// accumulator of 32 columns per input row.  In the epilogue each lane sums
+// its pixel's centre, left-tap and right-tap contributions over ky; the
+// output at lane m takes the centre of m, the left-tap sum of m - 1 and the
+// right-tap sum of m + 1 (warp shuffles, across warps through shared memory).
+constexpr int OT_R = 4;                  // output rows per unit (even; 2 measured slower)
+constexpr int OT_DR = OT_R + 2;          // input rows (TMEM accumulators)
+constexpr int OT_P = TC_M - 2;           // output columns per unit
+constexpr int OT_N = 32;                 // GEMM columns: 9 taps x 3 outputs, padded
+
+struct OutSmem {
+    static constexpr int CIN = 32, KG = CIN / 8;
+    static constexpr int PPLANE = OT_DR * TC_M * 16;   // one k-group of the patch
+    static constexpr int PATCH = KG * PPLANE;
+    static constexpr int WPLANE = OT_N * 16;
+    static constexpr size_t off_w = 2 * (size_t)PATCH;
+    static constexpr size_t off_x = off_w + KG * WPLANE;           // edge exchange
+    static constexpr size_t off_bar = off_x + 2 * 2 * 4 * 3 * 4;    // [row slot][side][quarter][co]
+    static constexpr size_t bytes = off_bar + 16;
+    static constexpr int TMEM_COLS = OT_DR * OT_N <= 128 ? 128 : (OT_DR * OT_N <= 256 ? 256 : 512);
+};
+
+__device__ __forceinline__ void load_patch_out(const ConvParams& p, unsigned char* sP, int unit,
+                                               int tid) {
+    using L = OutSmem;
+    const int segs = (p.W + OT_P - 1) / OT_P, bands = p.H / OT_R;
+    const int x0 = (unit % segs) * OT_P;
+    const int y0 = ((unit / segs) % bands) * OT_R;
+    const int b = unit / (segs * bands);
+    // consecutive threads take consecutive 16-byte pieces of a pixel's 64 bytes
+    for (int i = tid; i < OT_DR * TC_M * L::KG; i += TC_THREADS) {
+        const int kg = i % L::KG, pix = i / L::KG;
+        const int r = pix / TC_M, m = pix - r * TC_M;
+        const int ys = wrap(y0 - 1 + r, p.H);
+        int xs = x0 - 1 + m;
+        xs = xs < 0 ? xs + p.W : (xs >= p.W ? xs - p.W : xs);
+        if (xs >= p.W) xs -= p.W;  // the last unit's lanes past the right edge wrap again
+        cp_async16(sP + kg * L::PPLANE + pix * 16,
+                   p.x + (((size_t)b * p.H + ys) * p.W + xs) * L::CIN + kg * 8);
+    }
+}
+
+// p.w: the layer's forward packing [9][cout_pad][32]; EPI_FINAL only
+// two CTAs per SM (TMEM 2 x 256 columns): up to 128 registers a thread
+__global__ void __launch_bounds__(TC_THREADS, 2) k_conv_out_tc(const ConvParams p) {
+    using L = OutSmem;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sW = smem + L::off_w;
+    float* sX = reinterpret_cast<float*>(smem + L::off_x);
+    const uint32_t bar = saddr(smem + L::off_bar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::off_bar + 8);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int segs = (p.W + OT_P - 1) / OT_P, bands = p.H / OT_R;
+    const int nunit = p.B * bands * segs;
+    if ((int)blockIdx.x >= nunit) return;
+    // B: row n = tap 3 + co of the GEMM (zero past the real outputs), k-group kg
+    for (int i = tid; i < OT_N * L::KG; i += TC_THREADS) {
+        const int n = i / L::KG, kg = i - n * L::KG;
+        const int tap = n / 3, co = n - 3 * tap;
+        unsigned char* dst = sW + kg * L::WPLANE + n * 16;
+        if (tap < 9 && co < p.cout)
+            cp_async16(dst, p.w + ((size_t)tap * p.cout_pad + co) * L::CIN + kg * 8);
+        else
+            *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    float bias[3];
+#pragma unroll
+    for (int co = 0; co < 3; ++co) bias[co] = (p.bias && co < p.cout) ? p.bias[co] : 0.f;
+    pdl_wait();
+    pdl_trigger();
+    load_patch_out(p, smem, blockIdx.x, tid);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         saddr(tslot)),
+                     "r"(L::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OT_N >> 3) << 17) |
+                               ((uint32_t)(TC_M >> 4) << 24);
+    const int lq = warp & 3, half = warp >> 2;
+    const int m = 32 * lq + lane;  // TMEM lane: input pixel x0 - 1 + m
+    bool ok = true;
+    int it = 0;
+#pragma unroll 1
+    for (int unit = blockIdx.x; unit < nunit; unit += gridDim.x, ++it) {
+        const int buf = it & 1;
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint32_t pa = saddr(smem + buf * L::PATCH), pw = saddr(sW);
+#pragma unroll
+            for (int r = 0; r < OT_DR; ++r)
+#pragma unroll
+                for (int kc = 0; kc < L::CIN / 16; ++kc) {
+                    const uint64_t bd = smem_desc(pw + (2 * kc) * L::WPLANE, L::WPLANE, 128);
+                    const uint64_t ad =
+                        smem_desc(pa + (2 * kc) * L::PPLANE + r * TC_M * 16, L::PPLANE, 128);
+                    const uint32_t accum = kc != 0;
+                    asm volatile(
+                        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(
+                            tmem + r * OT_N),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    bar));
+        }
+        // the next unit's patch into the other buffer (its products were read
+        // before the previous unit's epilogue ended)
+        const int nxt = unit + gridDim.x;
+        if (nxt < nunit) load_patch_out(p, smem + (buf ^ 1) * L::PATCH, nxt, tid);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        const int x0 = (unit % segs) * OT_P;
+        const int y0 = ((unit / segs) % bands) * OT_R;
+        const int b = unit / (segs * bands);
+        const int x = x0 - 1 + m;
+        const bool mine = m >= 1 && m <= OT_P && x < p.W;  // this lane's output column
+        // the residual of this lane's two output pixels, requested before the wait
+        float res[OT_R / 2][3];
+#pragma unroll
+        for (int round = 0; round < OT_R / 2; ++round)
+#pragma unroll
+            for (int co = 0; co < 3; ++co) {
+                res[round][co] = 0.f;
+                if (mine && co < p.cout)
+                    res[round][co] = p.res[(size_t)b * p.bstride + (size_t)co * p.cstride + p.offset +
+                                           (size_t)(y0 + half + 2 * round) * p.pitch + x];
+            }
+        if (ok && !wait_bar(bar, it & 1)) ok = false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int okall = __syncthreads_and(ok);
+        if (!okall) {
+            ok = false;
+            break;
+        }
+        // OT_R / 2 rounds: warps 0-3 the even output rows, warps 4-7 the odd ones
+#pragma unroll
+        for (int round = 0; round < OT_R / 2; ++round) {
+            const int o = half + 2 * round;
+            float C[3] = {0.f, 0.f, 0.f}, Lt[3] = {0.f, 0.f, 0.f}, Rt[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) {
+                uint32_t v[32];
+                const uint32_t taddr = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)((o + ky) * OT_N);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+                    "%12,%13,%14,%15}, [%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                      "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                      "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                    : "r"(taddr));
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+                    "%12,%13,%14,%15}, [%16];"
+                    : "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                      "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr + 16));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int co = 0; co < 3; ++co) {
+                    Lt[co] += __uint_as_float(v[(3 * ky + 0) * 3 + co]);  // kx = 0: feeds x + 1
+                    C[co] += __uint_as_float(v[(3 * ky + 1) * 3 + co]);
+                    Rt[co] += __uint_as_float(v[(3 * ky + 2) * 3 + co]);  // kx = 2: feeds x - 1
+                }
+            }
+            // the warp's edge lanes hand their sums to the neighbouring quarters
+            float* xs = sX + (half * 2) * 4 * 3;  // [side][quarter][co] of this row slot
+            if (lane == 31)
+#pragma unroll
+                for (int co = 0; co < 3; ++co) xs[(0 * 4 + lq) * 3 + co] = Lt[co];
+            if (lane == 0)
+#pragma unroll
+                for (int co = 0; co < 3; ++co) xs[(1 * 4 + lq) * 3 + co] = Rt[co];
+            __syncthreads();
+            float out[3];
+#pragma unroll
+            for (int co = 0; co < 3; ++co) {
+                float left = __shfl_up_sync(0xffffffffu, Lt[co], 1);
+                float right = __shfl_down_sync(0xffffffffu, Rt[co], 1);
+                if (lane == 0) left = lq > 0 ? xs[(0 * 4 + lq - 1) * 3 + co] : 0.f;
+                if (lane == 31) right = lq < 3 ? xs[(1 * 4 + lq + 1) * 3 + co] : 0.f;
+                out[co] = C[co] + left + right;
+            }
+            if (mine) {
+                const int y = y0 + o;
+#pragma unroll
+                for (int co = 0; co < 3; ++co) {
+                    if (co >= p.cout) continue;
+                    const size_t oi = (size_t)b * p.bstride + (size_t)co * p.cstride + p.offset +
+                                      (size_t)y * p.pitch + x;
+                    p.fout[oi] = res[round][co] * p.rs + (out[co] + bias[co]) * p.os;
+                }
+            }
+            __syncthreads();  // the exchange slots are reused next round
+        }
+    }
+    if (!ok && tid == 0) {
+        if (p.status) atomicOr(p.status, 2u);  // a bounded wait ran out
+        wait_bar(bar, it & 1);                  // the products in flight, once more
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(L::TMEM_COLS));
+}
+
+int& out_grid_cap() {
+    static int cap = 0;
+    return cap;
+}
+
+cudaError_t out_prepare() {
+    using L = OutSmem;
+    if (out_grid_cap()) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_conv_out_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)L::bytes);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, smem = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    if ((e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) !=
+        cudaSuccess)
+        return e;
+    int per = smem / (int)(L::bytes + 1024);
+    per = per < 1 ? 1 : per;
+    if (per * L::TMEM_COLS > 512) per = 512 / L::TMEM_COLS;
+    if (per * TC_THREADS > 2048) per = 2048 / TC_THREADS;
+    out_grid_cap() = sms * per;
+    return cudaSuccess;
+}
+
 // ------------------------------------------------------------ weight gradient
 // dW[ky][kx][ci][co] = sum over output pixels p of x[p + (ky - 1, kx - 1)][ci] dz[p][co]
 // (x read through the nearest-neighbour doubling when the layer upsamples).
@@ -1549,8 +1807,22 @@ cudaError_t launch_conv_up_tc(const ConvParams& p, int cin, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
+bool conv_out_tc_supported(const ConvParams& p, int cin) {
+    return p.force_tc >= 0 && p.epi == EPI_FINAL && !p.up && cin == 32 && p.cout <= 3 &&
+           p.cout_pad >= 3 && p.H % OT_R == 0 && p.W >= TC_M;
+}
+
+cudaError_t launch_conv_out_tc(const ConvParams& p, cudaStream_t s) {
+    cudaError_t e = out_prepare();
+    if (e != cudaSuccess) return e;
+    const int nunit = p.B * (p.H / OT_R) * ((p.W + OT_P - 1) / OT_P);
+    int gx = out_grid_cap();
+    gx = gx < 1 ? 1 : (gx > nunit ? nunit : gx);
+    return launch_pdl(k_conv_out_tc, dim3(gx), dim3(TC_THREADS), OutSmem::bytes, s, p);
+}
+
 cudaError_t init_tc_kernels() {
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = out_prepare();
 #define PIC_TC_PREP(A, B, C) \
     if (e == cudaSuccess) e = tc_prepare<A, B, C>();
     PIC_TC_SHAPES(PIC_TC_PREP)
