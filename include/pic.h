@@ -375,12 +375,16 @@ pic_status pic_set_tiling(pic_sim* sim, int tile, int threads);
  * it is installed in a simulation it also runs on that simulation's stream.
  * The thin end layers c1 and c11 run on CUDA-core kernels (fused with the
  * input scaling and the residual output) when a pass has fewer than 2^18
- * pixels, else as implicit GEMMs like the others.  Convolutions whose rows
- * are multiples of 128 pixels and with at least 17 output channels run on
- * the tcgen05 tensor-core kernel when the launch is large (>= 600 work units
- * of 2 x 128 pixels), else on an mma.sync kernel;
- * the environment variable PIC_DENOISER_TC, read at creation, selects the
- * tcgen05 kernel whenever the shape allows (=always, used by the tests) or
+ * pixels, else on the tensor cores (c11 as one GEMM per input row with its
+ * nine taps side by side).  Convolutions whose rows are multiples of 128
+ * pixels and with at least 17 output channels run on the tcgen05 kernel when
+ * the launch is large (>= 600 work units of 2 x 128 pixels), else on an
+ * mma.sync kernel; the two layers that read a 2x upsampled input (c7, c9)
+ * run as four 2x2 convolutions of the coarse grid (tcgen05) whenever its rows
+ * are multiples of 128 pixels, with the 3x3 taps summed per output parity
+ * (each sum rounded to bfloat16 once).  The environment variable
+ * PIC_DENOISER_TC, read at creation, selects the tcgen05 kernels whenever
+ * the shape allows, the end layers included (=always, used by the tests), or
  * never (=never).
  * Low-wavenumber restoration (off unless pic_denoiser_set_low_k_restore sets
  * n > 0 passes): after the network, out <- out + L^n (J_in - out), where L is
