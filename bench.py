@@ -739,6 +739,11 @@ def run_denoiser(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# kernels of one forward pass from 2^18 pixels on: the input packing, eleven
+# convolutions and two poolings (counted from an ncu launch list at 2048^2)
+FWD_LAUNCHES = 14
+
+
 def run_denoiser_fwd(args, rank, world, local_rank):
     """Tensor-core throughput of the denoiser's forward pass on one large
     sample: K forwards timed with CUDA events on the launching stream, the
@@ -796,11 +801,11 @@ def run_denoiser_fwd(args, rank, world, local_rank):
                    "l2": "inputs larger than L2 (one full-resolution activation 268 MB > 129 MB)"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "whole forward pass (13 launches)",
+                     "kernel": f"whole forward pass ({FWD_LAUNCHES} launches)",
                      "peak_source": "measured bf16_tflops" if os.path.exists(p) else "fallback"},
         "e2e": {"value": flops / (e2e_ms * 1e-3) / 1e12 * world, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": xh.nbytes, "d2h_bytes_per_step": oh.nbytes},
-        "gpu_launches": 13 * args.steps,
+        "gpu_launches": FWD_LAUNCHES * args.steps,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
