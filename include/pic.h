@@ -373,10 +373,10 @@ pic_status pic_set_tiling(pic_sim* sim, int tile, int threads);
  * samples in the field layout of the header comment (3 x ny x nx FP32 each).
  * A handle is not thread-safe; its work is ordered on `cuda_stream`, and while
  * it is installed in a simulation it also runs on that simulation's stream.
- * The thin end layers c1 and c11 run on CUDA-core kernels (fused with the
- * input scaling and the residual output) when a pass has fewer than 2^18
- * pixels, else on the tensor cores (c11 as one GEMM per input row with its
- * nine taps side by side).  Convolutions whose rows are multiples of 128
+ * The thin first layer c1 runs on a CUDA-core kernel (fused with the input
+ * scaling) when a pass has fewer than 2^18 pixels, else on the tensor cores;
+ * the output layer c11 runs on the tensor cores as one GEMM per input row with
+ * its nine taps side by side (an mma.sync kernel below 128-pixel rows).  Convolutions whose rows are multiples of 128
  * pixels and with at least 17 output channels run on the tcgen05 kernel when
  * the launch is large (>= 600 work units of 2 x 128 pixels), else on an
  * mma.sync kernel; the two layers that read a 2x upsampled input (c7, c9)

@@ -50,7 +50,7 @@ constexpr LayerSpec kLayers[NL] = {
 int pad16(int c) { return (c + 15) / 16 * 16; }
 // c7 and c9 read the coarser level through the 2x upsampling
 bool up_input(int l) { return l == 6 || l == 8; }
-// below this many pixels per forward pass the thin end layers run on the CUDA cores
+// below this many pixels per forward pass the thin first layer runs on the CUDA cores
 constexpr long long kThinPixels = 1LL << 18;
 // output-channel tile of the convolution kernel for a given channel count
 int ctile(int cout) { return cout <= 8 ? 8 : (cout >= 64 ? 64 : 32); }
@@ -243,14 +243,12 @@ int forward(pic_denoiser* d, int B, const float* J, long long bstride, long long
         }                                                                           \
         ++n;                                                                        \
     } while (0)
-    // The thin end layers c1 (3 -> 32) and c11 (32 -> 3): on small lattices
-    // CUDA-core kernels fused with the input packing and the residual output
-    // (fewer launches, no padded tensor-core tiles); on large ones, where the
-    // CUDA cores' multiply-adds take longer than the tensor cores' padded
-    // products plus one more pass over memory, the packing kernel and the
-    // implicit-GEMM convolutions (measured on GB300 at 2048^2: 296 + 336 us
-    // against 180 + 230 us).
-    // (PIC_DENOISER_TC=always takes the tensor-core kernels at every size)
+    // The thin first layer c1 (3 -> 32): on small lattices a CUDA-core kernel
+    // fused with the input packing (one launch, no padded tensor-core tile);
+    // on large ones, where its multiply-adds take longer than the tensor
+    // cores' padded products plus one more pass over memory, the packing
+    // kernel and the implicit GEMM (measured on GB300 at 2048^2: 296 against
+    // 180 us).  (PIC_DENOISER_TC=always takes the tensor cores at every size.)
     const bool thin = (long long)B * H0 * W0 < kThinPixels && d->force_tc <= 0;
     if (thin) {
         const LayerDesc& L = d->tab.layer[0];
@@ -277,15 +275,10 @@ int forward(pic_denoiser* d, int B, const float* J, long long bstride, long long
     FW(conv(d, 8, B, d->a[7], EPI_ACT, keep ? d->a[8] : nullptr, d->a[1], d->y9, nullptr, s,
             nullptr, nullptr, 0, 0, 0, 0, 0.f, 0.f, 1));
     FW(conv(d, 9, B, d->y9, EPI_ACT, d->a[9], nullptr, nullptr, nullptr, s));
-    if (thin) {
-        const LayerDesc& L = d->tab.layer[NL - 1];
-        FW(launch_conv_last(d->a[9], B, H0, W0, d->wf + L.wf_off, L.cout_pad,
-                            d->master + d->boff[NL - 1], J, fout, bstride, cstride, pitch, offset,
-                            rs, os, s));
-    } else {
-        FW(conv(d, 10, B, d->a[9], EPI_FINAL, nullptr, nullptr, nullptr, nullptr, s, J, fout, bstride,
-                cstride, pitch, offset, rs, os));
-    }
+    // c11 on the tensor cores at every size (its nine taps in the GEMM's N; below
+    // 128-pixel rows the mma.sync kernel)
+    FW(conv(d, 10, B, d->a[9], EPI_FINAL, nullptr, nullptr, nullptr, nullptr, s, J, fout, bstride,
+            cstride, pitch, offset, rs, os));
     return n;
 }
 

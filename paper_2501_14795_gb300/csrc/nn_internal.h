@@ -152,10 +152,6 @@ cudaError_t launch_conv_first(const float* J, long long bstride, long long cstri
                               int offset, int B, int H, int W, float inv_scale,
                               const __nv_bfloat16* w, int cout_pad, const float* bias,
                               __nv_bfloat16* xin, __nv_bfloat16* a_out, cudaStream_t s);
-cudaError_t launch_conv_last(const __nv_bfloat16* x, int B, int H, int W, const __nv_bfloat16* w,
-                             int cout_pad, const float* bias, const float* res, float* fout,
-                             long long bstride, long long cstride, int pitch, int offset, float rs,
-                             float os, cudaStream_t s);
 cudaError_t launch_pack_input(const float* J, long long bstride, long long cstride, int pitch,
                               int offset, int B, int H, int W, float inv_scale, __nv_bfloat16* out,
                               cudaStream_t s);

@@ -451,62 +451,6 @@ __global__ void __launch_bounds__(256) k_conv_first(const float* J, long long bs
     for (int q = 0; q < C1 / 8; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
 }
 
-// c11 with the residual output: z = 3x3 circular convolution of the 32-channel
-// activation (bfloat16 NHWC), then fout = res * rs + (z + bias) * os in field
-// layout for the three components.
-__global__ void __launch_bounds__(256) k_conv_last(const bf16* x, int H, int W, const bf16* w,
-                                                   int cout_pad, const float* bias,
-                                                   const float* res, float* fout,
-                                                   long long bstride, long long cstride,
-                                                   int pitch, int offset, float rs, float os) {
-    constexpr int CI = 32, CO = 3, E = THIN_T + 2, PS = CI + 8;  // padded pixel stride
-    __shared__ __align__(16) bf16 sA[E * E * PS];
-    __shared__ float sW[9 * CI][CO];
-    const int tid = threadIdx.x, b = blockIdx.z;
-    const int x0 = blockIdx.x * THIN_T, y0 = blockIdx.y * THIN_T;
-    pdl_wait();
-    for (int i = tid; i < 9 * CI * CO; i += blockDim.x) {
-        const int co = i % CO, k = i / CO, tap = k / CI, ci = k - tap * CI;
-        sW[k][co] = __bfloat162float(w[((size_t)tap * cout_pad + co) * CI + ci]);
-    }
-    for (int i = tid; i < E * E * (CI / 8); i += blockDim.x) {
-        const int pixl = i / (CI / 8), part = i % (CI / 8);
-        const int r = pixl / E, q = pixl % E;
-        const int yy = wrap_idx(y0 + r - 1, H), xx = wrap_idx(x0 + q - 1, W);
-        const uint4 v = reinterpret_cast<const uint4*>(x + (((size_t)b * H + yy) * W + xx) * CI)[part];
-        *reinterpret_cast<uint4*>(sA + pixl * PS + part * 8) = v;
-    }
-    __syncthreads();
-    pdl_trigger();
-    const int ty = tid / THIN_T, tx = tid % THIN_T;
-    float acc[CO] = {0.f, 0.f, 0.f};
-#pragma unroll 1
-    for (int tap = 0; tap < 9; ++tap) {
-        const int ky = tap / 3, kx = tap - 3 * (tap / 3);
-        const bf16* a = sA + ((ty + ky) * E + tx + kx) * PS;
-#pragma unroll
-        for (int part = 0; part < CI / 8; ++part) {
-            const uint4 v = *reinterpret_cast<const uint4*>(a + part * 8);
-            const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&v);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float2 f = __bfloat1622float2(h2[e]);
-                const int ci = part * 8 + 2 * e;
-                const float* w0 = sW[tap * CI + ci];
-                const float* w1 = sW[tap * CI + ci + 1];
-#pragma unroll
-                for (int co = 0; co < CO; ++co) acc[co] += f.x * w0[co] + f.y * w1[co];
-            }
-        }
-    }
-    const int y = y0 + ty, xg = x0 + tx;
-#pragma unroll
-    for (int co = 0; co < CO; ++co) {
-        const size_t o = (size_t)b * bstride + (size_t)co * cstride + offset + (size_t)y * pitch + xg;
-        fout[o] = res[o] * rs + (acc[co] + bias[co]) * os;
-    }
-}
-
 // The network input on large lattices, where c1 runs as an implicit GEMM on
 // the tensor cores: the current (field layout) scaled and rounded to
 // bfloat16, NHWC with 16 channels (3 used).
@@ -1013,16 +957,6 @@ cudaError_t launch_conv_first(const float* J, long long bstride, long long cstri
     if (H % THIN_T || W % THIN_T) return cudaErrorInvalidValue;
     return launch_pdl(k_conv_first, dim3(W / THIN_T, H / THIN_T, B), dim3(256), 0, s, J, bstride,
                       cstride, pitch, offset, H, W, inv_scale, w, cout_pad, bias, xin, a_out);
-}
-
-cudaError_t launch_conv_last(const __nv_bfloat16* x, int B, int H, int W, const __nv_bfloat16* w,
-                             int cout_pad, const float* bias, const float* res, float* fout,
-                             long long bstride, long long cstride, int pitch, int offset, float rs,
-                             float os, cudaStream_t s) {
-    if (B <= 0) return cudaSuccess;
-    if (H % THIN_T || W % THIN_T) return cudaErrorInvalidValue;
-    return launch_pdl(k_conv_last, dim3(W / THIN_T, H / THIN_T, B), dim3(256), 0, s, x, H, W, w,
-                      cout_pad, bias, res, fout, bstride, cstride, pitch, offset, rs, os);
 }
 
 cudaError_t launch_pack_input(const float* J, long long bstride, long long cstride, int pitch,
