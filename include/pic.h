@@ -447,9 +447,9 @@ pic_status pic_set_denoiser(pic_sim* sim, pic_denoiser* d);
  * the network's grid (PIC_EINVAL otherwise, message through
  * pic_batch_last_error).  A member gets what pic_set_denoiser would give it
  * alone, up to the order of a convolution's FP32 sums: which kernel runs a
- * layer depends on the pixels of the pass (CUDA cores for the thin end layers
- * below 2^18 pixels, else implicit GEMMs; mma.sync or tcgen05 by shape and
- * size), and each sums in its own order.  d must stay alive while installed; kernel
+ * layer depends on the pixels of the pass (CUDA cores for the thin first
+ * layer below 2^18 pixels, else implicit GEMMs; mma.sync or tcgen05 by shape
+ * and size), and each sums in its own order.  d must stay alive while installed; kernel
  * timeouts show in the first member's status.  Synchronises. */
 pic_status pic_batch_set_denoiser(pic_batch* batch, pic_denoiser* d);
 

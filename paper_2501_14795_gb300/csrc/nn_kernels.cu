@@ -16,8 +16,8 @@
 //            raw FP32, or the network's residual output in field layout.
 //   k_wgrad  weight gradient: per tap a (cout x cin) GEMM over all pixels,
 //            split over CTAs (FP32 atomics into the gradient).
-//   k_conv_first / k_conv_last  the thin end layers (3 -> 32 with the input
-//            packing, 32 -> 3 with the residual output) on the CUDA cores.
+//   k_conv_first  the thin first layer (3 -> 32 with the input packing) on
+//            the CUDA cores, for passes below 2^18 pixels.
 //   elementwise: 2x2 mean pooling / nearest upsampling and
 //            their adjoints, ReLU backward with the bias gradient, MSE loss,
 //            Adam, weight packing.
@@ -376,12 +376,11 @@ __global__ void __launch_bounds__(WG_THREADS) k_wgrad(const WgradParams p) {
 
 // ----------------------------------------------------------- elementwise
 
-// The network's thin end layers on the CUDA cores.  c1 (3 -> 32 channels)
-// has 27 inputs per output and c11 (32 -> 3) three outputs per pixel: as
-// implicit GEMMs on the tensor cores most of each tile is padding, and at
-// small grids their time is launch and pipeline latency.  Both keep the
-// arithmetic of the tensor-core path: bfloat16 inputs and weights, FP32
-// products and sums, bias, then the epilogue.
+// The network's thin first layer on the CUDA cores.  c1 (3 -> 32 channels)
+// has 27 inputs per output: as an implicit GEMM on the tensor cores most of
+// each tile is padding, and at small grids its time is launch and pipeline
+// latency.  It keeps the arithmetic of the tensor-core path: bfloat16 inputs
+// and weights, FP32 products and sums, bias, then the epilogue.
 constexpr int THIN_T = 16;  // 16 x 16 output pixels per CTA, one per thread
 
 __device__ __forceinline__ int wrap_idx(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }

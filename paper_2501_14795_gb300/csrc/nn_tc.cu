@@ -24,6 +24,11 @@
 // accumulator, loading the next quarter while the tensor cores multiply the
 // current one.
 //
+// Beside it: the two layers that read a 2x upsampled input as four 2x2
+// convolutions of the coarse grid (k_conv_up_tc), the 3-channel output layer
+// with its nine taps in the GEMM's N (k_conv_out_tc), and the weight
+// gradients (k_wgrad_tc, k_wgrad_tcn), each described where it is defined.
+//
 // Every wait is bounded; on a timeout the kernel flags it in the status word,
 // frees its TMEM and returns.
 #include <cuda_bf16.h>
