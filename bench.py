@@ -360,10 +360,11 @@ def run_reference_denoiser_fwd(args, world):
 
 
 # kernels of one training step: 11 layers' forward, the loss, the input and
-# weight gradients and ReLU backward of each layer, the pooling and upsampling
-# backward, the weight packing and Adam (counted from an ncu launch list of the
-# 256x256 x 16 step; the same layers run at every grid size)
-TRAIN_LAUNCHES = 53
+# weight gradients and ReLU backward of each layer (the pooling and upsampling
+# adjoints fused into four of them), the weight packing and Adam (counted from
+# an ncu launch list of the 256x256 x 16 step; the same layers run at every
+# grid size)
+TRAIN_LAUNCHES = 49
 
 
 def oracle_train_rate(n, steps, warmup=0):

@@ -324,36 +324,32 @@ int backward(pic_denoiser* d, int B, const float* target, cudaStream_t s) {
     FW(launch_relu_back(d->S1, nullptr, d->a[8], P0, 32, d->dz, db(8), s));
     FW(wg(8, d->a[7], 1));
     FW(conv(d, 8, B, d->dz, EPI_GRAD, nullptr, nullptr, nullptr, d->G0, s));        // du2
-    FW(launch_up_back(d->G0, B, H1, W1, 64, d->G1, s));                              // dy8
-    // c8
-    FW(launch_relu_back(d->G1, nullptr, d->a[7], P1, 64, d->dz, db(7), s));
+    // c8: dy8 = the upsampling adjoint of du2, through the ReLU
+    FW(launch_up_relu_back(d->G0, B, H1, W1, 64, d->a[7], d->dz, db(7), s));
     FW(wg(7, d->y7));
     FW(conv(d, 7, B, d->dz, EPI_GRAD, nullptr, nullptr, nullptr, d->S2, s));        // dy7 (= ds2)
     // c7 (+s2)
     FW(launch_relu_back(d->S2, nullptr, d->a[6], P1, 64, d->dz, db(6), s));
     FW(wg(6, d->a[5], 1));
     FW(conv(d, 6, B, d->dz, EPI_GRAD, nullptr, nullptr, nullptr, d->G0, s));        // du1
-    FW(launch_up_back(d->G0, B, H2, W2, 128, d->G1, s));                             // dy6
-    // c6
-    FW(launch_relu_back(d->G1, nullptr, d->a[5], P2, 128, d->dz, db(5), s));
+    // c6: dy6 = the upsampling adjoint of du1, through the ReLU
+    FW(launch_up_relu_back(d->G0, B, H2, W2, 128, d->a[5], d->dz, db(5), s));
     FW(wg(5, d->a[4]));
     FW(conv(d, 5, B, d->dz, EPI_GRAD, nullptr, nullptr, nullptr, d->G0, s));        // dy5
     // c5
     FW(launch_relu_back(d->G0, nullptr, d->a[4], P2, 128, d->dz, db(4), s));
     FW(wg(4, d->p2));
     FW(conv(d, 4, B, d->dz, EPI_GRAD, nullptr, nullptr, nullptr, d->G1, s));        // dp2
-    FW(launch_pool_back(d->G1, B, H1, W1, 64, d->G0, s));                            // dy4 (pool path)
-    // c4: + ds2
-    FW(launch_relu_back(d->G0, d->S2, d->a[3], P1, 64, d->dz, db(3), s));
+    // c4: dy4 = the pooling adjoint of dp2 + ds2, through the ReLU
+    FW(launch_pool_relu_back(d->G1, B, H1, W1, 64, d->S2, d->a[3], d->dz, db(3), s));
     FW(wg(3, d->a[2]));
     FW(conv(d, 3, B, d->dz, EPI_GRAD, nullptr, nullptr, nullptr, d->G1, s));        // dy3
     // c3
     FW(launch_relu_back(d->G1, nullptr, d->a[2], P1, 64, d->dz, db(2), s));
     FW(wg(2, d->p1));
     FW(conv(d, 2, B, d->dz, EPI_GRAD, nullptr, nullptr, nullptr, d->G0, s));        // dp1
-    FW(launch_pool_back(d->G0, B, H0, W0, 32, d->G1, s));                            // dy2 (pool path)
-    // c2: + ds1
-    FW(launch_relu_back(d->G1, d->S1, d->a[1], P0, 32, d->dz, db(1), s));
+    // c2: dy2 = the pooling adjoint of dp1 + ds1, through the ReLU
+    FW(launch_pool_relu_back(d->G0, B, H0, W0, 32, d->S1, d->a[1], d->dz, db(1), s));
     FW(wg(1, d->a[0]));
     FW(conv(d, 1, B, d->dz, EPI_GRAD, nullptr, nullptr, nullptr, d->G0, s));        // dy1
     // c1

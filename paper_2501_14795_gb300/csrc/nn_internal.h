@@ -161,12 +161,18 @@ cudaError_t launch_pool_fwd(const __nv_bfloat16* in, int B, int H, int W, int C,
                             __nv_bfloat16* out, cudaStream_t s);
 cudaError_t launch_up_fwd(const __nv_bfloat16* in, int B, int H, int W, int C, __nv_bfloat16* out,
                           cudaStream_t s);
-cudaError_t launch_pool_back(const float* in, int B, int H, int W, int C, float* out,
-                             cudaStream_t s);
-cudaError_t launch_up_back(const float* in, int B, int H, int W, int C, float* out,
-                           cudaStream_t s);
+// ReLU backward: dz = bf16((dy + extra) * (a > 0)), db += the FP32 sum over
+// pixels; dy read directly (npix pixels), through the adjoint of the 2x2 mean
+// pooling (dp on the H/2 x W/2 grid; dz on B x H x W) or of the nearest 2x
+// upsampling (du on the 2H x 2W grid; dz on B x H x W)
 cudaError_t launch_relu_back(const float* dy, const float* extra, const __nv_bfloat16* a,
                              long long npix, int C, __nv_bfloat16* dz, float* db, cudaStream_t s);
+cudaError_t launch_pool_relu_back(const float* dp, int B, int H, int W, int C, const float* extra,
+                                  const __nv_bfloat16* a, __nv_bfloat16* dz, float* db,
+                                  cudaStream_t s);
+cudaError_t launch_up_relu_back(const float* du, int B, int H, int W, int C,
+                                const __nv_bfloat16* a, __nv_bfloat16* dz, float* db,
+                                cudaStream_t s);
 cudaError_t launch_mse(const float* out, const float* target, long long bstride, long long cstride,
                        int pitch, int offset, int B, int H, int W, float inv_scale,
                        __nv_bfloat16* dz, float* db, double* loss, cudaStream_t s);

@@ -517,53 +517,47 @@ __global__ void k_up_fwd(const bf16* in, int B, int H, int W, int C, bf16* out) 
 }
 
 // adjoint of pooling: out (H x W) = in (H/2 x W/2) / 4, FP32
-__global__ void k_pool_back(const float* in, int B, int H, int W, int C, float* out) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)B * H * W * C / 4) return;
-    const int G = C / 4;
-    const int gi = (int)(i % G);
-    const long long pix = i / G;
-    const int x = (int)(pix % W);
-    const long long t = pix / W;
-    const int y = (int)(t % H), b = (int)(t / H);
-    float4 v = *reinterpret_cast<const float4*>(
-        in + (((size_t)b * (H / 2) + y / 2) * (W / 2) + x / 2) * C + gi * 4);
-    v.x *= 0.25f;
-    v.y *= 0.25f;
-    v.z *= 0.25f;
-    v.w *= 0.25f;
-    *reinterpret_cast<float4*>(out + pix * C + gi * 4) = v;
-}
 
-// adjoint of upsampling: out (H x W) = sum of the 2x2 block of in (2H x 2W), FP32
-__global__ void k_up_back(const float* in, int B, int H, int W, int C, float* out) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)B * H * W * C / 4) return;
-    const int G = C / 4;
-    const int gi = (int)(i % G);
-    const long long pix = i / G;
+// the gradient arriving at the ReLU of the pixel pix (NHWC index on the
+// layer's grid, B x H x W) for channels c .. c + 7: read directly (RB_DIRECT),
+// through the adjoint of the 2x2 mean pooling (RB_POOL: a quarter of the
+// coarse pixel's value) or of the nearest 2x upsampling (RB_UP: the sum of
+// the four fine pixels), in the FP32 order the separate adjoint kernels had
+enum { RB_DIRECT = 0, RB_POOL = 1, RB_UP = 2 };
+__device__ __forceinline__ void rb_source(int mode, const float* src, long long pix, int H, int W,
+                                          int C, int c, float v[8]) {
+    if (mode == RB_DIRECT) {
+        const float4 d0 = *reinterpret_cast<const float4*>(src + pix * C + c);
+        const float4 d1 = *reinterpret_cast<const float4*>(src + pix * C + c + 4);
+        v[0] = d0.x; v[1] = d0.y; v[2] = d0.z; v[3] = d0.w;
+        v[4] = d1.x; v[5] = d1.y; v[6] = d1.z; v[7] = d1.w;
+        return;
+    }
     const int x = (int)(pix % W);
     const long long t = pix / W;
     const int y = (int)(t % H), b = (int)(t / H);
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (mode == RB_POOL) {
+        const float* q = src + (((size_t)b * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = q[k] * 0.25f;
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = 0.f;
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
         for (int dx = 0; dx < 2; ++dx) {
-            const float4 v = *reinterpret_cast<const float4*>(
-                in + (((size_t)b * 2 * H + 2 * y + dy) * 2 * W + 2 * x + dx) * C + gi * 4);
-            s.x += v.x;
-            s.y += v.y;
-            s.z += v.z;
-            s.w += v.w;
+            const float* q = src + (((size_t)b * 2 * H + 2 * y + dy) * 2 * W + 2 * x + dx) * C + c;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] += q[k];
         }
-    *reinterpret_cast<float4*>(out + pix * C + gi * 4) = s;
 }
 
 // dz = bf16((dy + extra) * (a > 0)); db[c] += sum over pixels of the FP32 product
-__global__ void __launch_bounds__(256) k_relu_back(const float* dy, const float* extra,
-                                                   const bf16* a, long long npix, int C, bf16* dz,
-                                                   float* db) {
+__global__ void __launch_bounds__(256) k_relu_back(int mode, const float* src, int H, int W,
+                                                   const float* extra, const bf16* a,
+                                                   long long npix, int C, bf16* dz, float* db) {
     __shared__ float sdb[128];
     for (int c = threadIdx.x; c < C; c += blockDim.x) sdb[c] = 0.f;
     __syncthreads();
@@ -577,12 +571,8 @@ __global__ void __launch_bounds__(256) k_relu_back(const float* dy, const float*
         const int gi = (int)(i % G);
         myg = gi;
         const long long pix = i / G;
-        const float* d = dy + pix * C + gi * 8;
         float v[8];
-        const float4 d0 = *reinterpret_cast<const float4*>(d);
-        const float4 d1 = *reinterpret_cast<const float4*>(d + 4);
-        v[0] = d0.x; v[1] = d0.y; v[2] = d0.z; v[3] = d0.w;
-        v[4] = d1.x; v[5] = d1.y; v[6] = d1.z; v[7] = d1.w;
+        rb_source(mode, src, pix, H, W, C, gi * 8, v);
         if (extra) {
             const float4 e0 = *reinterpret_cast<const float4*>(extra + pix * C + gi * 8);
             const float4 e1 = *reinterpret_cast<const float4*>(extra + pix * C + gi * 8 + 4);
@@ -980,29 +970,37 @@ cudaError_t launch_up_fwd(const __nv_bfloat16* in, int B, int H, int W, int C, _
     return cudaGetLastError();
 }
 
-cudaError_t launch_pool_back(const float* in, int B, int H, int W, int C, float* out,
+namespace {
+cudaError_t relu_back_launch(int mode, const float* src, int B, int H, int W, const float* extra,
+                             const __nv_bfloat16* a, int C, __nv_bfloat16* dz, float* db,
                              cudaStream_t s) {
-    const long long n = (long long)B * H * W * C / 4;
-    k_pool_back<<<blocks(n, 256), 256, 0, s>>>(in, B, H, W, C, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_up_back(const float* in, int B, int H, int W, int C, float* out,
-                           cudaStream_t s) {
-    const long long n = (long long)B * H * W * C / 4;
-    k_up_back<<<blocks(n, 256), 256, 0, s>>>(in, B, H, W, C, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_relu_back(const float* dy, const float* extra, const __nv_bfloat16* a,
-                             long long npix, int C, __nv_bfloat16* dz, float* db, cudaStream_t s) {
+    const long long npix = (long long)B * H * W;
     const int G = C / 8;
     // threads a multiple of G: each thread keeps one channel group
     const long long work = npix * G;
     long long nb = std::min<long long>((work + 255) / 256, 4 * 152);
     if (nb < 1) nb = 1;
-    k_relu_back<<<(int)nb, 256, 0, s>>>(dy, extra, a, npix, C, dz, db);
+    k_relu_back<<<(int)nb, 256, 0, s>>>(mode, src, H, W, extra, a, npix, C, dz, db);
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_relu_back(const float* dy, const float* extra, const __nv_bfloat16* a,
+                             long long npix, int C, __nv_bfloat16* dz, float* db, cudaStream_t s) {
+    if (npix > 0x7fffffffLL) return cudaErrorInvalidValue;
+    return relu_back_launch(RB_DIRECT, dy, 1, 1, (int)npix, extra, a, C, dz, db, s);
+}
+
+cudaError_t launch_pool_relu_back(const float* dp, int B, int H, int W, int C, const float* extra,
+                                  const __nv_bfloat16* a, __nv_bfloat16* dz, float* db,
+                                  cudaStream_t s) {
+    return relu_back_launch(RB_POOL, dp, B, H, W, extra, a, C, dz, db, s);
+}
+
+cudaError_t launch_up_relu_back(const float* du, int B, int H, int W, int C,
+                                const __nv_bfloat16* a, __nv_bfloat16* dz, float* db,
+                                cudaStream_t s) {
+    return relu_back_launch(RB_UP, du, B, H, W, nullptr, a, C, dz, db, s);
 }
 
 cudaError_t launch_mse(const float* out, const float* target, long long bstride, long long cstride,
