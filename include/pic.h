@@ -385,7 +385,9 @@ pic_status pic_set_tiling(pic_sim* sim, int tile, int threads);
  * (each sum rounded to bfloat16 once).  The environment variable
  * PIC_DENOISER_TC, read at creation, selects the tcgen05 kernels whenever
  * the shape allows, the end layers included (=always, used by the tests), or
- * never (=never).
+ * never (=never).  The network's kernels are launched with programmatic
+ * dependent launch (each waits for the previous one before it reads its
+ * inputs); PIC_NN_PDL=0, read once per process, launches them plainly.
  * Low-wavenumber restoration (off unless pic_denoiser_set_low_k_restore sets
  * n > 0 passes): after the network, out <- out + L^n (J_in - out), where L is
  * one pass of the periodic binomial smoothing (1/4, 1/2, 1/4) along x and
