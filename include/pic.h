@@ -378,7 +378,7 @@ pic_status pic_set_tiling(pic_sim* sim, int tile, int threads);
  * the output layer c11 runs on the tensor cores as one GEMM per input row with
  * its nine taps side by side (an mma.sync kernel below 128-pixel rows).  Convolutions whose rows are multiples of 128
  * pixels and with at least 17 output channels run on the tcgen05 kernel when
- * the launch is large (>= 600 work units of 2 x 128 pixels), else on an
+ * the launch is large (>= 200 work units of 2 x 128 pixels), else on an
  * mma.sync kernel; the two layers that read a 2x upsampled input (c7, c9)
  * run as four 2x2 convolutions of the coarse grid (tcgen05) whenever its rows
  * are multiples of 128 pixels, with the 3x3 taps summed per output parity

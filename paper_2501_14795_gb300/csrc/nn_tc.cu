@@ -1761,9 +1761,12 @@ static int tc_nt(int cout_pad) {
 
 bool conv_tc_supported(const ConvParams& p, int cin) {
     if (p.force_tc < 0 || p.W % TC_M || p.H % TC_R || p.cout_pad > 128) return false;
-    // small problems (a few hundred work units) finish sooner on the mma.sync
-    // kernel, whose CTAs do not each stage all nine taps of weights
-    if ((long long)p.B * (p.H / TC_R) * (p.W / TC_M) < 600 && p.force_tc <= 0) return false;
+    // small problems finish sooner on the mma.sync kernel, whose CTAs do not
+    // each stage all nine taps of weights (measured in the denoised step with
+    // programmatic dependent launch: from 200 work units on the tcgen05 kernel
+    // is faster, 512^2 0.306 -> 0.278 ms; 256 units of 32 channels at 256^2
+    // are within 1 % either way)
+    if ((long long)p.B * (p.H / TC_R) * (p.W / TC_M) < 200 && p.force_tc <= 0) return false;
     const int nt = tc_nt(p.cout_pad);
     // a 16-wide tile (the 3-channel output layer) is faster on the mma.sync
     // kernel (measured on GB300: 66 against 84 us at 1024^2)
