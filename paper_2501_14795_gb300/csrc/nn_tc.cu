@@ -341,6 +341,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
             const int pb = (i - 1) & 1;
             if (ok && !wait_bar(bar0 + 8 * pb, ((i - 1) >> 1) & 1)) ok = false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            ok = __all_sync(0xffffffffu, ok);  // the warp's TMEM loads are collective
         }
         const int nxt = seg + gridDim.x;
         if (nxt < nseg) load_patch<CIN, NT>(p, smem + (buf ^ 1) * L::PATCH, nxt, tid);
@@ -356,6 +357,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvParams p) {
         const int pb = (i - 1) & 1;
         if (ok && !wait_bar(bar0 + 8 * pb, ((i - 1) >> 1) & 1)) ok = false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        ok = __all_sync(0xffffffffu, ok);
         if (ok)
             for (int rr = 0; rr < TC_R; ++rr)
                 epilogue<NT>(p, sBias, tmem + (pb * TC_R + rr) * L::NTC, prev, rr, warp, lane, co0);
@@ -477,6 +479,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc_kc(const ConvParams p) {
             const int gp = g - 1;
             if (ok && !wait_bar(bar0 + 8 * (gp & 1), (gp >> 1) & 1)) ok = false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            ok = __all_sync(0xffffffffu, ok);  // the warp's TMEM loads are collective
         }
         if (g + 1 < nchunk) {
             const int un = (g + 1) / NCH, cn = (g + 1) - un * NCH;
@@ -492,6 +495,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc_kc(const ConvParams p) {
     // the last chunk's products, then the last unit's results
     if (ok && !wait_bar(bar0 + 8 * ((nchunk - 1) & 1), ((nchunk - 1) >> 1) & 1)) ok = false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ok = __all_sync(0xffffffffu, ok);
     if (ok)
         for (int rr = 0; rr < TC_R; ++rr)
             epilogue<NT>(p, sBias, tmem + (((nunit - 1) & 1) * TC_R + rr) * L::NTC,
@@ -800,6 +804,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_up_tc(const ConvParams p) {
             const int gp = g - 1;
             if (ok && !wait_bar(bar0 + 8 * (gp & 1), (gp >> 1) & 1)) ok = false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            ok = __all_sync(0xffffffffu, ok);  // the warp's TMEM loads are collective
         }
         if (g + 1 < nchunk) {
             const int un = (g + 1) / NCH, cn = (g + 1) - un * NCH;
@@ -812,6 +817,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_up_tc(const ConvParams p) {
     }
     if (ok && !wait_bar(bar0 + 8 * ((nchunk - 1) & 1), ((nchunk - 1) >> 1) & 1)) ok = false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ok = __all_sync(0xffffffffu, ok);
     if (ok)
         epilogue_up<L::NTC, NT>(p, sBias, tmem + ((nunit - 1) & 1) * 4 * L::NTC,
                                 seg_of(nunit - 1), warp, lane, co0);
